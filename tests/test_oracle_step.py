@@ -1,0 +1,107 @@
+"""Pins of the oracle's TR-BDF2 projection step (Section 2 of the paper)
+against closed forms and the paper's printed convergence table.
+
+ * Taylor-Green exact solution (Section 4.1): second order in time with the
+   space error made negligible (Q4), high order in space at small dt;
+ * the paper's Table of relative L2 errors (Q2-Q1, C = 1.63) as a sanity band
+   (factor 2: the paper leaves quadrature, penalty scale and solver
+   tolerances unstated);
+ * exact conservation of int p on periodic meshes (1^T K = 0 and F_p(1) = 0).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.dg import Mesh
+from oracle.trbdf2 import GAMMA, Stepper, interpolate, l2_error
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "tg_q2q1_paper.txt")
+
+
+def run_tg(N, k, dt, T, Re, extrapolate=True):
+    m = Mesh(2, [N, N], [0, 0], [2 * math.pi] * 2, [True, True], k)
+    st = Stepper(m, Re, extrapolate=extrapolate)
+    u = interpolate(m, lambda x, y: W.paper_tg_u(x, y, 0.0, Re))
+    p = interpolate(m, lambda x, y: W.paper_tg_p(x, y, 0.0, Re), p_space=True)
+    uh = interpolate(m, lambda x, y: W.paper_tg_u(x, y, -(1 - GAMMA) * dt, Re))
+    t = 0.0
+    pint0 = (st.Mp @ p).sum()
+    for _ in range(int(round(T / dt))):
+        u, p, uh = st.step(u, p, uh, t, dt)
+        t += dt
+    e2 = n2 = 0.0
+    for i in range(2):
+        e2 += l2_error(m, u[i], lambda x, y, i=i: W.paper_tg_u(x, y, t, Re)[i], relative=False) ** 2
+        n2 += l2_error(m, 0 * u[i], lambda x, y, i=i: W.paper_tg_u(x, y, t, Re)[i],
+                       relative=False) ** 2
+    ep = l2_error(m, p, lambda x, y: W.paper_tg_p(x, y, t, Re), p_space=True)
+    return math.sqrt(e2 / n2), ep, (st.Mp @ p).sum() - pint0
+
+
+def test_second_order_in_time():
+    errs = [run_tg(10, 4, dt, 1.0, 10.0)[0] for dt in (0.25, 0.125)]
+    assert math.log2(errs[0] / errs[1]) > 1.8, errs
+
+
+def test_convergence_under_hyperbolic_scaling():
+    """N = 8 -> 16 at the table's C = 1.63 (lagged field): rate above 2, as in
+    the paper's table (2.01).  At fixed h and dt -> 0 the error instead grows
+    with the number of steps, because the non-incremental pressure form
+    (Eq. helmholtz2a in weak form) solves K p^{n+1} against D M^-1 P p^n and
+    K differs from D M^-1 P by an O(h^r) term every step."""
+    e8 = run_tg(8, 2, 0.64, 3.2, 100.0, extrapolate=False)[0]
+    e16 = run_tg(16, 2, 0.32, 3.2, 100.0, extrapolate=False)[0]
+    assert math.log2(e8 / e16) > 2.0, (e8, e16)
+
+
+def _gold():
+    rows = [l.split() for l in open(GOLD) if l.strip() and not l.startswith("#")]
+    return [(float(a), int(b), float(c), float(d)) for a, b, c, d in rows]
+
+
+@pytest.mark.parametrize("row", _gold()[:2])
+def test_paper_table_band_lagged(row):
+    """At the table's C = 1.63 the extrapolated advecting field diverges (see
+    test_extrapolated_field_limit); the lagged one lands in the band."""
+    dt, N, eu_paper, ep_paper = row
+    eu, ep, dp = run_tg(N, 2, dt, 3.2, 100.0, extrapolate=False)
+    assert eu_paper / 2 < eu < eu_paper * 2, eu
+    assert ep_paper / 3 < ep < ep_paper * 3, ep
+    assert abs(dp) < 1e-7   # roundoff of the RHS amplified by 1/alpha ~ 1e5
+
+
+@pytest.mark.parametrize("row", _gold()[:2])
+def test_paper_table_band_extrapolated_at_quarter_courant(row):
+    """The table's errors are space-dominated (its text: the time step does
+    not affect second-order accuracy), so at C = 0.41 the extrapolated
+    scheme must land in the same band."""
+    dt, N, eu_paper, _ = row
+    eu, _, dp = run_tg(N, 2, dt / 4, 3.2, 100.0, extrapolate=True)
+    assert eu_paper / 2 < eu < eu_paper * 2, eu
+    assert abs(dp) < 1e-7   # roundoff of the RHS amplified by 1/alpha ~ 1e5
+
+
+def test_extrapolated_field_limit():
+    """Records the stability limit of the extrapolation readings: at C = 1.63
+    on the 8x8 Taylor-Green test the extrapolated advecting field grows."""
+    eu, _, _ = run_tg(8, 2, 0.64, 3.2, 100.0, extrapolate=True)
+    assert eu > 1.0
+
+
+def test_tg2d_workload_tracks_exact_decay():
+    w = W.TG2D
+    m = Mesh(2, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree)
+    st = Stepper(m, w.Re, c=w.c)
+    nu = 1.0 / w.Re
+    u = interpolate(m, lambda x, y: W.tg2d_u(x, y, 0.0, nu))
+    p = interpolate(m, lambda x, y: W.tg2d_p(x, y, 0.0, nu), p_space=True)
+    uh = interpolate(m, lambda x, y: W.tg2d_u(x, y, -(1 - GAMMA) * w.dt, nu))
+    t = 0.0
+    for _ in range(w.steps):
+        u, p, uh = st.step(u, p, uh, t, w.dt)
+        t += w.dt
+    err = max(l2_error(m, u[i], lambda x, y, i=i: W.tg2d_u(x, y, t, nu)[i]) for i in range(2))
+    assert err < 0.05
