@@ -1,0 +1,257 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) matrix-free DG TR-BDF2 projection
+ * solver for the incompressible Navier-Stokes equations in artificial
+ * compressibility form, after Orlando, Della Rocca, Barbante, Bonaventura,
+ * Parolini, "An efficient and accurate implicit DG solver for the
+ * incompressible Navier-Stokes equations" (arXiv 2107.07776).
+ *
+ * Conventions (all entry points):
+ *  - Every field pointer is a caller-owned DEVICE pointer on the current CUDA
+ *    device unless its comment says "host".  The library never frees caller
+ *    memory; it owns and frees its own scratch.
+ *  - Velocity fields are structure-of-arrays [component][cell][node], pressure
+ *    fields [cell][node].  Cells are lexicographic (x fastest) over the
+ *    structured box; nodes are lexicographic (x fastest) over the
+ *    Gauss-Legendre points of [0,1]^d: k+1 per direction for the velocity
+ *    space Q_k and k per direction for the pressure space Q_{k-1} (Section 3).
+ *  - Work is enqueued on the caller's stream (`stream` is a cudaStream_t, NULL
+ *    = legacy default stream).  Calls that return iteration counts or
+ *    residuals synchronise that stream before returning.
+ *  - Errors come back as dg_status; dg_last_error() gives a message for the
+ *    calling thread.  No C++ exception crosses the ABI and no kernel traps:
+ *    device-side failures set a device status word checked at call end.
+ *  - Velocity and pressure pointers passed to one call must not alias each
+ *    other unless stated.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = 1,        /* bad argument (null pointer, size, option) */
+  DG_ECUDA = 2,         /* CUDA runtime error (message in dg_last_error) */
+  DG_ENOMEM = 3,        /* device or host allocation failed */
+  DG_ENOCONV = 4,       /* Krylov solve hit max_iter above tolerance */
+  DG_EBREAKDOWN = 5,    /* non-finite residual or Krylov breakdown */
+  DG_ETIMEOUT = 6,      /* solve exceeded its wall-clock limit */
+  DG_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} dg_status;
+
+typedef struct dg_mesh dg_mesh;     /* geometry, 1D tables, MG hierarchy */
+typedef struct dg_solver dg_solver; /* Krylov/MG workspaces, history, guess net */
+
+enum { DG_MAP_CARTESIAN = 0, DG_MAP_GRADED_TANH = 1, DG_MAP_PERTURBED_SIN = 2 };
+
+/* Structured box mesh of hexahedra (quadrilaterals for dim = 2), Section 3.
+ *  n_cells[a]   cells along axis a (n_cells[2] ignored in 2D), >= 1
+ *  lo, hi       box corners
+ *  periodic[a]  1: periodic in axis a; 0: Dirichlet velocity walls with
+ *               homogeneous Neumann pressure (Section 2, Eq. ns_artcomp)
+ *  degree_u     velocity degree k (2..4); pressure degree k-1
+ *  map          DG_MAP_CARTESIAN; DG_MAP_GRADED_TANH with map_param[a] = beta
+ *               per axis (vertex x = lo + (hi-lo)(1 - tanh(beta(1-2 eta))/
+ *               tanh(beta))/2, beta = 0: uniform); DG_MAP_PERTURBED_SIN with
+ *               map_param[0] = A (every vertex shifted by
+ *               A (hi-lo) prod_a sin(2 pi eta_a), trilinear cells). */
+typedef struct {
+  int32_t dim;
+  int32_t n_cells[3];
+  double lo[3], hi[3];
+  int32_t periodic[3];
+  int32_t degree_u;
+  int32_t map;
+  double map_param[3];
+} dg_mesh_desc;
+
+/* Build geometry, penalties (sigma = (k+1)^2 |Gamma|/|K| for velocity,
+ * k^2 |Gamma|/|K| for pressure: Eq. penconst1 and its pressure analogue read
+ * with face measure over cell volume) and the 1D tables on the current
+ * device.  `stream` orders the uploads.  *out owns device memory until
+ * dg_mesh_destroy.  DG_EUNSUPPORTED for map/degree combinations not built. */
+dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out);
+void dg_mesh_destroy(dg_mesh* mesh);
+
+/* Sizes: cells, velocity DoFs (all components), pressure DoFs.  Any output
+ * pointer (host) may be NULL. */
+dg_status dg_mesh_info(const dg_mesh* mesh, int64_t* n_cells, int64_t* n_dofs_u,
+                       int64_t* n_dofs_p);
+
+/* Physical coordinates of the nodes of field 0 (velocity nodes, one
+ * component's worth) or 1 (pressure nodes): xyz [dim][cell][node], double,
+ * device.  Synchronous. */
+dg_status dg_mesh_node_coords(const dg_mesh* mesh, int32_t field, double* xyz, void* stream);
+
+/* Coefficients of the momentum operator of one TR-BDF2 stage (Section 3,
+ * Eqs. weakform_u_1 / weakform_u_2):
+ *   mass * M + visc * A + adv * C(ubar)
+ * stage 1: mass = 1/(gamma dt), visc = 1/(2 Re), adv = 1/2
+ * stage 2: mass = 1/((1-gamma) dt), visc = a33/Re, adv = a33. */
+typedef struct {
+  double mass, visc, adv;
+} dg_momentum_coeffs;
+
+/* dst = (mass M + visc A + adv C(ubar)) src for every velocity component
+ * (the operator is the same scalar operator per component, Section 3):
+ * M mass matrix, A the SIP form a_u (Eq. bilin_diff, interior and wall
+ * faces), C the local Lax-Friedrichs form c (Eq. trilinear) with the
+ * advecting field ubar.  Homogeneous: Dirichlet data enter only through
+ * dg_rhs_momentum.  src, ubar, dst: n_dofs_u doubles; dst must not alias
+ * src or ubar.  FP64 throughout. */
+dg_status dg_apply_momentum(dg_mesh* mesh, const dg_momentum_coeffs* co, const double* ubar,
+                            const double* src, double* dst, void* stream);
+
+/* FP32 variant of dg_apply_momentum (multigrid smoothing and mixed-precision
+ * preconditioning); same layout with float. */
+dg_status dg_apply_momentum_f32(dg_mesh* mesh, const dg_momentum_coeffs* co, const float* ubar,
+                                const float* src, float* dst, void* stream);
+
+/* dst = (alpha M^p + K) src: the pressure Helmholtz operator of Eqs.
+ * helmholtz_1 / helmholtz_2 (K the SIP form a_p of Eq. weakform_p_1, interior
+ * faces only; homogeneous Neumann walls add nothing).  alpha =
+ * 1/(c^2 gamma^2 dt^2) (stage 1) or 1/(c^2 (1-gamma)^2 dt^2) (stage 2).
+ * src, dst: n_dofs_p doubles, no aliasing. */
+dg_status dg_apply_poisson(dg_mesh* mesh, double alpha, const double* src, double* dst,
+                           void* stream);
+
+/* FP32 variant of dg_apply_poisson. */
+dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, float* dst,
+                               void* stream);
+
+/* ---------------------------------------------------------------------
+ * Stage right-hand sides and updates (once per stage; Sections 2-3).
+ * ------------------------------------------------------------------- */
+
+/* Explicit part of F_u (Eq. rhs1 and its stage-2 analogue) plus the mass
+ * term and data, for every velocity component:
+ *   rhs = mass * M u_mass
+ *       + sum_{t < n_terms} [ visc[t] * E_v w[t] + adv[t] * E_a(wbar[t]) w[t] ]
+ *       + G p
+ *       + dir_visc * B_v uD + dir_adv * B_a(ubar) uD      (uD != NULL)
+ *       + M f                                              (f != NULL)
+ * E_v: unpenalised viscous form -int grad w : grad v + sum_E {{grad w}}:<<v>>
+ * E_a: central advective form +int (w x wbar) : grad v - sum_E {{w x wbar}}:<<v>>
+ * G:   DG pressure gradient int p div v - sum_E {{p}} [[v]]
+ * B_v, B_a: boundary data terms of Eq. rhs1 (SIP and LF with the trace of uD).
+ * All faces of the skeleton take part in E_v, E_a, G (boundary averages are
+ * interior traces).  All fields device pointers; u_mass, w[t], wbar[t], uD,
+ * ubar, f have n_dofs_u doubles, p has n_dofs_p; rhs must alias none. */
+typedef struct {
+  double mass;
+  const double* u_mass;
+  int32_t n_terms;              /* 0, 1 or 2 */
+  double visc[2], adv[2];
+  const double* w[2];
+  const double* wbar[2];
+  const double* p;              /* NULL: no pressure gradient */
+  const double* uD;             /* NULL: no Dirichlet data */
+  double dir_visc, dir_adv;
+  const double* ubar;           /* advecting field of the stage (LF speed of B_a) */
+  const double* f;              /* NULL: no forcing */
+} dg_momentum_rhs;
+
+dg_status dg_rhs_momentum(dg_mesh* mesh, const dg_momentum_rhs* desc, double* rhs,
+                          void* stream);
+
+/* u_tilde = M^{-1} P p for every velocity component: the projection of the
+ * broken pressure gradient into V_h (Section 3, matrix P).  p: n_dofs_p,
+ * u_tilde: n_dofs_u. */
+dg_status dg_project_gradient(dg_mesh* mesh, const double* p, double* u_tilde, void* stream);
+
+/* rhs = alpha M^p p_old + (1/tau) sum_c D_c uss_c: right-hand side of the
+ * pressure Helmholtz equation (Eqs. helmholtz_1, weakform_p_1), D the DG
+ * divergence int u.grad q - sum_E {{u}}.[[q]] over all faces. */
+dg_status dg_rhs_pressure(dg_mesh* mesh, double alpha, double tau, const double* uss,
+                          const double* p_old, double* rhs, void* stream);
+
+/* Diagonal of mass M + visc A + adv C(ubar) (Jacobi preconditioner of the
+ * momentum systems, Section 4) for one scalar component: n_dofs_u/dim. */
+dg_status dg_momentum_diagonal(dg_mesh* mesh, const dg_momentum_coeffs* co, const double* ubar,
+                               double* diag, void* stream);
+
+/* Diagonal of alpha M^p + K: n_dofs_p. */
+dg_status dg_poisson_diagonal(dg_mesh* mesh, double alpha, double* diag, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Solvers and the TR-BDF2 step.
+ * ------------------------------------------------------------------- */
+enum { DG_SYS_MOMENTUM = 0, DG_SYS_HELMHOLTZ = 1 };
+enum { DG_PC_NONE = 0, DG_PC_JACOBI = 1, DG_PC_MG_FP64 = 2, DG_PC_MG_FP32 = 3 };
+enum { DG_GUESS_ZERO = 0, DG_GUESS_EXTRAP = 1, DG_GUESS_LEARNED = 2, DG_GUESS_GIVEN = 3 };
+
+typedef struct {
+  int32_t system;       /* DG_SYS_* */
+  double tol_rel;       /* stop when ||r|| <= tol_rel ||b|| */
+  int32_t max_iter;     /* iterations (GMRES: total inner iterations) */
+  int32_t restart;      /* GMRES restart length (momentum) */
+  int32_t precond;      /* DG_PC_*: momentum takes NONE/JACOBI, Helmholtz any */
+  int32_t guess;        /* DG_GUESS_* */
+  double timeout_s;     /* wall-clock limit, <= 0: none */
+} dg_solve_opts;
+
+typedef struct {
+  int32_t iterations;
+  double res0, res_final;   /* ||b - A x0||, ||b - A x|| (2-norms) */
+  int32_t status;           /* dg_status of this solve */
+} dg_solve_info;
+
+/* Solver for one mesh: Reynolds number Re and artificial sound speed c
+ * (Eq. ns_artcomp; the paper's default c = 1e3). */
+dg_status dg_solver_create(dg_mesh* mesh, double Re, double c, dg_solver** out);
+void dg_solver_destroy(dg_solver* solver);
+
+/* Solve one stage system on the solver's stream:
+ *   system MOMENTUM:  (co) applied per component with advecting field ubar,
+ *                     rhs and x have n_dofs_u doubles (all components);
+ *   system HELMHOLTZ: (alpha M^p + K), rhs and x have n_dofs_p doubles.
+ * x: in the guess when opts->guess == DG_GUESS_GIVEN (ignored otherwise),
+ * out the solution (best iterate on DG_ENOCONV).  Synchronous. */
+dg_status dg_solve_stage(dg_solver* solver, const dg_momentum_coeffs* co, double alpha,
+                         const double* ubar, const double* rhs, double* x,
+                         const dg_solve_opts* opts, dg_solve_info* info);
+
+/* TR-BDF2 step parameters.  dt, gamma (<= 0: 2 - sqrt(2)); extrapolate: 1 =
+ * extrapolated advecting fields (linear to t^{n+gamma/2} from u^n and
+ * u^{n-1+gamma}; linear to t^{n+1} from u^{n+gamma} and u^n), 0 = lagged
+ * (u^n, u^{n+gamma}).  uD_*: Dirichlet data as velocity-layout nodal fields
+ * whose wall traces are the data, or NULL (homogeneous).  f_*: forcing at
+ * velocity nodes at t^n, t^{n+gamma}, t^{n+1}, or NULL. */
+typedef struct {
+  double dt, gamma;
+  int32_t extrapolate;
+  const double* uD_stage1;
+  const double* uD_stage2;
+  const double* f_n;
+  const double* f_ng;
+  const double* f_n1;
+  dg_solve_opts mom, helm;
+} dg_step_params;
+
+/* One TR-BDF2 step (Section 2, Eqs. first_stage ... helmholtz3a; algebraic
+ * form of Section 3): u (n_dofs_u) in u^n, out u^{n+1}; p (n_dofs_p) in p^n,
+ * out p^{n+1}.  The solver keeps u^{n-1+gamma} for the stage-1 extrapolation
+ * (set with dg_solver_set_history; before the first step it is u^n).
+ * info[4] (host): momentum 1, Helmholtz 1, momentum 2, Helmholtz 2. */
+dg_status trbdf2_step(dg_solver* solver, const dg_step_params* params, double* u, double* p,
+                      dg_solve_info info[4]);
+
+/* Set (device pointer, n_dofs_u) or clear (NULL) the stored u^{n-1+gamma}. */
+dg_status dg_solver_set_history(dg_solver* solver, const double* u_hist);
+
+/* Checkpoint / resume of the solver state (history level, learned-guess
+ * weights and optimiser moments) to a host file path. */
+dg_status dg_solver_save(const dg_solver* solver, const char* path);
+dg_status dg_solver_load(dg_solver* solver, const char* path);
+
+const char* dg_status_string(dg_status status);
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

@@ -1,0 +1,88 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int kMaxN = 8;  // nodes per direction supported by the 1D tables
+
+// 1D tables of the nodal Lagrange basis on the n Gauss-Legendre points of
+// [0,1], passed to kernels by value (constant bank).
+template <typename T>
+struct Tab1D {
+  T D[kMaxN][kMaxN];  // D[q][i] = L_i'(x_q)
+  T L[2][kMaxN];      // L[s][i] = L_i(s), s = 0, 1 (cell faces)
+  T dL[2][kMaxN];     // dL[s][i] = L_i'(s)
+  T w[kMaxN];         // quadrature weights on [0,1]
+  T x[kMaxN];         // points
+};
+
+// Pressure basis (k points) evaluated at the velocity points (k+1): the 1D
+// factors of the mixed velocity-pressure forms.
+template <typename T>
+struct MixTab {
+  T I[kMaxN][kMaxN];  // I[q][j] = psi_j(x^u_q)
+  T D[kMaxN][kMaxN];  // D[q][j] = psi_j'(x^u_q)
+};
+
+// Host-side construction (FP64) of the tables for n points.
+void make_tables(int n, Tab1D<double>* t);
+void make_mix(const Tab1D<double>& tu, int nu, const Tab1D<double>& tp, int np, MixTab<double>* m);
+template <typename T>
+Tab1D<T> cast_tables(const Tab1D<double>& t);
+
+// Cell geometry of the affine paths: per-axis cell extents (the Jacobian is
+// diagonal, diag(h0, h1, h2), on Cartesian and tensor-graded meshes).
+template <typename T>
+struct AxisGeom {
+  const T* h[3];
+};
+
+}  // namespace dg
+
+struct dg_mesh {
+  dg_mesh_desc desc;
+  int dim = 0, k = 0;
+  int nu = 0, np = 0;      // nodes per direction: velocity k+1, pressure k
+  int nbu = 0, nbp = 0;    // nodes per cell
+  int64_t ncell = 0;
+  int n[3] = {1, 1, 1};
+  int periodic[3] = {1, 1, 1};
+  bool affine = true;
+  int device = 0;
+  std::vector<double> vx[3];        // vertex lattice coordinates per axis (affine)
+  double* d_h64[3] = {nullptr, nullptr, nullptr};
+  float* d_h32[3] = {nullptr, nullptr, nullptr};
+  dg::Tab1D<double> tu64, tp64;      // velocity / pressure tables
+  dg::Tab1D<float> tu32, tp32;
+  dg::MixTab<double> mix64;
+  int* d_status = nullptr;           // device error word
+};
+
+namespace dg {
+
+// thread-local error message, set by the entry points
+void set_error(const std::string& msg);
+dg_status cuda_fail(cudaError_t e, const char* where);
+
+#define DG_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return dg::cuda_fail(e_, #call); \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// launchers (dg_apply.cu)
+template <typename T>
+dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
+                           const T* ubar, const T* src, T* dst, int ncomp, cudaStream_t s);
+
+}  // namespace dg

@@ -1,0 +1,691 @@
+// Stage right-hand sides, gradient projection and Jacobi diagonals on affine
+// cells (Sections 2-3): the explicit viscous and advective terms of F_u
+// (Eq. rhs1 and its stage-2 analogue), the DG pressure gradient, the
+// Dirichlet data terms, the divergence functional F_p (Eq. weakform_p_1),
+// u~ = M^-1 P p, and diag(mass M + visc A + adv C(ubar)) / diag(alpha M^p + K).
+//
+// Same collocated layout as the operator kernels: one thread per node, CPB
+// cells per CTA, cell data in shared memory, neighbour traces from global
+// memory, every output written once (deterministic).  These run once per
+// stage, not per Krylov iteration.
+#include "dg_common.cuh"
+
+namespace dg {
+
+namespace {
+
+template <int N, int DIM>
+struct Sh {
+  static constexpr int NB = DIM == 3 ? N * N * N : N * N;
+  static constexpr int NF = DIM == 3 ? N * N : N;
+  static constexpr int NFP = 2 * DIM * NF;
+};
+
+struct Grid {
+  int64_t ncell;
+  int n[3];
+  int per[3];
+  const double* h[3];
+};
+
+__device__ __forceinline__ int nodeof(int N, int dim, int a, int i, int t) {
+  int idx[3] = {0, 0, 0};
+  idx[a] = i;
+  for (int b = 0; b < dim; ++b) {
+    if (b == a) continue;
+    idx[b] = t % N;
+    t /= N;
+  }
+  return idx[0] + N * (idx[1] + N * idx[2]);
+}
+
+__device__ __forceinline__ int tangof(int N, int dim, int a, const int i[3]) {
+  int t = 0, mul = 1;
+  for (int b = 0; b < dim; ++b) {
+    if (b == a) continue;
+    t += i[b] * mul;
+    mul *= N;
+  }
+  return t;
+}
+
+// neighbour of cell ci across face (a, s); -1 at a wall
+__device__ __forceinline__ int64_t neighbour(const Grid& g, const int ci[3], int a, int s) {
+  int nc[3] = {ci[0], ci[1], ci[2]};
+  nc[a] += s ? 1 : -1;
+  if (nc[a] < 0 || nc[a] >= g.n[a]) {
+    if (!g.per[a]) return -1;
+    nc[a] = (nc[a] + g.n[a]) % g.n[a];
+  }
+  return (int64_t)nc[0] + (int64_t)g.n[0] * (nc[1] + (int64_t)g.n[1] * nc[2]);
+}
+
+__device__ __forceinline__ void cell_coords(const Grid& g, int64_t cell, int ci[3]) {
+  ci[0] = (int)(cell % g.n[0]);
+  ci[1] = (int)((cell / g.n[0]) % g.n[1]);
+  ci[2] = (int)(cell / ((int64_t)g.n[0] * g.n[1]));
+}
+
+// ------------------------------------------------------------------
+// Explicit terms: MODE 0 adds visc E_v w + adv E_a(wb) w (all faces, central,
+// unpenalised); MODE 1 adds the Dirichlet data terms visc B_v w + adv B_a(wb) w
+// on wall faces (w = u_D, wb = the stage's advecting field).
+template <int DIM, int N, int MODE, int CPB>
+__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
+    explicit_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
+                    double visc, double adv, double pen, const double* __restrict__ w,
+                    const double* __restrict__ wb, double* __restrict__ rhs) {
+  constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
+  __shared__ double s_u[CPB][NB];
+  __shared__ double s_wb[DIM][CPB][NB];
+  __shared__ double s_q[DIM][CPB][NB];
+  __shared__ double s_f[CPB][NFP][2];
+  __shared__ double s_wn[CPB][NFP][2];
+  const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < g.ncell;
+  int ci[3] = {0, 0, 0};
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  double h[3] = {1, 1, 1}, W = 0;
+  if (active) {
+    cell_coords(g, cell, ci);
+    for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
+    W = 1.0;
+    for (int b = 0; b < DIM; ++b) W *= tb.w[ii[b]] * h[b];
+    for (int b = 0; b < DIM; ++b) s_wb[b][cl][node] = wb[((int64_t)b * g.ncell + cell) * NB + node];
+  }
+  for (int c = 0; c < DIM; ++c) {
+    const double* wc = w + (int64_t)c * g.ncell * NB;
+    if (active) s_u[cl][node] = wc[cell * NB + node];
+    __syncthreads();
+    if (active) {
+      for (int b = 0; b < DIM; ++b) {
+        double q = 0.0;
+        if (MODE == 0) {
+          double du = 0.0;
+          for (int m = 0; m < N; ++m) {
+            int j[3] = {ii[0], ii[1], ii[2]};
+            j[b] = m;
+            du += tb.D[ii[b]][m] * s_u[cl][j[0] + N * (j[1] + N * j[2])];
+          }
+          q = W * (-visc * du / h[b] + adv * s_u[cl][node] * s_wb[b][cl][node]);
+        }
+        s_q[b][cl][node] = q;
+      }
+      for (int fp = node; fp < NFP; fp += NB) {
+        const int f = fp / NF, t = fp % NF, ax = f >> 1, s = f & 1;
+        const double sgn = s ? 1.0 : -1.0;
+        const int64_t nb = neighbour(g, ci, ax, s);
+        const double hK = h[ax];
+        double wt = 1.0;
+        {
+          int tt = t;
+          for (int b = 0; b < DIM; ++b) {
+            if (b == ax) continue;
+            wt *= tb.w[tt % N] * h[b];
+            tt /= N;
+          }
+        }
+        double uin = 0, dnin = 0, wnin = 0;
+        for (int i = 0; i < N; ++i) {
+          const int nd = nodeof(N, DIM, ax, i, t);
+          uin += tb.L[s][i] * s_u[cl][nd];
+          dnin += tb.dL[s][i] * s_u[cl][nd];
+          wnin += tb.L[s][i] * s_wb[ax][cl][nd];
+        }
+        dnin *= sgn / hK;
+        wnin *= sgn;
+        double fv = 0.0, fg = 0.0;
+        if (MODE == 0) {
+          if (nb >= 0) {
+            int nc3[3];
+            cell_coords(g, nb, nc3);
+            const double hN = g.h[ax][nc3[ax]];
+            double uout = 0, dnout = 0, wnout = 0;
+            for (int i = 0; i < N; ++i) {
+              const int nd = nodeof(N, DIM, ax, i, t);
+              const double v = __ldg(&wc[nb * NB + nd]);
+              uout += tb.L[1 - s][i] * v;
+              dnout += tb.dL[1 - s][i] * v;
+              wnout += tb.L[1 - s][i] * __ldg(&wb[((int64_t)ax * g.ncell + nb) * NB + nd]);
+            }
+            dnout *= sgn / hN;
+            wnout *= sgn;
+            fv = visc * 0.5 * (dnin + dnout) - adv * 0.5 * (uin * wnin + uout * wnout);
+          } else {
+            fv = visc * dnin - adv * uin * wnin;
+          }
+        } else if (nb < 0) {
+          const double sig = pen / hK;
+          fv = visc * 2.0 * sig * uin + adv * (-uin * wnin + fabs(wnin) * uin);
+          fg = -visc * uin;
+        }
+        s_f[cl][fp][0] = wt * fv;
+        s_f[cl][fp][1] = wt * fg * sgn / hK;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      double y = 0.0;
+      for (int b = 0; b < DIM; ++b) {
+        double acc = 0.0;
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          acc += tb.D[m][ii[b]] * s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
+        }
+        y += acc / h[b];
+        const int t = tangof(N, DIM, b, ii);
+        for (int s = 0; s < 2; ++s) {
+          const int fp = (2 * b + s) * NF + t;
+          y += s_f[cl][fp][0] * tb.L[s][ii[b]] + s_f[cl][fp][1] * tb.dL[s][ii[b]];
+        }
+      }
+      rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += y;
+    }
+    __syncthreads();
+  }
+  (void)s_wn;
+}
+
+// ------------------------------------------------------------------
+// rhs = mass M u_mass + M f + G p (G the DG pressure gradient of Eq. rhs1);
+// writes (does not accumulate).  N velocity, NP pressure nodes per direction.
+template <int DIM, int N, int NP, int CPB>
+__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
+    mass_grad_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
+                     const __grid_constant__ Tab1D<double> tp,
+                     const __grid_constant__ MixTab<double> mx, double mass,
+                     const double* __restrict__ u_mass, const double* __restrict__ f,
+                     const double* __restrict__ p, double* __restrict__ rhs) {
+  constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
+  constexpr int NBP = Sh<NP, DIM>::NB;
+  __shared__ double s_p[CPB][NBP];
+  __shared__ double s_g[CPB][NB];
+  __shared__ double s_pu[CPB][NB];
+  __shared__ double s_f[CPB][NFP];
+  const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < g.ncell;
+  int ci[3] = {0, 0, 0};
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  double h[3] = {1, 1, 1}, W = 0;
+  if (active) {
+    cell_coords(g, cell, ci);
+    for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
+    W = 1.0;
+    for (int b = 0; b < DIM; ++b) W *= tb.w[ii[b]] * h[b];
+    if (p && node < NBP) s_p[cl][node] = p[cell * NBP + node];
+  }
+  __syncthreads();
+  if (active && p) {
+    // p at the velocity nodes (exact: Q_{k-1} lies in Q_k)
+    double pu = 0.0;
+    for (int j = 0; j < NBP; ++j) {
+      const int j0 = j % NP, j1 = (j / NP) % NP, j2 = DIM == 3 ? j / (NP * NP) : 0;
+      double wgt = mx.I[ii[0]][j0] * mx.I[ii[1]][j1];
+      if (DIM == 3) wgt *= mx.I[ii[2]][j2];
+      pu += wgt * s_p[cl][j];
+    }
+    s_pu[cl][node] = pu;
+    s_g[cl][node] = W * pu;
+  }
+  __syncthreads();
+  if (active && p) {
+    for (int fp = node; fp < NFP; fp += NB) {
+      const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
+      const double sgn = s ? 1.0 : -1.0;
+      const int64_t nb = neighbour(g, ci, ax, s);
+      double wt = 1.0;
+      int tb3[3] = {0, 0, 0};
+      {
+        int tt = t;
+        for (int b = 0; b < DIM; ++b) {
+          if (b == ax) continue;
+          tb3[b] = tt % N;
+          wt *= tb.w[tt % N] * h[b];
+          tt /= N;
+        }
+      }
+      double pin = 0.0;
+      for (int i = 0; i < N; ++i) pin += tb.L[s][i] * s_pu[cl][nodeof(N, DIM, ax, i, t)];
+      double pav = pin;
+      if (nb >= 0) {
+        double pout = 0.0;
+        for (int j = 0; j < NBP; ++j) {
+          const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
+          double wgt = tp.L[1 - s][jj[ax]];
+          for (int b = 0; b < DIM; ++b)
+            if (b != ax) wgt *= mx.I[tb3[b]][jj[b]];
+          pout += wgt * __ldg(&p[nb * NBP + j]);
+        }
+        pav = 0.5 * (pin + pout);
+      }
+      s_f[cl][fp] = -wt * sgn * pav;
+    }
+  }
+  __syncthreads();
+  if (active) {
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t o = (int64_t)c * g.ncell * NB + cell * NB + node;
+      double y = 0.0;
+      if (u_mass) y += mass * W * u_mass[o];
+      if (f) y += W * f[o];
+      if (p) {
+        double acc = 0.0;
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[c] = m;
+          acc += tb.D[m][ii[c]] * s_g[cl][j[0] + N * (j[1] + N * j[2])];
+        }
+        y += acc / h[c];
+        const int t = tangof(N, DIM, c, ii);
+        for (int s = 0; s < 2; ++s) y += s_f[cl][(2 * c + s) * NF + t] * tb.L[s][ii[c]];
+      }
+      rhs[o] = y;
+    }
+  }
+}
+
+// ------------------------------------------------------------------
+// rhs_p = alpha M^p p_old + (1/tau) sum_c D_c uss_c, one thread per pressure
+// node; D the DG divergence of Eq. weakform_p_1, integrated with the
+// velocity rule.
+template <int DIM, int N, int NP, int CPB>
+__global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
+    pressure_rhs_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
+                        const __grid_constant__ Tab1D<double> tp,
+                        const __grid_constant__ MixTab<double> mx, double alpha, double inv_tau,
+                        const double* __restrict__ uss, const double* __restrict__ p_old,
+                        double* __restrict__ rhs) {
+  constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
+  constexpr int NBP = Sh<NP, DIM>::NB;
+  __shared__ double s_u[DIM][CPB][NB];
+  __shared__ double s_f[CPB][NFP];
+  const int tid = threadIdx.x, cl = tid / NBP, node = tid % NBP;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < g.ncell;
+  int ci[3] = {0, 0, 0};
+  double h[3] = {1, 1, 1};
+  if (active) {
+    cell_coords(g, cell, ci);
+    for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
+    for (int idx = node; idx < DIM * NB; idx += NBP) {
+      const int c = idx / NB, nd = idx % NB;
+      s_u[c][cl][nd] = uss[((int64_t)c * g.ncell + cell) * NB + nd];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    for (int fp = node; fp < NFP; fp += NBP) {
+      const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
+      const double sgn = s ? 1.0 : -1.0;
+      const int64_t nb = neighbour(g, ci, ax, s);
+      double wt = 1.0;
+      {
+        int tt = t;
+        for (int b = 0; b < DIM; ++b) {
+          if (b == ax) continue;
+          wt *= tb.w[tt % N] * h[b];
+          tt /= N;
+        }
+      }
+      double uin = 0.0;
+      for (int i = 0; i < N; ++i) uin += tb.L[s][i] * s_u[ax][cl][nodeof(N, DIM, ax, i, t)];
+      double uav = uin;
+      if (nb >= 0) {
+        double uout = 0.0;
+        for (int i = 0; i < N; ++i)
+          uout += tb.L[1 - s][i] * __ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)]);
+        uav = 0.5 * (uin + uout);
+      }
+      s_f[cl][fp] = wt * sgn * uav;
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const int pi[3] = {node % NP, (node / NP) % NP, DIM == 3 ? node / (NP * NP) : 0};
+    double Wp = 1.0;
+    for (int b = 0; b < DIM; ++b) Wp *= tp.w[pi[b]] * h[b];
+    double acc = 0.0;
+    // cell term: sum over velocity quadrature points of W u_c d_c psi_i
+    for (int q = 0; q < NB; ++q) {
+      const int qq[3] = {q % N, (q / N) % N, DIM == 3 ? q / (N * N) : 0};
+      double Wq = 1.0, v[DIM];
+      for (int b = 0; b < DIM; ++b) {
+        Wq *= tb.w[qq[b]] * h[b];
+        v[b] = mx.I[qq[b]][pi[b]];
+      }
+      for (int c = 0; c < DIM; ++c) {
+        double dpsi = mx.D[qq[c]][pi[c]] / h[c];
+        for (int b = 0; b < DIM; ++b)
+          if (b != c) dpsi *= v[b];
+        acc += Wq * s_u[c][cl][q] * dpsi;
+      }
+    }
+    // face term: - sum_faces sum_t w_t {{u}}.n psi_i
+    for (int fc = 0; fc < 2 * DIM; ++fc) {
+      const int ax = fc >> 1, s = fc & 1;
+      for (int t = 0; t < NF; ++t) {
+        double psi = tp.L[s][pi[ax]];
+        int tt = t;
+        for (int b = 0; b < DIM; ++b) {
+          if (b == ax) continue;
+          psi *= mx.I[tt % N][pi[b]];
+          tt /= N;
+        }
+        acc -= s_f[cl][fc * NF + t] * psi;
+      }
+    }
+    rhs[cell * NBP + node] = alpha * Wp * p_old[cell * NBP + node] + inv_tau * acc;
+  }
+}
+
+// ------------------------------------------------------------------
+// u~_c = M^-1 P_c p: the broken gradient of p at the velocity nodes (exact
+// on affine cells, where M is diagonal and P_c p = W d_c p at the nodes).
+template <int DIM, int N, int NP, int CPB>
+__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
+    project_kernel(const __grid_constant__ Grid g, const __grid_constant__ MixTab<double> mx,
+                   const double* __restrict__ p, double* __restrict__ ut) {
+  constexpr int NB = Sh<N, DIM>::NB, NBP = Sh<NP, DIM>::NB;
+  __shared__ double s_p[CPB][NBP];
+  const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < g.ncell;
+  if (active && node < NBP) s_p[cl][node] = p[cell * NBP + node];
+  __syncthreads();
+  if (!active) return;
+  int ci[3];
+  cell_coords(g, cell, ci);
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  for (int c = 0; c < DIM; ++c) {
+    double acc = 0.0;
+    for (int j = 0; j < NBP; ++j) {
+      const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
+      double wgt = 1.0;
+      for (int b = 0; b < DIM; ++b) wgt *= b == c ? mx.D[ii[b]][jj[b]] : mx.I[ii[b]][jj[b]];
+      acc += wgt * s_p[cl][j];
+    }
+    ut[((int64_t)c * g.ncell + cell) * NB + node] = acc / g.h[c][ci[c]];
+  }
+}
+
+// ------------------------------------------------------------------
+// Diagonal of mass M + visc A + adv C(ubar) (walls = 1) or of
+// alpha M^p + K (walls = 0, adv = 0), one thread per node.
+template <int DIM, int N>
+__global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
+                            double mass, double visc, double adv, double pen, int walls,
+                            const double* __restrict__ ub, double* __restrict__ diag) {
+  constexpr int NB = Sh<N, DIM>::NB;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= g.ncell * NB) return;
+  const int64_t cell = gid / NB;
+  const int node = (int)(gid % NB);
+  int ci[3];
+  cell_coords(g, cell, ci);
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  double h[3] = {1, 1, 1};
+  for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
+  auto Wat = [&](const int j[3]) {
+    double W = 1.0;
+    for (int b = 0; b < DIM; ++b) W *= tb.w[j[b]] * h[b];
+    return W;
+  };
+  const double W = Wat(ii);
+  double d = mass * W;
+  for (int b = 0; b < DIM; ++b) {
+    double acc = 0.0;
+    for (int m = 0; m < N; ++m) {
+      int j[3] = {ii[0], ii[1], ii[2]};
+      j[b] = m;
+      const double dm = tb.D[m][ii[b]] / h[b];
+      acc += Wat(j) * dm * dm;
+    }
+    d += visc * acc;
+    if (adv != 0.0) d -= adv * W * ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] / h[b];
+  }
+  for (int ax = 0; ax < DIM; ++ax) {
+    const int t = tangof(N, DIM, ax, ii);
+    double wt = 1.0;
+    for (int b = 0; b < DIM; ++b)
+      if (b != ax) wt *= tb.w[ii[b]] * h[b];
+    for (int s = 0; s < 2; ++s) {
+      const double sgn = s ? 1.0 : -1.0;
+      const int64_t nb = neighbour(g, ci, ax, s);
+      const double hK = h[ax];
+      const double uin = tb.L[s][ii[ax]], dnin = sgn * tb.dL[s][ii[ax]] / hK;
+      double unin = 0.0;
+      if (adv != 0.0) {
+        for (int i = 0; i < N; ++i)
+          unin += tb.L[s][i] * ub[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)];
+        unin *= sgn;
+      }
+      double fv = 0.0, fg = 0.0;
+      if (nb >= 0) {
+        int nc3[3];
+        cell_coords(g, nb, nc3);
+        const double hN = g.h[ax][nc3[ax]];
+        // a one-cell period makes the cell its own neighbour
+        const double uout = nb == cell ? tb.L[1 - s][ii[ax]] : 0.0;
+        const double dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] / hN : 0.0;
+        const double C = 0.5 * (pen / hK + pen / hN);
+        const double jump = uin - uout;
+        fv = visc * (-0.5 * (dnin + dnout) + C * jump);
+        fg = -0.5 * visc * jump;
+        if (adv != 0.0) {
+          double unout = 0.0;
+          for (int i = 0; i < N; ++i)
+            unout += tb.L[1 - s][i] * ub[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)];
+          unout *= sgn;
+          const double lam = fmax(fabs(unin), fabs(unout));
+          fv += adv * (0.5 * (uin * unin + uout * unout) + 0.5 * lam * jump);
+        }
+      } else if (walls) {
+        fv = visc * (-dnin + 2.0 * (pen / hK) * uin) + adv * fabs(unin) * uin;
+        fg = -visc * uin;
+      }
+      d += wt * (fv * tb.L[s][ii[ax]] + fg * sgn * tb.dL[s][ii[ax]] / hK);
+    }
+  }
+  diag[gid] = d;
+}
+
+template <int DIM>
+Grid make_grid(const dg_mesh* m) {
+  Grid g;
+  g.ncell = m->ncell;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = m->n[a];
+    g.per[a] = m->periodic[a];
+    g.h[a] = m->d_h64[a];
+  }
+  return g;
+}
+
+template <int N, int DIM>
+constexpr int cpb_for() {
+  return Sh<N, DIM>::NB <= 8 ? 16 : (Sh<N, DIM>::NB <= 27 ? 8 : (Sh<N, DIM>::NB <= 64 ? 4 : 2));
+}
+
+template <int DIM, int N>
+dg_status run_explicit(const dg_mesh* m, int mode, double visc, double adv, const double* w,
+                       const double* wb, double* rhs, cudaStream_t s) {
+  constexpr int CPB = cpb_for<N, DIM>();
+  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
+  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  const Grid g = make_grid<DIM>(m);
+  const double pen = (double)(N * N);
+  if (mode == 0)
+    explicit_kernel<DIM, N, 0, CPB><<<blocks, threads, 0, s>>>(g, m->tu64, visc, adv, pen, w, wb, rhs);
+  else
+    explicit_kernel<DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(g, m->tu64, visc, adv, pen, w, wb, rhs);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <int DIM, int N>
+dg_status run_mass_grad(const dg_mesh* m, double mass, const double* um, const double* f,
+                        const double* p, double* rhs, cudaStream_t s) {
+  constexpr int CPB = cpb_for<N, DIM>();
+  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
+  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  mass_grad_kernel<DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), m->tu64, m->tp64,
+                                                                 m->mix64, mass, um, f, p, rhs);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <int DIM, int N>
+dg_status run_pressure_rhs(const dg_mesh* m, double alpha, double inv_tau, const double* uss,
+                           const double* p_old, double* rhs, cudaStream_t s) {
+  constexpr int NP = N - 1;
+  constexpr int CPB = cpb_for<NP, DIM>();
+  constexpr int threads = ((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32;
+  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  pressure_rhs_kernel<DIM, N, NP, CPB><<<blocks, threads, 0, s>>>(
+      make_grid<DIM>(m), m->tu64, m->tp64, m->mix64, alpha, inv_tau, uss, p_old, rhs);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <int DIM, int N>
+dg_status run_project(const dg_mesh* m, const double* p, double* ut, cudaStream_t s) {
+  constexpr int CPB = cpb_for<N, DIM>();
+  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
+  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  project_kernel<DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), m->mix64, p, ut);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <int DIM, int N>
+dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, double adv,
+                   const double* ub, double* diag, cudaStream_t s) {
+  const int64_t total = m->ncell * Sh<N, DIM>::NB;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  diag_kernel<DIM, N><<<blocks, 256, 0, s>>>(make_grid<DIM>(m), pressure ? m->tp64 : m->tu64, mass,
+                                             visc, adv, (double)(N * N), pressure ? 0 : 1, ub, diag);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// dispatch on (dim, velocity nodes) for velocity-space kernels
+#define DG_DISPATCH_U(m, FN, ...)                                        \
+  ((m)->dim == 2 ? ((m)->nu == 3 ? FN<2, 3>(__VA_ARGS__)                 \
+                    : (m)->nu == 4 ? FN<2, 4>(__VA_ARGS__)               \
+                                   : FN<2, 5>(__VA_ARGS__))              \
+                 : ((m)->nu == 3 ? FN<3, 3>(__VA_ARGS__)                 \
+                    : (m)->nu == 4 ? FN<3, 4>(__VA_ARGS__)               \
+                                   : FN<3, 5>(__VA_ARGS__)))
+
+bool check_affine(const dg_mesh* m, const char* who) {
+  if (!m->affine) {
+    set_error(std::string(who) + ": trilinear (perturbed) cells are not built in this library");
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+// internal entry used by the solver: diagonal of a pressure-space operator
+dg_status poisson_diagonal(const dg_mesh* m, double alpha, double* diag, cudaStream_t s) {
+  switch (m->dim * 10 + m->np) {
+    case 22: return run_diag<2, 2>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
+    case 23: return run_diag<2, 3>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
+    case 24: return run_diag<2, 4>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
+    case 32: return run_diag<3, 2>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
+    case 33: return run_diag<3, 3>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
+    case 34: return run_diag<3, 4>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
+  }
+  set_error("poisson_diagonal: unsupported degree");
+  return DG_EUNSUPPORTED;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+dg_status dg_rhs_momentum(dg_mesh* m, const dg_momentum_rhs* d, double* rhs, void* stream) {
+  if (!m || !d || !rhs || d->n_terms < 0 || d->n_terms > 2) {
+    set_error("dg_rhs_momentum: bad argument");
+    return DG_EINVAL;
+  }
+  if (!check_affine(m, "dg_rhs_momentum")) return DG_EUNSUPPORTED;
+  for (int t = 0; t < d->n_terms; ++t) {
+    if (!d->w[t] || (d->adv[t] != 0.0 && !d->wbar[t]) || d->w[t] == rhs || d->wbar[t] == rhs) {
+      set_error("dg_rhs_momentum: bad explicit term");
+      return DG_EINVAL;
+    }
+  }
+  if (d->uD && !d->ubar) {
+    set_error("dg_rhs_momentum: Dirichlet data need the stage's advecting field");
+    return DG_EINVAL;
+  }
+  if (d->u_mass == rhs || d->p == rhs || d->uD == rhs || d->f == rhs || d->ubar == rhs) {
+    set_error("dg_rhs_momentum: rhs aliases an input");
+    return DG_EINVAL;
+  }
+  cudaStream_t s = as_stream(stream);
+  dg_status st = DG_DISPATCH_U(m, run_mass_grad, m, d->mass, d->u_mass, d->f, d->p, rhs, s);
+  if (st != DG_OK) return st;
+  for (int t = 0; t < d->n_terms; ++t) {
+    // a term without advection still needs a field for the shared-memory
+    // staging; the term's own w stands in (multiplied by adv = 0)
+    const double* wb = d->wbar[t] ? d->wbar[t] : d->w[t];
+    st = DG_DISPATCH_U(m, run_explicit, m, 0, d->visc[t], d->adv[t], d->w[t], wb, rhs, s);
+    if (st != DG_OK) return st;
+  }
+  bool walls = false;
+  for (int a = 0; a < m->dim; ++a) walls |= !m->periodic[a];
+  if (d->uD && walls) {
+    st = DG_DISPATCH_U(m, run_explicit, m, 1, d->dir_visc, d->dir_adv, d->uD, d->ubar, rhs, s);
+    if (st != DG_OK) return st;
+  }
+  return DG_OK;
+}
+
+dg_status dg_project_gradient(dg_mesh* m, const double* p, double* ut, void* stream) {
+  if (!m || !p || !ut) {
+    set_error("dg_project_gradient: bad argument");
+    return DG_EINVAL;
+  }
+  if (!check_affine(m, "dg_project_gradient")) return DG_EUNSUPPORTED;
+  return DG_DISPATCH_U(m, run_project, m, p, ut, as_stream(stream));
+}
+
+dg_status dg_rhs_pressure(dg_mesh* m, double alpha, double tau, const double* uss,
+                          const double* p_old, double* rhs, void* stream) {
+  if (!m || !uss || !p_old || !rhs || !(tau != 0.0) || rhs == p_old) {
+    set_error("dg_rhs_pressure: bad argument");
+    return DG_EINVAL;
+  }
+  if (!check_affine(m, "dg_rhs_pressure")) return DG_EUNSUPPORTED;
+  return DG_DISPATCH_U(m, run_pressure_rhs, m, alpha, 1.0 / tau, uss, p_old, rhs, as_stream(stream));
+}
+
+dg_status dg_momentum_diagonal(dg_mesh* m, const dg_momentum_coeffs* co, const double* ubar,
+                               double* diag, void* stream) {
+  if (!m || !co || !diag || (co->adv != 0.0 && !ubar)) {
+    set_error("dg_momentum_diagonal: bad argument");
+    return DG_EINVAL;
+  }
+  if (!check_affine(m, "dg_momentum_diagonal")) return DG_EUNSUPPORTED;
+  return DG_DISPATCH_U(m, run_diag, m, false, co->mass, co->visc, co->adv, ubar, diag,
+                       as_stream(stream));
+}
+
+dg_status dg_poisson_diagonal(dg_mesh* m, double alpha, double* diag, void* stream) {
+  if (!m || !diag) {
+    set_error("dg_poisson_diagonal: bad argument");
+    return DG_EINVAL;
+  }
+  if (!check_affine(m, "dg_poisson_diagonal")) return DG_EUNSUPPORTED;
+  return poisson_diagonal(m, alpha, diag, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+"""Parity of the CUDA operator applies with the oracle's assembled operators
+(Section 3): element by element on seeded inputs, FP64 to 1e-12 relative
+(the tolerance the work states for applies), FP32 to 2e-5 relative (about
+100 ulp of the float path, accumulated over the O(10^2) terms per output).
+Meshes span several CTAs with ragged tails, 2D and 3D, periodic (including a
+one-cell period, where a cell is its own neighbour) and walled, Cartesian and
+tanh-graded, degrees 2 to 4; the 32^3 Taylor-Green workload is checked on
+sampled cells at full size."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.dg import Mesh as OMesh
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CASES = [
+    # dim, n, lo, hi, periodic, degree, map, map_param
+    (2, (5, 3), (0, 0), (1.0, 0.7), (True, True), 2, 0, (0, 0, 0)),
+    (2, (4, 6), (0, 0), (2.0, 1.0), (False, False), 3, 1, (0.0, 1.5, 0)),
+    (2, (1, 2), (0, 0), (1.0, 1.0), (True, False), 4, 0, (0, 0, 0)),
+    (3, (5, 3, 7), (0, 0, 0), (1.0, 0.8, 1.3), (True, True, True), 2, 0, (0, 0, 0)),
+    (3, (4, 5, 3), (0, 0, 0), (4.0, 1.0, 1.0), (True, False, False), 2, 1, (0.0, 1.5, 1.5)),
+    (3, (3, 2, 3), (0, 0, 0), (1.0, 1.0, 1.0), (False, False, False), 3, 0, (0, 0, 0)),
+    (3, (1, 1, 2), (0, 0, 0), (1.0, 1.0, 1.0), (True, True, False), 2, 0, (0, 0, 0)),
+    (3, (2, 3, 2), (0, 0, 0), (1.0, 1.0, 1.0), (True, False, True), 4, 1, (0.0, 1.2, 0.0)),
+]
+
+
+def meshes(case):
+    from paper_2107_07776_gb300.binding import Mesh
+    dim, n, lo, hi, per, k, mp, prm = case
+    return (Mesh(dim, n, lo, hi, per, k, mp, prm),
+            OMesh(dim, list(n), list(lo), list(hi), list(per), k, map=mp, map_param=list(prm)))
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_poisson_apply_matches_oracle(ci):
+    from paper_2107_07776_gb300 import binding as b
+    gm, om = meshes(CASES[ci])
+    x = W.random_vector(om.n_p, 100 + ci)
+    alpha = 2.9
+    ref = alpha * om.assemble("mass_p").apply(x) + om.assemble("sipg_p").apply(x)
+    y = torch.empty(om.n_p, dtype=torch.float64, device="cuda")
+    b.dg_apply_poisson(gm.handle, alpha, dev(x), y)
+    torch.cuda.synchronize()
+    assert rel_err(y.cpu().numpy(), ref) < 1e-12
+    y32 = torch.empty(om.n_p, dtype=torch.float32, device="cuda")
+    b.dg_apply_poisson_f32(gm.handle, alpha, dev(x, torch.float32), y32)
+    torch.cuda.synchronize()
+    assert rel_err(y32.double().cpu().numpy(), ref) < 2e-5
+
+
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_momentum_apply_matches_oracle(ci):
+    from paper_2107_07776_gb300 import binding as b
+    gm, om = meshes(CASES[ci])
+    d = om.dim
+    x = W.random_vector(d * om.n_u, 200 + ci)
+    ub = W.random_vector(d * om.n_u, 300 + ci)
+    mass, visc, adv = 1.0 / (b.GAMMA * 0.01), 1.0 / 200.0, 0.5
+    M = om.assemble("mass_u")
+    A = om.assemble("sipg_u")
+    C = om.assemble("adv_u", ub)
+    ref = np.concatenate([mass * M.apply(x[i * om.n_u:(i + 1) * om.n_u])
+                          + visc * A.apply(x[i * om.n_u:(i + 1) * om.n_u])
+                          + adv * C.apply(x[i * om.n_u:(i + 1) * om.n_u]) for i in range(d)])
+    co = b.momentum_coeffs(mass, visc, adv)
+    y = torch.empty(d * om.n_u, dtype=torch.float64, device="cuda")
+    b.dg_apply_momentum(gm.handle, co, dev(ub), dev(x), y)
+    torch.cuda.synchronize()
+    assert rel_err(y.cpu().numpy(), ref) < 1e-12
+    y32 = torch.empty(d * om.n_u, dtype=torch.float32, device="cuda")
+    b.dg_apply_momentum_f32(gm.handle, co, dev(ub, torch.float32), dev(x, torch.float32), y32)
+    torch.cuda.synchronize()
+    assert rel_err(y32.double().cpu().numpy(), ref) < 2e-5
+
+
+def test_node_coords_match_oracle():
+    for case in CASES:
+        gm, om = meshes(case)
+        for field in (0, 1):
+            g = gm.node_coords(field).cpu().numpy()
+            o = om.node_coords(p_space=bool(field))
+            assert np.abs(g - o).max() < 1e-13
+
+
+def test_full_size_tgv32_sampled_cells():
+    """The 32^3 Q2/Q1 Taylor-Green workload at full size, as the benchmark
+    launches it: every output of 64 sampled cells (corners, edges, random)
+    against the oracle's rows for those cells."""
+    from paper_2107_07776_gb300 import binding as b
+    w = W.TGV32
+    gm = b.Mesh.from_workload(w)
+    om = OMesh(w.dim, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree)
+    rng = np.random.default_rng(7)
+    N = om.n_cells
+    cells = np.unique(np.concatenate([[0, N - 1, 31, 32 * 31, N - 32], rng.integers(0, N, 59)]))
+    # pressure
+    xp = W.random_vector(om.n_p, 11)
+    y = torch.empty(om.n_p, dtype=torch.float64, device="cuda")
+    alpha = 1.0 / (w.c ** 2 * (b.GAMMA * w.dt) ** 2)
+    b.dg_apply_poisson(gm.handle, alpha, dev(xp), y)
+    yc = y.cpu().numpy().reshape(N, -1)[cells].reshape(-1)
+    ref = alpha * om.assemble("mass_p", cells=cells).apply(xp) + \
+        om.assemble("sipg_p", cells=cells).apply(xp)
+    assert rel_err(yc, ref) < 1e-12
+    # momentum with the workload's initial velocity as advecting field
+    X = gm.node_coords(0).cpu().numpy()
+    ub = W.tgv3d_u(*X).reshape(-1)
+    xu = W.random_vector(3 * om.n_u, 12)
+    mass, visc, adv = 1.0 / (b.GAMMA * w.dt), 1.0 / (2 * w.Re), 0.5
+    yu = torch.empty(3 * om.n_u, dtype=torch.float64, device="cuda")
+    b.dg_apply_momentum(gm.handle, b.momentum_coeffs(mass, visc, adv), dev(ub), dev(xu), yu)
+    yu = yu.cpu().numpy().reshape(3, N, -1)
+    Mb = om.assemble("mass_u", cells=cells)
+    Ab = om.assemble("sipg_u", cells=cells)
+    Cb = om.assemble("adv_u", ub, cells=cells)
+    for i in range(3):
+        xi = xu[i * om.n_u:(i + 1) * om.n_u]
+        ref = mass * Mb.apply(xi) + visc * Ab.apply(xi) + adv * Cb.apply(xi)
+        assert rel_err(yu[i][cells].reshape(-1), ref) < 1e-12
+
+
+def test_bad_arguments_are_rejected():
+    from paper_2107_07776_gb300 import binding as b
+    gm, om = meshes(CASES[0])
+    x = torch.zeros(om.n_p, dtype=torch.float64, device="cuda")
+    with pytest.raises(b.DGError):
+        b.dg_apply_poisson(gm.handle, 1.0, x, x)          # aliasing
+    with pytest.raises(b.DGError):
+        b.dg_apply_momentum(gm.handle, b.momentum_coeffs(1, 1, 1), None, x, x)
