@@ -37,6 +37,9 @@ struct OpArgs {
   const T* h0;
   const T* h1;
   const T* h2;
+  const T* hi0;  // inverse extents
+  const T* hi1;
+  const T* hi2;
   T mass, visc, adv, pen;
   int walls;   // 1: SIP + LF Dirichlet terms on wall faces; 0: none (Neumann)
   int ncomp;
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
   const bool active = cl < CPB && cell < a.ncell;
 
   int ci[3] = {0, 0, 0};
-  T h[3] = {T(1), T(1), T(1)};
+  T h[3] = {T(1), T(1), T(1)}, hi[3] = {T(1), T(1), T(1)};
   int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
   T W = T(0);
   if (active) {
@@ -92,7 +95,12 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
     ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
     h[0] = a.h0[ci[0]];
     h[1] = a.h1[ci[1]];
-    if (DIM == 3) h[2] = a.h2[ci[2]];
+    hi[0] = a.hi0[ci[0]];
+    hi[1] = a.hi1[ci[1]];
+    if (DIM == 3) {
+      h[2] = a.h2[ci[2]];
+      hi[2] = a.hi2[ci[2]];
+    }
     W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
     if (DIM == 3) W *= tb.w[ii[2]] * h[2];
     if (ADV) {
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
           j[b] = m;
           du += tb.D[ii[b]][m] * s_u[cl][j[0] + N * (j[1] + N * j[2])];
         }
-        T q = a.visc * du / h[b];
+        T q = a.visc * du * hi[b];
         if (ADV) q -= a.adv * s_u[cl][node] * s_ub[b][cl][node];
         s_q[b][cl][node] = W * q;
       }
@@ -136,8 +144,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
           else interior = false;
         }
         const int64_t nb = (int64_t)nc[0] + (int64_t)a.n0 * (nc[1] + (int64_t)a.n1 * nc[2]);
-        const T* hax = ax == 0 ? a.h0 : (ax == 1 ? a.h1 : a.h2);
-        const T hK = h[ax];
+        const T* hiax = ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2);
+        const T hiK = hi[ax];
         // tangential weight: face quadrature weight times the face measure
         T wt = T(1);
         {
@@ -156,10 +164,10 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
           uin += tb.L[s][i] * v;
           dnin += tb.dL[s][i] * v;
         }
-        dnin *= sgn / hK;
+        dnin *= sgn * hiK;
         T fv = T(0), fg = T(0);
         if (interior) {
-          const T hN = hax[nc[ax]];
+          const T hiN = hiax[nc[ax]];
           T uout = T(0), dnout = T(0);
 #pragma unroll
           for (int i = 0; i < N; ++i) {
@@ -167,8 +175,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
             uout += tb.L[1 - s][i] * v;
             dnout += tb.dL[1 - s][i] * v;
           }
-          dnout *= sgn / hN;
-          const T Cpen = T(0.5) * (a.pen / hK + a.pen / hN);
+          dnout *= sgn * hiN;
+          const T Cpen = T(0.5) * a.pen * (hiK + hiN);
           const T jump = uin - uout;
           fv = a.visc * (T(-0.5) * (dnin + dnout) + Cpen * jump);
           fg = T(-0.5) * a.visc * jump;
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
             fv += a.adv * (T(0.5) * (uin * unin + uout * unout) + T(0.5) * lam * jump);
           }
         } else if (a.walls) {
-          const T sig = a.pen / hK;
+          const T sig = a.pen * hiK;
           fv = a.visc * (-dnin + T(2) * sig * uin);
           fg = -a.visc * uin;
           if (ADV) {
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
           }
         }
         s_f[cl][fp][0] = wt * fv;
-        s_f[cl][fp][1] = wt * fg * sgn / hK;
+        s_f[cl][fp][1] = wt * fg * sgn * hiK;
       }
     }
     __syncthreads();
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
           j[b] = m;
           acc += tb.D[m][ii[b]] * s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
         }
-        y += acc / h[b];
+        y += acc * hi[b];
       }
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
@@ -283,11 +291,11 @@ static dg_status launch_dim(int N, const OpArgs<T>& args, const Tab1D<T>& tb, co
 }
 
 template <typename T>
-const T* axis_h(const dg_mesh* m, int a);
+const T* axis_h(const dg_mesh* m, int a, bool inv);
 template <>
-const double* axis_h<double>(const dg_mesh* m, int a) { return m->d_h64[a]; }
+const double* axis_h<double>(const dg_mesh* m, int a, bool inv) { return inv ? m->d_hi64[a] : m->d_h64[a]; }
 template <>
-const float* axis_h<float>(const dg_mesh* m, int a) { return m->d_h32[a]; }
+const float* axis_h<float>(const dg_mesh* m, int a, bool inv) { return inv ? m->d_hi32[a] : m->d_h32[a]; }
 template <typename T>
 const Tab1D<T>& tabs(const dg_mesh* m, bool pressure);
 template <>
@@ -310,9 +318,12 @@ dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T ad
   a.per0 = m->periodic[0];
   a.per1 = m->periodic[1];
   a.per2 = m->periodic[2];
-  a.h0 = axis_h<T>(m, 0);
-  a.h1 = axis_h<T>(m, 1);
-  a.h2 = axis_h<T>(m, 2);
+  a.h0 = axis_h<T>(m, 0, false);
+  a.h1 = axis_h<T>(m, 1, false);
+  a.h2 = axis_h<T>(m, 2, false);
+  a.hi0 = axis_h<T>(m, 0, true);
+  a.hi1 = axis_h<T>(m, 1, true);
+  a.hi2 = axis_h<T>(m, 2, true);
   a.mass = mass;
   a.visc = visc;
   a.adv = adv;

@@ -58,8 +58,10 @@ struct dg_mesh {
   bool affine = true;
   int device = 0;
   std::vector<double> vx[3];        // vertex lattice coordinates per axis (affine)
-  double* d_h64[3] = {nullptr, nullptr, nullptr};
+  double* d_h64[3] = {nullptr, nullptr, nullptr};   // cell extents per axis
   float* d_h32[3] = {nullptr, nullptr, nullptr};
+  double* d_hi64[3] = {nullptr, nullptr, nullptr};  // their inverses
+  float* d_hi32[3] = {nullptr, nullptr, nullptr};
   dg::Tab1D<double> tu64, tp64;      // velocity / pressure tables
   dg::Tab1D<float> tu32, tp32;
   dg::MixTab<double> mix64;

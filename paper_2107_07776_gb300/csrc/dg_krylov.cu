@@ -1,0 +1,391 @@
+// Krylov solvers for the stage systems (Section 4: GMRES with Jacobi for the
+// momentum predictors, preconditioned CG for the pressure Helmholtz
+// equations).  All vector work runs in the fused kernels below; the host only
+// keeps the (restart x restart) Hessenberg least-squares problem and the
+// scalar recurrences.  Reductions are deterministic: every inner product uses
+// a fixed grid, a fixed per-block tree and a fixed-order second pass, so a
+// solve gives the same bits on every run.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "dg_krylov.cuh"
+
+namespace dg {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+int red_blocks(int64_t n) {
+  int64_t b = (n + 4 * kRedThreads - 1) / (4 * kRedThreads);
+  if (b < 1) b = 1;
+  if (b > 1216) b = 1216;  // 8 CTAs per SM on 152 SMs
+  return (int)b;
+}
+
+// partial[blk * nv + i] = sum over this block's range of w * V_i
+__global__ void __launch_bounds__(kRedThreads)
+    multi_dot_kernel(int64_t n, int nv, const double* __restrict__ w, const double* __restrict__ V,
+                     int64_t ldv, double* __restrict__ partial) {
+  __shared__ double s[kRedThreads];
+  for (int i = 0; i < nv; ++i) {
+    const double* v = V + (int64_t)i * ldv;
+    double acc = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+      acc += w[k] * v[k];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = kRedThreads / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * nv + i] = s[0];
+    __syncthreads();
+  }
+}
+
+// out[i] = sum_blk partial[blk * nv + i], fixed order (one block per i)
+__global__ void __launch_bounds__(kRedThreads)
+    reduce_kernel(int nblk, int nv, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double s[kRedThreads];
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[(int64_t)b * nv + i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = kRedThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = s[0];
+}
+
+// w -= sum_i h[i] V_i  (h on the device)
+__global__ void multi_axpy_kernel(int64_t n, int nv, const double* __restrict__ h,
+                                  const double* __restrict__ V, int64_t ldv, double* __restrict__ w) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[k];
+    for (int i = 0; i < nv; ++i) acc -= h[i] * V[(int64_t)i * ldv + k];
+    w[k] = acc;
+  }
+}
+
+// x += dinv .* sum_i y[i] V_i  (dinv NULL: identity)
+__global__ void gmres_update_kernel(int64_t n, int nv, const double* __restrict__ y,
+                                    const double* __restrict__ V, int64_t ldv,
+                                    const double* __restrict__ dinv, double* __restrict__ x) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < nv; ++i) acc += y[i] * V[(int64_t)i * ldv + k];
+    x[k] += dinv ? dinv[k] * acc : acc;
+  }
+}
+
+__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b,
+                             const double* __restrict__ y, double* __restrict__ z) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    z[k] = a * x[k] + (b == 0.0 ? 0.0 : b * y[k]);
+}
+
+__global__ void mul_kernel(int64_t n, const double* __restrict__ d, const double* __restrict__ x,
+                           double* __restrict__ z) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    z[k] = d[k] * x[k];
+}
+
+__global__ void inv_kernel(int64_t n, const double* __restrict__ d, int64_t period,
+                           double* __restrict__ out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = 1.0 / d[k % period];
+}
+
+// CG update: x += a p; r_old = r; r -= a q
+__global__ void cg_update_kernel(int64_t n, double a, const double* __restrict__ p,
+                                 const double* __restrict__ q, double* __restrict__ x,
+                                 double* __restrict__ r, double* __restrict__ r_old) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    x[k] += a * p[k];
+    const double rk = r[k];
+    r_old[k] = rk;
+    r[k] = rk - a * q[k];
+  }
+}
+
+unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- VecOps
+dg_status VecOps::dots(int64_t n, int nv, const double* w, const double* V, int64_t ldv,
+                       double* out_dev) {
+  const int nb = red_blocks(n);
+  multi_dot_kernel<<<nb, kRedThreads, 0, stream>>>(n, nv, w, V, ldv, partial);
+  reduce_kernel<<<nv, kRedThreads, 0, stream>>>(nb, nv, partial, out_dev);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status VecOps::dots_host(int64_t n, int nv, const double* w, const double* V, int64_t ldv,
+                            double* out_host) {
+  dg_status st = dots(n, nv, w, V, ldv, scal);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemcpyAsync(host_scal, scal, sizeof(double) * nv, cudaMemcpyDeviceToHost, stream));
+  DG_CUDA(cudaStreamSynchronize(stream));
+  for (int i = 0; i < nv; ++i) out_host[i] = host_scal[i];
+  return DG_OK;
+}
+
+dg_status VecOps::axpby(int64_t n, double a, const double* x, double b, const double* y,
+                        double* z) {
+  axpby_kernel<<<grid_for(n), 256, 0, stream>>>(n, a, x, b, y, z);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status VecOps::mul(int64_t n, const double* d, const double* x, double* z) {
+  mul_kernel<<<grid_for(n), 256, 0, stream>>>(n, d, x, z);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status VecOps::invert(int64_t n, const double* d, int64_t period, double* out) {
+  inv_kernel<<<grid_for(n), 256, 0, stream>>>(n, d, period, out);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// --------------------------------------------------------------- GMRES
+// Restarted GMRES(m), right Jacobi preconditioning (x = x0 + D^-1 V y, so the
+// Arnoldi residual is the true residual), classical Gram-Schmidt applied
+// twice (CGS2) through the fused multi-dot / multi-axpy kernels.
+dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv, const double* b,
+                      double* x, double* V /* (m+1) n */, double* w, double* hdev, int m,
+                      double tol, int max_iter, double timeout_s, dg_solve_info* info) {
+  using clock = std::chrono::steady_clock;
+  const auto t0 = clock::now();
+  double bnorm2;
+  dg_status st = vo.dots_host(n, 1, b, b, n, &bnorm2);
+  if (st != DG_OK) return st;
+  const double bnorm = std::sqrt(bnorm2);
+  info->iterations = 0;
+  info->res0 = info->res_final = 0.0;
+  if (!std::isfinite(bnorm)) return DG_EBREAKDOWN;
+  if (bnorm == 0.0) {
+    DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, vo.stream));
+    return DG_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m), hcol(m + 2),
+      hcol2(m + 2);
+  int it = 0;
+  bool first = true;
+  while (true) {
+    // r = b - A x -> V_0
+    st = A(x, w);
+    if (st != DG_OK) return st;
+    st = vo.axpby(n, 1.0, b, -1.0, w, V);
+    if (st != DG_OK) return st;
+    double beta2;
+    st = vo.dots_host(n, 1, V, V, n, &beta2);
+    if (st != DG_OK) return st;
+    double beta = std::sqrt(beta2);
+    if (!std::isfinite(beta)) return DG_EBREAKDOWN;
+    if (first) {
+      info->res0 = beta;
+      first = false;
+    }
+    info->res_final = beta;
+    if (beta <= tol * bnorm) return DG_OK;
+    if (it >= max_iter) return DG_ENOCONV;
+    st = vo.axpby(n, 1.0 / beta, V, 0.0, nullptr, V);
+    if (st != DG_OK) return st;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    bool done = false;
+    for (; j < m && it < max_iter; ++j, ++it) {
+      double* vj = V + (int64_t)j * n;
+      double* vj1 = V + (int64_t)(j + 1) * n;
+      // w = A D^-1 v_j   (z = D^-1 v_j staged in v_{j+1})
+      if (dinv) {
+        st = vo.mul(n, dinv, vj, vj1);
+        if (st != DG_OK) return st;
+        st = A(vj1, w);
+      } else {
+        st = A(vj, w);
+      }
+      if (st != DG_OK) return st;
+      // two classical Gram-Schmidt passes
+      for (int pass = 0; pass < 2; ++pass) {
+        st = vo.dots(n, j + 1, w, V, n, hdev);
+        if (st != DG_OK) return st;
+        multi_axpy_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j + 1, hdev, V, n, w);
+        DG_CUDA(cudaGetLastError());
+        DG_CUDA(cudaMemcpyAsync(vo.host_scal, hdev, sizeof(double) * (j + 1),
+                                cudaMemcpyDeviceToHost, vo.stream));
+        DG_CUDA(cudaStreamSynchronize(vo.stream));
+        for (int i = 0; i <= j; ++i) (pass == 0 ? hcol : hcol2)[i] = vo.host_scal[i];
+      }
+      double hn2;
+      st = vo.dots_host(n, 1, w, w, n, &hn2);
+      if (st != DG_OK) return st;
+      for (int i = 0; i <= j; ++i) hcol[i] += hcol2[i];
+      hcol[j + 1] = std::sqrt(hn2);
+      if (!std::isfinite(hcol[j + 1])) return DG_EBREAKDOWN;
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        const double a = hcol[i], bb = hcol[i + 1];
+        hcol[i] = cs[i] * a + sn[i] * bb;
+        hcol[i + 1] = -sn[i] * a + cs[i] * bb;
+      }
+      const double a = hcol[j], bb = hcol[j + 1];
+      const double r = std::hypot(a, bb);
+      cs[j] = r == 0.0 ? 1.0 : a / r;
+      sn[j] = r == 0.0 ? 0.0 : bb / r;
+      hcol[j] = r;
+      hcol[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+      const double hnext = std::sqrt(hn2);
+      if (hnext > 0.0) {
+        st = vo.axpby(n, 1.0 / hnext, w, 0.0, nullptr, vj1);
+        if (st != DG_OK) return st;
+      }
+      info->iterations = it + 1;
+      info->res_final = std::fabs(g[j + 1]);
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hnext == 0.0) {
+        ++j;
+        ++it;
+        done = true;
+        break;
+      }
+      if (timeout_s > 0 &&
+          std::chrono::duration<double>(clock::now() - t0).count() > timeout_s) {
+        ++j;
+        ++it;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular), x += D^-1 V y
+    for (int i = j - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < j; ++l) s -= H[(size_t)i * m + l] * y[l];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    DG_CUDA(cudaMemcpyAsync(hdev, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, vo.stream));
+    gmres_update_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j, hdev, V, n, dinv, x);
+    DG_CUDA(cudaGetLastError());
+    DG_CUDA(cudaStreamSynchronize(vo.stream));  // y is host memory
+    if (timeout_s > 0 && std::chrono::duration<double>(clock::now() - t0).count() > timeout_s)
+      return DG_ETIMEOUT;
+    if (done) {
+      // true residual of the final iterate
+      st = A(x, w);
+      if (st != DG_OK) return st;
+      st = vo.axpby(n, 1.0, b, -1.0, w, w);
+      if (st != DG_OK) return st;
+      double rr;
+      st = vo.dots_host(n, 1, w, w, n, &rr);
+      if (st != DG_OK) return st;
+      info->res_final = std::sqrt(rr);
+      if (!std::isfinite(info->res_final)) return DG_EBREAKDOWN;
+      if (info->res_final <= tol * bnorm * 1.0000001) return DG_OK;
+      // rounding made the estimate optimistic: continue with a restart
+    }
+  }
+}
+
+// --------------------------------------------------------------- FCG
+// Flexible preconditioned CG (Polak-Ribiere beta = <z, r - r_old>/<z_old, r_old>),
+// robust when the preconditioner varies between iterations (multigrid in
+// reduced precision).  P == nullptr: unpreconditioned.
+dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const double* b,
+                   double* x, double* r, double* r_old, double* z, double* p, double* q,
+                   double tol, int max_iter, double timeout_s, dg_solve_info* info) {
+  using clock = std::chrono::steady_clock;
+  const auto t0 = clock::now();
+  info->iterations = 0;
+  double bb;
+  dg_status st = vo.dots_host(n, 1, b, b, n, &bb);
+  if (st != DG_OK) return st;
+  const double bnorm = std::sqrt(bb);
+  if (!std::isfinite(bnorm)) return DG_EBREAKDOWN;
+  if (bnorm == 0.0) {
+    DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, vo.stream));
+    info->res0 = info->res_final = 0.0;
+    return DG_OK;
+  }
+  st = A(x, q);
+  if (st != DG_OK) return st;
+  st = vo.axpby(n, 1.0, b, -1.0, q, r);
+  if (st != DG_OK) return st;
+  double rr;
+  st = vo.dots_host(n, 1, r, r, n, &rr);
+  if (st != DG_OK) return st;
+  info->res0 = info->res_final = std::sqrt(rr);
+  if (!std::isfinite(rr)) return DG_EBREAKDOWN;
+  if (info->res0 <= tol * bnorm) return DG_OK;
+  if (P) {
+    st = (*P)(r, z);
+    if (st != DG_OK) return st;
+  } else {
+    DG_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, vo.stream));
+  }
+  double rz;
+  st = vo.dots_host(n, 1, z, r, n, &rz);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, vo.stream));
+  for (int it = 0; it < max_iter; ++it) {
+    st = A(p, q);
+    if (st != DG_OK) return st;
+    double pq;
+    st = vo.dots_host(n, 1, p, q, n, &pq);
+    if (st != DG_OK) return st;
+    if (!std::isfinite(pq) || pq <= 0.0) return DG_EBREAKDOWN;
+    const double alpha = rz / pq;
+    cg_update_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, alpha, p, q, x, r, r_old);
+    DG_CUDA(cudaGetLastError());
+    st = vo.dots_host(n, 1, r, r, n, &rr);
+    if (st != DG_OK) return st;
+    info->iterations = it + 1;
+    info->res_final = std::sqrt(rr);
+    if (!std::isfinite(rr)) return DG_EBREAKDOWN;
+    if (info->res_final <= tol * bnorm) return DG_OK;
+    if (timeout_s > 0 && std::chrono::duration<double>(clock::now() - t0).count() > timeout_s)
+      return DG_ETIMEOUT;
+    if (P) {
+      st = (*P)(r, z);
+      if (st != DG_OK) return st;
+    } else {
+      DG_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, vo.stream));
+    }
+    // <z, r> and <z, r_old> in one pass
+    double zr[2];
+    {
+      // r_old and r are adjacent in the caller's workspace: r_old = r + n
+      st = vo.dots_host(n, 2, z, r, r_old - r, zr);
+      if (st != DG_OK) return st;
+    }
+    const double rz_new = zr[0];
+    const double beta = (zr[0] - zr[1]) / rz;
+    rz = rz_new;
+    st = vo.axpby(n, 1.0, z, beta, p, p);
+    if (st != DG_OK) return st;
+  }
+  return DG_ENOCONV;
+}
+
+}  // namespace dg

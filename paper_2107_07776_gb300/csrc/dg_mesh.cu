@@ -264,18 +264,26 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
         m->vx[a][i] = (double)i;  // unit extent in the absent axis of 2D meshes
       }
     }
-    std::vector<double> h(na);
-    std::vector<float> hf(na);
+    std::vector<double> h(na), hi(na);
+    std::vector<float> hf(na), hif(na);
     for (int i = 0; i < na; ++i) {
       h[i] = m->vx[a][i + 1] - m->vx[a][i];
+      hi[i] = 1.0 / h[i];
       hf[i] = (float)h[i];
+      hif[i] = (float)hi[i];
     }
     cudaError_t e = cudaMalloc(&m->d_h64[a], sizeof(double) * na);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_h32[a], sizeof(float) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_hi64[a], sizeof(double) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_hi32[a], sizeof(float) * na);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(m->d_h64[a], h.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(m->d_h32[a], hf.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_hi64[a], hi.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_hi32[a], hif.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die here
     if (e != cudaSuccess) {
       dg_mesh_destroy(m);
@@ -297,6 +305,8 @@ void dg_mesh_destroy(dg_mesh* m) {
   for (int a = 0; a < 3; ++a) {
     if (m->d_h64[a]) cudaFree(m->d_h64[a]);
     if (m->d_h32[a]) cudaFree(m->d_h32[a]);
+    if (m->d_hi64[a]) cudaFree(m->d_hi64[a]);
+    if (m->d_hi32[a]) cudaFree(m->d_hi32[a]);
   }
   if (m->d_status) cudaFree(m->d_status);
   delete m;

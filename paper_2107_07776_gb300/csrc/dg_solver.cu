@@ -1,0 +1,404 @@
+// Stage solves and the TR-BDF2 projection step (Section 2: Eqs. trbdf2,
+// first_stage, helmholtz2a, second_stage, helmholtz3a; algebraic form at the
+// end of Section 3).  Every vector operation of the step runs in the
+// library's kernels on the solver's stream; the host sequences them.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dg_krylov.cuh"
+
+struct dg_solver {
+  dg_mesh* mesh = nullptr;
+  double Re = 1.0, c = 1e3;
+  cudaStream_t stream = nullptr;  // legacy default stream
+  dg::VecOps vo;
+  int64_t nu = 0, np = 0, nus = 0;  // velocity (all comps), pressure, one component
+  int m_alloc = 0;
+  double* V = nullptr;  // GMRES basis (m_alloc + 1) * nu
+  double* w = nullptr;
+  double* hdev = nullptr;
+  double* dinv_u = nullptr;
+  double* diag_s = nullptr;
+  double* dinv_p = nullptr;
+  double* cgbuf = nullptr;  // r, r_old, z, p, q (np each)
+  // step state
+  double *ub = nullptr, *ustar = nullptr, *ut_old = nullptr, *ut_new = nullptr, *uss = nullptr,
+         *rhs_u = nullptr, *u_g = nullptr, *u_hist = nullptr, *fcomb = nullptr;
+  double *rhs_p = nullptr, *p_g = nullptr;
+  bool has_hist = false;
+  std::vector<void*> allocs;
+};
+
+namespace dg {
+namespace {
+
+dg_status dalloc(dg_solver* s, double** p, int64_t n) {
+  cudaError_t e = cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1));
+  if (e != cudaSuccess) {
+    set_error(std::string("solver workspace: ") + cudaGetErrorString(e));
+    return DG_ENOMEM;
+  }
+  s->allocs.push_back(*p);
+  return DG_OK;
+}
+
+dg_status ensure_basis(dg_solver* s, int m) {
+  if (m <= s->m_alloc) return DG_OK;
+  if (s->V) {
+    for (auto& a : s->allocs)
+      if (a == s->V) a = nullptr;
+    cudaFree(s->V);
+    s->V = nullptr;
+  }
+  dg_status st = dalloc(s, &s->V, (int64_t)(m + 1) * s->nu);
+  if (st != DG_OK) return st;
+  s->m_alloc = m;
+  return DG_OK;
+}
+
+bool check_opts(const dg_solve_opts* o, const char* who) {
+  if (!o || !(o->tol_rel > 0.0) || o->max_iter < 1 || o->restart < 1 || o->restart > 200) {
+    set_error(std::string(who) + ": bad solve options");
+    return false;
+  }
+  return true;
+}
+
+dg_status solve_momentum(dg_solver* s, const dg_momentum_coeffs* co, const double* ubar,
+                         const double* rhs, double* x, const dg_solve_opts* o,
+                         dg_solve_info* info) {
+  dg_mesh* m = s->mesh;
+  dg_status st;
+  const double* dinv = nullptr;
+  if (o->precond == DG_PC_JACOBI) {
+    st = dg_momentum_diagonal(m, co, ubar, s->diag_s, s->stream);
+    if (st != DG_OK) return st;
+    st = s->vo.invert(s->nu, s->diag_s, s->nus, s->dinv_u);
+    if (st != DG_OK) return st;
+    dinv = s->dinv_u;
+  } else if (o->precond != DG_PC_NONE) {
+    set_error("dg_solve_stage: momentum systems take NONE or JACOBI preconditioning");
+    return DG_EINVAL;
+  }
+  if (o->guess == DG_GUESS_ZERO) DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * s->nu, s->stream));
+  st = ensure_basis(s, o->restart);
+  if (st != DG_OK) return st;
+  LinOp A = [&](const double* in, double* out) {
+    return dg_apply_momentum(m, co, ubar, in, out, s->stream);
+  };
+  return gmres_solve(s->vo, s->nu, A, dinv, rhs, x, s->V, s->w, s->hdev, o->restart, o->tol_rel,
+                     o->max_iter, o->timeout_s, info);
+}
+
+dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double* x,
+                          const dg_solve_opts* o, dg_solve_info* info) {
+  dg_mesh* m = s->mesh;
+  dg_status st;
+  if (o->guess == DG_GUESS_ZERO) DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * s->np, s->stream));
+  LinOp A = [&](const double* in, double* out) {
+    return dg_apply_poisson(m, alpha, in, out, s->stream);
+  };
+  LinOp J = [&](const double* in, double* out) { return s->vo.mul(s->np, s->dinv_p, in, out); };
+  const LinOp* P = nullptr;
+  if (o->precond == DG_PC_JACOBI) {
+    st = poisson_diagonal(m, alpha, s->dinv_p, s->stream);
+    if (st != DG_OK) return st;
+    st = s->vo.invert(s->np, s->dinv_p, s->np, s->dinv_p);
+    if (st != DG_OK) return st;
+    P = &J;
+  } else if (o->precond != DG_PC_NONE) {
+    set_error("dg_solve_stage: multigrid preconditioning is not built yet");
+    return DG_EUNSUPPORTED;
+  }
+  double* r = s->cgbuf;
+  return cg_solve(s->vo, s->np, A, P, rhs, x, r, r + s->np, r + 2 * s->np, r + 3 * s->np,
+                  r + 4 * s->np, o->tol_rel, o->max_iter, o->timeout_s, info);
+}
+
+}  // namespace
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+dg_status dg_solver_create(dg_mesh* m, double Re, double c, dg_solver** out) {
+  if (!m || !out || !(Re > 0.0) || !(c > 0.0)) {
+    set_error("dg_solver_create: bad argument");
+    return DG_EINVAL;
+  }
+  *out = nullptr;
+  dg_solver* s = new (std::nothrow) dg_solver();
+  if (!s) return DG_ENOMEM;
+  s->mesh = m;
+  s->Re = Re;
+  s->c = c;
+  s->nus = m->ncell * m->nbu;
+  s->nu = s->nus * m->dim;
+  s->np = m->ncell * m->nbp;
+  s->vo.stream = s->stream;
+  dg_status st = DG_OK;
+  double** vecs_u[] = {&s->w, &s->dinv_u, &s->ub, &s->ustar, &s->ut_old, &s->ut_new, &s->uss,
+                       &s->rhs_u, &s->u_g, &s->u_hist, &s->fcomb};
+  for (double** v : vecs_u)
+    if (st == DG_OK) st = dalloc(s, v, s->nu);
+  if (st == DG_OK) st = dalloc(s, &s->diag_s, s->nus);
+  if (st == DG_OK) st = dalloc(s, &s->dinv_p, s->np);
+  if (st == DG_OK) st = dalloc(s, &s->cgbuf, 5 * s->np);
+  if (st == DG_OK) st = dalloc(s, &s->rhs_p, s->np);
+  if (st == DG_OK) st = dalloc(s, &s->p_g, s->np);
+  if (st == DG_OK) st = dalloc(s, &s->hdev, 256);
+  if (st == DG_OK) st = dalloc(s, &s->vo.partial, 1216 * 256);
+  if (st == DG_OK) st = dalloc(s, &s->vo.scal, 256);
+  if (st == DG_OK && cudaMallocHost(&s->vo.host_scal, sizeof(double) * 256) != cudaSuccess) {
+    set_error("dg_solver_create: pinned host scratch");
+    st = DG_ENOMEM;
+  }
+  if (st == DG_OK) st = ensure_basis(s, 30);
+  if (st != DG_OK) {
+    dg_solver_destroy(s);
+    return st;
+  }
+  *out = s;
+  return DG_OK;
+}
+
+void dg_solver_destroy(dg_solver* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  for (void* a : s->allocs)
+    if (a) cudaFree(a);
+  if (s->vo.host_scal) cudaFreeHost(s->vo.host_scal);
+  delete s;
+}
+
+dg_status dg_solve_stage(dg_solver* s, const dg_momentum_coeffs* co, double alpha,
+                         const double* ubar, const double* rhs, double* x,
+                         const dg_solve_opts* o, dg_solve_info* info) {
+  dg_solve_info tmp;
+  if (!info) info = &tmp;
+  std::memset(info, 0, sizeof(*info));
+  if (!s || !rhs || !x || !check_opts(o, "dg_solve_stage")) {
+    if (s && o) set_error("dg_solve_stage: bad argument");
+    info->status = DG_EINVAL;
+    return DG_EINVAL;
+  }
+  dg_status st;
+  if (o->system == DG_SYS_MOMENTUM) {
+    if (!co || (co->adv != 0.0 && !ubar)) {
+      set_error("dg_solve_stage: momentum solve needs coefficients and ubar");
+      info->status = DG_EINVAL;
+      return DG_EINVAL;
+    }
+    st = solve_momentum(s, co, ubar, rhs, x, o, info);
+  } else if (o->system == DG_SYS_HELMHOLTZ) {
+    st = solve_helmholtz(s, alpha, rhs, x, o, info);
+  } else {
+    set_error("dg_solve_stage: unknown system");
+    st = DG_EINVAL;
+  }
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (st == DG_OK && e != cudaSuccess) st = cuda_fail(e, "dg_solve_stage");
+  if (st == DG_ENOCONV) set_error("dg_solve_stage: max_iter reached above tolerance");
+  if (st == DG_EBREAKDOWN) set_error("dg_solve_stage: non-finite residual or breakdown");
+  if (st == DG_ETIMEOUT) set_error("dg_solve_stage: wall-clock limit reached");
+  info->status = st;
+  return st;
+}
+
+dg_status dg_solver_set_history(dg_solver* s, const double* u_hist) {
+  if (!s) {
+    set_error("dg_solver_set_history: null solver");
+    return DG_EINVAL;
+  }
+  if (!u_hist) {
+    s->has_hist = false;
+    return DG_OK;
+  }
+  DG_CUDA(cudaMemcpyAsync(s->u_hist, u_hist, sizeof(double) * s->nu, cudaMemcpyDeviceToDevice,
+                          s->stream));
+  DG_CUDA(cudaStreamSynchronize(s->stream));
+  s->has_hist = true;
+  return DG_OK;
+}
+
+dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double* p,
+                      dg_solve_info info[4]) {
+  if (!s || !prm || !u || !p || !(prm->dt > 0.0)) {
+    set_error("trbdf2_step: bad argument");
+    return DG_EINVAL;
+  }
+  if (!check_opts(&prm->mom, "trbdf2_step") || !check_opts(&prm->helm, "trbdf2_step"))
+    return DG_EINVAL;
+  dg_solve_info loc[4];
+  if (!info) info = loc;
+  std::memset(info, 0, sizeof(dg_solve_info) * 4);
+  dg_mesh* m = s->mesh;
+  VecOps& vo = s->vo;
+  const cudaStream_t st_ = s->stream;
+  const int64_t nu = s->nu, np = s->np;
+  const double g = prm->gamma > 0.0 ? prm->gamma : 2.0 - std::sqrt(2.0);
+  const double dt = prm->dt;
+  const double a31 = (1.0 - g) / (2.0 * (2.0 - g)), a32 = a31, a33 = 1.0 / (2.0 - g);
+  dg_solve_opts mo = prm->mom, ho = prm->helm;
+  mo.system = DG_SYS_MOMENTUM;
+  ho.system = DG_SYS_HELMHOLTZ;
+  dg_status st;
+#define STEP(call)                  \
+  do {                              \
+    st = (call);                    \
+    if (st != DG_OK) return st;     \
+  } while (0)
+  if (!s->has_hist) {
+    DG_CUDA(cudaMemcpyAsync(s->u_hist, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+    s->has_hist = true;
+  }
+  // ---------------- stage 1: momentum predictor (Eq. first_stage) -------
+  if (prm->extrapolate) {
+    const double c1 = g / (2.0 * (1.0 - g));
+    STEP(vo.axpby(nu, 1.0 + c1, u, -c1, s->u_hist, s->ub));
+  } else {
+    DG_CUDA(cudaMemcpyAsync(s->ub, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  }
+  dg_momentum_coeffs co1 = {1.0 / (g * dt), 1.0 / (2.0 * s->Re), 0.5};
+  dg_momentum_rhs r1;
+  std::memset(&r1, 0, sizeof(r1));
+  r1.mass = co1.mass;
+  r1.u_mass = u;
+  r1.n_terms = 1;
+  r1.visc[0] = co1.visc;
+  r1.adv[0] = co1.adv;
+  r1.w[0] = u;
+  r1.wbar[0] = s->ub;
+  r1.p = p;
+  r1.uD = prm->uD_stage1;
+  r1.dir_visc = co1.visc;
+  r1.dir_adv = co1.adv;
+  r1.ubar = s->ub;
+  if (prm->f_n && prm->f_ng) {
+    STEP(vo.axpby(nu, 0.5, prm->f_n, 0.5, prm->f_ng, s->fcomb));
+    r1.f = s->fcomb;
+  }
+  STEP(dg_rhs_momentum(m, &r1, s->rhs_u, st_));
+  if (mo.guess != DG_GUESS_ZERO)
+    DG_CUDA(cudaMemcpyAsync(s->ustar, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  STEP(dg_solve_stage(s, &co1, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[0]));
+  // ---------------- stage 1: projection (Eq. helmholtz2a) ---------------
+  const double tau1 = g * dt, alpha1 = 1.0 / (s->c * s->c * tau1 * tau1);
+  STEP(dg_project_gradient(m, p, s->ut_old, st_));
+  STEP(vo.axpby(nu, 1.0, s->ustar, tau1, s->ut_old, s->uss));
+  STEP(dg_rhs_pressure(m, alpha1, tau1, s->uss, p, s->rhs_p, st_));
+  if (ho.guess != DG_GUESS_ZERO)
+    DG_CUDA(cudaMemcpyAsync(s->p_g, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
+  STEP(dg_solve_stage(s, nullptr, alpha1, nullptr, s->rhs_p, s->p_g, &ho, &info[1]));
+  STEP(dg_project_gradient(m, s->p_g, s->ut_new, st_));
+  // u^{n+g} = u* - tau (u~new - u~old)
+  STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
+  STEP(vo.axpby(nu, 1.0, s->ustar, -tau1, s->ut_new, s->u_g));
+  // ---------------- stage 2: momentum predictor (Eq. second_stage) ------
+  if (prm->extrapolate) {
+    STEP(vo.axpby(nu, 1.0 / g, s->u_g, -(1.0 - g) / g, u, s->ub));
+  } else {
+    DG_CUDA(cudaMemcpyAsync(s->ub, s->u_g, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  }
+  dg_momentum_coeffs co2 = {1.0 / ((1.0 - g) * dt), a33 / s->Re, a33};
+  dg_momentum_rhs r2;
+  std::memset(&r2, 0, sizeof(r2));
+  r2.mass = co2.mass;
+  r2.u_mass = s->u_g;
+  r2.n_terms = 2;
+  r2.visc[0] = a32 / s->Re;
+  r2.adv[0] = a32;
+  r2.w[0] = s->u_g;
+  r2.wbar[0] = s->u_g;
+  r2.visc[1] = a31 / s->Re;
+  r2.adv[1] = a31;
+  r2.w[1] = u;
+  r2.wbar[1] = u;
+  r2.p = s->p_g;
+  r2.uD = prm->uD_stage2;
+  r2.dir_visc = co2.visc;
+  r2.dir_adv = co2.adv;
+  r2.ubar = s->ub;
+  if (prm->f_n && prm->f_ng && prm->f_n1) {
+    STEP(vo.axpby(nu, a31, prm->f_n, a32, prm->f_ng, s->fcomb));
+    STEP(vo.axpby(nu, 1.0, s->fcomb, a33, prm->f_n1, s->fcomb));
+    r2.f = s->fcomb;
+  }
+  STEP(dg_rhs_momentum(m, &r2, s->rhs_u, st_));
+  if (mo.guess != DG_GUESS_ZERO)
+    DG_CUDA(cudaMemcpyAsync(s->ustar, s->u_g, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  STEP(dg_solve_stage(s, &co2, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[2]));
+  // ---------------- stage 2: projection (Eq. helmholtz3a) ---------------
+  const double tau2 = (1.0 - g) * dt, alpha2 = 1.0 / (s->c * s->c * tau2 * tau2);
+  STEP(dg_project_gradient(m, s->p_g, s->ut_old, st_));
+  STEP(vo.axpby(nu, 1.0, s->ustar, tau2, s->ut_old, s->uss));
+  STEP(dg_rhs_pressure(m, alpha2, tau2, s->uss, s->p_g, s->rhs_p, st_));
+  if (ho.guess != DG_GUESS_ZERO)
+    DG_CUDA(cudaMemcpyAsync(p, s->p_g, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
+  // p (in: p^n, no longer needed) receives p^{n+1}
+  STEP(dg_solve_stage(s, nullptr, alpha2, nullptr, s->rhs_p, p, &ho, &info[3]));
+  STEP(dg_project_gradient(m, p, s->ut_new, st_));
+  STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
+  // history u^{n+g} before u is overwritten with u^{n+1}
+  DG_CUDA(cudaMemcpyAsync(s->u_hist, s->u_g, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  STEP(vo.axpby(nu, 1.0, s->ustar, -tau2, s->ut_new, u));
+  DG_CUDA(cudaStreamSynchronize(st_));
+#undef STEP
+  return DG_OK;
+}
+
+dg_status dg_solver_save(const dg_solver* s, const char* path) {
+  if (!s || !path) {
+    set_error("dg_solver_save: bad argument");
+    return DG_EINVAL;
+  }
+  std::vector<double> h(s->nu);
+  DG_CUDA(cudaStreamSynchronize(s->stream));
+  DG_CUDA(cudaMemcpy(h.data(), s->u_hist, sizeof(double) * s->nu, cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("dg_solver_save: cannot open ") + path);
+    return DG_EINVAL;
+  }
+  const char magic[8] = {'D', 'G', 'T', 'R', 'B', 'D', 'F', '2'};
+  int64_t hdr[4] = {1, s->nu, s->np, s->has_hist ? 1 : 0};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    set_error("dg_solver_save: write failed");
+    return DG_EINVAL;
+  }
+  return DG_OK;
+}
+
+dg_status dg_solver_load(dg_solver* s, const char* path) {
+  if (!s || !path) {
+    set_error("dg_solver_load: bad argument");
+    return DG_EINVAL;
+  }
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("dg_solver_load: cannot open ") + path);
+    return DG_EINVAL;
+  }
+  char magic[8];
+  int64_t hdr[4];
+  std::vector<double> h(s->nu);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "DGTRBDF2", 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 1 && hdr[1] == s->nu &&
+            hdr[2] == s->np && std::fread(h.data(), sizeof(double), h.size(), f) == h.size();
+  std::fclose(f);
+  if (!ok) {
+    set_error("dg_solver_load: not a checkpoint of this mesh");
+    return DG_EINVAL;
+  }
+  DG_CUDA(cudaMemcpy(s->u_hist, h.data(), sizeof(double) * s->nu, cudaMemcpyHostToDevice));
+  s->has_hist = hdr[3] != 0;
+  return DG_OK;
+}
+
+}  // extern "C"

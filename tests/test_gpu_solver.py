@@ -1,0 +1,207 @@
+"""Stage solves and full TR-BDF2 steps on the GPU against the oracle
+(Sections 2-3), plus host-side failure injection and checkpoint/resume.
+
+Both sides solve to a relative residual of 1e-13 here, so the step-by-step
+difference is bounded by the conditioning times that residual; the bound
+used, 1e-8 relative L2, is the tolerance stated for full steps."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.dg import Mesh as OMesh
+from oracle.trbdf2 import GAMMA, Stepper, interpolate
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def opts(b, system, tol=1e-13, precond=None, guess=None, max_iter=5000):
+    if precond is None:
+        precond = b.DG_PC_JACOBI
+    return b.solve_opts(system, tol=tol, max_iter=max_iter, restart=30, precond=precond,
+                        guess=b.DG_GUESS_ZERO if guess is None else guess)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_stage_solves_match_direct_solve(walls):
+    from paper_2107_07776_gb300 import binding as b
+    per = (True, not walls, not walls)
+    gm = b.Mesh(3, (4, 3, 5), (0, 0, 0), (1, 1, 1), per, 2)
+    om = OMesh(3, [4, 3, 5], [0, 0, 0], [1, 1, 1], list(per), 2)
+    s = b.dg_solver_create(gm.handle, 100.0, 1e3)
+    try:
+        ub = W.random_vector(3 * om.n_u, 5)
+        rhs = W.random_vector(3 * om.n_u, 6)
+        co = b.momentum_coeffs(1.0 / (GAMMA * 0.01), 1.0 / 200, 0.5)
+        x = torch.zeros(3 * om.n_u, dtype=torch.float64, device="cuda")
+        info = b.dg_solve_stage(s, co, 0.0, dev(ub), dev(rhs), x, opts(b, b.DG_SYS_MOMENTUM))
+        assert info.res_final <= 1e-13 * np.linalg.norm(rhs) * 1.01
+        st = Stepper(om, 100.0)
+        from oracle.trbdf2 import MomentumCoeffs
+        A = st.momentum_matrix(MomentumCoeffs(co.mass, co.visc, co.adv), ub.reshape(3, -1))
+        ref = st.solve_momentum(A, rhs.reshape(3, -1)).reshape(-1)
+        assert rel_l2(x.cpu().numpy(), ref) < 1e-10
+        # Helmholtz, Jacobi-preconditioned CG
+        rp = W.random_vector(om.n_p, 7)
+        xp = torch.zeros(om.n_p, dtype=torch.float64, device="cuda")
+        info = b.dg_solve_stage(s, None, 2.9, None, dev(rp), xp, opts(b, b.DG_SYS_HELMHOLTZ))
+        assert info.iterations > 1
+        from oracle.trbdf2 import solve
+        refp = solve(st.helmholtz_matrix(2.9), rp, spd=True)
+        assert rel_l2(xp.cpu().numpy(), refp) < 1e-9
+    finally:
+        b.dg_solver_destroy(s)
+
+
+def step_params(b, dt, fields=None, extrapolate=1, tol=1e-13):
+    prm = b.dg_step_params()
+    prm.dt, prm.gamma, prm.extrapolate = dt, 0.0, extrapolate
+    prm.mom = opts(b, b.DG_SYS_MOMENTUM, tol=tol, guess=b.DG_GUESS_EXTRAP)
+    prm.helm = opts(b, b.DG_SYS_HELMHOLTZ, tol=tol, guess=b.DG_GUESS_EXTRAP)
+    if fields:
+        for k, v in fields.items():
+            setattr(prm, k, v.data_ptr() if v is not None else None)
+    return prm
+
+
+def test_tg2d_workload_steps_match_oracle():
+    """The 2D Taylor-Green workload: 10 steps, every step compared."""
+    from paper_2107_07776_gb300 import binding as b
+    w = W.TG2D
+    gm = b.Mesh.from_workload(w)
+    om = OMesh(2, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree)
+    nu = 1.0 / w.Re
+    u0 = interpolate(om, lambda x, y: W.tg2d_u(x, y, 0.0, nu))
+    p0 = interpolate(om, lambda x, y: W.tg2d_p(x, y, 0.0, nu), p_space=True)
+    uh0 = interpolate(om, lambda x, y: W.tg2d_u(x, y, -(1 - GAMMA) * w.dt, nu))
+    st = Stepper(om, w.Re, c=w.c)
+    s = b.dg_solver_create(gm.handle, w.Re, w.c)
+    try:
+        u, p = dev(u0.reshape(-1)), dev(p0)
+        b.dg_solver_set_history(s, dev(uh0.reshape(-1)))
+        ou, op, ouh = u0, p0, uh0
+        for n in range(w.steps):
+            info = b.trbdf2_step(s, step_params(b, w.dt), u, p)
+            assert all(i.status == 0 for i in info)
+            ou, op, ouh = st.step(ou, op, ouh, n * w.dt, w.dt)
+            assert rel_l2(u.cpu().numpy(), ou.reshape(-1)) < 1e-8, n
+            assert rel_l2(p.cpu().numpy(), op) < 1e-8, n
+    finally:
+        b.dg_solver_destroy(s)
+
+
+@pytest.mark.parametrize("extrapolate", [1, 0])
+def test_walled_step_with_data_and_forcing_matches_oracle(extrapolate):
+    """3D, periodic in x, Dirichlet walls in y and z with time-dependent
+    wall data and forcing (graded mesh): 3 steps compared."""
+    from paper_2107_07776_gb300 import binding as b
+    n, lo, hi, per = (3, 4, 3), (0, 0, 0), (2.0, 1.0, 1.0), (True, False, False)
+    gm = b.Mesh(3, n, lo, hi, per, 2, 1, (0.0, 1.5, 1.5))
+    om = OMesh(3, list(n), list(lo), list(hi), list(per), 2, map=1, map_param=[0, 1.5, 1.5])
+    X = om.node_coords()
+    uD = lambda t: np.stack([np.sin(X[1] + t) * (1 + X[2]), 0.3 * np.cos(X[0] * math.pi),
+                             0.1 * X[1] * (1 + t)])
+    f = lambda t: (1 + t) * W.mms_forcing(*X)
+    rng = np.random.default_rng(3)
+    u0 = rng.standard_normal((3, om.n_u)) * 0.1
+    p0 = rng.standard_normal(om.n_p) * 0.1
+    st = Stepper(om, 50.0, c=30.0, extrapolate=bool(extrapolate))
+    s = b.dg_solver_create(gm.handle, 50.0, 30.0)
+    dt = 0.02
+    try:
+        u, p = dev(u0.reshape(-1)), dev(p0)
+        ou, op, ouh = u0, p0, u0
+        for k in range(3):
+            t = k * dt
+            fld = dict(uD_stage1=dev(uD(t + GAMMA * dt).reshape(-1)),
+                       uD_stage2=dev(uD(t + dt).reshape(-1)), f_n=dev(f(t).reshape(-1)),
+                       f_ng=dev(f(t + GAMMA * dt).reshape(-1)), f_n1=dev(f(t + dt).reshape(-1)))
+            b.trbdf2_step(s, step_params(b, dt, fld, extrapolate), u, p)
+            ou, op, ouh = st.step(ou, op, ouh, t, dt, uD=uD, f=f)
+            assert rel_l2(u.cpu().numpy(), ou.reshape(-1)) < 1e-8, k
+            assert rel_l2(p.cpu().numpy(), op) < 1e-8, k
+    finally:
+        b.dg_solver_destroy(s)
+
+
+def test_failures_are_reported_from_the_host():
+    """Failure injection without any GPU fault: max_iter = 1 (no
+    convergence), a NaN planted in the right-hand side on the host, bad
+    options, and an exhausted wall-clock limit."""
+    from paper_2107_07776_gb300 import binding as b
+    gm = b.Mesh(3, (4, 4, 4), (0, 0, 0), (1, 1, 1), (True,) * 3, 2)
+    s = b.dg_solver_create(gm.handle, 100.0, 1e3)
+    try:
+        rp = torch.tensor(W.random_vector(gm.n_dofs_p, 1), device="cuda")
+        xp = torch.zeros_like(rp)
+        o = opts(b, b.DG_SYS_HELMHOLTZ, tol=1e-12, max_iter=1)
+        info = b.dg_solve_stage(s, None, 2.9, None, rp, xp, o, raise_on_error=False)
+        assert info.status == b.DG_ENOCONV and info.iterations == 1
+        assert info.res_final < info.res0              # best iterate returned
+        bad = rp.clone()
+        bad[17] = float("nan")
+        info = b.dg_solve_stage(s, None, 2.9, None, bad, xp, opts(b, b.DG_SYS_HELMHOLTZ),
+                                raise_on_error=False)
+        assert info.status == b.DG_EBREAKDOWN
+        o = opts(b, b.DG_SYS_HELMHOLTZ)
+        o.tol_rel = -1.0
+        info = b.dg_solve_stage(s, None, 2.9, None, rp, xp, o, raise_on_error=False)
+        assert info.status == b.DG_EINVAL
+        o = opts(b, b.DG_SYS_HELMHOLTZ, tol=1e-14, precond=b.DG_PC_NONE)
+        o.timeout_s = 1e-9
+        info = b.dg_solve_stage(s, None, 2.9, None, rp, xp, o, raise_on_error=False)
+        assert info.status == b.DG_ETIMEOUT
+        ru = torch.tensor(W.random_vector(gm.n_dofs_u, 2), device="cuda")
+        xu = torch.zeros_like(ru)
+        ub = torch.zeros_like(ru)
+        o = opts(b, b.DG_SYS_MOMENTUM, tol=1e-14, max_iter=1)
+        info = b.dg_solve_stage(s, b.momentum_coeffs(1.0, 1.0, 0.5), 0.0, ub, ru, xu, o,
+                                raise_on_error=False)
+        assert info.status == b.DG_ENOCONV
+        # the library still works after every failure
+        info = b.dg_solve_stage(s, None, 2.9, None, rp, xp, opts(b, b.DG_SYS_HELMHOLTZ, tol=1e-10))
+        assert info.status == 0
+    finally:
+        b.dg_solver_destroy(s)
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    from paper_2107_07776_gb300 import binding as b
+    w = W.TG2D
+    gm = b.Mesh.from_workload(w)
+    X = gm.node_coords(0).cpu().numpy()
+    Xp = gm.node_coords(1).cpu().numpy()
+    u0 = dev(W.tg2d_u(*X, 0.0, 0.01).reshape(-1))
+    p0 = dev(W.tg2d_p(*Xp, 0.0, 0.01))
+    prm = step_params(b, w.dt, tol=1e-10)
+
+    def run(nsteps, u, p, s):
+        for _ in range(nsteps):
+            b.trbdf2_step(s, prm, u, p)
+
+    s1 = b.dg_solver_create(gm.handle, w.Re, w.c)
+    ua, pa = u0.clone(), p0.clone()
+    run(4, ua, pa, s1)
+    s2 = b.dg_solver_create(gm.handle, w.Re, w.c)
+    ub_, pb = u0.clone(), p0.clone()
+    run(2, ub_, pb, s2)
+    path = str(tmp_path / "ck.bin")
+    b.dg_solver_save(s2, path)
+    b.dg_solver_destroy(s2)
+    s3 = b.dg_solver_create(gm.handle, w.Re, w.c)
+    b.dg_solver_load(s3, path)
+    run(2, ub_, pb, s3)
+    assert torch.equal(ua, ub_) and torch.equal(pa, pb)
+    for s in (s1, s3):
+        b.dg_solver_destroy(s)
