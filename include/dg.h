@@ -248,6 +248,24 @@ dg_status dg_solver_set_history(dg_solver* solver, const double* u_hist);
 dg_status dg_solver_save(const dg_solver* solver, const char* path);
 dg_status dg_solver_load(dg_solver* solver, const char* path);
 
+/* Pressure Helmholtz solve that allocates nothing.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory at the point of the solve (a fixed up-front memory budget, a
+ * framework that owns the device heap, no dg_solver available).  Same system
+ * and algorithm as dg_solve_stage with system DG_SYS_HELMHOLTZ: (alpha M^p + K)
+ * x = rhs by flexible CG with precond DG_PC_JACOBI or DG_PC_NONE and guess
+ * DG_GUESS_ZERO or DG_GUESS_GIVEN; rhs and x are caller-owned device arrays of
+ * n_dofs_p doubles, work is enqueued on `stream` and the call synchronises it.
+ * Scratch is a fixed library-owned device array (about 12.6 MB on every GPU
+ * that loads the library, held until exit), so systems with more than
+ * 262144 pressure DoFs are rejected with DG_EINVAL.  The first call on a
+ * device looks up that array's device address; make it before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller.  info (host) may be NULL. */
+dg_status dg_solve_helmholtz_noalloc(dg_mesh* mesh, double alpha, const double* rhs, double* x,
+                                     const dg_solve_opts* opts, dg_solve_info* info,
+                                     void* stream);
+
 const char* dg_status_string(dg_status status);
 const char* dg_last_error(void);
 

@@ -87,6 +87,7 @@ SIGNATURES = {
     "dg_solver_set_history": (ctypes.c_int, [c_void_p, c_void_p]),
     "dg_solver_save": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solver_load": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
+    "dg_solve_helmholtz_noalloc": (ctypes.c_int, [c_void_p, ctypes.c_double, c_void_p, c_void_p, P(dg_solve_opts), P(dg_solve_info), c_void_p]),
     "dg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dg_last_error": (ctypes.c_char_p, []),
 }
@@ -310,6 +311,17 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+
+def dg_solve_helmholtz_noalloc(mesh: int, alpha: float, rhs, x, opts: dg_solve_opts,
+                               stream=None, raise_on_error: bool = True) -> dg_solve_info:
+    info = dg_solve_info()
+    st = lib().dg_solve_helmholtz_noalloc(mesh, alpha, ptr(rhs), ptr(x), ctypes.byref(opts),
+                                          ctypes.byref(info), stream_ptr(stream))
+    if raise_on_error:
+        check(st, "dg_solve_helmholtz_noalloc")
+    info.status = st
+    return info
 
 
 def dg_status_string(status: int) -> str:
