@@ -266,6 +266,10 @@ dg_status dg_solve_helmholtz_noalloc(dg_mesh* mesh, double alpha, const double* 
                                      const dg_solve_opts* opts, dg_solve_info* info,
                                      void* stream);
 
+/* Diagnostics (no counterpart in the paper): number of CUDA kernels this
+ * library has launched in the calling process so far. */
+int64_t dg_kernel_launches(void);
+
 const char* dg_status_string(dg_status status);
 const char* dg_last_error(void);
 

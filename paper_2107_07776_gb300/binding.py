@@ -88,6 +88,7 @@ SIGNATURES = {
     "dg_solver_save": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solver_load": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solve_helmholtz_noalloc": (ctypes.c_int, [c_void_p, ctypes.c_double, c_void_p, c_void_p, P(dg_solve_opts), P(dg_solve_info), c_void_p]),
+    "dg_kernel_launches": (ctypes.c_int64, []),
     "dg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dg_last_error": (ctypes.c_char_p, []),
 }
@@ -322,6 +323,10 @@ def dg_solve_helmholtz_noalloc(mesh: int, alpha: float, rhs, x, opts: dg_solve_o
         check(st, "dg_solve_helmholtz_noalloc")
     info.status = st
     return info
+
+
+def dg_kernel_launches() -> int:
+    return int(lib().dg_kernel_launches())
 
 
 def dg_status_string(status: int) -> str:

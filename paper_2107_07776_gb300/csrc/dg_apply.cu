@@ -273,7 +273,7 @@ static dg_status launch_fixed(const OpArgs<T>& args, const Tab1D<T>& tb, const T
     set_error("operator apply: grid too large");
     return DG_EINVAL;
   }
-  scalar_op_kernel<T, DIM, N, ADV, CPB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst);
+  scalar_op_kernel<T, DIM, N, ADV, CPB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }

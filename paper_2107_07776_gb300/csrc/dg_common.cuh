@@ -70,6 +70,9 @@ struct dg_mesh {
 
 namespace dg {
 
+// kernels launched by the library in this process (diagnostics)
+void count_launch();
+
 // thread-local error message, set by the entry points
 void set_error(const std::string& msg);
 dg_status cuda_fail(cudaError_t e, const char* where);
@@ -81,6 +84,10 @@ dg_status cuda_fail(cudaError_t e, const char* where);
   } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+dg_status finish_mesh(dg_mesh* m, cudaStream_t s);
+dg_status make_level_mesh(const dg_mesh* fine, const int coarsen[3], int degree_u, cudaStream_t s,
+                          dg_mesh** out);
 
 // launchers (dg_apply.cu)
 template <typename T>

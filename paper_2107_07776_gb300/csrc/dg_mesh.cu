@@ -6,6 +6,7 @@
 // affine cells).  Points come from Newton's method on the Legendre
 // polynomial; basis values and derivatives from barycentric Lagrange
 // interpolation (Berrut & Trefethen, SIAM Review 46, 2004).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,9 @@
 namespace dg {
 
 static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_kernel_launches{0};
+
+void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -174,6 +178,87 @@ static void lattice_vertex(const dg_mesh_desc& d, const int L[3], double X[3]) {
 
 }  // namespace dg
 
+
+namespace dg {
+
+// Tables, per-axis extents and the status word of a mesh whose sizes and
+// vertex lattice are set.
+dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
+  cudaGetDevice(&m->device);
+  m->nu = m->k + 1;
+  m->np = m->k;
+  m->nbu = m->dim == 3 ? m->nu * m->nu * m->nu : m->nu * m->nu;
+  m->nbp = m->dim == 3 ? m->np * m->np * m->np : m->np * m->np;
+  make_tables(m->nu, &m->tu64);
+  make_tables(m->np, &m->tp64);
+  make_mix(m->tu64, m->nu, m->tp64, m->np, &m->mix64);
+  m->tu32 = cast_tables<float>(m->tu64);
+  m->tp32 = cast_tables<float>(m->tp64);
+  for (int a = 0; a < 3; ++a) {
+    int na = m->n[a];
+    std::vector<double> h(na), hi(na);
+    std::vector<float> hf(na), hif(na);
+    for (int i = 0; i < na; ++i) {
+      h[i] = m->vx[a][i + 1] - m->vx[a][i];
+      hi[i] = 1.0 / h[i];
+      hf[i] = (float)h[i];
+      hif[i] = (float)hi[i];
+    }
+    cudaError_t e = cudaMalloc(&m->d_h64[a], sizeof(double) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_h32[a], sizeof(float) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_hi64[a], sizeof(double) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_hi32[a], sizeof(float) * na);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_h64[a], h.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_h32[a], hf.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_hi64[a], hi.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_hi32[a], hif.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die here
+    if (e != cudaSuccess) return cuda_fail(e, "mesh upload");
+  }
+  cudaError_t e = cudaMalloc(&m->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "mesh status word");
+  return DG_OK;
+}
+
+// Mesh of a coarser multigrid level: axes with coarsen[a] set keep every
+// other vertex of `fine`; `degree_u` sets the level's pressure nodes per
+// direction (np = degree_u).  Affine meshes only.
+dg_status make_level_mesh(const dg_mesh* fine, const int coarsen[3], int degree_u,
+                          cudaStream_t s, dg_mesh** out) {
+  *out = nullptr;
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return DG_ENOMEM;
+  m->desc = fine->desc;
+  m->dim = fine->dim;
+  m->k = degree_u;
+  m->desc.degree_u = degree_u;
+  m->affine = fine->affine;
+  m->ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    m->periodic[a] = fine->periodic[a];
+    const bool c = a < fine->dim && coarsen[a];
+    m->n[a] = c ? fine->n[a] / 2 : fine->n[a];
+    if (a < fine->dim) m->desc.n_cells[a] = m->n[a];
+    m->ncell *= m->n[a];
+    m->vx[a].resize(m->n[a] + 1);
+    for (int i = 0; i <= m->n[a]; ++i) m->vx[a][i] = fine->vx[a][c ? 2 * i : i];
+  }
+  dg_status st = finish_mesh(m, s);
+  if (st != DG_OK) {
+    dg_mesh_destroy(m);
+    return st;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+}  // namespace dg
+
 using namespace dg;
 
 extern "C" {
@@ -193,6 +278,8 @@ const char* dg_status_string(dg_status s) {
 }
 
 const char* dg_last_error(void) { return g_last_error.c_str(); }
+
+int64_t dg_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) {
   if (!desc || !out) {
@@ -230,24 +317,13 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   m->desc = d;
   m->dim = d.dim;
   m->k = d.degree_u;
-  m->nu = m->k + 1;
-  m->np = m->k;
-  m->nbu = m->dim == 3 ? m->nu * m->nu * m->nu : m->nu * m->nu;
-  m->nbp = m->dim == 3 ? m->np * m->np * m->np : m->np * m->np;
   m->ncell = nc;
   for (int a = 0; a < 3; ++a) {
     m->n[a] = a < d.dim ? d.n_cells[a] : 1;
     m->periodic[a] = a < d.dim ? (d.periodic[a] ? 1 : 0) : 1;
   }
   m->affine = d.map != DG_MAP_PERTURBED_SIN;
-  cudaGetDevice(&m->device);
-  make_tables(m->nu, &m->tu64);
-  make_tables(m->np, &m->tp64);
-  make_mix(m->tu64, m->nu, m->tp64, m->np, &m->mix64);
-  m->tu32 = cast_tables<float>(m->tu64);
-  m->tp32 = cast_tables<float>(m->tp64);
-  cudaStream_t s = as_stream(stream);
-  // per-axis vertex lattice and cell extents (affine maps)
+  // per-axis vertex lattice (affine maps; the trilinear map perturbs it)
   for (int a = 0; a < 3; ++a) {
     int na = m->n[a];
     m->vx[a].resize(na + 1);
@@ -264,37 +340,11 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
         m->vx[a][i] = (double)i;  // unit extent in the absent axis of 2D meshes
       }
     }
-    std::vector<double> h(na), hi(na);
-    std::vector<float> hf(na), hif(na);
-    for (int i = 0; i < na; ++i) {
-      h[i] = m->vx[a][i + 1] - m->vx[a][i];
-      hi[i] = 1.0 / h[i];
-      hf[i] = (float)h[i];
-      hif[i] = (float)hi[i];
-    }
-    cudaError_t e = cudaMalloc(&m->d_h64[a], sizeof(double) * na);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_h32[a], sizeof(float) * na);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_hi64[a], sizeof(double) * na);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_hi32[a], sizeof(float) * na);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(m->d_h64[a], h.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(m->d_h32[a], hf.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(m->d_hi64[a], hi.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(m->d_hi32[a], hif.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die here
-    if (e != cudaSuccess) {
-      dg_mesh_destroy(m);
-      return cuda_fail(e, "dg_mesh_create upload");
-    }
   }
-  cudaError_t e = cudaMalloc(&m->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(int), s);
-  if (e != cudaSuccess) {
+  dg_status st = finish_mesh(m, as_stream(stream));
+  if (st != DG_OK) {
     dg_mesh_destroy(m);
-    return cuda_fail(e, "dg_mesh_create status word");
+    return st;
   }
   *out = m;
   return DG_OK;

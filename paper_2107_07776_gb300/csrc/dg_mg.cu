@@ -1,0 +1,540 @@
+// h/p multigrid preconditioner for the pressure Helmholtz systems (Section 4
+// names a geometric multigrid preconditioner for them; its components are
+// the project's own):
+//   levels   the fine pressure space Q_{k-1}, then p-coarsening to Q_1 on the
+//            same cells, then h-coarsening by 2 along every axis with an even
+//            number of cells, down to at most 512 DoFs;
+//   operator alpha M^p + K rediscretised on every level (same alpha, that
+//            level's cell sizes and penalty, the same apply kernels);
+//   transfer cell-local DG embedding: prolongation evaluates the coarse
+//            polynomial at the fine nodes (exact: the coarse space is a
+//            subspace), restriction is its transpose;
+//   smoother Chebyshev iteration of degree 4 on D^-1 A over
+//            [lambda_max/20, 1.1 lambda_max], lambda_max from 15 Lanczos
+//            (Jacobi-CG) steps; the coarsest level runs a degree-30 Chebyshev
+//            over its full Lanczos spectrum estimate;
+//   cycle    one V-cycle (pre- and post-smoothing) per outer CG iteration.
+// T = float gives the mixed-precision preconditioner (all level vectors and
+// applies in FP32 inside the FP64 flexible CG), T = double the FP64 one.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dg_krylov.cuh"
+#include "dg_mg.cuh"
+
+namespace dg {
+
+namespace {
+
+unsigned grid1(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// 1D Lagrange basis on nodes xs (n) at x, product form
+void lagrange_at(const double* xs, int n, double x, double* out) {
+  for (int j = 0; j < n; ++j) {
+    double v = 1.0;
+    for (int l = 0; l < n; ++l)
+      if (l != j) v *= (x - xs[l]) / (xs[j] - xs[l]);
+    out[j] = v;
+  }
+}
+
+template <typename T>
+__global__ void cvt_kernel(int64_t n, const double* __restrict__ a, T* __restrict__ b) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = (T)a[k];
+}
+template <typename T>
+__global__ void cvt_back_kernel(int64_t n, const T* __restrict__ a, double* __restrict__ b) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = (double)a[k];
+}
+template <typename T>
+__global__ void inv_diag_kernel(int64_t n, const double* __restrict__ d, T* __restrict__ dinv) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dinv[k] = (T)(1.0 / d[k]);
+}
+// r = dinv .* (b - t) (t may be null: r = dinv .* b); d = r * inv_theta
+template <typename T>
+__global__ void cheb_init_kernel(int64_t n, const T* __restrict__ b, const T* __restrict__ t,
+                                 const T* __restrict__ dinv, T inv_theta, T* __restrict__ r,
+                                 T* __restrict__ d) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const T rk = dinv[k] * (t ? b[k] - t[k] : b[k]);
+    r[k] = rk;
+    d[k] = rk * inv_theta;
+  }
+}
+// x += d; r -= dinv .* t; d = c1 d + c2 r
+template <typename T>
+__global__ void cheb_step_kernel(int64_t n, T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
+                                 const T* __restrict__ t, const T* __restrict__ dinv, T c1, T c2) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const T dk = d[k];
+    x[k] += dk;
+    const T rk = r[k] - dinv[k] * t[k];
+    r[k] = rk;
+    d[k] = c1 * dk + c2 * rk;
+  }
+}
+template <typename T>
+__global__ void add_kernel(int64_t n, const T* __restrict__ d, T* __restrict__ x) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    x[k] += d[k];
+}
+template <typename T>
+__global__ void sub_kernel(int64_t n, const T* __restrict__ b, const T* __restrict__ t,
+                           T* __restrict__ r) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    r[k] = b[k] - t[k];
+}
+// deterministic pseudo-random start vector in [-1, 1] (splitmix64 hash)
+template <typename T>
+__global__ void hash_fill_kernel(int64_t n, T* __restrict__ x) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = (uint64_t)k + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[k] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+// partial dot products accumulated in double, fixed order
+template <typename T>
+__global__ void __launch_bounds__(256) dot_kernel(int64_t n, const T* __restrict__ a,
+                                                  const T* __restrict__ b, double* __restrict__ part) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)a[k] * (double)b[k];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+template <typename T>
+__global__ void prolong_add_kernel(const __grid_constant__ Transfer tr, int64_t nfine_dofs,
+                                   const T* __restrict__ xc, T* __restrict__ xf) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nfine_dofs) return;
+  const int nbf = tr.dim == 3 ? tr.nf * tr.nf * tr.nf : tr.nf * tr.nf;
+  const int nbc = tr.dim == 3 ? tr.nc * tr.nc * tr.nc : tr.nc * tr.nc;
+  const int64_t fc = gid / nbf;
+  const int node = (int)(gid % nbf);
+  int fi[3] = {(int)(fc % tr.nfine[0]), (int)((fc / tr.nfine[0]) % tr.nfine[1]),
+               (int)(fc / ((int64_t)tr.nfine[0] * tr.nfine[1]))};
+  int ci[3], bit[3];
+  for (int a = 0; a < 3; ++a) {
+    ci[a] = tr.hco[a] ? fi[a] >> 1 : fi[a];
+    bit[a] = tr.hco[a] ? (fi[a] & 1) : 0;
+  }
+  const int64_t cc = ci[0] + (int64_t)tr.ncoarse[0] * (ci[1] + (int64_t)tr.ncoarse[1] * ci[2]);
+  const int ii[3] = {node % tr.nf, (node / tr.nf) % tr.nf, tr.dim == 3 ? node / (tr.nf * tr.nf) : 0};
+  double acc = 0.0;
+  for (int j = 0; j < nbc; ++j) {
+    const int jj[3] = {j % tr.nc, (j / tr.nc) % tr.nc, tr.dim == 3 ? j / (tr.nc * tr.nc) : 0};
+    double w = 1.0;
+    for (int a = 0; a < tr.dim; ++a) w *= tr.M[tr.hco[a] ? bit[a] : 2][ii[a]][jj[a]];
+    acc += w * (double)xc[cc * nbc + j];
+  }
+  xf[gid] += (T)acc;
+}
+
+template <typename T>
+__global__ void restrict_kernel(const __grid_constant__ Transfer tr, int64_t ncoarse_dofs,
+                                const T* __restrict__ rf, T* __restrict__ bc) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ncoarse_dofs) return;
+  const int nbf = tr.dim == 3 ? tr.nf * tr.nf * tr.nf : tr.nf * tr.nf;
+  const int nbc = tr.dim == 3 ? tr.nc * tr.nc * tr.nc : tr.nc * tr.nc;
+  const int64_t cc = gid / nbc;
+  const int node = (int)(gid % nbc);
+  const int ci[3] = {(int)(cc % tr.ncoarse[0]), (int)((cc / tr.ncoarse[0]) % tr.ncoarse[1]),
+                     (int)(cc / ((int64_t)tr.ncoarse[0] * tr.ncoarse[1]))};
+  const int jj[3] = {node % tr.nc, (node / tr.nc) % tr.nc, tr.dim == 3 ? node / (tr.nc * tr.nc) : 0};
+  int nchild = 1;
+  for (int a = 0; a < tr.dim; ++a)
+    if (tr.hco[a]) nchild *= 2;
+  double acc = 0.0;
+  for (int ch = 0; ch < nchild; ++ch) {
+    int bit[3] = {0, 0, 0}, fi[3], t = ch;
+    for (int a = 0; a < tr.dim; ++a) {
+      if (tr.hco[a]) {
+        bit[a] = t & 1;
+        t >>= 1;
+        fi[a] = 2 * ci[a] + bit[a];
+      } else {
+        fi[a] = ci[a];
+      }
+    }
+    if (tr.dim == 2) fi[2] = 0;
+    const int64_t fc = fi[0] + (int64_t)tr.nfine[0] * (fi[1] + (int64_t)tr.nfine[1] * fi[2]);
+    for (int i = 0; i < nbf; ++i) {
+      const int ii[3] = {i % tr.nf, (i / tr.nf) % tr.nf, tr.dim == 3 ? i / (tr.nf * tr.nf) : 0};
+      double w = 1.0;
+      for (int a = 0; a < tr.dim; ++a) w *= tr.M[tr.hco[a] ? bit[a] : 2][ii[a]][jj[a]];
+      acc += w * (double)rf[fc * nbf + i];
+    }
+  }
+  bc[gid] = (T)acc;
+}
+
+// Largest/smallest eigenvalues of a symmetric tridiagonal matrix by
+// bisection on Sturm sequence counts.
+void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, double* lo,
+                      double* hi) {
+  const int n = (int)a.size();
+  double gl = a[0], gu = a[0];
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+    gl = std::min(gl, a[i] - r);
+    gu = std::max(gu, a[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double q = a[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < n; ++i) {
+      double qq = q == 0.0 ? 1e-300 : q;
+      q = a[i] - x - b[i - 1] * b[i - 1] / qq;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  double l = gl, u = gu;
+  for (int it = 0; it < 200; ++it) {  // largest: count_below(x) == n - 1 just below it
+    double mid = 0.5 * (l + u);
+    if (count_below(mid) < n) l = mid;
+    else u = mid;
+  }
+  *hi = u;
+  l = gl;
+  u = gu;
+  for (int it = 0; it < 200; ++it) {  // smallest
+    double mid = 0.5 * (l + u);
+    if (count_below(mid) >= 1) u = mid;
+    else l = mid;
+  }
+  *lo = l;
+}
+
+}  // namespace
+
+template <typename T>
+static dg_status level_apply(const MGLevel<T>& L, double alpha, const T* x, T* y, cudaStream_t s);
+template <>
+dg_status level_apply<float>(const MGLevel<float>& L, double alpha, const float* x, float* y,
+                             cudaStream_t s) {
+  return dg_apply_poisson_f32(L.mesh, alpha, x, y, s);
+}
+template <>
+dg_status level_apply<double>(const MGLevel<double>& L, double alpha, const double* x, double* y,
+                              cudaStream_t s) {
+  return dg_apply_poisson(L.mesh, alpha, x, y, s);
+}
+
+template <typename T>
+MultiGrid<T>::~MultiGrid() {
+  for (auto& L : lv) {
+    if (L.owned && L.mesh) dg_mesh_destroy(L.mesh);
+    T* vs[] = {L.x, L.b, L.r, L.d, L.t, L.dinv[0], L.dinv[1]};
+    for (T* p : vs)
+      if (p) cudaFree(p);
+  }
+  if (part) cudaFree(part);
+  if (host_part) cudaFreeHost(host_part);
+  if (diag) cudaFree(diag);
+}
+
+template <typename T>
+dg_status MultiGrid<T>::build(dg_mesh* fine, cudaStream_t s) {
+  stream = s;
+  lv.clear();
+  MGLevel<T> L0;
+  L0.mesh = fine;
+  L0.owned = false;
+  L0.np = fine->np;
+  lv.push_back(L0);
+  // p-coarsening on the same cells down to Q1, then h-coarsening
+  while (lv.back().np > 2) {
+    const int nocoarsen[3] = {0, 0, 0};
+    dg_mesh* m = nullptr;
+    dg_status st = make_level_mesh(lv.back().mesh, nocoarsen, lv.back().np - 1, s, &m);
+    if (st != DG_OK) return st;
+    MGLevel<T> L;
+    L.mesh = m;
+    L.owned = true;
+    L.np = m->np;
+    L.kind = 1;
+    lv.push_back(L);
+  }
+  while (true) {
+    const dg_mesh* m0 = lv.back().mesh;
+    if (m0->ncell * m0->nbp <= 512) break;
+    int hco[3] = {0, 0, 0}, any = 0;
+    for (int a = 0; a < m0->dim; ++a)
+      if (m0->n[a] % 2 == 0) hco[a] = any = 1;
+    if (!any) break;
+    dg_mesh* m = nullptr;
+    dg_status st = make_level_mesh(m0, hco, m0->np, s, &m);
+    if (st != DG_OK) return st;
+    MGLevel<T> L;
+    L.mesh = m;
+    L.owned = true;
+    L.np = m->np;
+    L.kind = 2;
+    for (int a = 0; a < 3; ++a) L.hco[a] = hco[a];
+    lv.push_back(L);
+  }
+  int64_t nmax = 0;
+  for (auto& L : lv) {
+    L.n = L.mesh->ncell * L.mesh->nbp;
+    nmax = std::max(nmax, L.n);
+    T** vs[] = {&L.x, &L.b, &L.r, &L.d, &L.t, &L.dinv[0], &L.dinv[1]};
+    for (T** v : vs) {
+      cudaError_t e = cudaMalloc(v, sizeof(T) * L.n);
+      if (e != cudaSuccess) return cuda_fail(e, "multigrid level vectors");
+    }
+  }
+  DG_CUDA(cudaMalloc(&part, sizeof(double) * 1216));
+  DG_CUDA(cudaMallocHost(&host_part, sizeof(double) * 1216));
+  DG_CUDA(cudaMalloc(&diag, sizeof(double) * nmax));
+  cache_alpha[0] = cache_alpha[1] = std::nan("");
+  return DG_OK;
+}
+
+template <typename T>
+dg_status MultiGrid<T>::dot(int64_t n, const T* a, const T* b, double* out) {
+  int64_t nb = (n + 1023) / 1024;
+  nb = std::max<int64_t>(1, std::min<int64_t>(nb, 1216));
+  dot_kernel<T><<<(unsigned)nb, 256, 0, stream>>>(n, a, b, part); count_launch();
+  DG_CUDA(cudaGetLastError());
+  DG_CUDA(cudaMemcpyAsync(host_part, part, sizeof(double) * nb, cudaMemcpyDeviceToHost, stream));
+  DG_CUDA(cudaStreamSynchronize(stream));
+  double s = 0.0;
+  for (int64_t i = 0; i < nb; ++i) s += host_part[i];
+  *out = s;
+  return DG_OK;
+}
+
+// Lanczos extremes of D^-1 A on level l from `steps` Jacobi-CG iterations.
+template <typename T>
+dg_status MultiGrid<T>::estimate(int l, int slot, int steps, double* lo, double* hi) {
+  MGLevel<T>& L = lv[l];
+  const int64_t n = L.n;
+  const T* dinv = L.dinv[slot];
+  steps = (int)std::min<int64_t>(steps, n);
+  // Jacobi-CG from a deterministic random right-hand side; the CG
+  // coefficients give the Lanczos tridiagonal matrix of D^-1 A.
+  T *r = L.r, *z = L.x, *p = L.d, *q = L.t;
+  double rz;
+  dg_status st;
+  hash_fill_kernel<T><<<grid1(n), 256, 0, stream>>>(n, r); count_launch();  // r = b
+  cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, r, nullptr, dinv, (T)1, z, p); count_launch();  // z = p = D^-1 r
+  st = dot(n, r, z, &rz);
+  if (st != DG_OK) return st;
+  double a_prev = 0.0, b_prev = 0.0;
+  std::vector<double> diagT, offT;
+  for (int k = 0; k < steps; ++k) {
+    st = level_apply<T>(L, alpha, p, q, stream);
+    if (st != DG_OK) return st;
+    double pq;
+    st = dot(n, p, q, &pq);
+    if (st != DG_OK) return st;
+    if (!(pq > 0.0) || !(rz > 0.0)) break;
+    const double a = rz / pq;
+    // r -= a q ; z = D^-1 r  (axpy in place, then scale)
+    lanczos_update(n, (T)a, q, dinv, r, z);
+    double rz_new;
+    st = dot(n, r, z, &rz_new);
+    if (st != DG_OK) return st;
+    const double b = rz_new / rz;
+    diagT.push_back(1.0 / a + (k > 0 ? b_prev / a_prev : 0.0));
+    if (k > 0) offT.push_back(std::sqrt(b_prev) / a_prev);
+    a_prev = a;
+    b_prev = b;
+    rz = rz_new;
+    // p = z + b p
+    lanczos_dir(n, (T)b, z, p);
+    if (!(rz_new > 0.0)) break;
+  }
+  if (diagT.empty()) {
+    *lo = *hi = 1.0;
+    return DG_OK;
+  }
+  offT.resize(diagT.size() - 1);
+  tridiag_extremes(diagT, offT, lo, hi);
+  return DG_OK;
+}
+
+template <typename T>
+__global__ void lanczos_update_kernel(int64_t n, T a, const T* __restrict__ q,
+                                      const T* __restrict__ dinv, T* __restrict__ r,
+                                      T* __restrict__ z) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const T rk = r[k] - a * q[k];
+    r[k] = rk;
+    z[k] = dinv[k] * rk;
+  }
+}
+template <typename T>
+__global__ void lanczos_dir_kernel(int64_t n, T b, const T* __restrict__ z, T* __restrict__ p) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    p[k] = z[k] + b * p[k];
+}
+
+template <typename T>
+void MultiGrid<T>::lanczos_update(int64_t n, T a, const T* q, const T* dinv, T* r, T* z) {
+  lanczos_update_kernel<T><<<grid1(n), 256, 0, stream>>>(n, a, q, dinv, r, z); count_launch();
+}
+template <typename T>
+void MultiGrid<T>::lanczos_dir(int64_t n, T b, const T* z, T* p) {
+  lanczos_dir_kernel<T><<<grid1(n), 256, 0, stream>>>(n, b, z, p); count_launch();
+}
+
+template <typename T>
+dg_status MultiGrid<T>::set_alpha(double a) {
+  int slot = -1;
+  for (int sl = 0; sl < 2; ++sl)
+    if (cache_alpha[sl] == a) slot = sl;
+  if (slot >= 0) {
+    cur = slot;
+    alpha = a;
+    return DG_OK;
+  }
+  slot = next_slot;
+  next_slot ^= 1;
+  cache_alpha[slot] = a;
+  alpha = a;
+  cur = slot;
+  for (size_t l = 0; l < lv.size(); ++l) {
+    MGLevel<T>& L = lv[l];
+    dg_status st = poisson_diagonal(L.mesh, a, diag, stream);
+    if (st != DG_OK) return st;
+    inv_diag_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, diag, L.dinv[slot]); count_launch();
+    DG_CUDA(cudaGetLastError());
+    const bool coarsest = l + 1 == lv.size();
+    double lo, hi;
+    st = estimate((int)l, slot, coarsest ? 60 : 15, &lo, &hi);
+    if (st != DG_OK) return st;
+    L.lmax[slot] = 1.1 * hi;
+    L.lmin[slot] = coarsest ? std::max(0.9 * lo, 1e-3 * hi) : L.lmax[slot] / 20.0;
+  }
+  // transfer tables
+  tr.clear();
+  for (size_t l = 1; l < lv.size(); ++l) {
+    const dg_mesh* f = lv[l - 1].mesh;
+    const dg_mesh* c = lv[l].mesh;
+    Transfer t;
+    std::memset(&t, 0, sizeof(t));
+    t.dim = f->dim;
+    t.nf = f->np;
+    t.nc = c->np;
+    for (int ax = 0; ax < 3; ++ax) {
+      t.hco[ax] = lv[l].hco[ax];
+      t.nfine[ax] = f->n[ax];
+      t.ncoarse[ax] = c->n[ax];
+    }
+    for (int i = 0; i < t.nf; ++i) {
+      const double x = f->tp64.x[i];
+      double v[kMaxN];
+      for (int b = 0; b < 2; ++b) {
+        lagrange_at(c->tp64.x, t.nc, 0.5 * (b + x), v);  // child b of the coarse interval
+        for (int j = 0; j < t.nc; ++j) t.M[b][i][j] = v[j];
+      }
+      lagrange_at(c->tp64.x, t.nc, x, v);                 // same interval
+      for (int j = 0; j < t.nc; ++j) t.M[2][i][j] = v[j];
+    }
+    tr.push_back(t);
+  }
+  return DG_OK;
+}
+
+// Chebyshev smoothing on level l: x <- x + poly(D^-1 A) D^-1 (b - A x)
+template <typename T>
+dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
+  MGLevel<T>& L = lv[l];
+  const int64_t n = L.n;
+  const T* dinv = L.dinv[cur];
+  const double lmax = L.lmax[cur], lmin = L.lmin[cur];
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  dg_status st;
+  if (x_zero) {
+    cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.b, nullptr, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
+  } else {
+    st = level_apply<T>(L, alpha, L.x, L.t, stream);
+    if (st != DG_OK) return st;
+    cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.b, L.t, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
+  }
+  if (x_zero) DG_CUDA(cudaMemsetAsync(L.x, 0, sizeof(T) * n, stream));
+  for (int k = 0; k + 1 < degree; ++k) {
+    st = level_apply<T>(L, alpha, L.d, L.t, stream);
+    if (st != DG_OK) return st;
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    cheb_step_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.x, L.d, L.r, L.t, dinv,
+                                                       (T)(rho_new * rho), (T)(2.0 * rho_new / delta)); count_launch();
+    rho = rho_new;
+  }
+  add_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.d, L.x); count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <typename T>
+dg_status MultiGrid<T>::vcycle(int l) {
+  dg_status st;
+  if (l + 1 == (int)lv.size()) return chebyshev(l, 30, true);
+  MGLevel<T>& L = lv[l];
+  MGLevel<T>& C = lv[l + 1];
+  st = chebyshev(l, smooth_degree, true);
+  if (st != DG_OK) return st;
+  st = level_apply<T>(L, alpha, L.x, L.t, stream);
+  if (st != DG_OK) return st;
+  sub_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, L.b, L.t, L.r); count_launch();
+  restrict_kernel<T><<<grid1(C.n), 256, 0, stream>>>(tr[l], C.n, L.r, C.b); count_launch();
+  DG_CUDA(cudaGetLastError());
+  st = vcycle(l + 1);
+  if (st != DG_OK) return st;
+  prolong_add_kernel<T><<<grid1(L.n), 256, 0, stream>>>(tr[l], L.n, C.x, L.x); count_launch();
+  DG_CUDA(cudaGetLastError());
+  return chebyshev(l, smooth_degree, false);
+}
+
+template <typename T>
+dg_status MultiGrid<T>::apply(const double* r, double* z) {
+  MGLevel<T>& L = lv[0];
+  cvt_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, r, L.b); count_launch();
+  dg_status st = vcycle(0);
+  if (st != DG_OK) return st;
+  cvt_back_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, L.x, z); count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template struct MultiGrid<float>;
+template struct MultiGrid<double>;
+
+}  // namespace dg

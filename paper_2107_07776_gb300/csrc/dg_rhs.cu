@@ -26,6 +26,7 @@ struct Grid {
   int n[3];
   int per[3];
   const double* h[3];
+  const double* hi[3];  // inverse extents (no FP64 division in the kernels)
 };
 
 __device__ __forceinline__ int nodeof(int N, int dim, int a, int i, int t) {
@@ -80,16 +81,18 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   __shared__ double s_wb[DIM][CPB][NB];
   __shared__ double s_q[DIM][CPB][NB];
   __shared__ double s_f[CPB][NFP][2];
-  __shared__ double s_wn[CPB][NFP][2];
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
   int ci[3] = {0, 0, 0};
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  double h[3] = {1, 1, 1}, W = 0;
+  double h[3] = {1, 1, 1}, hi[3] = {1, 1, 1}, W = 0;
   if (active) {
     cell_coords(g, cell, ci);
-    for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
+    for (int b = 0; b < DIM; ++b) {
+      h[b] = g.h[b][ci[b]];
+      hi[b] = g.hi[b][ci[b]];
+    }
     W = 1.0;
     for (int b = 0; b < DIM; ++b) W *= tb.w[ii[b]] * h[b];
     for (int b = 0; b < DIM; ++b) s_wb[b][cl][node] = wb[((int64_t)b * g.ncell + cell) * NB + node];
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
             j[b] = m;
             du += tb.D[ii[b]][m] * s_u[cl][j[0] + N * (j[1] + N * j[2])];
           }
-          q = W * (-visc * du / h[b] + adv * s_u[cl][node] * s_wb[b][cl][node]);
+          q = W * (-visc * du * hi[b] + adv * s_u[cl][node] * s_wb[b][cl][node]);
         }
         s_q[b][cl][node] = q;
       }
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
         const int f = fp / NF, t = fp % NF, ax = f >> 1, s = f & 1;
         const double sgn = s ? 1.0 : -1.0;
         const int64_t nb = neighbour(g, ci, ax, s);
-        const double hK = h[ax];
+        const double hiK = hi[ax];
         double wt = 1.0;
         {
           int tt = t;
@@ -133,14 +136,14 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
           dnin += tb.dL[s][i] * s_u[cl][nd];
           wnin += tb.L[s][i] * s_wb[ax][cl][nd];
         }
-        dnin *= sgn / hK;
+        dnin *= sgn * hiK;
         wnin *= sgn;
         double fv = 0.0, fg = 0.0;
         if (MODE == 0) {
           if (nb >= 0) {
             int nc3[3];
             cell_coords(g, nb, nc3);
-            const double hN = g.h[ax][nc3[ax]];
+            const double hiN = g.hi[ax][nc3[ax]];
             double uout = 0, dnout = 0, wnout = 0;
             for (int i = 0; i < N; ++i) {
               const int nd = nodeof(N, DIM, ax, i, t);
@@ -149,19 +152,19 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
               dnout += tb.dL[1 - s][i] * v;
               wnout += tb.L[1 - s][i] * __ldg(&wb[((int64_t)ax * g.ncell + nb) * NB + nd]);
             }
-            dnout *= sgn / hN;
+            dnout *= sgn * hiN;
             wnout *= sgn;
             fv = visc * 0.5 * (dnin + dnout) - adv * 0.5 * (uin * wnin + uout * wnout);
           } else {
             fv = visc * dnin - adv * uin * wnin;
           }
         } else if (nb < 0) {
-          const double sig = pen / hK;
+          const double sig = pen * hiK;
           fv = visc * 2.0 * sig * uin + adv * (-uin * wnin + fabs(wnin) * uin);
           fg = -visc * uin;
         }
         s_f[cl][fp][0] = wt * fv;
-        s_f[cl][fp][1] = wt * fg * sgn / hK;
+        s_f[cl][fp][1] = wt * fg * sgn * hiK;
       }
     }
     __syncthreads();
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
           j[b] = m;
           acc += tb.D[m][ii[b]] * s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
         }
-        y += acc / h[b];
+        y += acc * hi[b];
         const int t = tangof(N, DIM, b, ii);
         for (int s = 0; s < 2; ++s) {
           const int fp = (2 * b + s) * NF + t;
@@ -185,7 +188,6 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     }
     __syncthreads();
   }
-  (void)s_wn;
 }
 
 // ------------------------------------------------------------------
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
           j[c] = m;
           acc += tb.D[m][ii[c]] * s_g[cl][j[0] + N * (j[1] + N * j[2])];
         }
-        y += acc / h[c];
+        y += acc * g.hi[c][ci[c]];
         const int t = tangof(N, DIM, c, ii);
         for (int s = 0; s < 2; ++s) y += s_f[cl][(2 * c + s) * NF + t] * tb.L[s][ii[c]];
       }
@@ -345,8 +347,11 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
   __syncthreads();
   if (active) {
     const int pi[3] = {node % NP, (node / NP) % NP, DIM == 3 ? node / (NP * NP) : 0};
-    double Wp = 1.0;
-    for (int b = 0; b < DIM; ++b) Wp *= tp.w[pi[b]] * h[b];
+    double Wp = 1.0, hiv[3] = {1, 1, 1};
+    for (int b = 0; b < DIM; ++b) {
+      Wp *= tp.w[pi[b]] * h[b];
+      hiv[b] = g.hi[b][ci[b]];
+    }
     double acc = 0.0;
     // cell term: sum over velocity quadrature points of W u_c d_c psi_i
     for (int q = 0; q < NB; ++q) {
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
         v[b] = mx.I[qq[b]][pi[b]];
       }
       for (int c = 0; c < DIM; ++c) {
-        double dpsi = mx.D[qq[c]][pi[c]] / h[c];
+        double dpsi = mx.D[qq[c]][pi[c]] * hiv[c];
         for (int b = 0; b < DIM; ++b)
           if (b != c) dpsi *= v[b];
         acc += Wq * s_u[c][cl][q] * dpsi;
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       for (int b = 0; b < DIM; ++b) wgt *= b == c ? mx.D[ii[b]][jj[b]] : mx.I[ii[b]][jj[b]];
       acc += wgt * s_p[cl][j];
     }
-    ut[((int64_t)c * g.ncell + cell) * NB + node] = acc / g.h[c][ci[c]];
+    ut[((int64_t)c * g.ncell + cell) * NB + node] = acc * g.hi[c][ci[c]];
   }
 }
 
@@ -426,8 +431,11 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
   int ci[3];
   cell_coords(g, cell, ci);
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  double h[3] = {1, 1, 1};
-  for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
+  double h[3] = {1, 1, 1}, hi[3] = {1, 1, 1};
+  for (int b = 0; b < DIM; ++b) {
+    h[b] = g.h[b][ci[b]];
+    hi[b] = g.hi[b][ci[b]];
+  }
   auto Wat = [&](const int j[3]) {
     double W = 1.0;
     for (int b = 0; b < DIM; ++b) W *= tb.w[j[b]] * h[b];
@@ -440,11 +448,11 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
     for (int m = 0; m < N; ++m) {
       int j[3] = {ii[0], ii[1], ii[2]};
       j[b] = m;
-      const double dm = tb.D[m][ii[b]] / h[b];
+      const double dm = tb.D[m][ii[b]] * hi[b];
       acc += Wat(j) * dm * dm;
     }
     d += visc * acc;
-    if (adv != 0.0) d -= adv * W * ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] / h[b];
+    if (adv != 0.0) d -= adv * W * ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] * hi[b];
   }
   for (int ax = 0; ax < DIM; ++ax) {
     const int t = tangof(N, DIM, ax, ii);
@@ -454,8 +462,8 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
     for (int s = 0; s < 2; ++s) {
       const double sgn = s ? 1.0 : -1.0;
       const int64_t nb = neighbour(g, ci, ax, s);
-      const double hK = h[ax];
-      const double uin = tb.L[s][ii[ax]], dnin = sgn * tb.dL[s][ii[ax]] / hK;
+      const double hiK = hi[ax];
+      const double uin = tb.L[s][ii[ax]], dnin = sgn * tb.dL[s][ii[ax]] * hiK;
       double unin = 0.0;
       if (adv != 0.0) {
         for (int i = 0; i < N; ++i)
@@ -466,11 +474,11 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
       if (nb >= 0) {
         int nc3[3];
         cell_coords(g, nb, nc3);
-        const double hN = g.h[ax][nc3[ax]];
+        const double hiN = g.hi[ax][nc3[ax]];
         // a one-cell period makes the cell its own neighbour
         const double uout = nb == cell ? tb.L[1 - s][ii[ax]] : 0.0;
-        const double dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] / hN : 0.0;
-        const double C = 0.5 * (pen / hK + pen / hN);
+        const double dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] * hiN : 0.0;
+        const double C = 0.5 * pen * (hiK + hiN);
         const double jump = uin - uout;
         fv = visc * (-0.5 * (dnin + dnout) + C * jump);
         fg = -0.5 * visc * jump;
@@ -483,10 +491,10 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
           fv += adv * (0.5 * (uin * unin + uout * unout) + 0.5 * lam * jump);
         }
       } else if (walls) {
-        fv = visc * (-dnin + 2.0 * (pen / hK) * uin) + adv * fabs(unin) * uin;
+        fv = visc * (-dnin + 2.0 * (pen * hiK) * uin) + adv * fabs(unin) * uin;
         fg = -visc * uin;
       }
-      d += wt * (fv * tb.L[s][ii[ax]] + fg * sgn * tb.dL[s][ii[ax]] / hK);
+      d += wt * (fv * tb.L[s][ii[ax]] + fg * sgn * tb.dL[s][ii[ax]] * hiK);
     }
   }
   diag[gid] = d;
@@ -500,6 +508,7 @@ Grid make_grid(const dg_mesh* m) {
     g.n[a] = m->n[a];
     g.per[a] = m->periodic[a];
     g.h[a] = m->d_h64[a];
+    g.hi[a] = m->d_hi64[a];
   }
   return g;
 }
@@ -521,6 +530,7 @@ dg_status run_explicit(const dg_mesh* m, int mode, double visc, double adv, cons
     explicit_kernel<DIM, N, 0, CPB><<<blocks, threads, 0, s>>>(g, m->tu64, visc, adv, pen, w, wb, rhs);
   else
     explicit_kernel<DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(g, m->tu64, visc, adv, pen, w, wb, rhs);
+  count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -532,7 +542,7 @@ dg_status run_mass_grad(const dg_mesh* m, double mass, const double* um, const d
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
   mass_grad_kernel<DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), m->tu64, m->tp64,
-                                                                 m->mix64, mass, um, f, p, rhs);
+                                                                 m->mix64, mass, um, f, p, rhs); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -545,7 +555,7 @@ dg_status run_pressure_rhs(const dg_mesh* m, double alpha, double inv_tau, const
   constexpr int threads = ((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
   pressure_rhs_kernel<DIM, N, NP, CPB><<<blocks, threads, 0, s>>>(
-      make_grid<DIM>(m), m->tu64, m->tp64, m->mix64, alpha, inv_tau, uss, p_old, rhs);
+      make_grid<DIM>(m), m->tu64, m->tp64, m->mix64, alpha, inv_tau, uss, p_old, rhs); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -555,7 +565,7 @@ dg_status run_project(const dg_mesh* m, const double* p, double* ut, cudaStream_
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  project_kernel<DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), m->mix64, p, ut);
+  project_kernel<DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), m->mix64, p, ut); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -566,7 +576,7 @@ dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, do
   const int64_t total = m->ncell * Sh<N, DIM>::NB;
   const unsigned blocks = (unsigned)((total + 255) / 256);
   diag_kernel<DIM, N><<<blocks, 256, 0, s>>>(make_grid<DIM>(m), pressure ? m->tp64 : m->tu64, mass,
-                                             visc, adv, (double)(N * N), pressure ? 0 : 1, ub, diag);
+                                             visc, adv, (double)(N * N), pressure ? 0 : 1, ub, diag); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "dg_krylov.cuh"
+#include "dg_mg.cuh"
 
 struct dg_solver {
   dg_mesh* mesh = nullptr;
@@ -29,6 +30,8 @@ struct dg_solver {
   double *rhs_p = nullptr, *p_g = nullptr;
   bool has_hist = false;
   std::vector<void*> allocs;
+  dg::MultiGrid<float>* mg32 = nullptr;   // built on first use
+  dg::MultiGrid<double>* mg64 = nullptr;
 };
 
 namespace dg {
@@ -108,10 +111,45 @@ dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double*
     st = s->vo.invert(s->np, s->dinv_p, s->np, s->dinv_p);
     if (st != DG_OK) return st;
     P = &J;
+  } else if (o->precond == DG_PC_MG_FP32 || o->precond == DG_PC_MG_FP64) {
+    if (!m->affine) {
+      set_error("dg_solve_stage: multigrid needs affine cells");
+      return DG_EUNSUPPORTED;
+    }
+    if (o->precond == DG_PC_MG_FP32) {
+      if (!s->mg32) {
+        s->mg32 = new (std::nothrow) MultiGrid<float>();
+        if (!s->mg32) return DG_ENOMEM;
+        st = s->mg32->build(m, s->stream);
+        if (st != DG_OK) {
+          delete s->mg32;
+          s->mg32 = nullptr;
+          return st;
+        }
+      }
+      st = s->mg32->set_alpha(alpha);
+    } else {
+      if (!s->mg64) {
+        s->mg64 = new (std::nothrow) MultiGrid<double>();
+        if (!s->mg64) return DG_ENOMEM;
+        st = s->mg64->build(m, s->stream);
+        if (st != DG_OK) {
+          delete s->mg64;
+          s->mg64 = nullptr;
+          return st;
+        }
+      }
+      st = s->mg64->set_alpha(alpha);
+    }
+    if (st != DG_OK) return st;
   } else if (o->precond != DG_PC_NONE) {
-    set_error("dg_solve_stage: multigrid preconditioning is not built yet");
-    return DG_EUNSUPPORTED;
+    set_error("dg_solve_stage: unknown preconditioner");
+    return DG_EINVAL;
   }
+  LinOp MGP = [s, o](const double* in, double* out) {
+    return o->precond == DG_PC_MG_FP32 ? s->mg32->apply(in, out) : s->mg64->apply(in, out);
+  };
+  if (o->precond == DG_PC_MG_FP32 || o->precond == DG_PC_MG_FP64) P = &MGP;
   double* r = s->cgbuf;
   return cg_solve(s->vo, s->np, A, P, rhs, x, r, r + s->np, r + 2 * s->np, r + 3 * s->np,
                   r + 4 * s->np, o->tol_rel, o->max_iter, o->timeout_s, info);
@@ -168,6 +206,8 @@ dg_status dg_solver_create(dg_mesh* m, double Re, double c, dg_solver** out) {
 void dg_solver_destroy(dg_solver* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
+  delete s->mg32;
+  delete s->mg64;
   for (void* a : s->allocs)
     if (a) cudaFree(a);
   if (s->vo.host_scal) cudaFreeHost(s->vo.host_scal);
