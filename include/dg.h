@@ -240,6 +240,50 @@ typedef struct {
 dg_status trbdf2_step(dg_solver* solver, const dg_step_params* params, double* u, double* p,
                       dg_solve_info info[4]);
 
+/* Learned initial guess (a project addition; the paper starts each solve from
+ * the previous level).  For each (stage, system) the solver keeps the last
+ * four solutions; DG_GUESS_EXTRAP starts from their linear extrapolation
+ * 2 x_{k-1} - x_{k-2} and DG_GUESS_LEARNED adds the output of a per-cell MLP
+ * (4 linear layers n_in -> hidden -> hidden -> hidden -> n_out, SiLU; inputs
+ * the cell's DoFs of those four solutions, as x_{k-1} and its first, second
+ * and third backward differences in time, and of the right-hand side, each
+ * block scaled by 1/RMS of it; output times the RMS of the second
+ * difference, the size of the extrapolation error).  BF16
+ * weights and activations with FP32 accumulation; the output layer starts at
+ * zero, so an untrained net gives the extrapolated guess.  train = 1 takes
+ * one Adam step per solve on that solve's cells (target: the converged
+ * solution).  systems: bit 0 pressure Helmholtz, bit 1 momentum.  hidden and
+ * seed apply when a net is first built. */
+typedef struct {
+  int32_t enable;
+  int32_t train;
+  int32_t systems;
+  int32_t hidden;
+  float lr;
+  uint64_t seed;
+} dg_guess_opts;
+
+dg_status dg_guess_configure(dg_solver* solver, const dg_guess_opts* opts);
+
+typedef struct {
+  int64_t train_steps;   /* optimiser steps taken */
+  double last_loss;      /* mean squared error of the last training batch (scaled units) */
+  int32_t history[4];    /* stored solutions per slot (stage 1 momentum, stage 1 Helmholtz, stage 2 ...) */
+} dg_guess_stats;
+
+dg_status dg_guess_get_stats(const dg_solver* solver, dg_guess_stats* stats);
+
+/* The learned guess's network on its own (gradient checks): weights packed as
+ * W1 [hidden x n_in], b1, W2 [hidden x hidden], b2, W3, b3, W4 [n_out x hidden],
+ * b4 (FP32, device); X [M x n_in] FP32 (rounded to BF16 on entry); hidden
+ * activations rounded to BF16 after SiLU; Y [M x n_out] FP32 out.  When T is
+ * not NULL: loss (host float) = mean((Y - T)^2) and grad (device, packed like
+ * weights) = its gradient, with the error gradients rounded to BF16 before
+ * each product.  Allocates its own scratch; synchronous. */
+dg_status dg_mlp_forward_backward(int64_t M, int32_t n_in, int32_t hidden, int32_t n_out,
+                                  const float* weights, const float* X, const float* T, float* Y,
+                                  float* loss, float* grad, void* stream);
+
 /* Set (device pointer, n_dofs_u) or clear (NULL) the stored u^{n-1+gamma}. */
 dg_status dg_solver_set_history(dg_solver* solver, const double* u_hist);
 

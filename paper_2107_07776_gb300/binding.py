@@ -57,6 +57,17 @@ class dg_solve_info(ctypes.Structure):
                 ("res_final", ctypes.c_double), ("status", ctypes.c_int32)]
 
 
+class dg_guess_opts(ctypes.Structure):
+    _fields_ = [("enable", ctypes.c_int32), ("train", ctypes.c_int32),
+                ("systems", ctypes.c_int32), ("hidden", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class dg_guess_stats(ctypes.Structure):
+    _fields_ = [("train_steps", ctypes.c_int64), ("last_loss", ctypes.c_double),
+                ("history", ctypes.c_int32 * 4)]
+
+
 class dg_step_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("extrapolate", ctypes.c_int32), ("uD_stage1", c_void_p),
@@ -85,6 +96,9 @@ SIGNATURES = {
     "dg_solve_stage": (ctypes.c_int, [c_void_p, P(dg_momentum_coeffs), ctypes.c_double, c_void_p, c_void_p, c_void_p, P(dg_solve_opts), P(dg_solve_info)]),
     "trbdf2_step": (ctypes.c_int, [c_void_p, P(dg_step_params), c_void_p, c_void_p, P(dg_solve_info)]),
     "dg_solver_set_history": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_guess_configure": (ctypes.c_int, [c_void_p, P(dg_guess_opts)]),
+    "dg_guess_get_stats": (ctypes.c_int, [c_void_p, P(dg_guess_stats)]),
+    "dg_mlp_forward_backward": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_void_p, c_void_p, c_void_p, c_void_p, P(ctypes.c_float), c_void_p, c_void_p]),
     "dg_solver_save": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solver_load": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solve_helmholtz_noalloc": (ctypes.c_int, [c_void_p, ctypes.c_double, c_void_p, c_void_p, P(dg_solve_opts), P(dg_solve_info), c_void_p]),
@@ -237,6 +251,28 @@ def trbdf2_step(solver: int, params: dg_step_params, u, p):
 
 def dg_solver_set_history(solver: int, u_hist) -> None:
     check(lib().dg_solver_set_history(solver, ptr(u_hist)), "dg_solver_set_history")
+
+
+def dg_guess_configure(solver: int, enable: int = 1, train: int = 1, systems: int = 1,
+                       hidden: int = 128, lr: float = 1e-3, seed: int = 1) -> None:
+    o = dg_guess_opts()
+    o.enable, o.train, o.systems, o.hidden, o.lr, o.seed = enable, train, systems, hidden, lr, seed
+    check(lib().dg_guess_configure(solver, ctypes.byref(o)), "dg_guess_configure")
+
+
+def dg_guess_get_stats(solver: int) -> dg_guess_stats:
+    st = dg_guess_stats()
+    check(lib().dg_guess_get_stats(solver, ctypes.byref(st)), "dg_guess_get_stats")
+    return st
+
+
+def dg_mlp_forward_backward(M: int, n_in: int, hidden: int, n_out: int, weights, X, T, Y, grad,
+                            stream=None) -> float:
+    loss = ctypes.c_float(0.0)
+    check(lib().dg_mlp_forward_backward(M, n_in, hidden, n_out, ptr(weights), ptr(X), ptr(T),
+                                        ptr(Y), ctypes.byref(loss), ptr(grad), stream_ptr(stream)),
+          "dg_mlp_forward_backward")
+    return loss.value
 
 
 def dg_solver_save(solver: int, path: str) -> None:

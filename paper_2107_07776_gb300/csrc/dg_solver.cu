@@ -9,6 +9,7 @@
 
 #include "dg_krylov.cuh"
 #include "dg_mg.cuh"
+#include "dg_guess.cuh"
 
 struct dg_solver {
   dg_mesh* mesh = nullptr;
@@ -32,6 +33,7 @@ struct dg_solver {
   std::vector<void*> allocs;
   dg::MultiGrid<float>* mg32 = nullptr;   // built on first use
   dg::MultiGrid<double>* mg64 = nullptr;
+  dg::GuessState guess;                   // stage histories and learned-guess nets
 };
 
 namespace dg {
@@ -153,6 +155,119 @@ dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double*
   double* r = s->cgbuf;
   return cg_solve(s->vo, s->np, A, P, rhs, x, r, r + s->np, r + 2 * s->np, r + 3 * s->np,
                   r + 4 * s->np, o->tol_rel, o->max_iter, o->timeout_s, info);
+}
+
+
+// ---------------------------------------------------------------- guesses
+// slot = 2 (stage - 1) + (0 momentum, 1 Helmholtz)
+struct SysShape {
+  int ncomp, nbc;
+  int64_t n;
+};
+
+SysShape shape_of(const dg_solver* s, int slot) {
+  const dg_mesh* m = s->mesh;
+  if (slot & 1) return {1, m->nbp, s->np};
+  return {m->dim, m->nbu, s->nu};
+}
+
+dg_status ensure_net(dg_solver* s, int k, const SysShape& sh) {
+  GuessState& G = s->guess;
+  if (G.net[k]) return DG_OK;
+  Mlp* net = new (std::nothrow) Mlp();
+  if (!net) return DG_ENOMEM;
+  const int nbs = sh.ncomp * sh.nbc;
+  dg_status st = net->init(5 * nbs, G.hidden, nbs, G.seed + 7919ull * k, s->stream);
+  if (st != DG_OK) {
+    delete net;
+    return st;
+  }
+  G.net[k] = net;
+  return DG_OK;
+}
+
+// Writes the initial guess of a stage solve into x; *given = 1 when x holds
+// a guess for the solve (else the caller's value stays).
+dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, double* x) {
+  GuessState& G = s->guess;
+  G.predicted = false;
+  if (mode != DG_GUESS_EXTRAP && mode != DG_GUESS_LEARNED) return DG_OK;
+  const SysShape sh = shape_of(s, slot);
+  const int cnt = G.count[slot];
+  double* const* h = G.hist[slot];
+  const dg_mesh* m = s->mesh;
+  if (cnt == 1) {
+    DG_CUDA(cudaMemcpyAsync(x, h[0], sizeof(double) * sh.n, cudaMemcpyDeviceToDevice, s->stream));
+    return DG_OK;
+  }
+  if (cnt < 2) return DG_OK;
+  const int k = (slot & 1) ? 0 : 1;
+  const bool use_net = mode == DG_GUESS_LEARNED && G.enable && ((G.systems >> k) & 1) && cnt >= 4;
+  if (!use_net) return guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], nullptr, 0.0, x, s->stream);
+  dg_status st = ensure_net(s, k, sh);
+  if (st != DG_OK) return st;
+  if (!G.part) {
+    DG_CUDA(cudaMalloc(&G.part, sizeof(double) * 5 * 1216));
+    DG_CUDA(cudaMallocHost(&G.host_part, sizeof(double) * 5 * 1216));
+  }
+  Mlp& net = *G.net[k];
+  double sout = 1.0;
+  st = guess_features(net, m->ncell, sh.ncomp, sh.nbc, h, rhs, G.scale, &sout, G.part,
+                      G.host_part, s->stream);
+  if (st != DG_OK) return st;
+  const int64_t need = m->ncell * net.n_out;
+  if (need > G.out_cap) {
+    if (G.yout) cudaFree(G.yout);
+    if (G.target) cudaFree(G.target);
+    G.yout = G.target = nullptr;
+    DG_CUDA(cudaMalloc(&G.yout, sizeof(float) * need));
+    DG_CUDA(cudaMalloc(&G.target, sizeof(float) * need));
+    G.out_cap = need;
+  }
+  st = net.forward(m->ncell, G.yout, s->stream);
+  if (st != DG_OK) return st;
+  st = guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], G.yout, sout, x, s->stream);
+  if (st != DG_OK) return st;
+  G.predicted = true;
+  G.sout = sout;
+  return DG_OK;
+}
+
+// After a solve: one optimiser step on this solve (training mode) and the
+// solution into the slot's history.
+dg_status finish_guess(dg_solver* s, int slot, int mode, const double* xs) {
+  GuessState& G = s->guess;
+  if (mode != DG_GUESS_EXTRAP && mode != DG_GUESS_LEARNED) return DG_OK;
+  const SysShape sh = shape_of(s, slot);
+  const dg_mesh* m = s->mesh;
+  double** h = G.hist[slot];
+  if (G.predicted && G.train) {
+    const int k = (slot & 1) ? 0 : 1;
+    Mlp& net = *G.net[k];
+    dg_status st = guess_target(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], xs, G.sout, G.target, s->stream);
+    if (st != DG_OK) return st;
+    double loss;
+    st = net.backward(m->ncell, G.yout, G.target, &loss, s->stream);
+    if (st != DG_OK) return st;
+    st = net.adam_step(G.lr, s->stream);
+    if (st != DG_OK) return st;
+    G.last_loss = loss;
+    ++G.train_steps;
+  }
+  G.predicted = false;
+  if (!h[3]) {
+    for (int a = 0; a < 4; ++a)
+      if (!h[a]) DG_CUDA(cudaMalloc(&h[a], sizeof(double) * sh.n));
+    G.n[slot] = sh.n;
+  }
+  double* oldest = h[3];
+  h[3] = h[2];
+  h[2] = h[1];
+  h[1] = h[0];
+  h[0] = oldest;
+  DG_CUDA(cudaMemcpyAsync(h[0], xs, sizeof(double) * sh.n, cudaMemcpyDeviceToDevice, s->stream));
+  if (G.count[slot] < 4) ++G.count[slot];
+  return DG_OK;
 }
 
 }  // namespace
@@ -285,6 +400,10 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   dg_solve_opts mo = prm->mom, ho = prm->helm;
   mo.system = DG_SYS_MOMENTUM;
   ho.system = DG_SYS_HELMHOLTZ;
+  // the step prepares every guess itself (previous level, extrapolation or
+  // learned), so the solves start from the vector they are handed
+  if (mo.guess != DG_GUESS_ZERO) mo.guess = DG_GUESS_GIVEN;
+  if (ho.guess != DG_GUESS_ZERO) ho.guess = DG_GUESS_GIVEN;
   dg_status st;
 #define STEP(call)                  \
   do {                              \
@@ -324,7 +443,9 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   STEP(dg_rhs_momentum(m, &r1, s->rhs_u, st_));
   if (mo.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->ustar, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  STEP(prepare_guess(s, 0, prm->mom.guess, s->rhs_u, s->ustar));
   STEP(dg_solve_stage(s, &co1, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[0]));
+  STEP(finish_guess(s, 0, prm->mom.guess, s->ustar));
   // ---------------- stage 1: projection (Eq. helmholtz2a) ---------------
   const double tau1 = g * dt, alpha1 = 1.0 / (s->c * s->c * tau1 * tau1);
   STEP(dg_project_gradient(m, p, s->ut_old, st_));
@@ -332,7 +453,9 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   STEP(dg_rhs_pressure(m, alpha1, tau1, s->uss, p, s->rhs_p, st_));
   if (ho.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->p_g, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
+  STEP(prepare_guess(s, 1, prm->helm.guess, s->rhs_p, s->p_g));
   STEP(dg_solve_stage(s, nullptr, alpha1, nullptr, s->rhs_p, s->p_g, &ho, &info[1]));
+  STEP(finish_guess(s, 1, prm->helm.guess, s->p_g));
   STEP(dg_project_gradient(m, s->p_g, s->ut_new, st_));
   // u^{n+g} = u* - tau (u~new - u~old)
   STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
@@ -370,7 +493,9 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   STEP(dg_rhs_momentum(m, &r2, s->rhs_u, st_));
   if (mo.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->ustar, s->u_g, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  STEP(prepare_guess(s, 2, prm->mom.guess, s->rhs_u, s->ustar));
   STEP(dg_solve_stage(s, &co2, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[2]));
+  STEP(finish_guess(s, 2, prm->mom.guess, s->ustar));
   // ---------------- stage 2: projection (Eq. helmholtz3a) ---------------
   const double tau2 = (1.0 - g) * dt, alpha2 = 1.0 / (s->c * s->c * tau2 * tau2);
   STEP(dg_project_gradient(m, s->p_g, s->ut_old, st_));
@@ -379,7 +504,9 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   if (ho.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(p, s->p_g, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
   // p (in: p^n, no longer needed) receives p^{n+1}
+  STEP(prepare_guess(s, 3, prm->helm.guess, s->rhs_p, p));
   STEP(dg_solve_stage(s, nullptr, alpha2, nullptr, s->rhs_p, p, &ho, &info[3]));
+  STEP(finish_guess(s, 3, prm->helm.guess, p));
   STEP(dg_project_gradient(m, p, s->ut_new, st_));
   STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
   // history u^{n+g} before u is overwritten with u^{n+1}
@@ -390,23 +517,90 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   return DG_OK;
 }
 
+dg_status dg_guess_configure(dg_solver* s, const dg_guess_opts* o) {
+  if (!s || !o || o->hidden < 8 || o->hidden > 1024 || !(o->lr > 0.0f) || o->systems < 0 ||
+      o->systems > 3) {
+    set_error("dg_guess_configure: bad argument");
+    return DG_EINVAL;
+  }
+  GuessState& G = s->guess;
+  G.enable = o->enable ? 1 : 0;
+  G.train = o->train ? 1 : 0;
+  G.systems = o->systems;
+  G.lr = o->lr;
+  if (!G.net[0] && !G.net[1]) {
+    G.hidden = o->hidden;
+    G.seed = o->seed;
+  }
+  return DG_OK;
+}
+
+dg_status dg_guess_get_stats(const dg_solver* s, dg_guess_stats* st) {
+  if (!s || !st) {
+    set_error("dg_guess_get_stats: bad argument");
+    return DG_EINVAL;
+  }
+  st->train_steps = s->guess.train_steps;
+  st->last_loss = s->guess.last_loss;
+  for (int i = 0; i < 4; ++i) st->history[i] = s->guess.count[i];
+  return DG_OK;
+}
+
+}  // extern "C"
+
+// Checkpoint (version 2): u^{n-1+gamma}, the stage histories of the guesses
+// and the learned-guess networks with their optimiser state.
+namespace {
+bool put(FILE* f, const void* p, size_t n) { return std::fwrite(p, 1, n, f) == n; }
+bool get(FILE* f, void* p, size_t n) { return std::fread(p, 1, n, f) == n; }
+
+template <typename T>
+bool put_dev(FILE* f, const T* d, int64_t n) {
+  std::vector<T> h(n);
+  if (n > 0 && cudaMemcpy(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return false;
+  return put(f, h.data(), sizeof(T) * n);
+}
+template <typename T>
+bool get_dev(FILE* f, T* d, int64_t n) {
+  std::vector<T> h(n);
+  if (!get(f, h.data(), sizeof(T) * n)) return false;
+  return n == 0 || cudaMemcpy(d, h.data(), sizeof(T) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
 dg_status dg_solver_save(const dg_solver* s, const char* path) {
   if (!s || !path) {
     set_error("dg_solver_save: bad argument");
     return DG_EINVAL;
   }
-  std::vector<double> h(s->nu);
   DG_CUDA(cudaStreamSynchronize(s->stream));
-  DG_CUDA(cudaMemcpy(h.data(), s->u_hist, sizeof(double) * s->nu, cudaMemcpyDeviceToHost));
   FILE* f = std::fopen(path, "wb");
   if (!f) {
     set_error(std::string("dg_solver_save: cannot open ") + path);
     return DG_EINVAL;
   }
+  const GuessState& G = s->guess;
   const char magic[8] = {'D', 'G', 'T', 'R', 'B', 'D', 'F', '2'};
-  int64_t hdr[4] = {1, s->nu, s->np, s->has_hist ? 1 : 0};
-  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
-            std::fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
+  int64_t hdr[4] = {2, s->nu, s->np, s->has_hist ? 1 : 0};
+  bool ok = put(f, magic, 8) && put(f, hdr, sizeof(hdr)) && put_dev(f, s->u_hist, s->nu);
+  for (int sl = 0; sl < 4 && ok; ++sl) {
+    int64_t c[2] = {G.count[sl], G.n[sl]};
+    ok = put(f, c, sizeof(c));
+    for (int a = 0; a < G.count[sl] && ok; ++a) ok = put_dev(f, G.hist[sl][a], G.n[sl]);
+  }
+  for (int k = 0; k < 2 && ok; ++k) {
+    const Mlp* n = G.net[k];
+    int64_t d[6] = {n ? 1 : 0, n ? n->n_in : 0, n ? n->hidden : 0, n ? n->n_out : 0,
+                    n ? n->adam_t : 0, n ? n->nparam : 0};
+    ok = put(f, d, sizeof(d));
+    if (n && ok) ok = put_dev(f, n->w, n->nparam) && put_dev(f, n->m1, n->nparam) &&
+                      put_dev(f, n->m2, n->nparam);
+  }
+  int64_t tail[2] = {G.train_steps, 0};
+  ok = ok && put(f, tail, sizeof(tail));
   ok = (std::fclose(f) == 0) && ok;
   if (!ok) {
     set_error("dg_solver_save: write failed");
@@ -427,16 +621,49 @@ dg_status dg_solver_load(dg_solver* s, const char* path) {
   }
   char magic[8];
   int64_t hdr[4];
-  std::vector<double> h(s->nu);
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "DGTRBDF2", 8) == 0 &&
-            std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 1 && hdr[1] == s->nu &&
-            hdr[2] == s->np && std::fread(h.data(), sizeof(double), h.size(), f) == h.size();
+  bool ok = get(f, magic, 8) && std::memcmp(magic, "DGTRBDF2", 8) == 0 && get(f, hdr, sizeof(hdr)) &&
+            hdr[0] == 2 && hdr[1] == s->nu && hdr[2] == s->np && get_dev(f, s->u_hist, s->nu);
+  GuessState& G = s->guess;
+  for (int sl = 0; sl < 4 && ok; ++sl) {
+    int64_t c[2];
+    ok = get(f, c, sizeof(c)) && c[0] >= 0 && c[0] <= 4;
+    if (!ok) break;
+    const SysShape sh = shape_of(s, sl);
+    if (c[0] > 0 && c[1] != sh.n) {
+      ok = false;
+      break;
+    }
+    for (int a = 0; a < 4 && c[0] > 0; ++a)
+      if (!G.hist[sl][a] && cudaMalloc(&G.hist[sl][a], sizeof(double) * sh.n) != cudaSuccess) ok = false;
+    for (int a = 0; a < c[0] && ok; ++a) ok = get_dev(f, G.hist[sl][a], sh.n);
+    G.count[sl] = (int)c[0];
+    G.n[sl] = sh.n;
+  }
+  for (int k = 0; k < 2 && ok; ++k) {
+    int64_t d[6];
+    ok = get(f, d, sizeof(d));
+    if (!ok || !d[0]) continue;
+    if (!G.net[k]) {
+      G.hidden = (int)d[2];
+      G.net[k] = new (std::nothrow) Mlp();
+      ok = G.net[k] && G.net[k]->init((int)d[1], (int)d[2], (int)d[3], 1, s->stream) == DG_OK;
+    }
+    Mlp* n = G.net[k];
+    ok = ok && n->n_in == d[1] && n->hidden == d[2] && n->n_out == d[3] && n->nparam == d[5] &&
+         get_dev(f, n->w, n->nparam) && get_dev(f, n->m1, n->nparam) && get_dev(f, n->m2, n->nparam);
+    if (ok) {
+      n->adam_t = d[4];
+      ok = n->sync_bf16(s->stream) == DG_OK && cudaStreamSynchronize(s->stream) == cudaSuccess;
+    }
+  }
+  int64_t tail[2];
+  ok = ok && get(f, tail, sizeof(tail));
   std::fclose(f);
   if (!ok) {
     set_error("dg_solver_load: not a checkpoint of this mesh");
     return DG_EINVAL;
   }
-  DG_CUDA(cudaMemcpy(s->u_hist, h.data(), sizeof(double) * s->nu, cudaMemcpyHostToDevice));
+  G.train_steps = tail[0];
   s->has_hist = hdr[3] != 0;
   return DG_OK;
 }
