@@ -8,9 +8,12 @@ Jacobi-GMRES, two pressure Helmholtz solves by flexible CG with h/p multigrid,
 RHS assembly, projections and updates) on the workload's state, all inside
 the CUDA library; inputs resident in HBM.  value = (velocity + pressure
 DoFs) advanced per second (GDoF/s); ms_per_step = the time per TR-BDF2 step.
-"mixed" (default): FP32 multigrid inside the FP64 outer Krylov solves;
-"plain": FP64 multigrid.  The other solver's time per step is reported in
-"compare".  Solves stop at a relative residual of 1e-8.
+"mixed+learned" (default): FP32 multigrid inside the FP64 outer Krylov
+solves and the learned initial guess (trained in an untimed phase of
+--train-steps steps before the warm-up, inference only while timed);
+"mixed": the same with the linearly extrapolated guess; "plain": FP64
+multigrid and the extrapolated guess.  The other solvers' times per step are
+reported in "compare".  Solves stop at a relative residual of 1e-8.
 
 Timing: W untimed warm-up steps; K timed steps, each bracketed by CUDA events
 on the launching stream, with a 512 MiB buffer written between steps (L2 is
@@ -126,14 +129,22 @@ def initial_state(w, X, Xp):
     return np.zeros((w.dim, X.shape[1])), np.zeros(Xp.shape[1])
 
 
-def step_params(b, w, precond, tol=1e-8):
+def step_params(b, w, precond, guess, tol=1e-8):
     prm = b.dg_step_params()
     prm.dt, prm.gamma, prm.extrapolate = w.dt, 0.0, 1
     prm.mom = b.solve_opts(b.DG_SYS_MOMENTUM, tol=tol, max_iter=500, restart=30,
-                           precond=b.DG_PC_JACOBI, guess=b.DG_GUESS_EXTRAP)
+                           precond=b.DG_PC_JACOBI, guess=guess)
     prm.helm = b.solve_opts(b.DG_SYS_HELMHOLTZ, tol=tol, max_iter=500, precond=precond,
-                            guess=b.DG_GUESS_EXTRAP)
+                            guess=guess)
     return prm
+
+
+SOLVERS = {
+    # name: (Helmholtz preconditioner, initial guess, learned)
+    "mixed+learned": ("DG_PC_MG_FP32", "DG_GUESS_LEARNED", True),
+    "mixed": ("DG_PC_MG_FP32", "DG_GUESS_EXTRAP", False),
+    "plain": ("DG_PC_MG_FP64", "DG_GUESS_EXTRAP", False),
+}
 
 
 def run_ours(args, rank, world):
@@ -145,6 +156,10 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     w = W.WORKLOADS[args.workload]
     mesh = b.Mesh.from_workload(w)
+    autotune = None
+    if not args.no_autotune:
+        b.dg_autotune(mesh.handle)
+        autotune = json.loads(b.dg_autotune_report(mesh.handle))
     X = mesh.node_coords(0).cpu().numpy()
     Xp = mesh.node_coords(1).cpu().numpy()
     u0h, p0h = initial_state(w, X, Xp)
@@ -152,13 +167,17 @@ def run_ours(args, rank, world):
     p0 = torch.tensor(p0h, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    pc_main = b.DG_PC_MG_FP32 if args.solver == "mixed" else b.DG_PC_MG_FP64
-    pc_other = b.DG_PC_MG_FP64 if args.solver == "mixed" else b.DG_PC_MG_FP32
-
-    def timed_steps(precond, nsteps, nwarm, sample_clocks=False):
+    def timed_steps(name, nsteps, nwarm, sample_clocks=False):
+        pc, guess, learned = SOLVERS[name]
+        pc, guess = getattr(b, pc), getattr(b, guess)
         s = b.dg_solver_create(mesh.handle, w.Re, w.c)
         u, p = u0.clone(), p0.clone()
-        prm = step_params(b, w, precond)
+        prm = step_params(b, w, pc, guess)
+        if learned:  # untimed training phase, then inference only
+            b.dg_guess_configure(s, enable=1, train=1, systems=3, lr=1e-3, seed=1)
+            for _ in range(args.train_steps):
+                b.trbdf2_step(s, prm, u, p)
+            b.dg_guess_configure(s, enable=1, train=0, systems=3, lr=1e-3, seed=1)
         iters = []
         for _ in range(nwarm):
             b.trbdf2_step(s, prm, u, p)
@@ -184,10 +203,10 @@ def run_ours(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
         ms = [a.elapsed_time(c) for a, c in ev]
-        b.dg_solver_destroy(s)
-        return ms, iters, clk.summary(), launches
+        return ms, iters, clk.summary(), launches, (s, prm)
 
-    ms, iters, clocks, launches = timed_steps(pc_main, args.steps, args.warmup, True)
+    ms, iters, clocks, launches, (s_main, prm_main) = timed_steps(args.solver, args.steps,
+                                                                  args.warmup, True)
     total_ms = sum(ms)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -196,11 +215,17 @@ def run_ours(args, rank, world):
     ms_per_step = total_ms / args.steps
     dofs = mesh.n_dofs_u + mesh.n_dofs_p
     value = dofs * world / (ms_per_step * 1e-3) / 1e9
-    ms_o, iters_o, _, _ = timed_steps(pc_other, max(2, args.steps // 2), 3)
+    compare = {}
+    for other in SOLVERS:
+        if other == args.solver:
+            continue
+        ms_o, iters_o, _, _, (s_o, _) = timed_steps(other, max(3, args.steps // 2), 3)
+        b.dg_solver_destroy(s_o)
+        compare[other] = {"ms_per_step": statistics.mean(ms_o),
+                          "iterations_per_step": np.array(iters_o).mean(axis=0).round(2).tolist()}
 
     # ---- end to end through the C ABI with pinned host buffers ----
-    s = b.dg_solver_create(mesh.handle, w.Re, w.c)
-    prm = step_params(b, w, pc_main)
+    s, prm = s_main, prm_main
     hu = u0.cpu().pin_memory()
     hp = p0.cpu().pin_memory()
     u, p = torch.empty_like(u0), torch.empty_like(p0)
@@ -269,13 +294,10 @@ def run_ours(args, rank, world):
             "hbm_frac_poisson_fp32": (8 * mesh.n_dofs_p / (apply_ms["poisson_fp32"] * 1e-3) / 1e9)
                                      / pk["hbm_gbs"]}
     it = np.array(iters)
-    compare = {"solver": "plain" if args.solver == "mixed" else "mixed",
-               "ms_per_step": statistics.mean(ms_o),
-               "iterations_per_step": np.array(iters_o).mean(axis=0).round(2).tolist()}
     return dict(value=value, ms_per_step=ms_per_step, clocks=clocks, e2e=e2e, roofline=roof,
                 gpu_launches=launches,
                 iterations=it.mean(axis=0).round(2).tolist(), compare=compare, apply=apply,
-                dofs=dofs)
+                dofs=dofs, autotune=autotune)
 
 
 # ---------------------------------------------------------------- oracle
@@ -315,10 +337,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv32", choices=sorted(W.WORKLOADS))
-    ap.add_argument("--solver", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--solver", default="mixed+learned", choices=sorted(SOLVERS))
+    ap.add_argument("--train-steps", type=int, default=40,
+                    help="untimed training steps of the learned guess before warm-up")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -359,7 +384,7 @@ def main():
             "data": "synthetic", "config": cfg, "clocks": r["clocks"], "e2e": r["e2e"],
             "gpu_launches": r["gpu_launches"], "iterations_per_step": r["iterations"],
             "compare": r["compare"], "apply": r["apply"], "roofline": r["roofline"],
-            "cpu_baseline": cb}
+            "autotune": r["autotune"], "cpu_baseline": cb}
     print(json.dumps(line))
 
 

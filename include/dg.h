@@ -123,6 +123,18 @@ dg_status dg_apply_poisson(dg_mesh* mesh, double alpha, const double* src, doubl
 dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, float* dst,
                                void* stream);
 
+/* Autotuner (a project addition): times the candidate tile shapes (cells per
+ * CTA) of this mesh's operator kernels -- pressure Helmholtz, momentum with
+ * and without advection, FP64 and FP32 -- with CUDA events on `stream` and
+ * keeps the fastest for later applies; results do not depend on the choice.
+ * Multigrid levels built afterwards from a tuned mesh are tuned too.
+ * Allocates temporary device buffers; synchronous. */
+dg_status dg_autotune(dg_mesh* mesh, void* stream);
+
+/* JSON list of the tuning choices and timings of a mesh ("[]" if untuned),
+ * written to buf (host, size bytes). */
+dg_status dg_autotune_report(const dg_mesh* mesh, char* buf, int64_t size);
+
 /* ---------------------------------------------------------------------
  * Stage right-hand sides and updates (once per stage; Sections 2-3).
  * ------------------------------------------------------------------- */

@@ -86,6 +86,8 @@ SIGNATURES = {
     "dg_apply_momentum_f32": (ctypes.c_int, [c_void_p, P(dg_momentum_coeffs), c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_apply_poisson": (ctypes.c_int, [c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p]),
     "dg_apply_poisson_f32": (ctypes.c_int, [c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p]),
+    "dg_autotune": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_autotune_report": (ctypes.c_int, [c_void_p, ctypes.c_char_p, ctypes.c_int64]),
     "dg_rhs_momentum": (ctypes.c_int, [c_void_p, P(dg_momentum_rhs), c_void_p, c_void_p]),
     "dg_project_gradient": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_rhs_pressure": (ctypes.c_int, [c_void_p, ctypes.c_double, ctypes.c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -195,6 +197,16 @@ def dg_apply_poisson(mesh: int, alpha: float, src, dst, stream=None) -> None:
 def dg_apply_poisson_f32(mesh: int, alpha: float, src, dst, stream=None) -> None:
     check(lib().dg_apply_poisson_f32(mesh, alpha, ptr(src), ptr(dst), stream_ptr(stream)),
           "dg_apply_poisson_f32")
+
+
+def dg_autotune(mesh: int, stream=None) -> None:
+    check(lib().dg_autotune(mesh, stream_ptr(stream)), "dg_autotune")
+
+
+def dg_autotune_report(mesh: int) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(lib().dg_autotune_report(mesh, buf, len(buf)), "dg_autotune_report")
+    return buf.value.decode()
 
 
 def dg_rhs_momentum(mesh: int, desc: dg_momentum_rhs, rhs, stream=None) -> None:

@@ -16,7 +16,11 @@
 // each cell computes the face fluxes of its 2d faces itself (neighbour traces
 // from the neighbour's pencils), so every output is written once, without
 // atomics, and the result is deterministic.
+#include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
 
 #include "dg_common.cuh"
 
@@ -263,10 +267,31 @@ constexpr int default_cpb() {
   return Shape<N, DIM>::NB <= 8 ? 16 : (Shape<N, DIM>::NB <= 27 ? 8 : (Shape<N, DIM>::NB <= 64 ? 4 : 2));
 }
 
+template <typename T, int DIM, int N, bool ADV, int CPB>
+constexpr int smem_bytes() {
+  return (int)sizeof(T) * CPB *
+         (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
+          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4));
+}
+
+// Tile-shape candidates of the autotuner: half, default and double the
+// default cells per CTA, each clamped to the 48 KB static shared-memory and
+// 1024-thread limits.
 template <typename T, int DIM, int N, bool ADV>
-static dg_status launch_fixed(const OpArgs<T>& args, const Tab1D<T>& tb, const T* ub, const T* src,
-                              T* dst, cudaStream_t s) {
-  constexpr int CPB = default_cpb<N, DIM>();
+constexpr int cpb_variant(int v) {
+  int c = v == 0 ? default_cpb<N, DIM>() / 2 : (v == 2 ? default_cpb<N, DIM>() * 2 : default_cpb<N, DIM>());
+  if (c < 1) c = 1;
+  while (c > 1 && (c * Shape<N, DIM>::NB > 1024 ||
+                   (int)sizeof(T) * c * (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
+                                          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4)) >
+                       48 * 1024))
+    c /= 2;
+  return c;
+}
+
+template <typename T, int DIM, int N, bool ADV, int CPB>
+static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<T>& tb, const T* ub, const T* src,
+                            T* dst, cudaStream_t s) {
   constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
   const int64_t blocks = (args.ncell + CPB - 1) / CPB;
   if (blocks > 0x7fffffff) {
@@ -278,15 +303,40 @@ static dg_status launch_fixed(const OpArgs<T>& args, const Tab1D<T>& tb, const T
   return DG_OK;
 }
 
+template <typename T, int DIM, int N, bool ADV>
+static dg_status launch_fixed(int variant, const OpArgs<T>& args, const Tab1D<T>& tb, const T* ub,
+                              const T* src, T* dst, cudaStream_t s) {
+  switch (variant) {
+    case 0: return launch_cpb<T, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(0)>(args, tb, ub, src, dst, s);
+    case 2: return launch_cpb<T, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(2)>(args, tb, ub, src, dst, s);
+    default: return launch_cpb<T, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(1)>(args, tb, ub, src, dst, s);
+  }
+}
+
+template <typename T, int DIM, int N, bool ADV>
+static int cpb_of(int variant) {
+  return cpb_variant<T, DIM, N, ADV>(variant);
+}
+
 template <typename T, int DIM, bool ADV>
-static dg_status launch_dim(int N, const OpArgs<T>& args, const Tab1D<T>& tb, const T* ub,
-                            const T* src, T* dst, cudaStream_t s) {
+static dg_status launch_dim(int variant, int N, const OpArgs<T>& args, const Tab1D<T>& tb,
+                            const T* ub, const T* src, T* dst, cudaStream_t s) {
   switch (N) {
-    case 2: return launch_fixed<T, DIM, 2, ADV>(args, tb, ub, src, dst, s);
-    case 3: return launch_fixed<T, DIM, 3, ADV>(args, tb, ub, src, dst, s);
-    case 4: return launch_fixed<T, DIM, 4, ADV>(args, tb, ub, src, dst, s);
-    case 5: return launch_fixed<T, DIM, 5, ADV>(args, tb, ub, src, dst, s);
+    case 2: return launch_fixed<T, DIM, 2, ADV>(variant, args, tb, ub, src, dst, s);
+    case 3: return launch_fixed<T, DIM, 3, ADV>(variant, args, tb, ub, src, dst, s);
+    case 4: return launch_fixed<T, DIM, 4, ADV>(variant, args, tb, ub, src, dst, s);
+    case 5: return launch_fixed<T, DIM, 5, ADV>(variant, args, tb, ub, src, dst, s);
     default: set_error("operator apply: unsupported number of nodes"); return DG_EUNSUPPORTED;
+  }
+}
+
+template <typename T, int DIM, bool ADV>
+static int cpb_dim(int variant, int N) {
+  switch (N) {
+    case 2: return cpb_of<T, DIM, 2, ADV>(variant);
+    case 3: return cpb_of<T, DIM, 3, ADV>(variant);
+    case 4: return cpb_of<T, DIM, 4, ADV>(variant);
+    default: return cpb_of<T, DIM, 5, ADV>(variant);
   }
 }
 
@@ -333,11 +383,97 @@ dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T ad
   a.ncomp = ncomp;
   const Tab1D<T>& tb = tabs<T>(m, pressure);
   const bool use_adv = !pressure && ubar != nullptr && adv != T(0);
+  const int v = m->tune[sizeof(T) == 8 ? 0 : 1][pressure ? 0 : (use_adv ? 2 : 1)];
   if (m->dim == 2)
-    return use_adv ? launch_dim<T, 2, true>(N, a, tb, ubar, src, dst, s)
-                   : launch_dim<T, 2, false>(N, a, tb, ubar, src, dst, s);
-  return use_adv ? launch_dim<T, 3, true>(N, a, tb, ubar, src, dst, s)
-                 : launch_dim<T, 3, false>(N, a, tb, ubar, src, dst, s);
+    return use_adv ? launch_dim<T, 2, true>(v, N, a, tb, ubar, src, dst, s)
+                   : launch_dim<T, 2, false>(v, N, a, tb, ubar, src, dst, s);
+  return use_adv ? launch_dim<T, 3, true>(v, N, a, tb, ubar, src, dst, s)
+                 : launch_dim<T, 3, false>(v, N, a, tb, ubar, src, dst, s);
+}
+
+// cells per CTA of a tuning variant (reporting)
+template <typename T>
+static int cpb_for_mesh(const dg_mesh* m, bool pressure, bool adv, int v) {
+  const int N = pressure ? m->np : m->nu;
+  if (m->dim == 2) return adv ? cpb_dim<T, 2, true>(v, N) : cpb_dim<T, 2, false>(v, N);
+  return adv ? cpb_dim<T, 3, true>(v, N) : cpb_dim<T, 3, false>(v, N);
+}
+
+// Time every tile-shape variant of the mesh's operator kernels (CUDA events,
+// median of 7 launches after 2 warm-up launches, inputs zero: the kernels'
+// work does not depend on values) and keep the fastest.  Results do not
+// depend on the choice: each output is computed by one thread in a fixed
+// order whatever the number of cells per CTA.
+dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
+  const int64_t nu = m->ncell * m->nbu * m->dim, np = m->ncell * m->nbp;
+  void* buf = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)(3 * nu + 2 * np);
+  DG_CUDA(cudaMalloc(&buf, bytes));
+  DG_CUDA(cudaMemsetAsync(buf, 0, bytes, s));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double* d = static_cast<double*>(buf);
+  std::string rep = "[";
+  dg_status st = DG_OK;
+  const char* opname[3] = {"pressure", "momentum", "momentum+advection"};
+  for (int prec = 0; prec < 2 && st == DG_OK; ++prec) {
+    for (int op = 0; op < 3 && st == DG_OK; ++op) {
+      float best = 1e30f, times[3] = {0, 0, 0};
+      int bestv = 1;
+      for (int v = 0; v < 3 && st == DG_OK; ++v) {
+        m->tune[prec][op] = v;
+        auto run = [&]() -> dg_status {
+          const bool p = op == 0;
+          if (prec == 0)
+            return launch_scalar_op<double>(m, p, 1.0, 1.0, op == 2 ? 0.5 : 0.0, op == 2 ? d : nullptr,
+                                            d + nu, d + 2 * nu, p ? 1 : m->dim, s);
+          float* f = reinterpret_cast<float*>(buf);
+          return launch_scalar_op<float>(m, p, 1.0f, 1.0f, op == 2 ? 0.5f : 0.0f, op == 2 ? f : nullptr,
+                                         f + nu, f + 2 * nu, p ? 1 : m->dim, s);
+        };
+        for (int w = 0; w < 2 && st == DG_OK; ++w) st = run();
+        std::vector<float> ms;
+        for (int r = 0; r < 7 && st == DG_OK; ++r) {
+          cudaEventRecord(e0, s);
+          st = run();
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float t = 0.0f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms.push_back(t);
+        }
+        if (st != DG_OK) break;
+        std::sort(ms.begin(), ms.end());
+        times[v] = ms[ms.size() / 2];
+        if (times[v] < best) {
+          best = times[v];
+          bestv = v;
+        }
+      }
+      m->tune[prec][op] = bestv;
+      char line[256];
+      const bool p = op == 0, adv = op == 2;
+      auto cp = [&](int v) {
+        return prec == 0 ? cpb_for_mesh<double>(m, p, adv, v) : cpb_for_mesh<float>(m, p, adv, v);
+      };
+      std::snprintf(line, sizeof(line),
+                    "%s{\"op\": \"%s\", \"precision\": \"%s\", \"cells_per_cta\": [%d, %d, %d], "
+                    "\"ms\": [%.5f, %.5f, %.5f], \"chosen\": %d}",
+                    rep.size() > 1 ? ", " : "", opname[op], prec == 0 ? "f64" : "f32", cp(0), cp(1),
+                    cp(2), times[0], times[1], times[2], cp(bestv));
+      rep += line;
+    }
+  }
+  rep += "]";
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (st != DG_OK) return st;
+  m->tuned = true;
+  m->tune_report = rep;
+  return DG_OK;
 }
 
 template dg_status launch_scalar_op<double>(const dg_mesh*, bool, double, double, double,
@@ -379,6 +515,28 @@ dg_status dg_apply_poisson(dg_mesh* m, double alpha, const double* src, double* 
   }
   return launch_scalar_op<double>(m, true, alpha, 1.0, 0.0, nullptr, src, dst, 1,
                                   as_stream(stream));
+}
+
+dg_status dg_autotune(dg_mesh* m, void* stream) {
+  if (!m) {
+    set_error("dg_autotune: null mesh");
+    return DG_EINVAL;
+  }
+  return autotune_mesh(m, as_stream(stream));
+}
+
+dg_status dg_autotune_report(const dg_mesh* m, char* buf, int64_t size) {
+  if (!m || !buf || size < 1) {
+    set_error("dg_autotune_report: bad argument");
+    return DG_EINVAL;
+  }
+  const std::string& r = m->tuned ? m->tune_report : std::string("[]");
+  if ((int64_t)r.size() + 1 > size) {
+    set_error("dg_autotune_report: buffer too small");
+    return DG_EINVAL;
+  }
+  std::memcpy(buf, r.c_str(), r.size() + 1);
+  return DG_OK;
 }
 
 dg_status dg_apply_poisson_f32(dg_mesh* m, double alpha, const float* src, float* dst,

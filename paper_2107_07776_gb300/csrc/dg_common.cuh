@@ -66,6 +66,12 @@ struct dg_mesh {
   dg::Tab1D<float> tu32, tp32;
   dg::MixTab<double> mix64;
   int* d_status = nullptr;           // device error word
+  // autotuned tile shape of the operator kernels: variant index per
+  // [precision: 0 FP64, 1 FP32][operator: 0 pressure, 1 momentum, 2 momentum
+  // with advection]; 1 = default cells per CTA, 0 = half, 2 = double
+  int tune[2][3] = {{1, 1, 1}, {1, 1, 1}};
+  bool tuned = false;
+  std::string tune_report;
 };
 
 namespace dg {
@@ -88,6 +94,8 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 dg_status finish_mesh(dg_mesh* m, cudaStream_t s);
 dg_status make_level_mesh(const dg_mesh* fine, const int coarsen[3], int degree_u, cudaStream_t s,
                           dg_mesh** out);
+
+dg_status autotune_mesh(dg_mesh* m, cudaStream_t s);
 
 // launchers (dg_apply.cu)
 template <typename T>

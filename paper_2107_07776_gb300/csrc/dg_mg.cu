@@ -305,6 +305,11 @@ dg_status MultiGrid<T>::build(dg_mesh* fine, cudaStream_t s) {
     for (int a = 0; a < 3; ++a) L.hco[a] = hco[a];
     lv.push_back(L);
   }
+  if (fine->tuned)
+    for (size_t l = 1; l < lv.size(); ++l) {
+      dg_status st = autotune_mesh(lv[l].mesh, s);
+      if (st != DG_OK) return st;
+    }
   int64_t nmax = 0;
   for (auto& L : lv) {
     L.n = L.mesh->ncell * L.mesh->nbp;

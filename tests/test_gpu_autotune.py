@@ -1,0 +1,59 @@
+"""The autotuner: picks one of the candidate tile shapes per operator and
+precision, reports its timings, and never changes results (each output is
+computed by one thread in a fixed order whatever the tile shape)."""
+import json
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("dim,n,k", [(3, (9, 7, 8), 2), (2, (13, 11), 3), (3, (5, 4, 6), 3)])
+def test_autotune_keeps_results_and_reports(dim, n, k):
+    from paper_2107_07776_gb300 import binding as b
+    gm = b.Mesh(dim, n, (0,) * dim, (1.0,) * dim, (True,) + (False,) * (dim - 1), k)
+    xu = torch.tensor(W.random_vector(gm.n_dofs_u, 1), device="cuda")
+    ub = torch.tensor(W.random_vector(gm.n_dofs_u, 2), device="cuda")
+    xp = torch.tensor(W.random_vector(gm.n_dofs_p, 3), device="cuda")
+    co = b.momentum_coeffs(50.0, 0.01, 0.5)
+
+    def apply_all():
+        yu, yp = torch.empty_like(xu), torch.empty_like(xp)
+        b.dg_apply_momentum(gm.handle, co, ub, xu, yu)
+        b.dg_apply_poisson(gm.handle, 1.3, xp, yp)
+        yu32, yp32 = torch.empty_like(xu, dtype=torch.float32), torch.empty_like(xp, dtype=torch.float32)
+        b.dg_apply_momentum_f32(gm.handle, co, ub.float(), xu.float(), yu32)
+        b.dg_apply_poisson_f32(gm.handle, 1.3, xp.float(), yp32)
+        torch.cuda.synchronize()
+        return yu, yp, yu32, yp32
+
+    before = apply_all()
+    assert b.dg_autotune_report(gm.handle) == "[]"
+    b.dg_autotune(gm.handle)
+    rep = json.loads(b.dg_autotune_report(gm.handle))
+    assert len(rep) == 6
+    for r in rep:
+        assert r["chosen"] in r["cells_per_cta"]
+        assert all(t > 0 for t in r["ms"])
+    after = apply_all()
+    for a, c in zip(before, after):
+        assert torch.equal(a, c)
+
+
+def test_multigrid_levels_of_a_tuned_mesh():
+    from paper_2107_07776_gb300 import binding as b
+    gm = b.Mesh(3, (8, 8, 8), (0, 0, 0), (1, 1, 1), (True,) * 3, 2)
+    b.dg_autotune(gm.handle)
+    s = b.dg_solver_create(gm.handle, 100.0, 1e3)
+    try:
+        rhs = torch.tensor(W.random_vector(gm.n_dofs_p, 4), device="cuda")
+        x = torch.zeros_like(rhs)
+        o = b.solve_opts(b.DG_SYS_HELMHOLTZ, tol=1e-10, max_iter=100, precond=b.DG_PC_MG_FP32)
+        info = b.dg_solve_stage(s, None, 2.9, None, rhs, x, o)
+        assert info.iterations < 30
+    finally:
+        b.dg_solver_destroy(s)
