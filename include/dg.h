@@ -106,6 +106,13 @@ typedef struct {
 dg_status dg_apply_momentum(dg_mesh* mesh, const dg_momentum_coeffs* co, const double* ubar,
                             const double* src, double* dst, void* stream);
 
+/* Arithmetic of the FP64 operator applies of this mesh (storage stays FP64):
+ * mode 0 (default) float-float -- every number as the unevaluated sum of two
+ * FP32 values (48-bit significand, FP32 exponent range) computed on the FP32
+ * pipes, which GB300 issues at about 61x its FP64 rate; mode 1 native FP64.
+ * The environment variable DG_FP64_NATIVE=1 sets mode 1 for new meshes. */
+dg_status dg_mesh_set_fp64_arith(dg_mesh* mesh, int32_t mode);
+
 /* FP32 variant of dg_apply_momentum (multigrid smoothing and mixed-precision
  * preconditioning); same layout with float. */
 dg_status dg_apply_momentum_f32(dg_mesh* mesh, const dg_momentum_coeffs* co, const float* ubar,
@@ -298,6 +305,15 @@ dg_status dg_mlp_forward_backward(int64_t M, int32_t n_in, int32_t hidden, int32
 
 /* Set (device pointer, n_dofs_u) or clear (NULL) the stored u^{n-1+gamma}. */
 dg_status dg_solver_set_history(dg_solver* solver, const double* u_hist);
+
+/* Tracing: with on != 0, trbdf2_step records CUDA events on the solver's
+ * stream at its phase boundaries and accumulates the time (ms) spent in
+ * 0 extrapolation and momentum right-hand sides, 1 initial guesses (history,
+ * learned prediction and training), 2 momentum solves, 3 projections,
+ * pressure right-hand sides and velocity updates, 4 Helmholtz solves
+ * (phase_ms[5] stays 0); set_tracing resets the totals. */
+dg_status dg_solver_set_tracing(dg_solver* solver, int32_t on);
+dg_status dg_solver_get_trace(const dg_solver* solver, double phase_ms[6], int64_t* steps);
 
 /* Checkpoint / resume of the solver state (history level, learned-guess
  * weights and optimiser moments) to a host file path. */

@@ -82,6 +82,7 @@ SIGNATURES = {
     "dg_mesh_destroy": (None, [c_void_p]),
     "dg_mesh_info": (ctypes.c_int, [c_void_p, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]),
     "dg_mesh_node_coords": (ctypes.c_int, [c_void_p, ctypes.c_int32, c_void_p, c_void_p]),
+    "dg_mesh_set_fp64_arith": (ctypes.c_int, [c_void_p, ctypes.c_int32]),
     "dg_apply_momentum": (ctypes.c_int, [c_void_p, P(dg_momentum_coeffs), c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_apply_momentum_f32": (ctypes.c_int, [c_void_p, P(dg_momentum_coeffs), c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_apply_poisson": (ctypes.c_int, [c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p]),
@@ -98,6 +99,8 @@ SIGNATURES = {
     "dg_solve_stage": (ctypes.c_int, [c_void_p, P(dg_momentum_coeffs), ctypes.c_double, c_void_p, c_void_p, c_void_p, P(dg_solve_opts), P(dg_solve_info)]),
     "trbdf2_step": (ctypes.c_int, [c_void_p, P(dg_step_params), c_void_p, c_void_p, P(dg_solve_info)]),
     "dg_solver_set_history": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_solver_set_tracing": (ctypes.c_int, [c_void_p, ctypes.c_int32]),
+    "dg_solver_get_trace": (ctypes.c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_int64)]),
     "dg_guess_configure": (ctypes.c_int, [c_void_p, P(dg_guess_opts)]),
     "dg_guess_get_stats": (ctypes.c_int, [c_void_p, P(dg_guess_stats)]),
     "dg_mlp_forward_backward": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_void_p, c_void_p, c_void_p, c_void_p, P(ctypes.c_float), c_void_p, c_void_p]),
@@ -177,6 +180,10 @@ def dg_mesh_info(mesh: int):
 def dg_mesh_node_coords(mesh: int, field: int, xyz, stream=None) -> None:
     check(lib().dg_mesh_node_coords(mesh, field, ptr(xyz), stream_ptr(stream)),
           "dg_mesh_node_coords")
+
+
+def dg_mesh_set_fp64_arith(mesh: int, mode: int) -> None:
+    check(lib().dg_mesh_set_fp64_arith(mesh, mode), "dg_mesh_set_fp64_arith")
 
 
 def dg_apply_momentum(mesh: int, co: dg_momentum_coeffs, ubar, src, dst, stream=None) -> None:
@@ -263,6 +270,21 @@ def trbdf2_step(solver: int, params: dg_step_params, u, p):
 
 def dg_solver_set_history(solver: int, u_hist) -> None:
     check(lib().dg_solver_set_history(solver, ptr(u_hist)), "dg_solver_set_history")
+
+
+def dg_solver_set_tracing(solver: int, on: int) -> None:
+    check(lib().dg_solver_set_tracing(solver, on), "dg_solver_set_tracing")
+
+
+TRACE_PHASES = ("momentum_rhs", "guess", "momentum_solve", "projection_pressure_rhs",
+                "helmholtz_solve", "unused")
+
+
+def dg_solver_get_trace(solver: int):
+    arr = (ctypes.c_double * 6)()
+    steps = ctypes.c_int64()
+    check(lib().dg_solver_get_trace(solver, arr, ctypes.byref(steps)), "dg_solver_get_trace")
+    return dict(zip(TRACE_PHASES, list(arr))), steps.value
 
 
 def dg_guess_configure(solver: int, enable: int = 1, train: int = 1, systems: int = 1,

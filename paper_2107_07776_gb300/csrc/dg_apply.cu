@@ -22,323 +22,21 @@
 #include <string>
 #include <vector>
 
-#include "dg_common.cuh"
+#include "dg_apply_kernel.cuh"
 
 namespace dg {
 
-template <int N, int DIM>
-struct Shape {
-  static constexpr int NB = DIM == 3 ? N * N * N : N * N;   // nodes per cell
-  static constexpr int NF = DIM == 3 ? N * N : N;           // nodes per face
-  static constexpr int NFP = 2 * DIM * NF;                  // face points per cell
-};
-
-template <typename T>
-struct OpArgs {
-  int64_t ncell;
-  int n0, n1, n2;
-  int per0, per1, per2;
-  const T* h0;
-  const T* h1;
-  const T* h2;
-  const T* hi0;  // inverse extents
-  const T* hi1;
-  const T* hi2;
-  T mass, visc, adv, pen;
-  int walls;   // 1: SIP + LF Dirichlet terms on wall faces; 0: none (Neumann)
-  int ncomp;
-};
-
-__device__ __forceinline__ int node_of(int N, int a, int i, int t, int dim) {
-  // node index with coordinate i along axis a and tangential index t
-  int idx[3] = {0, 0, 0};
-  idx[a] = i;
-  for (int b = 0; b < dim; ++b) {
-    if (b == a) continue;
-    idx[b] = t % N;
-    t /= N;
-  }
-  return idx[0] + N * (idx[1] + N * idx[2]);
-}
-
-template <int N, int DIM>
-__device__ __forceinline__ int tang_of(int a, const int i[3]) {
-  // tangential index of node i on the faces normal to axis a
-  int t = 0, mul = 1;
-  for (int b = 0; b < DIM; ++b) {
-    if (b == a) continue;
-    t += i[b] * mul;
-    mul *= N;
-  }
-  return t;
-}
-
-template <typename T, int DIM, int N, bool ADV, int CPB>
-__global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
-    scalar_op_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<T> tb,
-                     const T* __restrict__ src, const T* __restrict__ ub, T* __restrict__ dst) {
-  constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF, NFP = Shape<N, DIM>::NFP;
-  __shared__ T s_u[CPB][NB];
-  __shared__ T s_q[DIM][CPB][NB];
-  __shared__ T s_f[CPB][NFP][2];
-  __shared__ T s_ub[ADV ? DIM : 1][CPB][ADV ? NB : 1];
-  __shared__ T s_un[ADV ? CPB : 1][ADV ? NFP : 1][3];  // ubar.n inside, outside, lambda
-
-  const int tid = threadIdx.x;
-  const int cl = tid / NB, node = tid - (tid / NB) * NB;
-  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
-  const bool active = cl < CPB && cell < a.ncell;
-
-  int ci[3] = {0, 0, 0};
-  T h[3] = {T(1), T(1), T(1)}, hi[3] = {T(1), T(1), T(1)};
-  int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  T W = T(0);
-  if (active) {
-    ci[0] = (int)(cell % a.n0);
-    ci[1] = (int)((cell / a.n0) % a.n1);
-    ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
-    h[0] = a.h0[ci[0]];
-    h[1] = a.h1[ci[1]];
-    hi[0] = a.hi0[ci[0]];
-    hi[1] = a.hi1[ci[1]];
-    if (DIM == 3) {
-      h[2] = a.h2[ci[2]];
-      hi[2] = a.hi2[ci[2]];
-    }
-    W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
-    if (DIM == 3) W *= tb.w[ii[2]] * h[2];
-    if (ADV) {
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) s_ub[b][cl][node] = ub[((int64_t)b * a.ncell + cell) * NB + node];
-    }
-  }
-  const int nn[3] = {a.n0, a.n1, a.n2};
-  const int per[3] = {a.per0, a.per1, a.per2};
-
-  for (int c = 0; c < a.ncomp; ++c) {
-    const T* srcc = src + (int64_t)c * a.ncell * NB;
-    if (active) s_u[cl][node] = srcc[cell * NB + node];
-    __syncthreads();
-    if (active) {
-      // ---- cell integrand at this node: W * (visc grad u - adv u ubar) ----
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        T du = T(0);
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          int j[3] = {ii[0], ii[1], ii[2]};
-          j[b] = m;
-          du += tb.D[ii[b]][m] * s_u[cl][j[0] + N * (j[1] + N * j[2])];
-        }
-        T q = a.visc * du * hi[b];
-        if (ADV) q -= a.adv * s_u[cl][node] * s_ub[b][cl][node];
-        s_q[b][cl][node] = W * q;
-      }
-      // ---- face fluxes at the face points handled by this thread ----
-      for (int fp = node; fp < NFP; fp += NB) {
-        const int f = fp / NF, t = fp - (fp / NF) * NF;
-        const int ax = f >> 1, s = f & 1;
-        const T sgn = s ? T(1) : T(-1);
-        // neighbour across this face
-        int nc[3] = {ci[0], ci[1], ci[2]};
-        nc[ax] += s ? 1 : -1;
-        bool interior = true;
-        if (nc[ax] < 0 || nc[ax] >= nn[ax]) {
-          if (per[ax]) nc[ax] = (nc[ax] + nn[ax]) % nn[ax];
-          else interior = false;
-        }
-        const int64_t nb = (int64_t)nc[0] + (int64_t)a.n0 * (nc[1] + (int64_t)a.n1 * nc[2]);
-        const T* hiax = ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2);
-        const T hiK = hi[ax];
-        // tangential weight: face quadrature weight times the face measure
-        T wt = T(1);
-        {
-          int tt = t;
-#pragma unroll
-          for (int b = 0; b < DIM; ++b) {
-            if (b == ax) continue;
-            wt *= tb.w[tt % N] * h[b];
-            tt /= N;
-          }
-        }
-        T uin = T(0), dnin = T(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          T v = s_u[cl][node_of(N, ax, i, t, DIM)];
-          uin += tb.L[s][i] * v;
-          dnin += tb.dL[s][i] * v;
-        }
-        dnin *= sgn * hiK;
-        T fv = T(0), fg = T(0);
-        if (interior) {
-          const T hiN = hiax[nc[ax]];
-          T uout = T(0), dnout = T(0);
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            T v = __ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]);
-            uout += tb.L[1 - s][i] * v;
-            dnout += tb.dL[1 - s][i] * v;
-          }
-          dnout *= sgn * hiN;
-          const T Cpen = T(0.5) * a.pen * (hiK + hiN);
-          const T jump = uin - uout;
-          fv = a.visc * (T(-0.5) * (dnin + dnout) + Cpen * jump);
-          fg = T(-0.5) * a.visc * jump;
-          if (ADV) {
-            T unin, unout, lam;
-            if (c == 0) {
-              unin = T(0);
-              unout = T(0);
-#pragma unroll
-              for (int i = 0; i < N; ++i) {
-                unin += tb.L[s][i] * s_ub[ax][cl][node_of(N, ax, i, t, DIM)];
-                unout += tb.L[1 - s][i] *
-                         __ldg(&ub[((int64_t)ax * a.ncell + nb) * NB + node_of(N, ax, i, t, DIM)]);
-              }
-              unin *= sgn;
-              unout *= sgn;
-              lam = fmax(fabs(unin), fabs(unout));
-              s_un[cl][fp][0] = unin;
-              s_un[cl][fp][1] = unout;
-              s_un[cl][fp][2] = lam;
-            } else {
-              unin = s_un[cl][fp][0];
-              unout = s_un[cl][fp][1];
-              lam = s_un[cl][fp][2];
-            }
-            fv += a.adv * (T(0.5) * (uin * unin + uout * unout) + T(0.5) * lam * jump);
-          }
-        } else if (a.walls) {
-          const T sig = a.pen * hiK;
-          fv = a.visc * (-dnin + T(2) * sig * uin);
-          fg = -a.visc * uin;
-          if (ADV) {
-            T unin, lam;
-            if (c == 0) {
-              unin = T(0);
-#pragma unroll
-              for (int i = 0; i < N; ++i)
-                unin += tb.L[s][i] * s_ub[ax][cl][node_of(N, ax, i, t, DIM)];
-              unin *= sgn;
-              lam = fabs(unin);
-              s_un[cl][fp][0] = unin;
-              s_un[cl][fp][2] = lam;
-            } else {
-              lam = s_un[cl][fp][2];
-            }
-            fv += a.adv * lam * uin;
-          }
-        }
-        s_f[cl][fp][0] = wt * fv;
-        s_f[cl][fp][1] = wt * fg * sgn * hiK;
-      }
-    }
-    __syncthreads();
-    if (active) {
-      T y = a.mass * W * s_u[cl][node];
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        T acc = T(0);
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          int j[3] = {ii[0], ii[1], ii[2]};
-          j[b] = m;
-          acc += tb.D[m][ii[b]] * s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
-        }
-        y += acc * hi[b];
-      }
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        const int t = tang_of<N, DIM>(b, ii);
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const int fp = (2 * b + s) * NF + t;
-          y += s_f[cl][fp][0] * tb.L[s][ii[b]] + s_f[cl][fp][1] * tb.dL[s][ii[b]];
-        }
-      }
-      dst[(int64_t)c * a.ncell * NB + cell * NB + node] = y;
-    }
-    __syncthreads();
-  }
-}
-
-template <int N, int DIM>
-constexpr int default_cpb() {
-  return Shape<N, DIM>::NB <= 8 ? 16 : (Shape<N, DIM>::NB <= 27 ? 8 : (Shape<N, DIM>::NB <= 64 ? 4 : 2));
-}
-
-template <typename T, int DIM, int N, bool ADV, int CPB>
-constexpr int smem_bytes() {
-  return (int)sizeof(T) * CPB *
-         (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
-          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4));
-}
-
-// Tile-shape candidates of the autotuner: half, default and double the
-// default cells per CTA, each clamped to the 48 KB static shared-memory and
-// 1024-thread limits.
-template <typename T, int DIM, int N, bool ADV>
-constexpr int cpb_variant(int v) {
-  int c = v == 0 ? default_cpb<N, DIM>() / 2 : (v == 2 ? default_cpb<N, DIM>() * 2 : default_cpb<N, DIM>());
-  if (c < 1) c = 1;
-  while (c > 1 && (c * Shape<N, DIM>::NB > 1024 ||
-                   (int)sizeof(T) * c * (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
-                                          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4)) >
-                       48 * 1024))
-    c /= 2;
-  return c;
-}
-
-template <typename T, int DIM, int N, bool ADV, int CPB>
-static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<T>& tb, const T* ub, const T* src,
-                            T* dst, cudaStream_t s) {
-  constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
-  const int64_t blocks = (args.ncell + CPB - 1) / CPB;
-  if (blocks > 0x7fffffff) {
-    set_error("operator apply: grid too large");
-    return DG_EINVAL;
-  }
-  scalar_op_kernel<T, DIM, N, ADV, CPB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst); count_launch();
-  DG_CUDA(cudaGetLastError());
-  return DG_OK;
-}
-
-template <typename T, int DIM, int N, bool ADV>
-static dg_status launch_fixed(int variant, const OpArgs<T>& args, const Tab1D<T>& tb, const T* ub,
-                              const T* src, T* dst, cudaStream_t s) {
-  switch (variant) {
-    case 0: return launch_cpb<T, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(0)>(args, tb, ub, src, dst, s);
-    case 2: return launch_cpb<T, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(2)>(args, tb, ub, src, dst, s);
-    default: return launch_cpb<T, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(1)>(args, tb, ub, src, dst, s);
-  }
-}
-
-template <typename T, int DIM, int N, bool ADV>
-static int cpb_of(int variant) {
-  return cpb_variant<T, DIM, N, ADV>(variant);
-}
-
-template <typename T, int DIM, bool ADV>
-static dg_status launch_dim(int variant, int N, const OpArgs<T>& args, const Tab1D<T>& tb,
-                            const T* ub, const T* src, T* dst, cudaStream_t s) {
-  switch (N) {
-    case 2: return launch_fixed<T, DIM, 2, ADV>(variant, args, tb, ub, src, dst, s);
-    case 3: return launch_fixed<T, DIM, 3, ADV>(variant, args, tb, ub, src, dst, s);
-    case 4: return launch_fixed<T, DIM, 4, ADV>(variant, args, tb, ub, src, dst, s);
-    case 5: return launch_fixed<T, DIM, 5, ADV>(variant, args, tb, ub, src, dst, s);
-    default: set_error("operator apply: unsupported number of nodes"); return DG_EUNSUPPORTED;
-  }
-}
-
-template <typename T, int DIM, bool ADV>
-static int cpb_dim(int variant, int N) {
-  switch (N) {
-    case 2: return cpb_of<T, DIM, 2, ADV>(variant);
-    case 3: return cpb_of<T, DIM, 3, ADV>(variant);
-    case 4: return cpb_of<T, DIM, 4, ADV>(variant);
-    default: return cpb_of<T, DIM, 5, ADV>(variant);
-  }
-}
+// instantiation units (dg_apply_inst_*.cu)
+#define DG_DECL_LAUNCH(NAME, T, A)                                                        \
+  dg_status NAME(int variant, int N, bool adv, const OpArgs<T>& a, const Tab1D<A>& tb, \
+                 const T* ub, const T* src, T* dst, cudaStream_t s);
+DG_DECL_LAUNCH(launch_f64_2d, double, double)
+DG_DECL_LAUNCH(launch_f64_3d, double, double)
+DG_DECL_LAUNCH(launch_df_2d, double, df64)
+DG_DECL_LAUNCH(launch_df_3d, double, df64)
+DG_DECL_LAUNCH(launch_f32_2d, float, float)
+DG_DECL_LAUNCH(launch_f32_3d, float, float)
+#undef DG_DECL_LAUNCH
 
 template <typename T>
 const T* axis_h(const dg_mesh* m, int a, bool inv);
@@ -353,9 +51,62 @@ const Tab1D<double>& tabs<double>(const dg_mesh* m, bool p) { return p ? m->tp64
 template <>
 const Tab1D<float>& tabs<float>(const dg_mesh* m, bool p) { return p ? m->tp32 : m->tu32; }
 
+static dg_status dispatch(const dg_mesh* m, bool pressure, int v, int N, bool adv,
+                          const OpArgs<double>& a, const double* ub, const double* src, double* dst,
+                          cudaStream_t s) {
+  if (m->fp64_arith == 0) {  // FP64-accurate arithmetic as float-float on the FP32 pipes
+    const Tab1D<df64>& tb = pressure ? m->tpdf : m->tudf;
+    return m->dim == 2 ? launch_df_2d(v, N, adv, a, tb, ub, src, dst, s)
+                       : launch_df_3d(v, N, adv, a, tb, ub, src, dst, s);
+  }
+  const Tab1D<double>& tb = pressure ? m->tp64 : m->tu64;
+  return m->dim == 2 ? launch_f64_2d(v, N, adv, a, tb, ub, src, dst, s)
+                     : launch_f64_3d(v, N, adv, a, tb, ub, src, dst, s);
+}
+
+static dg_status dispatch(const dg_mesh* m, bool pressure, int v, int N, bool adv,
+                          const OpArgs<float>& a, const float* ub, const float* src, float* dst,
+                          cudaStream_t s) {
+  const Tab1D<float>& tb = pressure ? m->tp32 : m->tu32;
+  return m->dim == 2 ? launch_f32_2d(v, N, adv, a, tb, ub, src, dst, s)
+                     : launch_f32_3d(v, N, adv, a, tb, ub, src, dst, s);
+}
+
+template <typename T>
+static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
+                                       const T* ubar, const T* src, T* dst, int ncomp,
+                                       const OpArgs<T>* cheb, cudaStream_t s);
+
 template <typename T>
 dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T adv, const T* ubar,
                            const T* src, T* dst, int ncomp, cudaStream_t s) {
+  return launch_scalar_op_impl<T>(m, pressure, mass, visc, adv, ubar, src, dst, ncomp, nullptr, s);
+}
+
+// dst = c1 src + c2 r after x += src, r -= dinv (alpha M^p + K) src
+template <typename T>
+dg_status launch_poisson_cheb(const dg_mesh* m, double alpha, const T* src, T* dst, T* x, T* r,
+                              const T* dinv, double c1, double c2, cudaStream_t s) {
+  OpArgs<T> ch;
+  std::memset(&ch, 0, sizeof(ch));
+  ch.cheb = 1;
+  ch.cx = x;
+  ch.cr = r;
+  ch.cdinv = dinv;
+  ch.cc1 = (T)c1;
+  ch.cc2 = (T)c2;
+  return launch_scalar_op_impl<T>(m, true, (T)alpha, T(1), T(0), nullptr, src, dst, 1, &ch, s);
+}
+template dg_status launch_poisson_cheb<float>(const dg_mesh*, double, const float*, float*, float*,
+                                              float*, const float*, double, double, cudaStream_t);
+template dg_status launch_poisson_cheb<double>(const dg_mesh*, double, const double*, double*,
+                                               double*, double*, const double*, double, double,
+                                               cudaStream_t);
+
+template <typename T>
+static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
+                                       const T* ubar, const T* src, T* dst, int ncomp,
+                                       const OpArgs<T>* cheb, cudaStream_t s) {
   if (!m->affine) {
     set_error("operator apply: trilinear (perturbed) cells are not built in this library");
     return DG_EUNSUPPORTED;
@@ -381,14 +132,21 @@ dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T ad
   a.pen = (T)(N * N);  // (k+1)^2 for velocity, k^2 for pressure
   a.walls = pressure ? 0 : 1;
   a.ncomp = ncomp;
-  const Tab1D<T>& tb = tabs<T>(m, pressure);
+  a.cheb = 0;
+  a.cx = a.cr = nullptr;
+  a.cdinv = nullptr;
+  a.cc1 = a.cc2 = T(0);
+  if (cheb) {
+    a.cheb = 1;
+    a.cx = cheb->cx;
+    a.cr = cheb->cr;
+    a.cdinv = cheb->cdinv;
+    a.cc1 = cheb->cc1;
+    a.cc2 = cheb->cc2;
+  }
   const bool use_adv = !pressure && ubar != nullptr && adv != T(0);
   const int v = m->tune[sizeof(T) == 8 ? 0 : 1][pressure ? 0 : (use_adv ? 2 : 1)];
-  if (m->dim == 2)
-    return use_adv ? launch_dim<T, 2, true>(v, N, a, tb, ubar, src, dst, s)
-                   : launch_dim<T, 2, false>(v, N, a, tb, ubar, src, dst, s);
-  return use_adv ? launch_dim<T, 3, true>(v, N, a, tb, ubar, src, dst, s)
-                 : launch_dim<T, 3, false>(v, N, a, tb, ubar, src, dst, s);
+  return dispatch(m, pressure, v, N, use_adv, a, ubar, src, dst, s);
 }
 
 // cells per CTA of a tuning variant (reporting)

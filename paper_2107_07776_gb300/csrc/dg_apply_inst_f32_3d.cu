@@ -1,0 +1,12 @@
+// Instantiation unit of the operator kernel: FP32 storage and arithmetic, 3D.
+#include "dg_apply_kernel.cuh"
+
+namespace dg {
+
+dg_status launch_f32_3d(int variant, int N, bool adv, const OpArgs<float>& a, const Tab1D<float>& tb,
+               const float* ub, const float* src, float* dst, cudaStream_t s) {
+  return adv ? launch_dim<float, float, 3, true>(variant, N, a, tb, ub, src, dst, s)
+             : launch_dim<float, float, 3, false>(variant, N, a, tb, ub, src, dst, s);
+}
+
+}  // namespace dg

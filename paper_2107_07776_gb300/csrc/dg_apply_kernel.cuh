@@ -1,0 +1,349 @@
+// Operator kernel of the matrix-free DG applies (templates); instantiated in
+// dg_apply_inst_*.cu, dispatched from dg_apply.cu.
+#pragma once
+
+#include <cstdio>
+
+#include "dg_common.cuh"
+#include "dg_df64.cuh"
+
+namespace dg {
+
+template <int N, int DIM>
+struct Shape {
+  static constexpr int NB = DIM == 3 ? N * N * N : N * N;   // nodes per cell
+  static constexpr int NF = DIM == 3 ? N * N : N;           // nodes per face
+  static constexpr int NFP = 2 * DIM * NF;                  // face points per cell
+};
+
+template <typename T>
+struct OpArgs {
+  int64_t ncell;
+  int n0, n1, n2;
+  int per0, per1, per2;
+  const T* h0;
+  const T* h1;
+  const T* h2;
+  const T* hi0;  // inverse extents
+  const T* hi1;
+  const T* hi2;
+  T mass, visc, adv, pen;
+  int walls;   // 1: SIP + LF Dirichlet terms on wall faces; 0: none (Neumann)
+  int ncomp;
+  // fused Chebyshev update (multigrid smoothing, one component): with
+  // y = A src, x += src; r -= dinv y; dst = c1 src + c2 r
+  int cheb;
+  T* cx;
+  T* cr;
+  const T* cdinv;
+  T cc1, cc2;
+};
+
+__device__ __forceinline__ int node_of(int N, int a, int i, int t, int dim) {
+  // node index with coordinate i along axis a and tangential index t
+  int idx[3] = {0, 0, 0};
+  idx[a] = i;
+  for (int b = 0; b < dim; ++b) {
+    if (b == a) continue;
+    idx[b] = t % N;
+    t /= N;
+  }
+  return idx[0] + N * (idx[1] + N * idx[2]);
+}
+
+template <int N, int DIM>
+__device__ __forceinline__ int tang_of(int a, const int i[3]) {
+  // tangential index of node i on the faces normal to axis a
+  int t = 0, mul = 1;
+  for (int b = 0; b < DIM; ++b) {
+    if (b == a) continue;
+    t += i[b] * mul;
+    mul *= N;
+  }
+  return t;
+}
+
+// T: storage type of the vectors (double or float); A: arithmetic type
+// (double, float, or df64 = float-float on the FP32 pipes).
+template <typename T, typename A, int DIM, int N, bool ADV, int CPB>
+__global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
+    scalar_op_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
+                     const T* __restrict__ src, const T* __restrict__ ub, T* __restrict__ dst) {
+  using Ar = Arith<A>;
+  constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF, NFP = Shape<N, DIM>::NFP;
+  __shared__ A s_u[CPB][NB];
+  __shared__ A s_q[DIM][CPB][NB];
+  __shared__ A s_f[CPB][NFP][2];
+  __shared__ A s_ub[ADV ? DIM : 1][CPB][ADV ? NB : 1];
+  __shared__ A s_un[ADV ? CPB : 1][ADV ? NFP : 1][3];  // ubar.n inside, outside, lambda
+
+  const int tid = threadIdx.x;
+  const int cl = tid / NB, node = tid - (tid / NB) * NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < a.ncell;
+  const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
+  const A mass = Ar::from(a.mass), visc = Ar::from(a.visc), advc = Ar::from(a.adv),
+          pen = Ar::from(a.pen);
+
+  int ci[3] = {0, 0, 0};
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
+  int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  A W = zero;
+  if (active) {
+    ci[0] = (int)(cell % a.n0);
+    ci[1] = (int)((cell / a.n0) % a.n1);
+    ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
+    h[0] = Ar::from(a.h0[ci[0]]);
+    h[1] = Ar::from(a.h1[ci[1]]);
+    hi[0] = Ar::from(a.hi0[ci[0]]);
+    hi[1] = Ar::from(a.hi1[ci[1]]);
+    if (DIM == 3) {
+      h[2] = Ar::from(a.h2[ci[2]]);
+      hi[2] = Ar::from(a.hi2[ci[2]]);
+    }
+    W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
+    if (DIM == 3) W = W * tb.w[ii[2]] * h[2];
+    if (ADV) {
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) s_ub[b][cl][node] = Ar::from(ub[((int64_t)b * a.ncell + cell) * NB + node]);
+    }
+  }
+  const int nn[3] = {a.n0, a.n1, a.n2};
+  const int per[3] = {a.per0, a.per1, a.per2};
+
+  for (int c = 0; c < a.ncomp; ++c) {
+    const T* srcc = src + (int64_t)c * a.ncell * NB;
+    if (active) s_u[cl][node] = Ar::from(srcc[cell * NB + node]);
+    __syncthreads();
+    if (active) {
+      // ---- cell integrand at this node: W * (visc grad u - adv u ubar) ----
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A du = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          du += tb.D[ii[b]][m] * s_u[cl][j[0] + N * (j[1] + N * j[2])];
+        }
+        A q = visc * du * hi[b];
+        if (ADV) q -= advc * s_u[cl][node] * s_ub[b][cl][node];
+        s_q[b][cl][node] = W * q;
+      }
+      // ---- face fluxes at the face points handled by this thread ----
+      for (int fp = node; fp < NFP; fp += NB) {
+        const int f = fp / NF, t = fp - (fp / NF) * NF;
+        const int ax = f >> 1, s = f & 1;
+        const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
+        // neighbour across this face
+        int nc[3] = {ci[0], ci[1], ci[2]};
+        nc[ax] += s ? 1 : -1;
+        bool interior = true;
+        if (nc[ax] < 0 || nc[ax] >= nn[ax]) {
+          if (per[ax]) nc[ax] = (nc[ax] + nn[ax]) % nn[ax];
+          else interior = false;
+        }
+        const int64_t nb = (int64_t)nc[0] + (int64_t)a.n0 * (nc[1] + (int64_t)a.n1 * nc[2]);
+        const T* hiax = ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2);
+        const A hiK = hi[ax];
+        // tangential weight: face quadrature weight times the face measure
+        A wt = Ar::c(1.0);
+        {
+          int tt = t;
+#pragma unroll
+          for (int b = 0; b < DIM; ++b) {
+            if (b == ax) continue;
+            wt = wt * tb.w[tt % N] * h[b];
+            tt /= N;
+          }
+        }
+        A uin = zero, dnin = zero;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const A v = s_u[cl][node_of(N, ax, i, t, DIM)];
+          uin += tb.L[s][i] * v;
+          dnin += tb.dL[s][i] * v;
+        }
+        dnin = dnin * sgn * hiK;
+        A fv = zero, fg = zero;
+        if (interior) {
+          const A hiN = Ar::from(hiax[nc[ax]]);
+          A uout = zero, dnout = zero;
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            const A v = Ar::from(__ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]));
+            uout += tb.L[1 - s][i] * v;
+            dnout += tb.dL[1 - s][i] * v;
+          }
+          dnout = dnout * sgn * hiN;
+          const A Cpen = half * pen * (hiK + hiN);
+          const A jump = uin - uout;
+          fv = visc * (Cpen * jump - half * (dnin + dnout));
+          fg = -(half * visc * jump);
+          if (ADV) {
+            A unin, unout, lam;
+            if (c == 0) {
+              unin = zero;
+              unout = zero;
+#pragma unroll
+              for (int i = 0; i < N; ++i) {
+                unin += tb.L[s][i] * s_ub[ax][cl][node_of(N, ax, i, t, DIM)];
+                unout += tb.L[1 - s][i] *
+                         Ar::from(__ldg(&ub[((int64_t)ax * a.ncell + nb) * NB + node_of(N, ax, i, t, DIM)]));
+              }
+              unin = unin * sgn;
+              unout = unout * sgn;
+              lam = Ar::max(Ar::abs(unin), Ar::abs(unout));
+              s_un[cl][fp][0] = unin;
+              s_un[cl][fp][1] = unout;
+              s_un[cl][fp][2] = lam;
+            } else {
+              unin = s_un[cl][fp][0];
+              unout = s_un[cl][fp][1];
+              lam = s_un[cl][fp][2];
+            }
+            fv += advc * (half * (uin * unin + uout * unout) + half * lam * jump);
+          }
+        } else if (a.walls) {
+          const A sig = pen * hiK;
+          fv = visc * (two * sig * uin - dnin);
+          fg = -(visc * uin);
+          if (ADV) {
+            A unin, lam;
+            if (c == 0) {
+              unin = zero;
+#pragma unroll
+              for (int i = 0; i < N; ++i)
+                unin += tb.L[s][i] * s_ub[ax][cl][node_of(N, ax, i, t, DIM)];
+              unin = unin * sgn;
+              lam = Ar::abs(unin);
+              s_un[cl][fp][0] = unin;
+              s_un[cl][fp][2] = lam;
+            } else {
+              lam = s_un[cl][fp][2];
+            }
+            fv += advc * lam * uin;
+          }
+        }
+        s_f[cl][fp][0] = wt * fv;
+        s_f[cl][fp][1] = wt * fg * sgn * hiK;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      A y = mass * W * s_u[cl][node];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A acc = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          acc += tb.D[m][ii[b]] * s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
+        }
+        y += acc * hi[b];
+      }
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        const int t = tang_of<N, DIM>(b, ii);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int fp = (2 * b + s) * NF + t;
+          y += s_f[cl][fp][0] * tb.L[s][ii[b]] + s_f[cl][fp][1] * tb.dL[s][ii[b]];
+        }
+      }
+      const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
+      const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
+      if (a.cheb) {
+        const T dk = srcc[cell * NB + node];
+        a.cx[o] += dk;
+        const T rk = a.cr[o] - a.cdinv[o] * yt;
+        a.cr[o] = rk;
+        dst[o] = a.cc1 * dk + a.cc2 * rk;
+      } else {
+        dst[o] = yt;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int N, int DIM>
+constexpr int default_cpb() {
+  return Shape<N, DIM>::NB <= 8 ? 16 : (Shape<N, DIM>::NB <= 27 ? 8 : (Shape<N, DIM>::NB <= 64 ? 4 : 2));
+}
+
+template <typename T, int DIM, int N, bool ADV, int CPB>
+constexpr int smem_bytes() {
+  return (int)sizeof(T) * CPB *
+         (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
+          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4));
+}
+
+// Tile-shape candidates of the autotuner: half, default and double the
+// default cells per CTA, each clamped to the 48 KB static shared-memory and
+// 1024-thread limits.
+template <typename T, int DIM, int N, bool ADV>
+constexpr int cpb_variant(int v) {
+  int c = v == 0 ? default_cpb<N, DIM>() / 2 : (v == 2 ? default_cpb<N, DIM>() * 2 : default_cpb<N, DIM>());
+  if (c < 1) c = 1;
+  while (c > 1 && (c * Shape<N, DIM>::NB > 1024 ||
+                   (int)sizeof(T) * c * (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
+                                          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4)) >
+                       48 * 1024))
+    c /= 2;
+  return c;
+}
+
+template <typename T, typename A, int DIM, int N, bool ADV, int CPB>
+static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
+                            T* dst, cudaStream_t s) {
+  constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
+  const int64_t blocks = (args.ncell + CPB - 1) / CPB;
+  if (blocks > 0x7fffffff) {
+    set_error("operator apply: grid too large");
+    return DG_EINVAL;
+  }
+  scalar_op_kernel<T, A, DIM, N, ADV, CPB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst); count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <typename T, typename A, int DIM, int N, bool ADV>
+static dg_status launch_fixed(int variant, const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub,
+                              const T* src, T* dst, cudaStream_t s) {
+  switch (variant) {
+    case 0: return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(0)>(args, tb, ub, src, dst, s);
+    case 2: return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(2)>(args, tb, ub, src, dst, s);
+    default: return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(1)>(args, tb, ub, src, dst, s);
+  }
+}
+
+template <typename T, int DIM, int N, bool ADV>
+static int cpb_of(int variant) {
+  return cpb_variant<T, DIM, N, ADV>(variant);
+}
+
+template <typename T, typename A, int DIM, bool ADV>
+static dg_status launch_dim(int variant, int N, const OpArgs<T>& args, const Tab1D<A>& tb,
+                            const T* ub, const T* src, T* dst, cudaStream_t s) {
+  switch (N) {
+    case 2: return launch_fixed<T, A, DIM, 2, ADV>(variant, args, tb, ub, src, dst, s);
+    case 3: return launch_fixed<T, A, DIM, 3, ADV>(variant, args, tb, ub, src, dst, s);
+    case 4: return launch_fixed<T, A, DIM, 4, ADV>(variant, args, tb, ub, src, dst, s);
+    case 5: return launch_fixed<T, A, DIM, 5, ADV>(variant, args, tb, ub, src, dst, s);
+    default: set_error("operator apply: unsupported number of nodes"); return DG_EUNSUPPORTED;
+  }
+}
+
+template <typename T, int DIM, bool ADV>
+static int cpb_dim(int variant, int N) {
+  switch (N) {
+    case 2: return cpb_of<T, DIM, 2, ADV>(variant);
+    case 3: return cpb_of<T, DIM, 3, ADV>(variant);
+    case 4: return cpb_of<T, DIM, 4, ADV>(variant);
+    default: return cpb_of<T, DIM, 5, ADV>(variant);
+  }
+}
+
+}  // namespace dg

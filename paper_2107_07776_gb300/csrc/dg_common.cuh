@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/dg.h"
+#include "dg_df64.cuh"
 
 namespace dg {
 
@@ -37,6 +38,7 @@ void make_tables(int n, Tab1D<double>* t);
 void make_mix(const Tab1D<double>& tu, int nu, const Tab1D<double>& tp, int np, MixTab<double>* m);
 template <typename T>
 Tab1D<T> cast_tables(const Tab1D<double>& t);
+Tab1D<df64> split_tables(const Tab1D<double>& t);
 
 // Cell geometry of the affine paths: per-axis cell extents (the Jacobian is
 // diagonal, diag(h0, h1, h2), on Cartesian and tensor-graded meshes).
@@ -65,6 +67,8 @@ struct dg_mesh {
   dg::Tab1D<double> tu64, tp64;      // velocity / pressure tables
   dg::Tab1D<float> tu32, tp32;
   dg::MixTab<double> mix64;
+  dg::Tab1D<dg::df64> tudf, tpdf;    // float-float copies of the FP64 tables
+  int fp64_arith = 0;                // FP64 operator arithmetic: 0 float-float, 1 native FP64
   int* d_status = nullptr;           // device error word
   // autotuned tile shape of the operator kernels: variant index per
   // [precision: 0 FP64, 1 FP32][operator: 0 pressure, 1 momentum, 2 momentum
@@ -101,5 +105,9 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s);
 template <typename T>
 dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
                            const T* ubar, const T* src, T* dst, int ncomp, cudaStream_t s);
+// fused Chebyshev smoothing step on a pressure-space level (see dg_mg.cu)
+template <typename T>
+dg_status launch_poisson_cheb(const dg_mesh* m, double alpha, const T* src, T* dst, T* x, T* r,
+                              const T* dinv, double c1, double c2, cudaStream_t s);
 
 }  // namespace dg

@@ -1,0 +1,114 @@
+// Float-float ("double-float") arithmetic for the FP64-accurate operator
+// kernels on GB300, whose FP32 pipes issue about 61 times the FP64 rate.
+//
+// A value is the unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi)/2, a 48-bit significand within FP32's exponent range.  The
+// operations are the error-free transformations of Knuth (TwoSum, The Art of
+// Computer Programming vol. 2, 4.2.2) and Dekker (FastTwoSum; "A
+// floating-point technique for extending the available precision", Numer.
+// Math. 18, 1971), with the exact product error from one fused multiply-add.
+// Every step uses explicitly rounded intrinsics so the compiler cannot
+// contract or reorder them.  Relative error of one operation is a few units
+// of 2^-48; the kernels that use it keep FP64 storage and convert at loads
+// and stores.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dg {
+
+struct df64 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// requires |a| >= |b| or a == 0
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df64 df_add(df64 a, df64 b) {
+  df64 s = df_two_sum(a.hi, b.hi);
+  const df64 t = df_two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = df_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df64 df_neg(df64 a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) { return df_add(a, b); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df64 operator-(df64 a) { return df_neg(a); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) { return df_mul(a, b); }
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = df_add(a, b); }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = df_add(a, df_neg(b)); }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = df_mul(a, b); }
+
+__device__ __forceinline__ df64 df_abs(df64 a) { return a.hi < 0.0f ? df_neg(a) : a; }
+__device__ __forceinline__ bool df_less(df64 a, df64 b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ df64 df_max(df64 a, df64 b) { return df_less(a, b) ? b : a; }
+
+__device__ __forceinline__ df64 df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// Arithmetic-type adapters for kernels templated on the arithmetic type A
+// (float, double or df64) and the storage type T (float or double).
+template <typename A>
+struct Arith;
+
+template <>
+struct Arith<float> {
+  __device__ static float from(double x) { return (float)x; }
+  __device__ static float from(float x) { return x; }
+  __device__ static float c(double x) { return (float)x; }
+  __device__ static float abs(float x) { return fabsf(x); }
+  __device__ static float max(float a, float b) { return fmaxf(a, b); }
+  __device__ static float to_f(float x) { return x; }
+  __device__ static double to_d(float x) { return (double)x; }
+};
+
+template <>
+struct Arith<double> {
+  __device__ static double from(double x) { return x; }
+  __device__ static double from(float x) { return (double)x; }
+  __device__ static double c(double x) { return x; }
+  __device__ static double abs(double x) { return fabs(x); }
+  __device__ static double max(double a, double b) { return fmax(a, b); }
+  __device__ static float to_f(double x) { return (float)x; }
+  __device__ static double to_d(double x) { return x; }
+};
+
+template <>
+struct Arith<df64> {
+  __device__ static df64 from(double x) { return df_from(x); }
+  __device__ static df64 from(float x) { return {x, 0.0f}; }
+  __device__ static df64 c(double x) { return df_from(x); }
+  __device__ static df64 abs(df64 x) { return df_abs(x); }
+  __device__ static df64 max(df64 a, df64 b) { return df_max(a, b); }
+  __device__ static float to_f(df64 x) { return x.hi; }
+  __device__ static double to_d(df64 x) { return df_to(x); }
+};
+
+}  // namespace dg

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -154,6 +155,25 @@ Tab1D<T> cast_tables(const Tab1D<double>& t) {
   return o;
 }
 template Tab1D<float> cast_tables<float>(const Tab1D<double>&);
+
+// float-float split of every table entry: hi = fl32(x), lo = fl32(x - hi)
+Tab1D<df64> split_tables(const Tab1D<double>& t) {
+  Tab1D<df64> o;
+  auto sp = [](double x) {
+    const float h = (float)x;
+    return df64{h, (float)(x - (double)h)};
+  };
+  for (int a = 0; a < kMaxN; ++a) {
+    for (int b = 0; b < kMaxN; ++b) o.D[a][b] = sp(t.D[a][b]);
+    o.w[a] = sp(t.w[a]);
+    o.x[a] = sp(t.x[a]);
+    for (int s = 0; s < 2; ++s) {
+      o.L[s][a] = sp(t.L[s][a]);
+      o.dL[s][a] = sp(t.dL[s][a]);
+    }
+  }
+  return o;
+}
 template Tab1D<double> cast_tables<double>(const Tab1D<double>&);
 
 // Vertex of the structured lattice (lattice index L) under the mesh map.
@@ -194,6 +214,12 @@ dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
   make_mix(m->tu64, m->nu, m->tp64, m->np, &m->mix64);
   m->tu32 = cast_tables<float>(m->tu64);
   m->tp32 = cast_tables<float>(m->tp64);
+  m->tudf = split_tables(m->tu64);
+  m->tpdf = split_tables(m->tp64);
+  {
+    const char* env = std::getenv("DG_FP64_NATIVE");
+    m->fp64_arith = env && env[0] == '1' ? 1 : 0;
+  }
   for (int a = 0; a < 3; ++a) {
     int na = m->n[a];
     std::vector<double> h(na), hi(na);
@@ -280,6 +306,15 @@ const char* dg_status_string(dg_status s) {
 const char* dg_last_error(void) { return g_last_error.c_str(); }
 
 int64_t dg_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
+
+dg_status dg_mesh_set_fp64_arith(dg_mesh* m, int32_t mode) {
+  if (!m || (mode != 0 && mode != 1)) {
+    set_error("dg_mesh_set_fp64_arith: mode must be 0 (float-float) or 1 (native FP64)");
+    return DG_EINVAL;
+  }
+  m->fp64_arith = mode;
+  return DG_OK;
+}
 
 dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) {
   if (!desc || !out) {

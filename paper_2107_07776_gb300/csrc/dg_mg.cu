@@ -11,8 +11,10 @@
 //            subspace), restriction is its transpose;
 //   smoother Chebyshev iteration of degree 4 on D^-1 A over
 //            [lambda_max/20, 1.1 lambda_max], lambda_max from 15 Lanczos
-//            (Jacobi-CG) steps; the coarsest level runs a degree-30 Chebyshev
-//            over its full Lanczos spectrum estimate;
+//            (Jacobi-CG) steps, each step after the first one fused launch;
+//   coarse   the coarsest level (at most 2048 DoFs) is solved exactly by a
+//            dense inverse built once per alpha from applies to unit vectors
+//            (else a degree-30 Chebyshev over its Lanczos spectrum estimate);
 //   cycle    one V-cycle (pre- and post-smoothing) per outer CG iteration.
 // T = float gives the mixed-precision preconditioner (all level vectors and
 // applies in FP32 inside the FP64 flexible CG), T = double the FP64 one.
@@ -25,6 +27,9 @@
 #include "dg_mg.cuh"
 
 namespace dg {
+
+// coarsest levels up to this many DoFs are solved exactly by a dense inverse
+constexpr int64_t kCoarseDenseMax = 2048;
 
 namespace {
 
@@ -101,6 +106,28 @@ __global__ void sub_kernel(int64_t n, const T* __restrict__ b, const T* __restri
        k += (int64_t)gridDim.x * blockDim.x)
     r[k] = b[k] - t[k];
 }
+// I = identity (n x n)
+template <typename T>
+__global__ void identity_kernel(int64_t n, T* __restrict__ I) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n * n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    I[k] = (k / n == k % n) ? T(1) : T(0);
+}
+// x = Ainv b with Ainv stored column by column (coalesced over rows)
+template <typename T>
+__global__ void __launch_bounds__(256) dense_matvec_kernel(int n, const T* __restrict__ Ainv,
+                                                           const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ unsigned char smraw[];
+  T* sb = reinterpret_cast<T*>(smraw);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = b[j];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T acc = T(0);
+  for (int j = 0; j < n; ++j) acc += Ainv[(int64_t)j * n + i] * sb[j];
+  x[i] = acc;
+}
+
 // deterministic pseudo-random start vector in [-1, 1] (splitmix64 hash)
 template <typename T>
 __global__ void hash_fill_kernel(int64_t n, T* __restrict__ x) {
@@ -256,7 +283,7 @@ template <typename T>
 MultiGrid<T>::~MultiGrid() {
   for (auto& L : lv) {
     if (L.owned && L.mesh) dg_mesh_destroy(L.mesh);
-    T* vs[] = {L.x, L.b, L.r, L.d, L.t, L.dinv[0], L.dinv[1]};
+    T* vs[] = {L.x, L.b, L.r, L.d, L.t, L.d2, L.dinv[0], L.dinv[1], L.ainv[0], L.ainv[1]};
     for (T* p : vs)
       if (p) cudaFree(p);
   }
@@ -314,7 +341,7 @@ dg_status MultiGrid<T>::build(dg_mesh* fine, cudaStream_t s) {
   for (auto& L : lv) {
     L.n = L.mesh->ncell * L.mesh->nbp;
     nmax = std::max(nmax, L.n);
-    T** vs[] = {&L.x, &L.b, &L.r, &L.d, &L.t, &L.dinv[0], &L.dinv[1]};
+    T** vs[] = {&L.x, &L.b, &L.r, &L.d, &L.t, &L.d2, &L.dinv[0], &L.dinv[1]};
     for (T** v : vs) {
       cudaError_t e = cudaMalloc(v, sizeof(T) * L.n);
       if (e != cudaSuccess) return cuda_fail(e, "multigrid level vectors");
@@ -446,6 +473,10 @@ dg_status MultiGrid<T>::set_alpha(double a) {
     L.lmax[slot] = 1.1 * hi;
     L.lmin[slot] = coarsest ? std::max(0.9 * lo, 1e-3 * hi) : L.lmax[slot] / 20.0;
   }
+  if (lv.back().n <= kCoarseDenseMax) {
+    dg_status st = coarse_inverse(slot);
+    if (st != DG_OK) return st;
+  }
   // transfer tables
   tr.clear();
   for (size_t l = 1; l < lv.size(); ++l) {
@@ -476,7 +507,10 @@ dg_status MultiGrid<T>::set_alpha(double a) {
   return DG_OK;
 }
 
-// Chebyshev smoothing on level l: x <- x + poly(D^-1 A) D^-1 (b - A x)
+// Chebyshev smoothing on level l: x <- x + poly(D^-1 A) D^-1 (b - A x).
+// Every step after the first is one fused launch: the operator apply whose
+// epilogue does x += d, r -= D^-1 A d, d' = c1 d + c2 r (into the second
+// direction buffer, since neighbouring cells still read d).
 template <typename T>
 dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
   MGLevel<T>& L = lv[l];
@@ -489,18 +523,20 @@ dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
   dg_status st;
   if (x_zero) {
     cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.b, nullptr, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
+    DG_CUDA(cudaMemsetAsync(L.x, 0, sizeof(T) * n, stream));
   } else {
     st = level_apply<T>(L, alpha, L.x, L.t, stream);
     if (st != DG_OK) return st;
     cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.b, L.t, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
   }
-  if (x_zero) DG_CUDA(cudaMemsetAsync(L.x, 0, sizeof(T) * n, stream));
   for (int k = 0; k + 1 < degree; ++k) {
-    st = level_apply<T>(L, alpha, L.d, L.t, stream);
-    if (st != DG_OK) return st;
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    cheb_step_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.x, L.d, L.r, L.t, dinv,
-                                                       (T)(rho_new * rho), (T)(2.0 * rho_new / delta)); count_launch();
+    st = launch_poisson_cheb<T>(L.mesh, alpha, L.d, L.d2, L.x, L.r, dinv, rho_new * rho,
+                                2.0 * rho_new / delta, stream);
+    if (st != DG_OK) return st;
+    T* tmp = L.d;
+    L.d = L.d2;
+    L.d2 = tmp;
     rho = rho_new;
   }
   add_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.d, L.x); count_launch();
@@ -508,10 +544,96 @@ dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
   return DG_OK;
 }
 
+// Dense inverse of the coarsest level operator for one cached alpha: its
+// columns are applies to the unit vectors, inverted on the host by
+// Gauss-Jordan elimination with partial pivoting in FP64.
+template <typename T>
+dg_status MultiGrid<T>::coarse_inverse(int slot) {
+  MGLevel<T>& L = lv.back();
+  const int64_t n = L.n;
+  T *I = nullptr, *Acol = nullptr;
+  DG_CUDA(cudaMalloc(&I, sizeof(T) * n * n));
+  DG_CUDA(cudaMalloc(&Acol, sizeof(T) * n * n));
+  identity_kernel<T><<<grid1(n * n), 256, 0, stream>>>(n, I); count_launch();
+  dg_status st = DG_OK;
+  for (int64_t j = 0; j < n && st == DG_OK; ++j)
+    st = level_apply<T>(L, alpha, I + j * n, Acol + j * n, stream);
+  std::vector<T> ht(n * n);
+  if (st == DG_OK) {
+    cudaError_t e = cudaMemcpyAsync(ht.data(), Acol, sizeof(T) * n * n, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "coarse inverse");
+  }
+  cudaFree(I);
+  if (st != DG_OK) {
+    cudaFree(Acol);
+    return st;
+  }
+  // column j of ht is A e_j: a[i][j] = ht[j*n + i]
+  std::vector<double> a(n * n), inv(n * n, 0.0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) a[i * n + j] = (double)ht[j * n + i];
+  for (int64_t i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int64_t c = 0; c < n; ++c) {
+    int64_t piv = c;
+    for (int64_t r = c + 1; r < n; ++r)
+      if (std::fabs(a[r * n + c]) > std::fabs(a[piv * n + c])) piv = r;
+    if (a[piv * n + c] == 0.0) {
+      cudaFree(Acol);
+      set_error("multigrid: singular coarse operator");
+      return DG_EBREAKDOWN;
+    }
+    if (piv != c)
+      for (int64_t k = 0; k < n; ++k) {
+        std::swap(a[c * n + k], a[piv * n + k]);
+        std::swap(inv[c * n + k], inv[piv * n + k]);
+      }
+    const double p = 1.0 / a[c * n + c];
+    for (int64_t k = 0; k < n; ++k) {
+      a[c * n + k] *= p;
+      inv[c * n + k] *= p;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[r * n + c];
+      if (f == 0.0) continue;
+      for (int64_t k = 0; k < n; ++k) {
+        a[r * n + k] -= f * a[c * n + k];
+        inv[r * n + k] -= f * inv[c * n + k];
+      }
+    }
+  }
+  // store column by column: Ainv[j*n + i] = inv[i][j]
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) ht[j * n + i] = (T)inv[i * n + j];
+  if (!L.ainv[slot]) {
+    cudaError_t e = cudaMalloc(&L.ainv[slot], sizeof(T) * n * n);
+    if (e != cudaSuccess) {
+      cudaFree(Acol);
+      return cuda_fail(e, "coarse inverse");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(L.ainv[slot], ht.data(), sizeof(T) * n * n, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // ht dies here
+  cudaFree(Acol);
+  if (e != cudaSuccess) return cuda_fail(e, "coarse inverse");
+  return DG_OK;
+}
+
 template <typename T>
 dg_status MultiGrid<T>::vcycle(int l) {
   dg_status st;
-  if (l + 1 == (int)lv.size()) return chebyshev(l, 30, true);
+  if (l + 1 == (int)lv.size()) {
+    MGLevel<T>& Lc = lv[l];
+    if (Lc.ainv[cur]) {
+      dense_matvec_kernel<T><<<(unsigned)((Lc.n + 255) / 256), 256, sizeof(T) * Lc.n, stream>>>(
+          (int)Lc.n, Lc.ainv[cur], Lc.b, Lc.x);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+      return DG_OK;
+    }
+    return chebyshev(l, 30, true);
+  }
   MGLevel<T>& L = lv[l];
   MGLevel<T>& C = lv[l + 1];
   st = chebyshev(l, smooth_degree, true);

@@ -33,7 +33,9 @@ struct MGLevel {
   T* r = nullptr;
   T* d = nullptr;
   T* t = nullptr;
+  T* d2 = nullptr;                  // second Chebyshev direction (ping-pong)
   T* dinv[2] = {nullptr, nullptr};  // per cached alpha
+  T* ainv[2] = {nullptr, nullptr};  // dense inverse of the coarsest level, per cached alpha
   double lmin[2] = {0, 0}, lmax[2] = {0, 0};
 };
 
@@ -60,6 +62,7 @@ struct MultiGrid {
   dg_status vcycle(int l);
   dg_status chebyshev(int l, int degree, bool x_zero);
   dg_status estimate(int l, int slot, int steps, double* lo, double* hi);
+  dg_status coarse_inverse(int slot);
   dg_status dot(int64_t n, const T* a, const T* b, double* out);
   void lanczos_update(int64_t n, T a, const T* q, const T* dinv, T* r, T* z);
   void lanczos_dir(int64_t n, T b, const T* z, T* p);

@@ -419,9 +419,9 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 // ------------------------------------------------------------------
 // Diagonal of mass M + visc A + adv C(ubar) (walls = 1) or of
 // alpha M^p + K (walls = 0, adv = 0), one thread per node.
-template <int DIM, int N>
-__global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
-                            double mass, double visc, double adv, double pen, int walls,
+template <int DIM, int N, typename R>
+__global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb,
+                            R mass, R visc, R adv, R pen, int walls,
                             const double* __restrict__ ub, double* __restrict__ diag) {
   constexpr int NB = Sh<N, DIM>::NB;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -431,73 +431,73 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
   int ci[3];
   cell_coords(g, cell, ci);
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  double h[3] = {1, 1, 1}, hi[3] = {1, 1, 1};
+  R h[3] = {1, 1, 1}, hi[3] = {1, 1, 1};
   for (int b = 0; b < DIM; ++b) {
-    h[b] = g.h[b][ci[b]];
-    hi[b] = g.hi[b][ci[b]];
+    h[b] = (R)g.h[b][ci[b]];
+    hi[b] = (R)g.hi[b][ci[b]];
   }
   auto Wat = [&](const int j[3]) {
-    double W = 1.0;
+    R W = 1.0;
     for (int b = 0; b < DIM; ++b) W *= tb.w[j[b]] * h[b];
     return W;
   };
-  const double W = Wat(ii);
-  double d = mass * W;
+  const R W = Wat(ii);
+  R d = mass * W;
   for (int b = 0; b < DIM; ++b) {
-    double acc = 0.0;
+    R acc = 0.0;
     for (int m = 0; m < N; ++m) {
       int j[3] = {ii[0], ii[1], ii[2]};
       j[b] = m;
-      const double dm = tb.D[m][ii[b]] * hi[b];
+      const R dm = tb.D[m][ii[b]] * hi[b];
       acc += Wat(j) * dm * dm;
     }
     d += visc * acc;
-    if (adv != 0.0) d -= adv * W * ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] * hi[b];
+    if (adv != 0.0) d -= adv * W * (R)ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] * hi[b];
   }
   for (int ax = 0; ax < DIM; ++ax) {
     const int t = tangof(N, DIM, ax, ii);
-    double wt = 1.0;
+    R wt = 1.0;
     for (int b = 0; b < DIM; ++b)
       if (b != ax) wt *= tb.w[ii[b]] * h[b];
     for (int s = 0; s < 2; ++s) {
-      const double sgn = s ? 1.0 : -1.0;
+      const R sgn = s ? R(1.0) : R(-1.0);
       const int64_t nb = neighbour(g, ci, ax, s);
-      const double hiK = hi[ax];
-      const double uin = tb.L[s][ii[ax]], dnin = sgn * tb.dL[s][ii[ax]] * hiK;
-      double unin = 0.0;
+      const R hiK = hi[ax];
+      const R uin = tb.L[s][ii[ax]], dnin = sgn * tb.dL[s][ii[ax]] * hiK;
+      R unin = 0.0;
       if (adv != 0.0) {
         for (int i = 0; i < N; ++i)
-          unin += tb.L[s][i] * ub[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)];
+          unin += tb.L[s][i] * (R)ub[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)];
         unin *= sgn;
       }
-      double fv = 0.0, fg = 0.0;
+      R fv = 0.0, fg = 0.0;
       if (nb >= 0) {
         int nc3[3];
         cell_coords(g, nb, nc3);
-        const double hiN = g.hi[ax][nc3[ax]];
+        const R hiN = (R)g.hi[ax][nc3[ax]];
         // a one-cell period makes the cell its own neighbour
-        const double uout = nb == cell ? tb.L[1 - s][ii[ax]] : 0.0;
-        const double dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] * hiN : 0.0;
-        const double C = 0.5 * pen * (hiK + hiN);
-        const double jump = uin - uout;
-        fv = visc * (-0.5 * (dnin + dnout) + C * jump);
-        fg = -0.5 * visc * jump;
+        const R uout = nb == cell ? tb.L[1 - s][ii[ax]] : R(0.0);
+        const R dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] * hiN : R(0.0);
+        const R C = R(0.5) * pen * (hiK + hiN);
+        const R jump = uin - uout;
+        fv = visc * (R(-0.5) * (dnin + dnout) + C * jump);
+        fg = R(-0.5) * visc * jump;
         if (adv != 0.0) {
-          double unout = 0.0;
+          R unout = 0.0;
           for (int i = 0; i < N; ++i)
-            unout += tb.L[1 - s][i] * ub[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)];
+            unout += tb.L[1 - s][i] * (R)ub[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)];
           unout *= sgn;
-          const double lam = fmax(fabs(unin), fabs(unout));
-          fv += adv * (0.5 * (uin * unin + uout * unout) + 0.5 * lam * jump);
+          const R lam = fmax(fabs(unin), fabs(unout));
+          fv += adv * (R(0.5) * (uin * unin + uout * unout) + R(0.5) * lam * jump);
         }
       } else if (walls) {
-        fv = visc * (-dnin + 2.0 * (pen * hiK) * uin) + adv * fabs(unin) * uin;
+        fv = visc * (-dnin + R(2.0) * (pen * hiK) * uin) + adv * fabs(unin) * uin;
         fg = -visc * uin;
       }
       d += wt * (fv * tb.L[s][ii[ax]] + fg * sgn * tb.dL[s][ii[ax]] * hiK);
     }
   }
-  diag[gid] = d;
+  diag[gid] = (double)d;
 }
 
 template <int DIM>
@@ -572,11 +572,18 @@ dg_status run_project(const dg_mesh* m, const double* p, double* ut, cudaStream_
 
 template <int DIM, int N>
 dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, double adv,
-                   const double* ub, double* diag, cudaStream_t s) {
+                   const double* ub, double* diag, cudaStream_t s, bool fp32 = false) {
   const int64_t total = m->ncell * Sh<N, DIM>::NB;
   const unsigned blocks = (unsigned)((total + 255) / 256);
-  diag_kernel<DIM, N><<<blocks, 256, 0, s>>>(make_grid<DIM>(m), pressure ? m->tp64 : m->tu64, mass,
-                                             visc, adv, (double)(N * N), pressure ? 0 : 1, ub, diag); count_launch();
+  if (fp32)
+    diag_kernel<DIM, N, float><<<blocks, 256, 0, s>>>(
+        make_grid<DIM>(m), pressure ? m->tp32 : m->tu32, (float)mass, (float)visc, (float)adv,
+        (float)(N * N), pressure ? 0 : 1, ub, diag);
+  else
+    diag_kernel<DIM, N, double><<<blocks, 256, 0, s>>>(make_grid<DIM>(m), pressure ? m->tp64 : m->tu64,
+                                                       mass, visc, adv, (double)(N * N),
+                                                       pressure ? 0 : 1, ub, diag);
+  count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -599,6 +606,14 @@ bool check_affine(const dg_mesh* m, const char* who) {
 }
 
 }  // namespace
+
+// internal entry used by the solver: the momentum diagonal in FP32
+// arithmetic (it only scales the Jacobi preconditioner)
+dg_status momentum_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co, const double* ub,
+                                 double* diag, cudaStream_t s) {
+  if (!check_affine(m, "momentum diagonal")) return DG_EUNSUPPORTED;
+  return DG_DISPATCH_U(m, run_diag, m, false, co->mass, co->visc, co->adv, ub, diag, s, true);
+}
 
 // internal entry used by the solver: diagonal of a pressure-space operator
 dg_status poisson_diagonal(const dg_mesh* m, double alpha, double* diag, cudaStream_t s) {

@@ -34,6 +34,11 @@ struct dg_solver {
   dg::MultiGrid<float>* mg32 = nullptr;   // built on first use
   dg::MultiGrid<double>* mg64 = nullptr;
   dg::GuessState guess;                   // stage histories and learned-guess nets
+  // per-phase CUDA-event tracing of trbdf2_step (dg_solver_set_tracing)
+  bool tracing = false;
+  cudaEvent_t ev[24] = {};
+  double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  int64_t traced_steps = 0;
 };
 
 namespace dg {
@@ -78,7 +83,7 @@ dg_status solve_momentum(dg_solver* s, const dg_momentum_coeffs* co, const doubl
   dg_status st;
   const double* dinv = nullptr;
   if (o->precond == DG_PC_JACOBI) {
-    st = dg_momentum_diagonal(m, co, ubar, s->diag_s, s->stream);
+    st = momentum_diagonal_fp32(m, co, ubar, s->diag_s, s->stream);
     if (st != DG_OK) return st;
     st = s->vo.invert(s->nu, s->diag_s, s->nus, s->dinv_u);
     if (st != DG_OK) return st;
@@ -157,6 +162,32 @@ dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double*
                   r + 4 * s->np, o->tol_rel, o->max_iter, o->timeout_s, info);
 }
 
+
+// ---------------------------------------------------------------- tracing
+// phases: 0 extrapolation + momentum RHS, 1 initial guesses (history,
+// learned prediction and training), 2 momentum solves, 3 projections +
+// pressure RHS + velocity updates, 4 Helmholtz solves
+struct Tracer {
+  dg_solver* s;
+  int n = 0;
+  int phase[24];
+  void mark(int ph) {
+    if (!s->tracing || n >= 24) return;
+    cudaEventRecord(s->ev[n], s->stream);
+    phase[n] = ph;
+    ++n;
+  }
+  void finish() {
+    if (!s->tracing || n < 2) return;
+    cudaEventSynchronize(s->ev[n - 1]);
+    for (int i = 0; i + 1 < n; ++i) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, s->ev[i], s->ev[i + 1]);
+      s->phase_ms[phase[i]] += ms;
+    }
+    ++s->traced_steps;
+  }
+};
 
 // ---------------------------------------------------------------- guesses
 // slot = 2 (stage - 1) + (0 momentum, 1 Helmholtz)
@@ -310,6 +341,8 @@ dg_status dg_solver_create(dg_mesh* m, double Re, double c, dg_solver** out) {
     st = DG_ENOMEM;
   }
   if (st == DG_OK) st = ensure_basis(s, 30);
+  for (int i = 0; i < 24 && st == DG_OK; ++i)
+    if (cudaEventCreate(&s->ev[i]) != cudaSuccess) st = DG_ECUDA;
   if (st != DG_OK) {
     dg_solver_destroy(s);
     return st;
@@ -323,6 +356,8 @@ void dg_solver_destroy(dg_solver* s) {
   cudaStreamSynchronize(s->stream);
   delete s->mg32;
   delete s->mg64;
+  for (int i = 0; i < 24; ++i)
+    if (s->ev[i]) cudaEventDestroy(s->ev[i]);
   for (void* a : s->allocs)
     if (a) cudaFree(a);
   if (s->vo.host_scal) cudaFreeHost(s->vo.host_scal);
@@ -410,6 +445,8 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
     st = (call);                    \
     if (st != DG_OK) return st;     \
   } while (0)
+  Tracer tr{s};
+  tr.mark(0);
   if (!s->has_hist) {
     DG_CUDA(cudaMemcpyAsync(s->u_hist, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
     s->has_hist = true;
@@ -443,9 +480,13 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   STEP(dg_rhs_momentum(m, &r1, s->rhs_u, st_));
   if (mo.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->ustar, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  tr.mark(1);
   STEP(prepare_guess(s, 0, prm->mom.guess, s->rhs_u, s->ustar));
+  tr.mark(2);
   STEP(dg_solve_stage(s, &co1, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[0]));
+  tr.mark(1);
   STEP(finish_guess(s, 0, prm->mom.guess, s->ustar));
+  tr.mark(3);
   // ---------------- stage 1: projection (Eq. helmholtz2a) ---------------
   const double tau1 = g * dt, alpha1 = 1.0 / (s->c * s->c * tau1 * tau1);
   STEP(dg_project_gradient(m, p, s->ut_old, st_));
@@ -453,13 +494,18 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   STEP(dg_rhs_pressure(m, alpha1, tau1, s->uss, p, s->rhs_p, st_));
   if (ho.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->p_g, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
+  tr.mark(1);
   STEP(prepare_guess(s, 1, prm->helm.guess, s->rhs_p, s->p_g));
+  tr.mark(4);
   STEP(dg_solve_stage(s, nullptr, alpha1, nullptr, s->rhs_p, s->p_g, &ho, &info[1]));
+  tr.mark(1);
   STEP(finish_guess(s, 1, prm->helm.guess, s->p_g));
+  tr.mark(3);
   STEP(dg_project_gradient(m, s->p_g, s->ut_new, st_));
   // u^{n+g} = u* - tau (u~new - u~old)
   STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
   STEP(vo.axpby(nu, 1.0, s->ustar, -tau1, s->ut_new, s->u_g));
+  tr.mark(0);
   // ---------------- stage 2: momentum predictor (Eq. second_stage) ------
   if (prm->extrapolate) {
     STEP(vo.axpby(nu, 1.0 / g, s->u_g, -(1.0 - g) / g, u, s->ub));
@@ -493,9 +539,13 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   STEP(dg_rhs_momentum(m, &r2, s->rhs_u, st_));
   if (mo.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->ustar, s->u_g, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  tr.mark(1);
   STEP(prepare_guess(s, 2, prm->mom.guess, s->rhs_u, s->ustar));
+  tr.mark(2);
   STEP(dg_solve_stage(s, &co2, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[2]));
+  tr.mark(1);
   STEP(finish_guess(s, 2, prm->mom.guess, s->ustar));
+  tr.mark(3);
   // ---------------- stage 2: projection (Eq. helmholtz3a) ---------------
   const double tau2 = (1.0 - g) * dt, alpha2 = 1.0 / (s->c * s->c * tau2 * tau2);
   STEP(dg_project_gradient(m, s->p_g, s->ut_old, st_));
@@ -504,16 +554,43 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   if (ho.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(p, s->p_g, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
   // p (in: p^n, no longer needed) receives p^{n+1}
+  tr.mark(1);
   STEP(prepare_guess(s, 3, prm->helm.guess, s->rhs_p, p));
+  tr.mark(4);
   STEP(dg_solve_stage(s, nullptr, alpha2, nullptr, s->rhs_p, p, &ho, &info[3]));
+  tr.mark(1);
   STEP(finish_guess(s, 3, prm->helm.guess, p));
+  tr.mark(3);
   STEP(dg_project_gradient(m, p, s->ut_new, st_));
   STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
   // history u^{n+g} before u is overwritten with u^{n+1}
   DG_CUDA(cudaMemcpyAsync(s->u_hist, s->u_g, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
   STEP(vo.axpby(nu, 1.0, s->ustar, -tau2, s->ut_new, u));
+  tr.mark(5);
   DG_CUDA(cudaStreamSynchronize(st_));
+  tr.finish();
 #undef STEP
+  return DG_OK;
+}
+
+dg_status dg_solver_set_tracing(dg_solver* s, int32_t on) {
+  if (!s) {
+    set_error("dg_solver_set_tracing: null solver");
+    return DG_EINVAL;
+  }
+  s->tracing = on != 0;
+  for (double& x : s->phase_ms) x = 0.0;
+  s->traced_steps = 0;
+  return DG_OK;
+}
+
+dg_status dg_solver_get_trace(const dg_solver* s, double phase_ms[6], int64_t* steps) {
+  if (!s || !phase_ms) {
+    set_error("dg_solver_get_trace: bad argument");
+    return DG_EINVAL;
+  }
+  for (int i = 0; i < 6; ++i) phase_ms[i] = s->phase_ms[i];
+  if (steps) *steps = s->traced_steps;
   return DG_OK;
 }
 

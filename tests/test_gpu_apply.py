@@ -45,10 +45,14 @@ def dev(x, dtype=torch.float64):
     return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
 
 
+@pytest.mark.parametrize("fp64_arith", [0, 1])
 @pytest.mark.parametrize("ci", range(len(CASES)))
-def test_poisson_apply_matches_oracle(ci):
+def test_poisson_apply_matches_oracle(ci, fp64_arith):
+    """fp64_arith 0: float-float arithmetic (48-bit significands, error a few
+    2^-48 per operation, far inside 1e-12); 1: native FP64."""
     from paper_2107_07776_gb300 import binding as b
     gm, om = meshes(CASES[ci])
+    b.dg_mesh_set_fp64_arith(gm.handle, fp64_arith)
     x = W.random_vector(om.n_p, 100 + ci)
     alpha = 2.9
     ref = alpha * om.assemble("mass_p").apply(x) + om.assemble("sipg_p").apply(x)
@@ -62,10 +66,12 @@ def test_poisson_apply_matches_oracle(ci):
     assert rel_err(y32.double().cpu().numpy(), ref) < 2e-5
 
 
+@pytest.mark.parametrize("fp64_arith", [0, 1])
 @pytest.mark.parametrize("ci", range(len(CASES)))
-def test_momentum_apply_matches_oracle(ci):
+def test_momentum_apply_matches_oracle(ci, fp64_arith):
     from paper_2107_07776_gb300 import binding as b
     gm, om = meshes(CASES[ci])
+    b.dg_mesh_set_fp64_arith(gm.handle, fp64_arith)
     d = om.dim
     x = W.random_vector(d * om.n_u, 200 + ci)
     ub = W.random_vector(d * om.n_u, 300 + ci)
@@ -96,13 +102,15 @@ def test_node_coords_match_oracle():
             assert np.abs(g - o).max() < 1e-13
 
 
-def test_full_size_tgv32_sampled_cells():
+@pytest.mark.parametrize("fp64_arith", [0, 1])
+def test_full_size_tgv32_sampled_cells(fp64_arith):
     """The 32^3 Q2/Q1 Taylor-Green workload at full size, as the benchmark
     launches it: every output of 64 sampled cells (corners, edges, random)
     against the oracle's rows for those cells."""
     from paper_2107_07776_gb300 import binding as b
     w = W.TGV32
     gm = b.Mesh.from_workload(w)
+    b.dg_mesh_set_fp64_arith(gm.handle, fp64_arith)
     om = OMesh(w.dim, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree)
     rng = np.random.default_rng(7)
     N = om.n_cells
