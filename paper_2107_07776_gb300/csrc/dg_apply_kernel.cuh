@@ -273,11 +273,12 @@ constexpr int default_cpb() {
   return Shape<N, DIM>::NB <= 8 ? 16 : (Shape<N, DIM>::NB <= 27 ? 8 : (Shape<N, DIM>::NB <= 64 ? 4 : 2));
 }
 
-template <typename T, int DIM, int N, bool ADV, int CPB>
-constexpr int smem_bytes() {
-  return (int)sizeof(T) * CPB *
-         (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
-          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4));
+// shared memory of one CTA (arithmetic type of size sizeof(T); float-float
+// has the size of double)
+template <int N, int DIM, bool ADV>
+constexpr int smem_words(int cpb) {
+  return cpb * (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
+                (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4));
 }
 
 // Tile-shape candidates of the autotuner: half, default and double the
@@ -287,10 +288,7 @@ template <typename T, int DIM, int N, bool ADV>
 constexpr int cpb_variant(int v) {
   int c = v == 0 ? default_cpb<N, DIM>() / 2 : (v == 2 ? default_cpb<N, DIM>() * 2 : default_cpb<N, DIM>());
   if (c < 1) c = 1;
-  while (c > 1 && (c * Shape<N, DIM>::NB > 1024 ||
-                   (int)sizeof(T) * c * (Shape<N, DIM>::NB * (1 + DIM) + 2 * Shape<N, DIM>::NFP +
-                                          (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4)) >
-                       48 * 1024))
+  while (c > 1 && (c * Shape<N, DIM>::NB > 1024 || (int)sizeof(T) * smem_words<N, DIM, ADV>(c) > 46 * 1024))
     c /= 2;
   return c;
 }

@@ -39,6 +39,7 @@ void make_mix(const Tab1D<double>& tu, int nu, const Tab1D<double>& tp, int np, 
 template <typename T>
 Tab1D<T> cast_tables(const Tab1D<double>& t);
 Tab1D<df64> split_tables(const Tab1D<double>& t);
+MixTab<df64> split_mix(const MixTab<double>& t);
 
 // Cell geometry of the affine paths: per-axis cell extents (the Jacobian is
 // diagonal, diag(h0, h1, h2), on Cartesian and tensor-graded meshes).
@@ -68,6 +69,7 @@ struct dg_mesh {
   dg::Tab1D<float> tu32, tp32;
   dg::MixTab<double> mix64;
   dg::Tab1D<dg::df64> tudf, tpdf;    // float-float copies of the FP64 tables
+  dg::MixTab<dg::df64> mixdf;
   int fp64_arith = 0;                // FP64 operator arithmetic: 0 float-float, 1 native FP64
   int* d_status = nullptr;           // device error word
   // autotuned tile shape of the operator kernels: variant index per

@@ -73,6 +73,30 @@ __device__ __forceinline__ df64 df_from(double x) {
 }
 __device__ __forceinline__ double df_to(df64 a) { return (double)a.hi + (double)a.lo; }
 
+// Split of a double into a float pair with integer operations only (no FP64
+// instruction): hi keeps the sign, exponent and leading 23 fraction bits; the
+// remaining 29 fraction bits become lo (truncated to 24 significant bits, a
+// relative error below 2^-48 of x), and one FastTwoSum renormalises the pair.
+// Zero, values outside FP32's normal range, infinities and NaNs take the
+// conversion path above.
+__device__ __forceinline__ df64 df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFull);
+  const int ef = e - 1023 + 127;
+  if (ef <= 0 || ef >= 255) return df_from(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const float hi = __int_as_float((int)(sign | ((unsigned int)ef << 23) | (unsigned int)(m >> 29)));
+  const unsigned int r = (unsigned int)(m & 0x1FFFFFFFull);
+  if (r == 0u) return {hi, 0.0f};
+  const int p = 31 - __clz((int)r);  // position of the remainder's leading one
+  const int el = ef - 52 + p;        // its biased FP32 exponent
+  if (el <= 0) return {hi, 0.0f};
+  const unsigned int mant = p >= 23 ? (r >> (p - 23)) : (r << (23 - p));
+  const float lo = __int_as_float((int)(sign | ((unsigned int)el << 23) | (mant & 0x7FFFFFu)));
+  return df_fast_two_sum(hi, lo);
+}
+
 // Arithmetic-type adapters for kernels templated on the arithmetic type A
 // (float, double or df64) and the storage type T (float or double).
 template <typename A>
@@ -102,7 +126,7 @@ struct Arith<double> {
 
 template <>
 struct Arith<df64> {
-  __device__ static df64 from(double x) { return df_from(x); }
+  __device__ static df64 from(double x) { return df_split(x); }
   __device__ static df64 from(float x) { return {x, 0.0f}; }
   __device__ static df64 c(double x) { return df_from(x); }
   __device__ static df64 abs(df64 x) { return df_abs(x); }

@@ -156,6 +156,17 @@ Tab1D<T> cast_tables(const Tab1D<double>& t) {
 }
 template Tab1D<float> cast_tables<float>(const Tab1D<double>&);
 
+MixTab<df64> split_mix(const MixTab<double>& t) {
+  MixTab<df64> o;
+  for (int a = 0; a < kMaxN; ++a)
+    for (int b = 0; b < kMaxN; ++b) {
+      const float hI = (float)t.I[a][b], hD = (float)t.D[a][b];
+      o.I[a][b] = df64{hI, (float)(t.I[a][b] - (double)hI)};
+      o.D[a][b] = df64{hD, (float)(t.D[a][b] - (double)hD)};
+    }
+  return o;
+}
+
 // float-float split of every table entry: hi = fl32(x), lo = fl32(x - hi)
 Tab1D<df64> split_tables(const Tab1D<double>& t) {
   Tab1D<df64> o;
@@ -216,6 +227,7 @@ dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
   m->tp32 = cast_tables<float>(m->tp64);
   m->tudf = split_tables(m->tu64);
   m->tpdf = split_tables(m->tp64);
+  m->mixdf = split_mix(m->mix64);
   {
     const char* env = std::getenv("DG_FP64_NATIVE");
     m->fp64_arith = env && env[0] == '1' ? 1 : 0;

@@ -113,19 +113,18 @@ __global__ void identity_kernel(int64_t n, T* __restrict__ I) {
        k += (int64_t)gridDim.x * blockDim.x)
     I[k] = (k / n == k % n) ? T(1) : T(0);
 }
-// x = Ainv b with Ainv stored column by column (coalesced over rows)
+// x = Ainv b, one warp per row: the inverse of the symmetric coarse operator
+// is symmetric, so row i is read contiguously (stored column j at j*n)
 template <typename T>
 __global__ void __launch_bounds__(256) dense_matvec_kernel(int n, const T* __restrict__ Ainv,
                                                            const T* __restrict__ b, T* __restrict__ x) {
-  extern __shared__ unsigned char smraw[];
-  T* sb = reinterpret_cast<T*>(smraw);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = b[j];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const T* a = Ainv + (int64_t)row * n;
   T acc = T(0);
-  for (int j = 0; j < n; ++j) acc += Ainv[(int64_t)j * n + i] * sb[j];
-  x[i] = acc;
+  for (int j = lane; j < n; j += 32) acc += a[j] * b[j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[row] = acc;
 }
 
 // deterministic pseudo-random start vector in [-1, 1] (splitmix64 hash)
@@ -186,43 +185,51 @@ __global__ void prolong_add_kernel(const __grid_constant__ Transfer tr, int64_t 
   xf[gid] += (T)acc;
 }
 
+// Restriction, pass 1: part[(cc * nchild + ch) * nbc + j] = sum_i M r_f[i]
+// over the fine nodes i of child ch of coarse cell cc (one thread per term
+// set; the child's nodes are contiguous)
 template <typename T>
-__global__ void restrict_kernel(const __grid_constant__ Transfer tr, int64_t ncoarse_dofs,
-                                const T* __restrict__ rf, T* __restrict__ bc) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= ncoarse_dofs) return;
+__global__ void restrict_part_kernel(const __grid_constant__ Transfer tr, int64_t ncc, int nchild,
+                                     const T* __restrict__ rf, T* __restrict__ part) {
   const int nbf = tr.dim == 3 ? tr.nf * tr.nf * tr.nf : tr.nf * tr.nf;
   const int nbc = tr.dim == 3 ? tr.nc * tr.nc * tr.nc : tr.nc * tr.nc;
-  const int64_t cc = gid / nbc;
-  const int node = (int)(gid % nbc);
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ncc * nchild * nbc) return;
+  const int j = (int)(gid % nbc);
+  const int ch = (int)((gid / nbc) % nchild);
+  const int64_t cc = gid / ((int64_t)nbc * nchild);
   const int ci[3] = {(int)(cc % tr.ncoarse[0]), (int)((cc / tr.ncoarse[0]) % tr.ncoarse[1]),
                      (int)(cc / ((int64_t)tr.ncoarse[0] * tr.ncoarse[1]))};
-  const int jj[3] = {node % tr.nc, (node / tr.nc) % tr.nc, tr.dim == 3 ? node / (tr.nc * tr.nc) : 0};
-  int nchild = 1;
+  const int jj[3] = {j % tr.nc, (j / tr.nc) % tr.nc, tr.dim == 3 ? j / (tr.nc * tr.nc) : 0};
+  int bit[3] = {0, 0, 0}, fi[3] = {ci[0], ci[1], ci[2]}, t = ch;
   for (int a = 0; a < tr.dim; ++a)
-    if (tr.hco[a]) nchild *= 2;
+    if (tr.hco[a]) {
+      bit[a] = t & 1;
+      t >>= 1;
+      fi[a] = 2 * ci[a] + bit[a];
+    }
+  const int64_t fc = fi[0] + (int64_t)tr.nfine[0] * (fi[1] + (int64_t)tr.nfine[1] * fi[2]);
   double acc = 0.0;
-  for (int ch = 0; ch < nchild; ++ch) {
-    int bit[3] = {0, 0, 0}, fi[3], t = ch;
-    for (int a = 0; a < tr.dim; ++a) {
-      if (tr.hco[a]) {
-        bit[a] = t & 1;
-        t >>= 1;
-        fi[a] = 2 * ci[a] + bit[a];
-      } else {
-        fi[a] = ci[a];
-      }
-    }
-    if (tr.dim == 2) fi[2] = 0;
-    const int64_t fc = fi[0] + (int64_t)tr.nfine[0] * (fi[1] + (int64_t)tr.nfine[1] * fi[2]);
-    for (int i = 0; i < nbf; ++i) {
-      const int ii[3] = {i % tr.nf, (i / tr.nf) % tr.nf, tr.dim == 3 ? i / (tr.nf * tr.nf) : 0};
-      double w = 1.0;
-      for (int a = 0; a < tr.dim; ++a) w *= tr.M[tr.hco[a] ? bit[a] : 2][ii[a]][jj[a]];
-      acc += w * (double)rf[fc * nbf + i];
-    }
+  for (int i = 0; i < nbf; ++i) {
+    const int ii[3] = {i % tr.nf, (i / tr.nf) % tr.nf, tr.dim == 3 ? i / (tr.nf * tr.nf) : 0};
+    double w = 1.0;
+    for (int a = 0; a < tr.dim; ++a) w *= tr.M[tr.hco[a] ? bit[a] : 2][ii[a]][jj[a]];
+    acc += w * (double)rf[fc * nbf + i];
   }
-  bc[gid] = (T)acc;
+  part[gid] = (T)acc;
+}
+
+// Restriction, pass 2: b_c = sum over the children, fixed order
+template <typename T>
+__global__ void restrict_sum_kernel(int64_t ncoarse_dofs, int nbc, int nchild,
+                                    const T* __restrict__ part, T* __restrict__ bc) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= ncoarse_dofs) return;
+  const int64_t cc = gid / nbc;
+  const int j = (int)(gid % nbc);
+  T acc = T(0);
+  for (int ch = 0; ch < nchild; ++ch) acc += part[(cc * nchild + ch) * nbc + j];
+  bc[gid] = acc;
 }
 
 // Largest/smallest eigenvalues of a symmetric tridiagonal matrix by
@@ -626,8 +633,8 @@ dg_status MultiGrid<T>::vcycle(int l) {
   if (l + 1 == (int)lv.size()) {
     MGLevel<T>& Lc = lv[l];
     if (Lc.ainv[cur]) {
-      dense_matvec_kernel<T><<<(unsigned)((Lc.n + 255) / 256), 256, sizeof(T) * Lc.n, stream>>>(
-          (int)Lc.n, Lc.ainv[cur], Lc.b, Lc.x);
+      dense_matvec_kernel<T><<<(unsigned)((Lc.n + 7) / 8), 256, 0, stream>>>((int)Lc.n, Lc.ainv[cur],
+                                                                              Lc.b, Lc.x);
       count_launch();
       DG_CUDA(cudaGetLastError());
       return DG_OK;
@@ -641,7 +648,20 @@ dg_status MultiGrid<T>::vcycle(int l) {
   st = level_apply<T>(L, alpha, L.x, L.t, stream);
   if (st != DG_OK) return st;
   sub_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, L.b, L.t, L.r); count_launch();
-  restrict_kernel<T><<<grid1(C.n), 256, 0, stream>>>(tr[l], C.n, L.r, C.b); count_launch();
+  {
+    const Transfer& t = tr[l];
+    int nchild = 1;
+    for (int a = 0; a < t.dim; ++a)
+      if (t.hco[a]) nchild *= 2;
+    const int nbc = t.dim == 3 ? t.nc * t.nc * t.nc : t.nc * t.nc;
+    const int64_t ncc = C.n / nbc, nterm = C.n * nchild;
+    // the fine level's spare direction buffer holds the partial sums
+    // (nchild * coarse DoFs = fine cells * coarse nodes <= fine DoFs)
+    restrict_part_kernel<T><<<(unsigned)((nterm + 255) / 256), 256, 0, stream>>>(t, ncc, nchild, L.r, L.d2);
+    count_launch();
+    restrict_sum_kernel<T><<<(unsigned)((C.n + 255) / 256), 256, 0, stream>>>(C.n, nbc, nchild, L.d2, C.b);
+    count_launch();
+  }
   DG_CUDA(cudaGetLastError());
   st = vcycle(l + 1);
   if (st != DG_OK) return st;

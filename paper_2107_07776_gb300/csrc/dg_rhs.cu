@@ -9,6 +9,7 @@
 // memory, every output written once (deterministic).  These run once per
 // stage, not per Krylov iteration.
 #include "dg_common.cuh"
+#include "dg_df64.cuh"
 
 namespace dg {
 
@@ -50,6 +51,9 @@ __device__ __forceinline__ int tangof(int N, int dim, int a, const int i[3]) {
   return t;
 }
 
+template <typename A>
+__device__ __forceinline__ A b0_or(bool c, A x, A y) { return c ? x : y; }
+
 // neighbour of cell ci across face (a, s); -1 at a wall
 __device__ __forceinline__ int64_t neighbour(const Grid& g, const int ci[3], int a, int s) {
   int nc[3] = {ci[0], ci[1], ci[2]};
@@ -67,101 +71,113 @@ __device__ __forceinline__ void cell_coords(const Grid& g, int64_t cell, int ci[
   ci[2] = (int)(cell / ((int64_t)g.n[0] * g.n[1]));
 }
 
+// All kernels below keep FP64 storage and compute in the arithmetic type A:
+// df64 (float-float on the FP32 pipes, the default) or double (native FP64;
+// selected per mesh with dg_mesh_set_fp64_arith).
+
 // ------------------------------------------------------------------
 // Explicit terms: MODE 0 adds visc E_v w + adv E_a(wb) w (all faces, central,
 // unpenalised); MODE 1 adds the Dirichlet data terms visc B_v w + adv B_a(wb) w
 // on wall faces (w = u_D, wb = the stage's advecting field).
-template <int DIM, int N, int MODE, int CPB>
+template <typename A, int DIM, int N, int MODE, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
-    explicit_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
-                    double visc, double adv, double pen, const double* __restrict__ w,
+    explicit_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
+                    double visc_d, double adv_d, double pen_d, const double* __restrict__ w,
                     const double* __restrict__ wb, double* __restrict__ rhs) {
+  using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
-  __shared__ double s_u[CPB][NB];
-  __shared__ double s_wb[DIM][CPB][NB];
-  __shared__ double s_q[DIM][CPB][NB];
-  __shared__ double s_f[CPB][NFP][2];
+  __shared__ A s_u[CPB][NB];
+  __shared__ A s_wb[DIM][CPB][NB];
+  __shared__ A s_q[DIM][CPB][NB];
+  __shared__ A s_f[CPB][NFP][2];
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
+  const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
+  const A visc = Ar::from(visc_d), adv = Ar::from(adv_d), pen = Ar::from(pen_d);
   int ci[3] = {0, 0, 0};
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  double h[3] = {1, 1, 1}, hi[3] = {1, 1, 1}, W = 0;
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
+  A W = zero;
   if (active) {
     cell_coords(g, cell, ci);
     for (int b = 0; b < DIM; ++b) {
-      h[b] = g.h[b][ci[b]];
-      hi[b] = g.hi[b][ci[b]];
+      h[b] = Ar::from(g.h[b][ci[b]]);
+      hi[b] = Ar::from(g.hi[b][ci[b]]);
     }
-    W = 1.0;
-    for (int b = 0; b < DIM; ++b) W *= tb.w[ii[b]] * h[b];
-    for (int b = 0; b < DIM; ++b) s_wb[b][cl][node] = wb[((int64_t)b * g.ncell + cell) * NB + node];
+    W = Ar::c(1.0);
+    for (int b = 0; b < DIM; ++b) W = W * tb.w[ii[b]] * h[b];
+    for (int b = 0; b < DIM; ++b) s_wb[b][cl][node] = Ar::from(wb[((int64_t)b * g.ncell + cell) * NB + node]);
   }
   for (int c = 0; c < DIM; ++c) {
     const double* wc = w + (int64_t)c * g.ncell * NB;
-    if (active) s_u[cl][node] = wc[cell * NB + node];
+    if (active) s_u[cl][node] = Ar::from(wc[cell * NB + node]);
     __syncthreads();
     if (active) {
+#pragma unroll
       for (int b = 0; b < DIM; ++b) {
-        double q = 0.0;
+        A q = zero;
         if (MODE == 0) {
-          double du = 0.0;
+          A du = zero;
+#pragma unroll
           for (int m = 0; m < N; ++m) {
             int j[3] = {ii[0], ii[1], ii[2]};
             j[b] = m;
             du += tb.D[ii[b]][m] * s_u[cl][j[0] + N * (j[1] + N * j[2])];
           }
-          q = W * (-visc * du * hi[b] + adv * s_u[cl][node] * s_wb[b][cl][node]);
+          q = W * (adv * s_u[cl][node] * s_wb[b][cl][node] - visc * du * hi[b]);
         }
         s_q[b][cl][node] = q;
       }
       for (int fp = node; fp < NFP; fp += NB) {
         const int f = fp / NF, t = fp % NF, ax = f >> 1, s = f & 1;
-        const double sgn = s ? 1.0 : -1.0;
+        const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
         const int64_t nb = neighbour(g, ci, ax, s);
-        const double hiK = hi[ax];
-        double wt = 1.0;
+        const A hiK = hi[ax];
+        A wt = Ar::c(1.0);
         {
           int tt = t;
           for (int b = 0; b < DIM; ++b) {
             if (b == ax) continue;
-            wt *= tb.w[tt % N] * h[b];
+            wt = wt * tb.w[tt % N] * h[b];
             tt /= N;
           }
         }
-        double uin = 0, dnin = 0, wnin = 0;
+        A uin = zero, dnin = zero, wnin = zero;
+#pragma unroll
         for (int i = 0; i < N; ++i) {
           const int nd = nodeof(N, DIM, ax, i, t);
           uin += tb.L[s][i] * s_u[cl][nd];
           dnin += tb.dL[s][i] * s_u[cl][nd];
           wnin += tb.L[s][i] * s_wb[ax][cl][nd];
         }
-        dnin *= sgn * hiK;
-        wnin *= sgn;
-        double fv = 0.0, fg = 0.0;
+        dnin = dnin * sgn * hiK;
+        wnin = wnin * sgn;
+        A fv = zero, fg = zero;
         if (MODE == 0) {
           if (nb >= 0) {
             int nc3[3];
             cell_coords(g, nb, nc3);
-            const double hiN = g.hi[ax][nc3[ax]];
-            double uout = 0, dnout = 0, wnout = 0;
+            const A hiN = Ar::from(g.hi[ax][nc3[ax]]);
+            A uout = zero, dnout = zero, wnout = zero;
+#pragma unroll
             for (int i = 0; i < N; ++i) {
               const int nd = nodeof(N, DIM, ax, i, t);
-              const double v = __ldg(&wc[nb * NB + nd]);
+              const A v = Ar::from(__ldg(&wc[nb * NB + nd]));
               uout += tb.L[1 - s][i] * v;
               dnout += tb.dL[1 - s][i] * v;
-              wnout += tb.L[1 - s][i] * __ldg(&wb[((int64_t)ax * g.ncell + nb) * NB + nd]);
+              wnout += tb.L[1 - s][i] * Ar::from(__ldg(&wb[((int64_t)ax * g.ncell + nb) * NB + nd]));
             }
-            dnout *= sgn * hiN;
-            wnout *= sgn;
-            fv = visc * 0.5 * (dnin + dnout) - adv * 0.5 * (uin * wnin + uout * wnout);
+            dnout = dnout * sgn * hiN;
+            wnout = wnout * sgn;
+            fv = half * (visc * (dnin + dnout) - adv * (uin * wnin + uout * wnout));
           } else {
             fv = visc * dnin - adv * uin * wnin;
           }
         } else if (nb < 0) {
-          const double sig = pen * hiK;
-          fv = visc * 2.0 * sig * uin + adv * (-uin * wnin + fabs(wnin) * uin);
-          fg = -visc * uin;
+          const A sig = pen * hiK;
+          fv = visc * two * sig * uin + adv * (Ar::abs(wnin) * uin - uin * wnin);
+          fg = -(visc * uin);
         }
         s_f[cl][fp][0] = wt * fv;
         s_f[cl][fp][1] = wt * fg * sgn * hiK;
@@ -169,9 +185,11 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     }
     __syncthreads();
     if (active) {
-      double y = 0.0;
+      A y = zero;
+#pragma unroll
       for (int b = 0; b < DIM; ++b) {
-        double acc = 0.0;
+        A acc = zero;
+#pragma unroll
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
@@ -184,7 +202,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
           y += s_f[cl][fp][0] * tb.L[s][ii[b]] + s_f[cl][fp][1] * tb.dL[s][ii[b]];
         }
       }
-      rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += y;
+      rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += Ar::to_d(y);
     }
     __syncthreads();
   }
@@ -193,40 +211,41 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 // ------------------------------------------------------------------
 // rhs = mass M u_mass + M f + G p (G the DG pressure gradient of Eq. rhs1);
 // writes (does not accumulate).  N velocity, NP pressure nodes per direction.
-template <int DIM, int N, int NP, int CPB>
+template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
-    mass_grad_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
-                     const __grid_constant__ Tab1D<double> tp,
-                     const __grid_constant__ MixTab<double> mx, double mass,
-                     const double* __restrict__ u_mass, const double* __restrict__ f,
+    mass_grad_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
+                     const __grid_constant__ Tab1D<A> tp, const __grid_constant__ MixTab<A> mx,
+                     double mass_d, const double* __restrict__ u_mass, const double* __restrict__ f,
                      const double* __restrict__ p, double* __restrict__ rhs) {
+  using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
   constexpr int NBP = Sh<NP, DIM>::NB;
-  __shared__ double s_p[CPB][NBP];
-  __shared__ double s_g[CPB][NB];
-  __shared__ double s_pu[CPB][NB];
-  __shared__ double s_f[CPB][NFP];
+  __shared__ A s_p[CPB][NBP];
+  __shared__ A s_g[CPB][NB];
+  __shared__ A s_pu[CPB][NB];
+  __shared__ A s_f[CPB][NFP];
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
+  const A zero = Ar::c(0.0), half = Ar::c(0.5), mass = Ar::from(mass_d);
   int ci[3] = {0, 0, 0};
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  double h[3] = {1, 1, 1}, W = 0;
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, W = zero;
   if (active) {
     cell_coords(g, cell, ci);
-    for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
-    W = 1.0;
-    for (int b = 0; b < DIM; ++b) W *= tb.w[ii[b]] * h[b];
-    if (p && node < NBP) s_p[cl][node] = p[cell * NBP + node];
+    for (int b = 0; b < DIM; ++b) h[b] = Ar::from(g.h[b][ci[b]]);
+    W = Ar::c(1.0);
+    for (int b = 0; b < DIM; ++b) W = W * tb.w[ii[b]] * h[b];
+    if (p && node < NBP) s_p[cl][node] = Ar::from(p[cell * NBP + node]);
   }
   __syncthreads();
   if (active && p) {
     // p at the velocity nodes (exact: Q_{k-1} lies in Q_k)
-    double pu = 0.0;
+    A pu = zero;
     for (int j = 0; j < NBP; ++j) {
       const int j0 = j % NP, j1 = (j / NP) % NP, j2 = DIM == 3 ? j / (NP * NP) : 0;
-      double wgt = mx.I[ii[0]][j0] * mx.I[ii[1]][j1];
-      if (DIM == 3) wgt *= mx.I[ii[2]][j2];
+      A wgt = mx.I[ii[0]][j0] * mx.I[ii[1]][j1];
+      if (DIM == 3) wgt = wgt * mx.I[ii[2]][j2];
       pu += wgt * s_p[cl][j];
     }
     s_pu[cl][node] = pu;
@@ -236,55 +255,55 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   if (active && p) {
     for (int fp = node; fp < NFP; fp += NB) {
       const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
-      const double sgn = s ? 1.0 : -1.0;
+      const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
       const int64_t nb = neighbour(g, ci, ax, s);
-      double wt = 1.0;
+      A wt = Ar::c(1.0);
       int tb3[3] = {0, 0, 0};
       {
         int tt = t;
         for (int b = 0; b < DIM; ++b) {
           if (b == ax) continue;
           tb3[b] = tt % N;
-          wt *= tb.w[tt % N] * h[b];
+          wt = wt * tb.w[tt % N] * h[b];
           tt /= N;
         }
       }
-      double pin = 0.0;
+      A pin = zero;
       for (int i = 0; i < N; ++i) pin += tb.L[s][i] * s_pu[cl][nodeof(N, DIM, ax, i, t)];
-      double pav = pin;
+      A pav = pin;
       if (nb >= 0) {
-        double pout = 0.0;
+        A pout = zero;
         for (int j = 0; j < NBP; ++j) {
           const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
-          double wgt = tp.L[1 - s][jj[ax]];
+          A wgt = tp.L[1 - s][jj[ax]];
           for (int b = 0; b < DIM; ++b)
-            if (b != ax) wgt *= mx.I[tb3[b]][jj[b]];
-          pout += wgt * __ldg(&p[nb * NBP + j]);
+            if (b != ax) wgt = wgt * mx.I[tb3[b]][jj[b]];
+          pout += wgt * Ar::from(__ldg(&p[nb * NBP + j]));
         }
-        pav = 0.5 * (pin + pout);
+        pav = half * (pin + pout);
       }
-      s_f[cl][fp] = -wt * sgn * pav;
+      s_f[cl][fp] = -(wt * sgn * pav);
     }
   }
   __syncthreads();
   if (active) {
     for (int c = 0; c < DIM; ++c) {
       const int64_t o = (int64_t)c * g.ncell * NB + cell * NB + node;
-      double y = 0.0;
-      if (u_mass) y += mass * W * u_mass[o];
-      if (f) y += W * f[o];
+      A y = zero;
+      if (u_mass) y += mass * W * Ar::from(u_mass[o]);
+      if (f) y += W * Ar::from(f[o]);
       if (p) {
-        double acc = 0.0;
+        A acc = zero;
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[c] = m;
           acc += tb.D[m][ii[c]] * s_g[cl][j[0] + N * (j[1] + N * j[2])];
         }
-        y += acc * g.hi[c][ci[c]];
+        y += acc * Ar::from(g.hi[c][ci[c]]);
         const int t = tangof(N, DIM, c, ii);
         for (int s = 0; s < 2; ++s) y += s_f[cl][(2 * c + s) * NF + t] * tb.L[s][ii[c]];
       }
-      rhs[o] = y;
+      rhs[o] = Ar::to_d(y);
     }
   }
 }
@@ -293,53 +312,55 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 // rhs_p = alpha M^p p_old + (1/tau) sum_c D_c uss_c, one thread per pressure
 // node; D the DG divergence of Eq. weakform_p_1, integrated with the
 // velocity rule.
-template <int DIM, int N, int NP, int CPB>
+template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
-    pressure_rhs_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<double> tb,
-                        const __grid_constant__ Tab1D<double> tp,
-                        const __grid_constant__ MixTab<double> mx, double alpha, double inv_tau,
-                        const double* __restrict__ uss, const double* __restrict__ p_old,
-                        double* __restrict__ rhs) {
+    pressure_rhs_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
+                        const __grid_constant__ Tab1D<A> tp, const __grid_constant__ MixTab<A> mx,
+                        double alpha_d, double inv_tau_d, const double* __restrict__ uss,
+                        const double* __restrict__ p_old, double* __restrict__ rhs) {
+  using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
   constexpr int NBP = Sh<NP, DIM>::NB;
-  __shared__ double s_u[DIM][CPB][NB];
-  __shared__ double s_f[CPB][NFP];
+  __shared__ A s_u[DIM][CPB][NB];
+  __shared__ A s_f[CPB][NFP];
   const int tid = threadIdx.x, cl = tid / NBP, node = tid % NBP;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
+  const A zero = Ar::c(0.0), half = Ar::c(0.5);
   int ci[3] = {0, 0, 0};
-  double h[3] = {1, 1, 1};
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
   if (active) {
     cell_coords(g, cell, ci);
-    for (int b = 0; b < DIM; ++b) h[b] = g.h[b][ci[b]];
+    for (int b = 0; b < DIM; ++b) h[b] = Ar::from(g.h[b][ci[b]]);
     for (int idx = node; idx < DIM * NB; idx += NBP) {
       const int c = idx / NB, nd = idx % NB;
-      s_u[c][cl][nd] = uss[((int64_t)c * g.ncell + cell) * NB + nd];
+      s_u[c][cl][nd] = Ar::from(uss[((int64_t)c * g.ncell + cell) * NB + nd]);
     }
   }
   __syncthreads();
   if (active) {
     for (int fp = node; fp < NFP; fp += NBP) {
       const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
-      const double sgn = s ? 1.0 : -1.0;
+      const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
       const int64_t nb = neighbour(g, ci, ax, s);
-      double wt = 1.0;
+      A wt = Ar::c(1.0);
       {
         int tt = t;
         for (int b = 0; b < DIM; ++b) {
           if (b == ax) continue;
-          wt *= tb.w[tt % N] * h[b];
+          wt = wt * tb.w[tt % N] * h[b];
           tt /= N;
         }
       }
-      double uin = 0.0;
+      A uin = zero;
       for (int i = 0; i < N; ++i) uin += tb.L[s][i] * s_u[ax][cl][nodeof(N, DIM, ax, i, t)];
-      double uav = uin;
+      A uav = uin;
       if (nb >= 0) {
-        double uout = 0.0;
+        A uout = zero;
         for (int i = 0; i < N; ++i)
-          uout += tb.L[1 - s][i] * __ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)]);
-        uav = 0.5 * (uin + uout);
+          uout += tb.L[1 - s][i] *
+                  Ar::from(__ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)]));
+        uav = half * (uin + uout);
       }
       s_f[cl][fp] = wt * sgn * uav;
     }
@@ -347,24 +368,24 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
   __syncthreads();
   if (active) {
     const int pi[3] = {node % NP, (node / NP) % NP, DIM == 3 ? node / (NP * NP) : 0};
-    double Wp = 1.0, hiv[3] = {1, 1, 1};
+    A Wp = Ar::c(1.0), hiv[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
     for (int b = 0; b < DIM; ++b) {
-      Wp *= tp.w[pi[b]] * h[b];
-      hiv[b] = g.hi[b][ci[b]];
+      Wp = Wp * tp.w[pi[b]] * h[b];
+      hiv[b] = Ar::from(g.hi[b][ci[b]]);
     }
-    double acc = 0.0;
+    A acc = zero;
     // cell term: sum over velocity quadrature points of W u_c d_c psi_i
     for (int q = 0; q < NB; ++q) {
       const int qq[3] = {q % N, (q / N) % N, DIM == 3 ? q / (N * N) : 0};
-      double Wq = 1.0, v[DIM];
+      A Wq = Ar::c(1.0), v[DIM];
       for (int b = 0; b < DIM; ++b) {
-        Wq *= tb.w[qq[b]] * h[b];
+        Wq = Wq * tb.w[qq[b]] * h[b];
         v[b] = mx.I[qq[b]][pi[b]];
       }
       for (int c = 0; c < DIM; ++c) {
-        double dpsi = mx.D[qq[c]][pi[c]] * hiv[c];
+        A dpsi = mx.D[qq[c]][pi[c]] * hiv[c];
         for (int b = 0; b < DIM; ++b)
-          if (b != c) dpsi *= v[b];
+          if (b != c) dpsi = dpsi * v[b];
         acc += Wq * s_u[c][cl][q] * dpsi;
       }
     }
@@ -372,47 +393,49 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
     for (int fc = 0; fc < 2 * DIM; ++fc) {
       const int ax = fc >> 1, s = fc & 1;
       for (int t = 0; t < NF; ++t) {
-        double psi = tp.L[s][pi[ax]];
+        A psi = tp.L[s][pi[ax]];
         int tt = t;
         for (int b = 0; b < DIM; ++b) {
           if (b == ax) continue;
-          psi *= mx.I[tt % N][pi[b]];
+          psi = psi * mx.I[tt % N][pi[b]];
           tt /= N;
         }
         acc -= s_f[cl][fc * NF + t] * psi;
       }
     }
-    rhs[cell * NBP + node] = alpha * Wp * p_old[cell * NBP + node] + inv_tau * acc;
+    rhs[cell * NBP + node] =
+        Ar::to_d(Ar::from(alpha_d) * Wp * Ar::from(p_old[cell * NBP + node]) + Ar::from(inv_tau_d) * acc);
   }
 }
 
 // ------------------------------------------------------------------
 // u~_c = M^-1 P_c p: the broken gradient of p at the velocity nodes (exact
 // on affine cells, where M is diagonal and P_c p = W d_c p at the nodes).
-template <int DIM, int N, int NP, int CPB>
+template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
-    project_kernel(const __grid_constant__ Grid g, const __grid_constant__ MixTab<double> mx,
+    project_kernel(const __grid_constant__ Grid g, const __grid_constant__ MixTab<A> mx,
                    const double* __restrict__ p, double* __restrict__ ut) {
+  using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NBP = Sh<NP, DIM>::NB;
-  __shared__ double s_p[CPB][NBP];
+  __shared__ A s_p[CPB][NBP];
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
-  if (active && node < NBP) s_p[cl][node] = p[cell * NBP + node];
+  if (active && node < NBP) s_p[cl][node] = Ar::from(p[cell * NBP + node]);
   __syncthreads();
   if (!active) return;
   int ci[3];
   cell_coords(g, cell, ci);
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
   for (int c = 0; c < DIM; ++c) {
-    double acc = 0.0;
+    A acc = Ar::c(0.0);
     for (int j = 0; j < NBP; ++j) {
       const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
-      double wgt = 1.0;
-      for (int b = 0; b < DIM; ++b) wgt *= b == c ? mx.D[ii[b]][jj[b]] : mx.I[ii[b]][jj[b]];
+      A wgt = b0_or(c == 0, mx.D[ii[0]][jj[0]], mx.I[ii[0]][jj[0]]);
+      for (int b = 1; b < DIM; ++b) wgt = wgt * (b == c ? mx.D[ii[b]][jj[b]] : mx.I[ii[b]][jj[b]]);
       acc += wgt * s_p[cl][j];
     }
-    ut[((int64_t)c * g.ncell + cell) * NB + node] = acc * g.hi[c][ci[c]];
+    ut[((int64_t)c * g.ncell + cell) * NB + node] = Ar::to_d(acc * Ar::from(g.hi[c][ci[c]]));
   }
 }
 
@@ -518,18 +541,57 @@ constexpr int cpb_for() {
   return Sh<N, DIM>::NB <= 8 ? 16 : (Sh<N, DIM>::NB <= 27 ? 8 : (Sh<N, DIM>::NB <= 64 ? 4 : 2));
 }
 
-template <int DIM, int N>
-dg_status run_explicit(const dg_mesh* m, int mode, double visc, double adv, const double* w,
-                       const double* wb, double* rhs, cudaStream_t s) {
+template <typename A>
+const Tab1D<A>& tab_u(const dg_mesh* m);
+template <>
+const Tab1D<double>& tab_u<double>(const dg_mesh* m) { return m->tu64; }
+template <>
+const Tab1D<df64>& tab_u<df64>(const dg_mesh* m) { return m->tudf; }
+template <typename A>
+const Tab1D<A>& tab_p(const dg_mesh* m);
+template <>
+const Tab1D<double>& tab_p<double>(const dg_mesh* m) { return m->tp64; }
+template <>
+const Tab1D<df64>& tab_p<df64>(const dg_mesh* m) { return m->tpdf; }
+template <typename A>
+const MixTab<A>& tab_mix(const dg_mesh* m);
+template <>
+const MixTab<double>& tab_mix<double>(const dg_mesh* m) { return m->mix64; }
+template <>
+const MixTab<df64>& tab_mix<df64>(const dg_mesh* m) { return m->mixdf; }
+
+template <typename A, int DIM, int N>
+dg_status run_explicit_a(const dg_mesh* m, int mode, double visc, double adv, const double* w,
+                         const double* wb, double* rhs, cudaStream_t s) {
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
   const Grid g = make_grid<DIM>(m);
   const double pen = (double)(N * N);
   if (mode == 0)
-    explicit_kernel<DIM, N, 0, CPB><<<blocks, threads, 0, s>>>(g, m->tu64, visc, adv, pen, w, wb, rhs);
+    explicit_kernel<A, DIM, N, 0, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), visc, adv, pen, w, wb, rhs);
   else
-    explicit_kernel<DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(g, m->tu64, visc, adv, pen, w, wb, rhs);
+    explicit_kernel<A, DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), visc, adv, pen, w, wb, rhs);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <int DIM, int N>
+dg_status run_explicit(const dg_mesh* m, int mode, double visc, double adv, const double* w,
+                       const double* wb, double* rhs, cudaStream_t s) {
+  return m->fp64_arith ? run_explicit_a<double, DIM, N>(m, mode, visc, adv, w, wb, rhs, s)
+                       : run_explicit_a<df64, DIM, N>(m, mode, visc, adv, w, wb, rhs, s);
+}
+
+template <typename A, int DIM, int N>
+dg_status run_mass_grad_a(const dg_mesh* m, double mass, const double* um, const double* f,
+                          const double* p, double* rhs, cudaStream_t s) {
+  constexpr int CPB = cpb_for<N, DIM>();
+  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
+  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  mass_grad_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(
+      make_grid<DIM>(m), tab_u<A>(m), tab_p<A>(m), tab_mix<A>(m), mass, um, f, p, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -538,11 +600,20 @@ dg_status run_explicit(const dg_mesh* m, int mode, double visc, double adv, cons
 template <int DIM, int N>
 dg_status run_mass_grad(const dg_mesh* m, double mass, const double* um, const double* f,
                         const double* p, double* rhs, cudaStream_t s) {
-  constexpr int CPB = cpb_for<N, DIM>();
-  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
+  return m->fp64_arith ? run_mass_grad_a<double, DIM, N>(m, mass, um, f, p, rhs, s)
+                       : run_mass_grad_a<df64, DIM, N>(m, mass, um, f, p, rhs, s);
+}
+
+template <typename A, int DIM, int N>
+dg_status run_pressure_rhs_a(const dg_mesh* m, double alpha, double inv_tau, const double* uss,
+                             const double* p_old, double* rhs, cudaStream_t s) {
+  constexpr int NP = N - 1;
+  constexpr int CPB = cpb_for<NP, DIM>();
+  constexpr int threads = ((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  mass_grad_kernel<DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), m->tu64, m->tp64,
-                                                                 m->mix64, mass, um, f, p, rhs); count_launch();
+  pressure_rhs_kernel<A, DIM, N, NP, CPB><<<blocks, threads, 0, s>>>(
+      make_grid<DIM>(m), tab_u<A>(m), tab_p<A>(m), tab_mix<A>(m), alpha, inv_tau, uss, p_old, rhs);
+  count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -550,24 +621,25 @@ dg_status run_mass_grad(const dg_mesh* m, double mass, const double* um, const d
 template <int DIM, int N>
 dg_status run_pressure_rhs(const dg_mesh* m, double alpha, double inv_tau, const double* uss,
                            const double* p_old, double* rhs, cudaStream_t s) {
-  constexpr int NP = N - 1;
-  constexpr int CPB = cpb_for<NP, DIM>();
-  constexpr int threads = ((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32;
+  return m->fp64_arith ? run_pressure_rhs_a<double, DIM, N>(m, alpha, inv_tau, uss, p_old, rhs, s)
+                       : run_pressure_rhs_a<df64, DIM, N>(m, alpha, inv_tau, uss, p_old, rhs, s);
+}
+
+template <typename A, int DIM, int N>
+dg_status run_project_a(const dg_mesh* m, const double* p, double* ut, cudaStream_t s) {
+  constexpr int CPB = cpb_for<N, DIM>();
+  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  pressure_rhs_kernel<DIM, N, NP, CPB><<<blocks, threads, 0, s>>>(
-      make_grid<DIM>(m), m->tu64, m->tp64, m->mix64, alpha, inv_tau, uss, p_old, rhs); count_launch();
+  project_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_mix<A>(m), p, ut);
+  count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 template <int DIM, int N>
 dg_status run_project(const dg_mesh* m, const double* p, double* ut, cudaStream_t s) {
-  constexpr int CPB = cpb_for<N, DIM>();
-  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
-  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  project_kernel<DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), m->mix64, p, ut); count_launch();
-  DG_CUDA(cudaGetLastError());
-  return DG_OK;
+  return m->fp64_arith ? run_project_a<double, DIM, N>(m, p, ut, s)
+                       : run_project_a<df64, DIM, N>(m, p, ut, s);
 }
 
 template <int DIM, int N>

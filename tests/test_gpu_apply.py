@@ -149,3 +149,29 @@ def test_bad_arguments_are_rejected():
         b.dg_apply_poisson(gm.handle, 1.0, x, x)          # aliasing
     with pytest.raises(b.DGError):
         b.dg_apply_momentum(gm.handle, b.momentum_coeffs(1, 1, 1), None, x, x)
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1e-12, 1e12, 1e25])
+def test_float_float_apply_keeps_relative_accuracy_over_magnitudes(scale):
+    """The FP64-accurate applies split doubles into float pairs with integer
+    operations; the operators are linear, so inputs scaled over 50 orders of
+    magnitude keep the 1e-12 relative parity."""
+    from paper_2107_07776_gb300 import binding as b
+    gm, om = meshes(CASES[4])
+    x = W.random_vector(om.n_p, 500) * scale
+    ref = 2.9 * om.assemble("mass_p").apply(x) + om.assemble("sipg_p").apply(x)
+    y = torch.empty(om.n_p, dtype=torch.float64, device="cuda")
+    b.dg_apply_poisson(gm.handle, 2.9, dev(x), y)
+    torch.cuda.synchronize()
+    assert rel_err(y.cpu().numpy(), ref) < 1e-12
+    d = om.dim
+    xu = W.random_vector(d * om.n_u, 501) * scale
+    ub = W.random_vector(d * om.n_u, 502)
+    M, A, C = om.assemble("mass_u"), om.assemble("sipg_u"), om.assemble("adv_u", ub)
+    ref = np.concatenate([300.0 * M.apply(xu[i * om.n_u:(i + 1) * om.n_u])
+                          + 0.01 * A.apply(xu[i * om.n_u:(i + 1) * om.n_u])
+                          + 0.5 * C.apply(xu[i * om.n_u:(i + 1) * om.n_u]) for i in range(d)])
+    yu = torch.empty(d * om.n_u, dtype=torch.float64, device="cuda")
+    b.dg_apply_momentum(gm.handle, b.momentum_coeffs(300.0, 0.01, 0.5), dev(ub), dev(xu), yu)
+    torch.cuda.synchronize()
+    assert rel_err(yu.cpu().numpy(), ref) < 1e-12
