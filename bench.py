@@ -119,16 +119,6 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def initial_state(w, X, Xp):
-    if w.name.startswith("tgv"):
-        return W.tgv3d_u(*X), W.tgv3d_p(*Xp)
-    if w.name == "tg2d":
-        return W.tg2d_u(*X, 0.0, 1.0 / w.Re), W.tg2d_p(*Xp, 0.0, 1.0 / w.Re)
-    if w.name == "channel":
-        return W.channel_u0(*X), np.zeros(Xp.shape[1])
-    return np.zeros((w.dim, X.shape[1])), np.zeros(Xp.shape[1])
-
-
 def step_params(b, w, precond, guess, tol=1e-8):
     prm = b.dg_step_params()
     prm.dt, prm.gamma, prm.extrapolate = w.dt, 0.0, 1
@@ -162,7 +152,7 @@ def run_ours(args, rank, world):
         autotune = json.loads(b.dg_autotune_report(mesh.handle))
     X = mesh.node_coords(0).cpu().numpy()
     Xp = mesh.node_coords(1).cpu().numpy()
-    u0h, p0h = initial_state(w, X, Xp)
+    u0h, p0h = W.initial_state(w, X, Xp)
     u0 = torch.tensor(u0h.reshape(-1), dtype=torch.float64, device=dev)
     p0 = torch.tensor(p0h, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -192,9 +182,13 @@ def run_ours(args, rank, world):
         launches0 = b.dg_kernel_launches()
         for i in range(nsteps):
             flush.fill_(i & 0xFF)
+            if sample_clocks and args.profile_step and i == 0:
+                torch.cuda.profiler.start()
             ev[i][0].record(stream)
             info = b.trbdf2_step(s, prm, u, p)
             ev[i][1].record(stream)
+            if sample_clocks and args.profile_step and i == 0:
+                torch.cuda.profiler.stop()
             iters.append([x.iterations for x in info])
         launches = b.dg_kernel_launches() - launches0
         torch.cuda.synchronize()
@@ -291,7 +285,8 @@ def run_ours(args, rank, world):
     fl = w.dim * mesh.n_cells * apply_flops_per_cell(w.dim, w.degree + 1, True)
     achieved = fl / (apply_ms["momentum_fp64"] * 1e-3) / 1e12
     pk, src = peaks()
-    roof = {"bound": "alu", "kernel": "scalar_op_kernel<double> (momentum apply)",
+    roof = {"bound": "alu",
+            "kernel": "scalar_op_kernel<double,df64> (momentum apply, float-float FP64 arithmetic)",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
             "peak_source": "measured FP64 FMA probe (DESIGN.md)",
@@ -314,7 +309,7 @@ def oracle_step_rate(w, budget_s: float = 15.0, n_small: int = 4):
     om = OMesh(ws.dim, list(ws.n), list(ws.lo), list(ws.hi), list(ws.periodic), ws.degree,
                map=ws.map, map_param=list(ws.map_param))
     X, Xp = om.node_coords(), om.node_coords(True)
-    u, p = initial_state(ws, X, Xp)
+    u, p = W.initial_state(ws, X, Xp)
     uh = u.copy()
     t0 = time.perf_counter()
     st = Stepper(om, ws.Re, c=ws.c)
@@ -348,6 +343,9 @@ def main():
                     help="ncu DRAM bytes per launch of the dominant kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="bracket the first timed step with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

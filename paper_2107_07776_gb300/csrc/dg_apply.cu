@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "dg_apply_kernel.cuh"
+#include "dg_general_kernel.cuh"
 
 namespace dg {
 
@@ -37,6 +38,93 @@ DG_DECL_LAUNCH(launch_df_3d, double, df64)
 DG_DECL_LAUNCH(launch_f32_2d, float, float)
 DG_DECL_LAUNCH(launch_f32_3d, float, float)
 #undef DG_DECL_LAUNCH
+#define DG_DECL_GEN(NAME, T, A)                                                            \
+  dg_status NAME(int kind, int N, const GenArgs<T>& a, const Tab1D<A>& tb, const T* ub, \
+                 const T* src, T* dst, cudaStream_t s);
+DG_DECL_GEN(gen_f64_2d, double, double)
+DG_DECL_GEN(gen_f64_3d, double, double)
+DG_DECL_GEN(gen_df_2d, double, df64)
+DG_DECL_GEN(gen_df_3d, double, df64)
+DG_DECL_GEN(gen_f32_2d, float, float)
+DG_DECL_GEN(gen_f32_3d, float, float)
+#undef DG_DECL_GEN
+
+template <typename T>
+struct GeomPtr;
+template <>
+struct GeomPtr<double> {
+  static const double* vol(const dg_mesh* m, bool p) { return p ? m->gvp64 : m->gvu64; }
+  static const double* face(const dg_mesh* m, bool p) { return p ? m->gfp64 : m->gfu64; }
+  static const double* pen(const dg_mesh* m) { return m->gpen64; }
+};
+template <>
+struct GeomPtr<float> {
+  static const float* vol(const dg_mesh* m, bool p) { return p ? m->gvp32 : m->gvu32; }
+  static const float* face(const dg_mesh* m, bool p) { return p ? m->gfp32 : m->gfu32; }
+  static const float* pen(const dg_mesh* m) { return m->gpen32; }
+};
+
+static dg_status dispatch_general(const dg_mesh* m, bool pressure, int kind, int N,
+                                  const GenArgs<double>& a, const double* ub, const double* src,
+                                  double* dst, cudaStream_t s) {
+  if (m->fp64_arith == 0) {
+    const Tab1D<df64>& tb = pressure ? m->tpdf : m->tudf;
+    return m->dim == 2 ? gen_df_2d(kind, N, a, tb, ub, src, dst, s)
+                       : gen_df_3d(kind, N, a, tb, ub, src, dst, s);
+  }
+  const Tab1D<double>& tb = pressure ? m->tp64 : m->tu64;
+  return m->dim == 2 ? gen_f64_2d(kind, N, a, tb, ub, src, dst, s)
+                     : gen_f64_3d(kind, N, a, tb, ub, src, dst, s);
+}
+
+static dg_status dispatch_general(const dg_mesh* m, bool pressure, int kind, int N,
+                                  const GenArgs<float>& a, const float* ub, const float* src,
+                                  float* dst, cudaStream_t s) {
+  const Tab1D<float>& tb = pressure ? m->tp32 : m->tu32;
+  return m->dim == 2 ? gen_f32_2d(kind, N, a, tb, ub, src, dst, s)
+                     : gen_f32_3d(kind, N, a, tb, ub, src, dst, s);
+}
+
+// the operator on trilinear cells (metric terms of dg_geom.cuh)
+template <typename T>
+static dg_status launch_general_op(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
+                                   const T* ubar, const T* src, T* dst, int ncomp,
+                                   const OpArgs<T>* cheb, cudaStream_t s) {
+  if (!pressure && !m->geom_u) {
+    set_error("operator apply: velocity metric terms missing on this mesh");
+    return DG_EINVAL;
+  }
+  GenArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.ncell = m->ncell;
+  a.n0 = m->n[0];
+  a.n1 = m->n[1];
+  a.n2 = m->n[2];
+  a.per0 = m->periodic[0];
+  a.per1 = m->periodic[1];
+  a.per2 = m->periodic[2];
+  a.gv = GeomPtr<T>::vol(m, pressure);
+  a.gf = GeomPtr<T>::face(m, pressure);
+  a.gpen = GeomPtr<T>::pen(m);
+  a.mass = mass;
+  a.visc = visc;
+  a.adv = adv;
+  // SIP penalty factor: (k+1)^2 velocity, k^2 pressure (k the velocity degree)
+  a.pen = pressure ? (T)(m->k * m->k) : (T)((m->k + 1) * (m->k + 1));
+  a.walls = pressure ? 0 : 1;
+  a.ncomp = ncomp;
+  if (cheb) {
+    a.cheb = 1;
+    a.cx = cheb->cx;
+    a.cr = cheb->cr;
+    a.cdinv = cheb->cdinv;
+    a.cc1 = cheb->cc1;
+    a.cc2 = cheb->cc2;
+  }
+  const bool use_adv = !pressure && ubar != nullptr && adv != T(0);
+  const int kind = pressure ? 0 : (use_adv ? 2 : 1);
+  return dispatch_general(m, pressure, kind, pressure ? m->np : m->nu, a, ubar, src, dst, s);
+}
 
 template <typename T>
 const T* axis_h(const dg_mesh* m, int a, bool inv);
@@ -107,10 +195,7 @@ template <typename T>
 static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
                                        const T* ubar, const T* src, T* dst, int ncomp,
                                        const OpArgs<T>* cheb, cudaStream_t s) {
-  if (!m->affine) {
-    set_error("operator apply: trilinear (perturbed) cells are not built in this library");
-    return DG_EUNSUPPORTED;
-  }
+  if (!m->affine) return launch_general_op<T>(m, pressure, mass, visc, adv, ubar, src, dst, ncomp, cheb, s);
   OpArgs<T> a;
   a.ncell = m->ncell;
   a.n0 = m->n[0];
@@ -163,6 +248,11 @@ static int cpb_for_mesh(const dg_mesh* m, bool pressure, bool adv, int v) {
 // depend on the choice: each output is computed by one thread in a fixed
 // order whatever the number of cells per CTA.
 dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
+  if (!m->affine) {  // trilinear cells: one tile shape per kernel, nothing to choose
+    m->tuned = true;
+    m->tune_report = "[]";
+    return DG_OK;
+  }
   const int64_t nu = m->ncell * m->nbu * m->dim, np = m->ncell * m->nbp;
   void* buf = nullptr;
   const size_t bytes = sizeof(double) * (size_t)(3 * nu + 2 * np);

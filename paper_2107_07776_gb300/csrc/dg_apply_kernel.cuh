@@ -40,15 +40,20 @@ struct OpArgs {
 };
 
 __device__ __forceinline__ int node_of(int N, int a, int i, int t, int dim) {
-  // node index with coordinate i along axis a and tangential index t
-  int idx[3] = {0, 0, 0};
-  idx[a] = i;
-  for (int b = 0; b < dim; ++b) {
-    if (b == a) continue;
-    idx[b] = t % N;
-    t /= N;
-  }
-  return idx[0] + N * (idx[1] + N * idx[2]);
+  // node index with coordinate i along axis a and tangential index t (the
+  // other axes in increasing order, t = t0 + N t1); no local arrays, so a
+  // run-time axis costs no local-memory traffic
+  if (dim == 2) return a == 0 ? i + N * t : t + N * i;
+  return a == 0 ? i + N * t : (a == 1 ? t % N + N * (i + N * (t / N)) : t + N * N * i);
+}
+
+// v[ax] for a run-time axis without a local-memory array access
+template <int DIM, typename X>
+__device__ __forceinline__ X pick(const X (&v)[DIM], int ax) {
+  return ax == 0 ? v[0] : (ax == 1 || DIM == 2 ? v[1] : v[DIM - 1]);
+}
+__device__ __forceinline__ int pick3(int ax, int v0, int v1, int v2) {
+  return ax == 0 ? v0 : (ax == 1 ? v1 : v2);
 }
 
 template <int N, int DIM>
@@ -108,9 +113,6 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
       for (int b = 0; b < DIM; ++b) s_ub[b][cl][node] = Ar::from(ub[((int64_t)b * a.ncell + cell) * NB + node]);
     }
   }
-  const int nn[3] = {a.n0, a.n1, a.n2};
-  const int per[3] = {a.per0, a.per1, a.per2};
-
   for (int c = 0; c < a.ncomp; ++c) {
     const T* srcc = src + (int64_t)c * a.ncell * NB;
     if (active) s_u[cl][node] = Ar::from(srcc[cell * NB + node]);
@@ -135,17 +137,20 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
         const int f = fp / NF, t = fp - (fp / NF) * NF;
         const int ax = f >> 1, s = f & 1;
         const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
-        // neighbour across this face
-        int nc[3] = {ci[0], ci[1], ci[2]};
-        nc[ax] += s ? 1 : -1;
+        // neighbour across this face (selects instead of run-time indexed
+        // arrays: no local memory)
+        const int cax = pick3(ax, ci[0], ci[1], ci[2]);
+        const int nax = pick3(ax, a.n0, a.n1, a.n2);
+        const int64_t cstr = ax == 0 ? 1 : (ax == 1 ? (int64_t)a.n0 : (int64_t)a.n0 * a.n1);
+        int cn = cax + (s ? 1 : -1);
         bool interior = true;
-        if (nc[ax] < 0 || nc[ax] >= nn[ax]) {
-          if (per[ax]) nc[ax] = (nc[ax] + nn[ax]) % nn[ax];
+        if (cn < 0 || cn >= nax) {
+          if (pick3(ax, a.per0, a.per1, a.per2)) cn = cn < 0 ? nax - 1 : 0;
           else interior = false;
         }
-        const int64_t nb = (int64_t)nc[0] + (int64_t)a.n0 * (nc[1] + (int64_t)a.n1 * nc[2]);
+        const int64_t nb = cell + (int64_t)(cn - cax) * cstr;
         const T* hiax = ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2);
-        const A hiK = hi[ax];
+        const A hiK = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
         // tangential weight: face quadrature weight times the face measure
         A wt = Ar::c(1.0);
         {
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
         dnin = dnin * sgn * hiK;
         A fv = zero, fg = zero;
         if (interior) {
-          const A hiN = Ar::from(hiax[nc[ax]]);
+          const A hiN = Ar::from(hiax[cn]);
           A uout = zero, dnout = zero;
 #pragma unroll
           for (int i = 0; i < N; ++i) {

@@ -72,6 +72,19 @@ struct dg_mesh {
   dg::MixTab<dg::df64> mixdf;
   int fp64_arith = 0;                // FP64 operator arithmetic: 0 float-float, 1 native FP64
   int* d_status = nullptr;           // device error word
+  // metric terms of trilinear cells (dg_geom.cuh); null on affine meshes
+  double* gvu64 = nullptr;  // velocity-node volume terms
+  float* gvu32 = nullptr;
+  double* gfu64 = nullptr;  // velocity face terms
+  float* gfu32 = nullptr;
+  double* gvp64 = nullptr;  // pressure-node volume terms
+  float* gvp32 = nullptr;
+  double* gfp64 = nullptr;  // pressure face terms
+  float* gfp32 = nullptr;
+  double* gpen64 = nullptr; // penalty geometry per cell face
+  float* gpen32 = nullptr;
+  bool geom_u = false;      // velocity terms present (not on multigrid levels)
+  bool level = false;       // a multigrid level (pressure space only)
   // autotuned tile shape of the operator kernels: variant index per
   // [precision: 0 FP64, 1 FP32][operator: 0 pressure, 1 momentum, 2 momentum
   // with advection]; 1 = default cells per CTA, 0 = half, 2 = double
@@ -98,6 +111,9 @@ dg_status cuda_fail(cudaError_t e, const char* where);
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 dg_status finish_mesh(dg_mesh* m, cudaStream_t s);
+// mapped lattice vertex L of a mesh description; Gauss-Legendre rule on [0,1]
+void lattice_vertex(const dg_mesh_desc& d, const int L[3], double X[3]);
+void gauss_legendre_01(int n, double* x, double* w);
 dg_status make_level_mesh(const dg_mesh* fine, const int coarsen[3], int degree_u, cudaStream_t s,
                           dg_mesh** out);
 

@@ -71,7 +71,32 @@ __device__ __forceinline__ df64 df_from(double x) {
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double df_to(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// Split of a constant: plain casts (round to nearest, like the intrinsics
+// above) that the compiler folds for literal arguments, so constants cost no
+// conversion instruction at run time.
+__device__ __forceinline__ df64 df_const(double x) {
+  const float h = static_cast<float>(x);
+  return {h, static_cast<float>(x - static_cast<double>(h))};
+}
+
+// Exact widening of a float to double with integer operations (no FP64-pipe
+// conversion): the sign is kept, the exponent rebiased (127 -> 1023) and the
+// 23 fraction bits moved to the top of the 52.  Zeros are built directly;
+// subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double df_widen(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sgn);
+  if (e == 0u || e == 0xFFu) return (double)f;
+  const unsigned long long bits =
+      sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// hi + lo rounded once to double (a single FP64 addition)
+__device__ __forceinline__ double df_to(df64 a) { return df_widen(a.hi) + df_widen(a.lo); }
 
 // Split of a double into a float pair with integer operations only (no FP64
 // instruction): hi keeps the sign, exponent and leading 23 fraction bits; the
@@ -128,7 +153,7 @@ template <>
 struct Arith<df64> {
   __device__ static df64 from(double x) { return df_split(x); }
   __device__ static df64 from(float x) { return {x, 0.0f}; }
-  __device__ static df64 c(double x) { return df_from(x); }
+  __device__ static df64 c(double x) { return df_const(x); }
   __device__ static df64 abs(df64 x) { return df_abs(x); }
   __device__ static df64 max(df64 a, df64 b) { return df_max(a, b); }
   __device__ static float to_f(df64 x) { return x.hi; }

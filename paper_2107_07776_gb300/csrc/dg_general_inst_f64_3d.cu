@@ -1,0 +1,12 @@
+// Instantiation unit of the general-geometry operator kernel: storage double,
+// arithmetic double, 3D.
+#include "dg_general_kernel.cuh"
+
+namespace dg {
+
+dg_status gen_f64_3d(int kind, int N, const GenArgs<double>& a, const Tab1D<double>& tb,
+                      const double* ub, const double* src, double* dst, cudaStream_t s) {
+  return launch_general_dim<double, double, 3>(kind, N, a, tb, ub, src, dst, s);
+}
+
+}  // namespace dg

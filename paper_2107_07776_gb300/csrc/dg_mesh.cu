@@ -14,6 +14,7 @@
 #include <string>
 
 #include "dg_common.cuh"
+#include "dg_geom.cuh"
 
 namespace dg {
 
@@ -60,6 +61,15 @@ static void gauss_legendre_pm1(int n, double* z, double* w) {
     dp = n * (pnm1 - t * pn) / (1.0 - t * t);
     z[r] = t;
     w[r] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+void gauss_legendre_01(int n, double* x, double* w) {
+  double z[16], wz[16];
+  gauss_legendre_pm1(n, z, wz);
+  for (int i = 0; i < n; ++i) {
+    x[i] = 0.5 * (1.0 - z[i]);
+    w[i] = 0.5 * wz[i];
   }
 }
 
@@ -188,7 +198,7 @@ Tab1D<df64> split_tables(const Tab1D<double>& t) {
 template Tab1D<double> cast_tables<double>(const Tab1D<double>&);
 
 // Vertex of the structured lattice (lattice index L) under the mesh map.
-static void lattice_vertex(const dg_mesh_desc& d, const int L[3], double X[3]) {
+void lattice_vertex(const dg_mesh_desc& d, const int L[3], double X[3]) {
   double eta[3] = {0, 0, 0};
   for (int a = 0; a < d.dim; ++a) eta[a] = (double)L[a] / d.n_cells[a];
   for (int a = 0; a < 3; ++a) X[a] = 0.0;
@@ -260,6 +270,7 @@ dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
   cudaError_t e = cudaMalloc(&m->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "mesh status word");
+  if (!m->affine) return build_geometry(m, !m->level, s);
   return DG_OK;
 }
 
@@ -276,6 +287,7 @@ dg_status make_level_mesh(const dg_mesh* fine, const int coarsen[3], int degree_
   m->k = degree_u;
   m->desc.degree_u = degree_u;
   m->affine = fine->affine;
+  m->level = true;
   m->ncell = 1;
   for (int a = 0; a < 3; ++a) {
     m->periodic[a] = fine->periodic[a];
@@ -406,6 +418,7 @@ void dg_mesh_destroy(dg_mesh* m) {
     if (m->d_hi32[a]) cudaFree(m->d_hi32[a]);
   }
   if (m->d_status) cudaFree(m->d_status);
+  free_geometry(m);
   delete m;
 }
 

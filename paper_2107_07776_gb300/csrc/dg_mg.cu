@@ -175,14 +175,14 @@ __global__ void prolong_add_kernel(const __grid_constant__ Transfer tr, int64_t 
   }
   const int64_t cc = ci[0] + (int64_t)tr.ncoarse[0] * (ci[1] + (int64_t)tr.ncoarse[1] * ci[2]);
   const int ii[3] = {node % tr.nf, (node / tr.nf) % tr.nf, tr.dim == 3 ? node / (tr.nf * tr.nf) : 0};
-  double acc = 0.0;
+  T acc = T(0);
   for (int j = 0; j < nbc; ++j) {
     const int jj[3] = {j % tr.nc, (j / tr.nc) % tr.nc, tr.dim == 3 ? j / (tr.nc * tr.nc) : 0};
-    double w = 1.0;
-    for (int a = 0; a < tr.dim; ++a) w *= tr.M[tr.hco[a] ? bit[a] : 2][ii[a]][jj[a]];
-    acc += w * (double)xc[cc * nbc + j];
+    T w = T(1);
+    for (int a = 0; a < tr.dim; ++a) w *= transfer_w<T>(tr, tr.hco[a] ? bit[a] : 2, ii[a], jj[a]);
+    acc += w * xc[cc * nbc + j];
   }
-  xf[gid] += (T)acc;
+  xf[gid] += acc;
 }
 
 // Restriction, pass 1: part[(cc * nchild + ch) * nbc + j] = sum_i M r_f[i]
@@ -209,14 +209,14 @@ __global__ void restrict_part_kernel(const __grid_constant__ Transfer tr, int64_
       fi[a] = 2 * ci[a] + bit[a];
     }
   const int64_t fc = fi[0] + (int64_t)tr.nfine[0] * (fi[1] + (int64_t)tr.nfine[1] * fi[2]);
-  double acc = 0.0;
+  T acc = T(0);
   for (int i = 0; i < nbf; ++i) {
     const int ii[3] = {i % tr.nf, (i / tr.nf) % tr.nf, tr.dim == 3 ? i / (tr.nf * tr.nf) : 0};
-    double w = 1.0;
-    for (int a = 0; a < tr.dim; ++a) w *= tr.M[tr.hco[a] ? bit[a] : 2][ii[a]][jj[a]];
-    acc += w * (double)rf[fc * nbf + i];
+    T w = T(1);
+    for (int a = 0; a < tr.dim; ++a) w *= transfer_w<T>(tr, tr.hco[a] ? bit[a] : 2, ii[a], jj[a]);
+    acc += w * rf[fc * nbf + i];
   }
-  part[gid] = (T)acc;
+  part[gid] = acc;
 }
 
 // Restriction, pass 2: b_c = sum over the children, fixed order
@@ -509,6 +509,9 @@ dg_status MultiGrid<T>::set_alpha(double a) {
       lagrange_at(c->tp64.x, t.nc, x, v);                 // same interval
       for (int j = 0; j < t.nc; ++j) t.M[2][i][j] = v[j];
     }
+    for (int b = 0; b < 3; ++b)
+      for (int i = 0; i < kMaxN; ++i)
+        for (int j = 0; j < kMaxN; ++j) t.Mf[b][i][j] = (float)t.M[b][i][j];
     tr.push_back(t);
   }
   return DG_OK;

@@ -18,7 +18,19 @@ struct Transfer {
   int hco[3];
   int nfine[3], ncoarse[3];
   double M[3][kMaxN][kMaxN];
+  float Mf[3][kMaxN][kMaxN];  // FP32 copy for the FP32 hierarchy
 };
+
+template <typename T>
+__device__ __forceinline__ T transfer_w(const Transfer& tr, int s, int i, int j);
+template <>
+__device__ __forceinline__ double transfer_w<double>(const Transfer& tr, int s, int i, int j) {
+  return tr.M[s][i][j];
+}
+template <>
+__device__ __forceinline__ float transfer_w<float>(const Transfer& tr, int s, int i, int j) {
+  return tr.Mf[s][i][j];
+}
 
 template <typename T>
 struct MGLevel {

@@ -10,6 +10,7 @@
 // stage, not per Krylov iteration.
 #include "dg_common.cuh"
 #include "dg_df64.cuh"
+#include "dg_geom.cuh"
 
 namespace dg {
 
@@ -31,14 +32,15 @@ struct Grid {
 };
 
 __device__ __forceinline__ int nodeof(int N, int dim, int a, int i, int t) {
-  int idx[3] = {0, 0, 0};
-  idx[a] = i;
-  for (int b = 0; b < dim; ++b) {
-    if (b == a) continue;
-    idx[b] = t % N;
-    t /= N;
-  }
-  return idx[0] + N * (idx[1] + N * idx[2]);
+  // node with coordinate i along axis a and tangential index t (other axes
+  // in increasing order); array-free, so a run-time axis stays in registers
+  if (dim == 2) return a == 0 ? i + N * t : t + N * i;
+  return a == 0 ? i + N * t : (a == 1 ? t % N + N * (i + N * (t / N)) : t + N * N * i);
+}
+
+template <typename X>
+__device__ __forceinline__ X sel3(int ax, X v0, X v1, X v2) {
+  return ax == 0 ? v0 : (ax == 1 ? v1 : v2);
 }
 
 __device__ __forceinline__ int tangof(int N, int dim, int a, const int i[3]) {
@@ -56,13 +58,15 @@ __device__ __forceinline__ A b0_or(bool c, A x, A y) { return c ? x : y; }
 
 // neighbour of cell ci across face (a, s); -1 at a wall
 __device__ __forceinline__ int64_t neighbour(const Grid& g, const int ci[3], int a, int s) {
-  int nc[3] = {ci[0], ci[1], ci[2]};
-  nc[a] += s ? 1 : -1;
-  if (nc[a] < 0 || nc[a] >= g.n[a]) {
-    if (!g.per[a]) return -1;
-    nc[a] = (nc[a] + g.n[a]) % g.n[a];
+  const int ca = sel3(a, ci[0], ci[1], ci[2]), na = sel3(a, g.n[0], g.n[1], g.n[2]);
+  int cn = ca + (s ? 1 : -1);
+  if (cn < 0 || cn >= na) {
+    if (!sel3(a, g.per[0], g.per[1], g.per[2])) return -1;
+    cn = cn < 0 ? na - 1 : 0;
   }
-  return (int64_t)nc[0] + (int64_t)g.n[0] * (nc[1] + (int64_t)g.n[1] * nc[2]);
+  const int64_t stride = a == 0 ? 1 : (a == 1 ? (int64_t)g.n[0] : (int64_t)g.n[0] * g.n[1]);
+  const int64_t cell = (int64_t)ci[0] + (int64_t)g.n[0] * (ci[1] + (int64_t)g.n[1] * ci[2]);
+  return cell + (int64_t)(cn - ca) * stride;
 }
 
 __device__ __forceinline__ void cell_coords(const Grid& g, int64_t cell, int ci[3]) {
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
         const int f = fp / NF, t = fp % NF, ax = f >> 1, s = f & 1;
         const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
         const int64_t nb = neighbour(g, ci, ax, s);
-        const A hiK = hi[ax];
+        const A hiK = sel3(ax, hi[0], hi[1], hi[2]);
         A wt = Ar::c(1.0);
         {
           int tt = t;
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
           if (nb >= 0) {
             int nc3[3];
             cell_coords(g, nb, nc3);
-            const A hiN = Ar::from(g.hi[ax][nc3[ax]]);
+            const A hiN = Ar::from(sel3(ax, g.hi[0], g.hi[1], g.hi[2])[sel3(ax, nc3[0], nc3[1], nc3[2])]);
             A uout = zero, dnout = zero, wnout = zero;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
         A pout = zero;
         for (int j = 0; j < NBP; ++j) {
           const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
-          A wgt = tp.L[1 - s][jj[ax]];
+          A wgt = tp.L[1 - s][sel3(ax, jj[0], jj[1], jj[2])];
           for (int b = 0; b < DIM; ++b)
             if (b != ax) wgt = wgt * mx.I[tb3[b]][jj[b]];
           pout += wgt * Ar::from(__ldg(&p[nb * NBP + j]));
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
     for (int fc = 0; fc < 2 * DIM; ++fc) {
       const int ax = fc >> 1, s = fc & 1;
       for (int t = 0; t < NF; ++t) {
-        A psi = tp.L[s][pi[ax]];
+        A psi = tp.L[s][sel3(ax, pi[0], pi[1], pi[2])];
         int tt = t;
         for (int b = 0; b < DIM; ++b) {
           if (b == ax) continue;
@@ -669,13 +673,6 @@ dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, do
                     : (m)->nu == 4 ? FN<3, 4>(__VA_ARGS__)               \
                                    : FN<3, 5>(__VA_ARGS__)))
 
-bool check_affine(const dg_mesh* m, const char* who) {
-  if (!m->affine) {
-    set_error(std::string(who) + ": trilinear (perturbed) cells are not built in this library");
-    return false;
-  }
-  return true;
-}
 
 }  // namespace
 
@@ -683,12 +680,13 @@ bool check_affine(const dg_mesh* m, const char* who) {
 // arithmetic (it only scales the Jacobi preconditioner)
 dg_status momentum_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co, const double* ub,
                                  double* diag, cudaStream_t s) {
-  if (!check_affine(m, "momentum diagonal")) return DG_EUNSUPPORTED;
+  if (!m->affine) return general_diag(m, false, co->mass, co->visc, co->adv, ub, diag, true, s);
   return DG_DISPATCH_U(m, run_diag, m, false, co->mass, co->visc, co->adv, ub, diag, s, true);
 }
 
 // internal entry used by the solver: diagonal of a pressure-space operator
 dg_status poisson_diagonal(const dg_mesh* m, double alpha, double* diag, cudaStream_t s) {
+  if (!m->affine) return general_diag(m, true, alpha, 1.0, 0.0, nullptr, diag, false, s);
   switch (m->dim * 10 + m->np) {
     case 22: return run_diag<2, 2>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
     case 23: return run_diag<2, 3>(m, true, alpha, 1.0, 0.0, nullptr, diag, s);
@@ -712,7 +710,6 @@ dg_status dg_rhs_momentum(dg_mesh* m, const dg_momentum_rhs* d, double* rhs, voi
     set_error("dg_rhs_momentum: bad argument");
     return DG_EINVAL;
   }
-  if (!check_affine(m, "dg_rhs_momentum")) return DG_EUNSUPPORTED;
   for (int t = 0; t < d->n_terms; ++t) {
     if (!d->w[t] || (d->adv[t] != 0.0 && !d->wbar[t]) || d->w[t] == rhs || d->wbar[t] == rhs) {
       set_error("dg_rhs_momentum: bad explicit term");
@@ -728,19 +725,23 @@ dg_status dg_rhs_momentum(dg_mesh* m, const dg_momentum_rhs* d, double* rhs, voi
     return DG_EINVAL;
   }
   cudaStream_t s = as_stream(stream);
-  dg_status st = DG_DISPATCH_U(m, run_mass_grad, m, d->mass, d->u_mass, d->f, d->p, rhs, s);
+  dg_status st = m->affine ? DG_DISPATCH_U(m, run_mass_grad, m, d->mass, d->u_mass, d->f, d->p, rhs, s)
+                           : general_mass_grad(m, d->mass, d->u_mass, d->f, d->p, rhs, s);
   if (st != DG_OK) return st;
   for (int t = 0; t < d->n_terms; ++t) {
     // a term without advection still needs a field for the shared-memory
     // staging; the term's own w stands in (multiplied by adv = 0)
     const double* wb = d->wbar[t] ? d->wbar[t] : d->w[t];
-    st = DG_DISPATCH_U(m, run_explicit, m, 0, d->visc[t], d->adv[t], d->w[t], wb, rhs, s);
+    st = m->affine ? DG_DISPATCH_U(m, run_explicit, m, 0, d->visc[t], d->adv[t], d->w[t], wb, rhs, s)
+                   : general_explicit(m, 0, d->visc[t], d->adv[t], d->w[t], wb, rhs, s);
     if (st != DG_OK) return st;
   }
   bool walls = false;
   for (int a = 0; a < m->dim; ++a) walls |= !m->periodic[a];
   if (d->uD && walls) {
-    st = DG_DISPATCH_U(m, run_explicit, m, 1, d->dir_visc, d->dir_adv, d->uD, d->ubar, rhs, s);
+    st = m->affine
+             ? DG_DISPATCH_U(m, run_explicit, m, 1, d->dir_visc, d->dir_adv, d->uD, d->ubar, rhs, s)
+             : general_explicit(m, 1, d->dir_visc, d->dir_adv, d->uD, d->ubar, rhs, s);
     if (st != DG_OK) return st;
   }
   return DG_OK;
@@ -751,7 +752,7 @@ dg_status dg_project_gradient(dg_mesh* m, const double* p, double* ut, void* str
     set_error("dg_project_gradient: bad argument");
     return DG_EINVAL;
   }
-  if (!check_affine(m, "dg_project_gradient")) return DG_EUNSUPPORTED;
+  if (!m->affine) return general_project(m, p, ut, as_stream(stream));
   return DG_DISPATCH_U(m, run_project, m, p, ut, as_stream(stream));
 }
 
@@ -761,7 +762,7 @@ dg_status dg_rhs_pressure(dg_mesh* m, double alpha, double tau, const double* us
     set_error("dg_rhs_pressure: bad argument");
     return DG_EINVAL;
   }
-  if (!check_affine(m, "dg_rhs_pressure")) return DG_EUNSUPPORTED;
+  if (!m->affine) return general_pressure_rhs(m, alpha, 1.0 / tau, uss, p_old, rhs, as_stream(stream));
   return DG_DISPATCH_U(m, run_pressure_rhs, m, alpha, 1.0 / tau, uss, p_old, rhs, as_stream(stream));
 }
 
@@ -771,7 +772,8 @@ dg_status dg_momentum_diagonal(dg_mesh* m, const dg_momentum_coeffs* co, const d
     set_error("dg_momentum_diagonal: bad argument");
     return DG_EINVAL;
   }
-  if (!check_affine(m, "dg_momentum_diagonal")) return DG_EUNSUPPORTED;
+  if (!m->affine)
+    return general_diag(m, false, co->mass, co->visc, co->adv, ubar, diag, false, as_stream(stream));
   return DG_DISPATCH_U(m, run_diag, m, false, co->mass, co->visc, co->adv, ubar, diag,
                        as_stream(stream));
 }
@@ -781,7 +783,6 @@ dg_status dg_poisson_diagonal(dg_mesh* m, double alpha, double* diag, void* stre
     set_error("dg_poisson_diagonal: bad argument");
     return DG_EINVAL;
   }
-  if (!check_affine(m, "dg_poisson_diagonal")) return DG_EUNSUPPORTED;
   return poisson_diagonal(m, alpha, diag, as_stream(stream));
 }
 

@@ -119,10 +119,6 @@ dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double*
     if (st != DG_OK) return st;
     P = &J;
   } else if (o->precond == DG_PC_MG_FP32 || o->precond == DG_PC_MG_FP64) {
-    if (!m->affine) {
-      set_error("dg_solve_stage: multigrid needs affine cells");
-      return DG_EUNSUPPORTED;
-    }
     if (o->precond == DG_PC_MG_FP32) {
       if (!s->mg32) {
         s->mg32 = new (std::nothrow) MultiGrid<float>();

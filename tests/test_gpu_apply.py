@@ -27,6 +27,13 @@ CASES = [
     (3, (3, 2, 3), (0, 0, 0), (1.0, 1.0, 1.0), (False, False, False), 3, 0, (0, 0, 0)),
     (3, (1, 1, 2), (0, 0, 0), (1.0, 1.0, 1.0), (True, True, False), 2, 0, (0, 0, 0)),
     (3, (2, 3, 2), (0, 0, 0), (1.0, 1.0, 1.0), (True, False, True), 4, 1, (0.0, 1.2, 0.0)),
+    # trilinear (sine-perturbed vertices): general-geometry kernels
+    (2, (4, 3), (0, 0), (1.0, 0.8), (False, False), 2, 2, (0.04, 0, 0)),
+    (2, (5, 4), (0, 0), (1.0, 1.0), (True, True), 3, 2, (0.05, 0, 0)),
+    (3, (3, 4, 2), (0, 0, 0), (1.0, 1.0, 1.0), (False, False, False), 3, 2, (0.03, 0, 0)),
+    (3, (4, 3, 3), (0, 0, 0), (1.0, 1.2, 0.9), (True, True, True), 2, 2, (0.05, 0, 0)),
+    (3, (1, 2, 3), (0, 0, 0), (1.0, 1.0, 1.0), (True, False, False), 2, 2, (0.04, 0, 0)),
+    (3, (2, 2, 3), (0, 0, 0), (1.0, 1.0, 1.0), (True, False, True), 4, 2, (0.03, 0, 0)),
 ]
 
 

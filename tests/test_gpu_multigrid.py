@@ -2,7 +2,7 @@
 flexible CG with an FP32 (mixed precision) or FP64 V-cycle reaches the same
 solution as the oracle's direct solve, on meshes that exercise p-coarsening
 (k = 3, 4), h-coarsening along some axes only (odd cell counts), walls,
-tanh grading and 2D, and needs far fewer iterations than Jacobi."""
+tanh grading, trilinear cells and 2D, and needs far fewer iterations than Jacobi."""
 import numpy as np
 import pytest
 
@@ -18,6 +18,9 @@ CASES = [
     (3, (6, 4, 5), (0, 0, 0), (1.0, 0.7, 0.9), (True, False, True), 3, 0, (0, 0, 0)),
     (3, (4, 8, 4), (0, 0, 0), (2.0, 1.0, 1.0), (True, False, False), 2, 1, (0.0, 1.5, 1.5)),
     (2, (16, 12), (0, 0), (1.0, 1.0), (False, True), 4, 0, (0, 0, 0)),
+    # trilinear cells: rediscretised levels on the coarsened vertex lattice
+    (3, (8, 6, 4), (0, 0, 0), (1.0, 1.0, 1.0), (False, False, False), 3, 2, (0.03, 0, 0)),
+    (2, (12, 8), (0, 0), (1.0, 1.0), (True, True), 2, 2, (0.05, 0, 0)),
 ]
 
 

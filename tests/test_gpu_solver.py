@@ -101,14 +101,17 @@ def test_tg2d_workload_steps_match_oracle():
         b.dg_solver_destroy(s)
 
 
+@pytest.mark.parametrize("geom", ["graded", "trilinear"])
 @pytest.mark.parametrize("extrapolate", [1, 0])
-def test_walled_step_with_data_and_forcing_matches_oracle(extrapolate):
+def test_walled_step_with_data_and_forcing_matches_oracle(extrapolate, geom):
     """3D, periodic in x, Dirichlet walls in y and z with time-dependent
-    wall data and forcing (graded mesh): 3 steps compared."""
+    wall data and forcing, on a tanh-graded mesh (Q2) or on sine-perturbed
+    trilinear cells (Q3): 3 steps compared."""
     from paper_2107_07776_gb300 import binding as b
     n, lo, hi, per = (3, 4, 3), (0, 0, 0), (2.0, 1.0, 1.0), (True, False, False)
-    gm = b.Mesh(3, n, lo, hi, per, 2, 1, (0.0, 1.5, 1.5))
-    om = OMesh(3, list(n), list(lo), list(hi), list(per), 2, map=1, map_param=[0, 1.5, 1.5])
+    k, mp, prm = (2, 1, [0.0, 1.5, 1.5]) if geom == "graded" else (3, 2, [0.03, 0.0, 0.0])
+    gm = b.Mesh(3, n, lo, hi, per, k, mp, tuple(prm))
+    om = OMesh(3, list(n), list(lo), list(hi), list(per), k, map=mp, map_param=prm)
     X = om.node_coords()
     uD = lambda t: np.stack([np.sin(X[1] + t) * (1 + X[2]), 0.3 * np.cos(X[0] * math.pi),
                              0.1 * X[1] * (1 + t)])

@@ -171,3 +171,15 @@ def mms_forcing(x, y, z, t=0.0, seed: int = 0):
 def random_vector(n: int, seed: int) -> np.ndarray:
     """Seeded N(0,1) FP64 vector."""
     return np.random.default_rng(seed).standard_normal(n)
+
+
+def initial_state(w: Workload, X, Xp):
+    """Initial velocity [dim, n] and pressure [n_p] of a workload at the
+    velocity node coordinates X and pressure node coordinates Xp."""
+    if w.name.startswith("tgv"):
+        return tgv3d_u(*X), tgv3d_p(*Xp)
+    if w.name == "tg2d":
+        return tg2d_u(*X, 0.0, 1.0 / w.Re), tg2d_p(*Xp, 0.0, 1.0 / w.Re)
+    if w.name == "channel":
+        return channel_u0(*X), np.zeros(Xp.shape[1])
+    return np.zeros((w.dim, X.shape[1])), np.zeros(Xp.shape[1])
