@@ -160,29 +160,31 @@ __global__ void __launch_bounds__(256) dot_kernel(int64_t n, const T* __restrict
 template <typename T>
 __global__ void prolong_add_kernel(const __grid_constant__ Transfer tr, int64_t nfine_dofs,
                                    const T* __restrict__ xc, T* __restrict__ xf) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= nfine_dofs) return;
   const int nbf = tr.dim == 3 ? tr.nf * tr.nf * tr.nf : tr.nf * tr.nf;
   const int nbc = tr.dim == 3 ? tr.nc * tr.nc * tr.nc : tr.nc * tr.nc;
-  const int64_t fc = gid / nbf;
-  const int node = (int)(gid % nbf);
-  int fi[3] = {(int)(fc % tr.nfine[0]), (int)((fc / tr.nfine[0]) % tr.nfine[1]),
-               (int)(fc / ((int64_t)tr.nfine[0] * tr.nfine[1]))};
-  int ci[3], bit[3];
-  for (int a = 0; a < 3; ++a) {
-    ci[a] = tr.hco[a] ? fi[a] >> 1 : fi[a];
-    bit[a] = tr.hco[a] ? (fi[a] & 1) : 0;
+  // grid-stride: the launch grid is capped (grid1), levels can be larger
+  for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < nfine_dofs;
+       gid += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t fc = gid / nbf;
+    const int node = (int)(gid % nbf);
+    int fi[3] = {(int)(fc % tr.nfine[0]), (int)((fc / tr.nfine[0]) % tr.nfine[1]),
+                 (int)(fc / ((int64_t)tr.nfine[0] * tr.nfine[1]))};
+    int ci[3], bit[3];
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = tr.hco[a] ? fi[a] >> 1 : fi[a];
+      bit[a] = tr.hco[a] ? (fi[a] & 1) : 0;
+    }
+    const int64_t cc = ci[0] + (int64_t)tr.ncoarse[0] * (ci[1] + (int64_t)tr.ncoarse[1] * ci[2]);
+    const int ii[3] = {node % tr.nf, (node / tr.nf) % tr.nf, tr.dim == 3 ? node / (tr.nf * tr.nf) : 0};
+    T acc = T(0);
+    for (int j = 0; j < nbc; ++j) {
+      const int jj[3] = {j % tr.nc, (j / tr.nc) % tr.nc, tr.dim == 3 ? j / (tr.nc * tr.nc) : 0};
+      T w = T(1);
+      for (int a = 0; a < tr.dim; ++a) w *= transfer_w<T>(tr, tr.hco[a] ? bit[a] : 2, ii[a], jj[a]);
+      acc += w * xc[cc * nbc + j];
+    }
+    xf[gid] += acc;
   }
-  const int64_t cc = ci[0] + (int64_t)tr.ncoarse[0] * (ci[1] + (int64_t)tr.ncoarse[1] * ci[2]);
-  const int ii[3] = {node % tr.nf, (node / tr.nf) % tr.nf, tr.dim == 3 ? node / (tr.nf * tr.nf) : 0};
-  T acc = T(0);
-  for (int j = 0; j < nbc; ++j) {
-    const int jj[3] = {j % tr.nc, (j / tr.nc) % tr.nc, tr.dim == 3 ? j / (tr.nc * tr.nc) : 0};
-    T w = T(1);
-    for (int a = 0; a < tr.dim; ++a) w *= transfer_w<T>(tr, tr.hco[a] ? bit[a] : 2, ii[a], jj[a]);
-    acc += w * xc[cc * nbc + j];
-  }
-  xf[gid] += acc;
 }
 
 // Restriction, pass 1: part[(cc * nchild + ch) * nbc + j] = sum_i M r_f[i]

@@ -4,8 +4,9 @@
 100 ulp of the float path, accumulated over the O(10^2) terms per output).
 Meshes span several CTAs with ragged tails, 2D and 3D, periodic (including a
 one-cell period, where a cell is its own neighbour) and walled, Cartesian and
-tanh-graded, degrees 2 to 4; the 32^3 Taylor-Green workload is checked on
-sampled cells at full size."""
+tanh-graded and sine-perturbed trilinear, degrees 2 to 4; the benchmark-size
+workloads (32^3 Taylor-Green, 64^3 Q3 trilinear, 256x64x64 graded channel)
+are checked on sampled cells at full size."""
 import math
 
 import numpy as np
@@ -110,18 +111,24 @@ def test_node_coords_match_oracle():
 
 
 @pytest.mark.parametrize("fp64_arith", [0, 1])
-def test_full_size_tgv32_sampled_cells(fp64_arith):
-    """The 32^3 Q2/Q1 Taylor-Green workload at full size, as the benchmark
-    launches it: every output of 64 sampled cells (corners, edges, random)
-    against the oracle's rows for those cells."""
+@pytest.mark.parametrize("wname", ["tgv32", "mms64", "channel"])
+def test_full_size_workload_sampled_cells(wname, fp64_arith):
+    """The benchmark-size meshes as the library launches them: 32^3 Q2/Q1
+    Taylor-Green (periodic), 64^3 Q3/Q2 on sine-perturbed trilinear cells
+    (walls), 256x64x64 Q2/Q1 tanh-graded channel (walls in y, z): every
+    output of 64 sampled cells (first/last cells, a wall row, random) against
+    the oracle's rows for those cells."""
     from paper_2107_07776_gb300 import binding as b
-    w = W.TGV32
+    w = W.WORKLOADS[wname]
     gm = b.Mesh.from_workload(w)
     b.dg_mesh_set_fp64_arith(gm.handle, fp64_arith)
-    om = OMesh(w.dim, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree)
+    om = OMesh(w.dim, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree,
+               map=w.map, map_param=list(w.map_param))
     rng = np.random.default_rng(7)
     N = om.n_cells
-    cells = np.unique(np.concatenate([[0, N - 1, 31, 32 * 31, N - 32], rng.integers(0, N, 59)]))
+    n0, n1 = w.n[0], w.n[1]
+    cells = np.unique(np.concatenate([[0, N - 1, n0 - 1, n0 * (n1 - 1), N - n0],
+                                      rng.integers(0, N, 59)]))
     # pressure
     xp = W.random_vector(om.n_p, 11)
     y = torch.empty(om.n_p, dtype=torch.float64, device="cuda")
@@ -131,9 +138,14 @@ def test_full_size_tgv32_sampled_cells(fp64_arith):
     ref = alpha * om.assemble("mass_p", cells=cells).apply(xp) + \
         om.assemble("sipg_p", cells=cells).apply(xp)
     assert rel_err(yc, ref) < 1e-12
-    # momentum with the workload's initial velocity as advecting field
+    # momentum; advecting field: the workload's initial velocity (its forcing
+    # for the manufactured case, which starts from rest)
     X = gm.node_coords(0).cpu().numpy()
-    ub = W.tgv3d_u(*X).reshape(-1)
+    Xp = gm.node_coords(1).cpu().numpy()
+    ub = W.initial_state(w, X, Xp)[0]
+    if not np.any(ub):
+        ub = W.forcing(w, X)
+    ub = ub.reshape(-1)
     xu = W.random_vector(3 * om.n_u, 12)
     mass, visc, adv = 1.0 / (b.GAMMA * w.dt), 1.0 / (2 * w.Re), 0.5
     yu = torch.empty(3 * om.n_u, dtype=torch.float64, device="cuda")

@@ -138,6 +138,74 @@ def test_walled_step_with_data_and_forcing_matches_oracle(extrapolate, geom):
         b.dg_solver_destroy(s)
 
 
+@pytest.mark.parametrize("precond", ["jacobi", "mg_fp32"])
+def test_trilinear_forced_workload_reduced_matches_oracle(precond):
+    """The manufactured-forcing workload on sine-perturbed trilinear Q3/Q2
+    cells with no-slip walls, reduced to 4^3 cells: from rest, constant
+    seeded forcing, 3 steps compared with the oracle.  The Helmholtz solves
+    use Jacobi or the FP32 multigrid (mixed precision) at the same 1e-13
+    tolerance: the preconditioner changes the path, not the solution."""
+    from paper_2107_07776_gb300 import binding as b
+    w = W.MMS64.scaled((4, 4, 4))
+    gm = b.Mesh.from_workload(w)
+    om = OMesh(3, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree, map=w.map,
+               map_param=list(w.map_param))
+    X = om.node_coords()
+    fh = W.forcing(w, X)
+    st = Stepper(om, w.Re, c=w.c)
+    s = b.dg_solver_create(gm.handle, w.Re, w.c)
+    try:
+        u = torch.zeros(3 * om.n_u, dtype=torch.float64, device="cuda")
+        p = torch.zeros(om.n_p, dtype=torch.float64, device="cuda")
+        fd = dev(fh.reshape(-1))
+        ou, op = np.zeros((3, om.n_u)), np.zeros(om.n_p)
+        ouh = ou
+        prm = step_params(b, w.dt, dict(f_n=fd, f_ng=fd, f_n1=fd))
+        if precond == "mg_fp32":
+            prm.helm = opts(b, b.DG_SYS_HELMHOLTZ, precond=b.DG_PC_MG_FP32, guess=b.DG_GUESS_EXTRAP)
+        for k in range(3):
+            info = b.trbdf2_step(s, prm, u, p)
+            assert all(i.status == 0 for i in info)
+            ou, op, ouh = st.step(ou, op, ouh, k * w.dt, w.dt, f=lambda t: fh)
+            assert rel_l2(u.cpu().numpy(), ou.reshape(-1)) < 1e-8, k
+            assert rel_l2(p.cpu().numpy(), op) < 1e-8, k
+    finally:
+        b.dg_solver_destroy(s)
+
+
+def test_trilinear_workload_mixed_precision_error_vs_fp64():
+    """The trilinear workload at 16^3 Q3/Q2 (1.6 M DoFs), 5 steps at the
+    benchmark tolerance (1e-8 relative residual): FP32 multigrid + learned
+    guess (trained on the first steps) against the plain FP64 solver (FP64
+    multigrid, extrapolated guess).  Both stop at the same residual, so the
+    difference is of the order of the tolerance times the conditioning."""
+    from paper_2107_07776_gb300 import binding as b
+    w = W.MMS64.scaled((16, 16, 16))
+    gm = b.Mesh.from_workload(w)
+    X = gm.node_coords(0).cpu().numpy()
+    fd = dev(W.forcing(w, X).reshape(-1))
+    res = {}
+    for name, pc, guess in (("plain", b.DG_PC_MG_FP64, b.DG_GUESS_EXTRAP),
+                            ("mixed", b.DG_PC_MG_FP32, b.DG_GUESS_LEARNED)):
+        s = b.dg_solver_create(gm.handle, w.Re, w.c)
+        try:
+            if guess == b.DG_GUESS_LEARNED:
+                b.dg_guess_configure(s, enable=1, train=1, systems=1)
+            u = torch.zeros(gm.n_dofs_u, dtype=torch.float64, device="cuda")
+            p = torch.zeros(gm.n_dofs_p, dtype=torch.float64, device="cuda")
+            prm = step_params(b, w.dt, dict(f_n=fd, f_ng=fd, f_n1=fd), tol=1e-8)
+            prm.helm = opts(b, b.DG_SYS_HELMHOLTZ, tol=1e-8, precond=pc, guess=guess)
+            for _ in range(5):
+                info = b.trbdf2_step(s, prm, u, p)
+                assert all(i.status == 0 for i in info)
+            res[name] = (u.cpu().numpy(), p.cpu().numpy())
+        finally:
+            b.dg_solver_destroy(s)
+    eu = rel_l2(res["mixed"][0], res["plain"][0])
+    ep = rel_l2(res["mixed"][1], res["plain"][1])
+    assert eu < 1e-6 and ep < 1e-5, (eu, ep)
+
+
 def test_failures_are_reported_from_the_host():
     """Failure injection without any GPU fault: max_iter = 1 (no
     convergence), a NaN planted in the right-hand side on the host, bad

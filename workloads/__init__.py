@@ -183,3 +183,12 @@ def initial_state(w: Workload, X, Xp):
     if w.name == "channel":
         return channel_u0(*X), np.zeros(Xp.shape[1])
     return np.zeros((w.dim, X.shape[1])), np.zeros(Xp.shape[1])
+
+
+def forcing(w: Workload, X):
+    """Body force [dim, n] at the velocity nodes X, or None: the manufactured
+    forcing of the trilinear workload (constant in time); the other workloads
+    are unforced."""
+    if w.name.startswith("mms"):
+        return mms_forcing(*X)
+    return None
