@@ -73,7 +73,13 @@ typedef struct {
  * k^2 |Gamma|/|K| for pressure: Eq. penconst1 and its pressure analogue read
  * with face measure over cell volume) and the 1D tables on the current
  * device.  `stream` orders the uploads.  *out owns device memory until
- * dg_mesh_destroy.  DG_EUNSUPPORTED for map/degree combinations not built. */
+ * dg_mesh_destroy.  Trilinear (DG_MAP_PERTURBED_SIN) meshes also hold the
+ * per-point metric terms of their cells, computed once here in FP64 (with
+ * FP32 copies): per velocity node the diffusion metric, mass weight and
+ * inverse-Jacobian weights (16 doubles in 3D), per pressure node 7, per face
+ * point the surface weight, normal and normal-derivative coefficients of
+ * both sides (10 velocity, 7 pressure).  DG_EUNSUPPORTED for map/degree
+ * combinations not built. */
 dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out);
 void dg_mesh_destroy(dg_mesh* mesh);
 
@@ -135,7 +141,8 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * and without advection, FP64 and FP32 -- with CUDA events on `stream` and
  * keeps the fastest for later applies; results do not depend on the choice.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
- * Allocates temporary device buffers; synchronous. */
+ * Trilinear meshes use one tile shape per kernel: the call records an empty
+ * report.  Allocates temporary device buffers; synchronous. */
 dg_status dg_autotune(dg_mesh* mesh, void* stream);
 
 /* JSON list of the tuning choices and timings of a mesh ("[]" if untuned),
