@@ -267,9 +267,9 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
   const char* opname[3] = {"pressure", "momentum", "momentum+advection"};
   for (int prec = 0; prec < 2 && st == DG_OK; ++prec) {
     for (int op = 0; op < 3 && st == DG_OK; ++op) {
-      float best = 1e30f, times[3] = {0, 0, 0};
+      float best = 1e30f, times[kTuneVariants] = {0, 0, 0, 0, 0};
       int bestv = 1;
-      for (int v = 0; v < 3 && st == DG_OK; ++v) {
+      for (int v = 0; v < kTuneVariants && st == DG_OK; ++v) {
         m->tune[prec][op] = v;
         auto run = [&]() -> dg_status {
           const bool p = op == 0;
@@ -300,16 +300,17 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
         }
       }
       m->tune[prec][op] = bestv;
-      char line[256];
+      char line[512];
       const bool p = op == 0, adv = op == 2;
       auto cp = [&](int v) {
         return prec == 0 ? cpb_for_mesh<double>(m, p, adv, v) : cpb_for_mesh<float>(m, p, adv, v);
       };
       std::snprintf(line, sizeof(line),
-                    "%s{\"op\": \"%s\", \"precision\": \"%s\", \"cells_per_cta\": [%d, %d, %d], "
-                    "\"ms\": [%.5f, %.5f, %.5f], \"chosen\": %d}",
+                    "%s{\"op\": \"%s\", \"precision\": \"%s\", "
+                    "\"cells_per_cta\": [%d, %d, %d, %d, %d], \"register_cap\": [0, 0, 0, 96, 80], "
+                    "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f], \"chosen_variant\": %d}",
                     rep.size() > 1 ? ", " : "", opname[op], prec == 0 ? "f64" : "f32", cp(0), cp(1),
-                    cp(2), times[0], times[1], times[2], cp(bestv));
+                    cp(2), cp(3), cp(4), times[0], times[1], times[2], times[3], times[4], bestv);
       rep += line;
     }
   }

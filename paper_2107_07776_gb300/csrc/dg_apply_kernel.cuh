@@ -70,8 +70,8 @@ __device__ __forceinline__ int tang_of(int a, const int i[3]) {
 
 // T: storage type of the vectors (double or float); A: arithmetic type
 // (double, float, or df64 = float-float on the FP32 pipes).
-template <typename T, typename A, int DIM, int N, bool ADV, int CPB>
-__global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
+template <typename T, typename A, int DIM, int N, bool ADV, int CPB, int MINB = 1>
+__global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MINB)
     scalar_op_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
                      const T* __restrict__ src, const T* __restrict__ ub, T* __restrict__ dst) {
   using Ar = Arith<A>;
@@ -286,9 +286,13 @@ constexpr int smem_words(int cpb) {
                 (ADV ? DIM * Shape<N, DIM>::NB + 3 * Shape<N, DIM>::NFP : 4));
 }
 
-// Tile-shape candidates of the autotuner: half, default and double the
-// default cells per CTA, each clamped to the 48 KB static shared-memory and
-// 1024-thread limits.
+// Tile-shape candidates of the autotuner: variants 0-2 take half, the
+// default and double the default cells per CTA, each clamped to the 48 KB
+// static shared-memory and 1024-thread limits; variants 3 and 4 take the
+// default cells per CTA with the registers per thread capped at 96 and 80
+// (more resident CTAs per SM, possibly at the price of spills).
+constexpr int kTuneVariants = 5;
+
 template <typename T, int DIM, int N, bool ADV>
 constexpr int cpb_variant(int v) {
   int c = v == 0 ? default_cpb<N, DIM>() / 2 : (v == 2 ? default_cpb<N, DIM>() * 2 : default_cpb<N, DIM>());
@@ -298,7 +302,17 @@ constexpr int cpb_variant(int v) {
   return c;
 }
 
-template <typename T, typename A, int DIM, int N, bool ADV, int CPB>
+// minimum resident CTAs per SM requested from the compiler for variant v
+template <typename T, int DIM, int N, bool ADV>
+constexpr int minb_variant(int v) {
+  const int threads = ((cpb_variant<T, DIM, N, ADV>(v) * Shape<N, DIM>::NB + 31) / 32) * 32;
+  const int cap = v == 3 ? 96 : (v == 4 ? 80 : 0);
+  if (cap == 0) return 1;
+  const int b = 65536 / (threads * cap);
+  return b < 1 ? 1 : b;
+}
+
+template <typename T, typename A, int DIM, int N, bool ADV, int CPB, int MINB>
 static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
                             T* dst, cudaStream_t s) {
   constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
@@ -307,18 +321,28 @@ static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<A>& tb, const T* 
     set_error("operator apply: grid too large");
     return DG_EINVAL;
   }
-  scalar_op_kernel<T, A, DIM, N, ADV, CPB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst); count_launch();
+  scalar_op_kernel<T, A, DIM, N, ADV, CPB, MINB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst);
+  count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
+}
+
+template <typename T, typename A, int DIM, int N, bool ADV, int V>
+static dg_status launch_v(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
+                          T* dst, cudaStream_t s) {
+  return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V)>(
+      args, tb, ub, src, dst, s);
 }
 
 template <typename T, typename A, int DIM, int N, bool ADV>
 static dg_status launch_fixed(int variant, const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub,
                               const T* src, T* dst, cudaStream_t s) {
   switch (variant) {
-    case 0: return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(0)>(args, tb, ub, src, dst, s);
-    case 2: return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(2)>(args, tb, ub, src, dst, s);
-    default: return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(1)>(args, tb, ub, src, dst, s);
+    case 0: return launch_v<T, A, DIM, N, ADV, 0>(args, tb, ub, src, dst, s);
+    case 2: return launch_v<T, A, DIM, N, ADV, 2>(args, tb, ub, src, dst, s);
+    case 3: return launch_v<T, A, DIM, N, ADV, 3>(args, tb, ub, src, dst, s);
+    case 4: return launch_v<T, A, DIM, N, ADV, 4>(args, tb, ub, src, dst, s);
+    default: return launch_v<T, A, DIM, N, ADV, 1>(args, tb, ub, src, dst, s);
   }
 }
 

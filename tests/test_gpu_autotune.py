@@ -1,6 +1,7 @@
-"""The autotuner: picks one of the candidate tile shapes per operator and
-precision, reports its timings, and never changes results (each output is
-computed by one thread in a fixed order whatever the tile shape)."""
+"""The autotuner: picks one of the candidate tile shapes (cells per CTA,
+register cap) per operator and precision, reports its timings, and never
+changes results (each output is computed by one thread in a fixed order
+whatever the tile shape)."""
 import json
 
 import numpy as np
@@ -37,7 +38,9 @@ def test_autotune_keeps_results_and_reports(dim, n, k):
     rep = json.loads(b.dg_autotune_report(gm.handle))
     assert len(rep) == 6
     for r in rep:
-        assert r["chosen"] in r["cells_per_cta"]
+        assert len(r["cells_per_cta"]) == len(r["ms"]) == len(r["register_cap"]) == 5
+        assert 0 <= r["chosen_variant"] < 5
+        assert r["ms"][r["chosen_variant"]] == min(r["ms"])
         assert all(t > 0 for t in r["ms"])
     after = apply_all()
     for a, c in zip(before, after):
@@ -57,3 +60,10 @@ def test_multigrid_levels_of_a_tuned_mesh():
         assert info.iterations < 30
     finally:
         b.dg_solver_destroy(s)
+
+
+def test_autotune_on_trilinear_mesh_is_a_no_op():
+    from paper_2107_07776_gb300 import binding as b
+    gm = b.Mesh(3, (4, 3, 3), (0, 0, 0), (1, 1, 1), (False,) * 3, 2, 2, (0.04, 0, 0))
+    b.dg_autotune(gm.handle)
+    assert json.loads(b.dg_autotune_report(gm.handle)) == []
