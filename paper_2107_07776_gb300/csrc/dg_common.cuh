@@ -97,6 +97,8 @@ namespace dg {
 
 // kernels launched by the library in this process (diagnostics)
 void count_launch();
+void count_launches(int64_t n);  // kernels of a replayed CUDA graph
+int64_t launches_so_far();
 
 // thread-local error message, set by the entry points
 void set_error(const std::string& msg);

@@ -22,6 +22,8 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_kernel_launches{0};
 
 void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 

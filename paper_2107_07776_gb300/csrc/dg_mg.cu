@@ -290,6 +290,8 @@ dg_status level_apply<double>(const MGLevel<double>& L, double alpha, const doub
 
 template <typename T>
 MultiGrid<T>::~MultiGrid() {
+  drop_graphs(-1);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   for (auto& L : lv) {
     if (L.owned && L.mesh) dg_mesh_destroy(L.mesh);
     T* vs[] = {L.x, L.b, L.r, L.d, L.t, L.d2, L.dinv[0], L.dinv[1], L.ainv[0], L.ainv[1]};
@@ -466,6 +468,7 @@ dg_status MultiGrid<T>::set_alpha(double a) {
   }
   slot = next_slot;
   next_slot ^= 1;
+  drop_graphs(slot);  // its diagonal, bounds and coarse inverse change
   cache_alpha[slot] = a;
   alpha = a;
   cur = slot;
@@ -541,6 +544,7 @@ dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
     if (st != DG_OK) return st;
     cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.b, L.t, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
   }
+  int swaps = 0;
   for (int k = 0; k + 1 < degree; ++k) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     st = launch_poisson_cheb<T>(L.mesh, alpha, L.d, L.d2, L.x, L.r, dinv, rho_new * rho,
@@ -549,10 +553,16 @@ dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
     T* tmp = L.d;
     L.d = L.d2;
     L.d2 = tmp;
+    ++swaps;
     rho = rho_new;
   }
   add_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.d, L.x); count_launch();
   DG_CUDA(cudaGetLastError());
+  if (swaps & 1) {  // the direction is consumed: give every call the same buffers
+    T* tmp = L.d;
+    L.d = L.d2;
+    L.d2 = tmp;
+  }
   return DG_OK;
 }
 
@@ -676,13 +686,79 @@ dg_status MultiGrid<T>::vcycle(int l) {
 }
 
 template <typename T>
-dg_status MultiGrid<T>::apply(const double* r, double* z) {
+dg_status MultiGrid<T>::apply_direct(const double* r, double* z) {
   MGLevel<T>& L = lv[0];
   cvt_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, r, L.b); count_launch();
   dg_status st = vcycle(0);
   if (st != DG_OK) return st;
   cvt_back_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, L.x, z); count_launch();
   DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// slot < 0: all
+template <typename T>
+void MultiGrid<T>::drop_graphs(int slot) {
+  std::vector<Captured> keep;
+  for (auto& g : graphs) {
+    if (slot < 0 || g.slot == slot) cudaGraphExecDestroy(g.exec);
+    else keep.push_back(g);
+  }
+  graphs.swap(keep);
+}
+
+// Replays the captured V-cycle for (r, z, current alpha slot); captures it
+// on first use.  Capturing runs no kernel, so the new graph is launched once
+// after instantiation; its kernels were counted while they were recorded.
+template <typename T>
+dg_status MultiGrid<T>::apply(const double* r, double* z) {
+  for (auto& g : graphs)
+    if (g.r == r && g.z == z && g.slot == cur) {
+      DG_CUDA(cudaGraphLaunch(g.exec, stream));
+      count_launches(g.launches);
+      return DG_OK;
+    }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DG_CUDA(cudaStreamIsCapturing(stream, &cs));
+  if (!use_graphs || cs != cudaStreamCaptureStatusNone) return apply_direct(r, z);
+  // record on a private stream (the solver's stream may be the legacy
+  // default stream, which cannot be captured); nothing runs while recording
+  if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cap_stream = nullptr;
+    use_graphs = false;
+    return apply_direct(r, z);
+  }
+  const int64_t before = launches_so_far();
+  const cudaStream_t run_stream = stream;
+  if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    use_graphs = false;
+    return apply_direct(r, z);
+  }
+  stream = cap_stream;
+  const dg_status st = apply_direct(r, z);
+  stream = run_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+  if (st != DG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {  // fall back to direct launches for good
+    cudaGetLastError();
+    use_graphs = false;
+    return apply_direct(r, z);
+  }
+  if (graphs.size() >= 8) {
+    cudaGraphExecDestroy(graphs.front().exec);
+    graphs.erase(graphs.begin());
+  }
+  graphs.push_back(Captured{r, z, cur, exec, launches_so_far() - before});
+  DG_CUDA(cudaGraphLaunch(exec, stream));
   return DG_OK;
 }
 

@@ -64,6 +64,20 @@ struct MultiGrid {
   double* host_part = nullptr;
   double* diag = nullptr;
 
+  // V-cycles captured as CUDA graphs, per (r, z, alpha slot): the cycle is a
+  // fixed launch sequence on fixed buffers, so replaying it removes the
+  // per-kernel launch cost of the small coarse levels
+  struct Captured {
+    const double* r;
+    double* z;
+    int slot;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<Captured> graphs;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;  // private stream the cycles are recorded on
+
   ~MultiGrid();
   dg_status build(dg_mesh* fine, cudaStream_t s);
   dg_status set_alpha(double alpha);
@@ -71,6 +85,8 @@ struct MultiGrid {
   dg_status apply(const double* r, double* z);
 
  private:
+  dg_status apply_direct(const double* r, double* z);
+  void drop_graphs(int slot);
   dg_status vcycle(int l);
   dg_status chebyshev(int l, int degree, bool x_zero);
   dg_status estimate(int l, int slot, int steps, double* lo, double* hi);

@@ -213,6 +213,199 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 }
 
 // ------------------------------------------------------------------
+// The explicit terms of one stage in one pass: rhs += sum_t (visc_t E_v w_t +
+// adv_t E_a(wb_t) w_t) over NT = 1 or 2 terms (stage 2 has two).  E_v is
+// linear, so it is evaluated once on v = sum_t visc_t w_t; the normal traces
+// of the advecting fields are computed once per cell, not per component.
+struct ExplTerms {
+  double visc[2], adv[2];
+  const double* w[2];
+  const double* wb[2];
+};
+
+template <int N, int DIM>
+constexpr int expl_minb(int threads) {
+  return 65536 / (threads * 96) < 1 ? 1 : 65536 / (threads * 96);
+}
+
+template <typename A, int DIM, int N, int NT, int CPB>
+__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
+                                  expl_minb<N, DIM>(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32))
+    explicit_terms_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
+                          const __grid_constant__ ExplTerms et, double* __restrict__ rhs) {
+  using Ar = Arith<A>;
+  constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
+  __shared__ A s_u[NT][CPB][NB];
+  __shared__ A s_v[CPB][NB];
+  __shared__ A s_wb[NT][DIM][CPB][NB];
+  __shared__ A s_q[DIM][CPB][NB];
+  __shared__ A s_f[CPB][NFP];
+  __shared__ A s_wn[NT][CPB][NFP][2];
+  const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < g.ncell;
+  const A zero = Ar::c(0.0), half = Ar::c(0.5);
+  A visc[NT], adv[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    visc[t] = Ar::from(et.visc[t]);
+    adv[t] = Ar::from(et.adv[t]);
+  }
+  int ci[3] = {0, 0, 0};
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
+  A W = zero;
+  if (active) {
+    cell_coords(g, cell, ci);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      h[b] = Ar::from(g.h[b][ci[b]]);
+      hi[b] = Ar::from(g.hi[b][ci[b]]);
+    }
+    W = Ar::c(1.0);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) W = W * tb.w[ii[b]] * h[b];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b)
+        s_wb[t][b][cl][node] = Ar::from(et.wb[t][((int64_t)b * g.ncell + cell) * NB + node]);
+  }
+  __syncthreads();
+  if (active) {  // normal traces of the advecting fields, both sides (walls: inside only)
+    for (int fp = node; fp < NFP; fp += NB) {
+      const int f = fp / NF, t = fp % NF, ax = f >> 1, s = f & 1;
+      const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
+      const int64_t nb = neighbour(g, ci, ax, s);
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) {
+        A wi = zero, wo = zero;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int nd = nodeof(N, DIM, ax, i, t);
+          wi += tb.L[s][i] * s_wb[tt][ax][cl][nd];
+          if (nb >= 0) wo += tb.L[1 - s][i] * Ar::from(__ldg(&et.wb[tt][((int64_t)ax * g.ncell + nb) * NB + nd]));
+        }
+        s_wn[tt][cl][fp][0] = wi * sgn;
+        s_wn[tt][cl][fp][1] = wo * sgn;
+      }
+    }
+  }
+  for (int c = 0; c < DIM; ++c) {
+    if (active) {
+      A v = zero;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const A u = Ar::from(et.w[t][((int64_t)c * g.ncell + cell) * NB + node]);
+        s_u[t][cl][node] = u;
+        v += visc[t] * u;
+      }
+      s_v[cl][node] = v;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A dv = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          dv += tb.D[ii[b]][m] * s_v[cl][j[0] + N * (j[1] + N * j[2])];
+        }
+        A q = -(dv * hi[b]);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) q += adv[t] * s_u[t][cl][node] * s_wb[t][b][cl][node];
+        s_q[b][cl][node] = W * q;
+      }
+      for (int fp = node; fp < NFP; fp += NB) {
+        const int f = fp / NF, t = fp % NF, ax = f >> 1, s = f & 1;
+        const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
+        const int64_t nb = neighbour(g, ci, ax, s);
+        const A hiK = sel3(ax, hi[0], hi[1], hi[2]);
+        A wt = Ar::c(1.0);
+        {
+          int tt = t;
+#pragma unroll
+          for (int b = 0; b < DIM; ++b) {
+            if (b == ax) continue;
+            wt = wt * tb.w[tt % N] * h[b];
+            tt /= N;
+          }
+        }
+        A vin = zero, dvin = zero, uin[NT];
+#pragma unroll
+        for (int tt = 0; tt < NT; ++tt) uin[tt] = zero;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int nd = nodeof(N, DIM, ax, i, t);
+          const A v = s_v[cl][nd];
+          vin += tb.L[s][i] * v;
+          dvin += tb.dL[s][i] * v;
+#pragma unroll
+          for (int tt = 0; tt < NT; ++tt) uin[tt] += tb.L[s][i] * s_u[tt][cl][nd];
+        }
+        dvin = dvin * sgn * hiK;
+        A fv;
+        if (nb >= 0) {
+          int nc3[3];
+          cell_coords(g, nb, nc3);
+          const A hiN = Ar::from(sel3(ax, g.hi[0], g.hi[1], g.hi[2])[sel3(ax, nc3[0], nc3[1], nc3[2])]);
+          A vout = zero, dvout = zero, uout[NT];
+#pragma unroll
+          for (int tt = 0; tt < NT; ++tt) uout[tt] = zero;
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            const int nd = nodeof(N, DIM, ax, i, t);
+            A v = zero;
+#pragma unroll
+            for (int tt = 0; tt < NT; ++tt) {
+              const A u = Ar::from(__ldg(&et.w[tt][((int64_t)c * g.ncell + nb) * NB + nd]));
+              uout[tt] += tb.L[1 - s][i] * u;
+              v += visc[tt] * u;
+            }
+            vout += tb.L[1 - s][i] * v;
+            dvout += tb.dL[1 - s][i] * v;
+          }
+          dvout = dvout * sgn * hiN;
+          A a = zero;
+#pragma unroll
+          for (int tt = 0; tt < NT; ++tt)
+            a += adv[tt] * (uin[tt] * s_wn[tt][cl][fp][0] + uout[tt] * s_wn[tt][cl][fp][1]);
+          fv = half * (dvin + dvout - a);
+        } else {
+          A a = zero;
+#pragma unroll
+          for (int tt = 0; tt < NT; ++tt) a += adv[tt] * uin[tt] * s_wn[tt][cl][fp][0];
+          fv = dvin - a;
+        }
+        s_f[cl][fp] = wt * fv;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      A y = zero;
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A acc = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          acc += tb.D[m][ii[b]] * s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
+        }
+        y += acc * hi[b];
+        const int t = tangof(N, DIM, b, ii);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) y += s_f[cl][(2 * b + s) * NF + t] * tb.L[s][ii[b]];
+      }
+      rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += Ar::to_d(y);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------
 // rhs = mass M u_mass + M f + G p (G the DG pressure gradient of Eq. rhs1);
 // writes (does not accumulate).  N velocity, NP pressure nodes per direction.
 template <typename A, int DIM, int N, int NP, int CPB>
@@ -581,6 +774,28 @@ dg_status run_explicit_a(const dg_mesh* m, int mode, double visc, double adv, co
   return DG_OK;
 }
 
+template <typename A, int DIM, int N>
+dg_status run_explicit_terms_a(const dg_mesh* m, const ExplTerms& et, int nt, double* rhs,
+                               cudaStream_t s) {
+  constexpr int CPB = cpb_for<N, DIM>();
+  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
+  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  if (nt == 2)
+    explicit_terms_kernel<A, DIM, N, 2, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_u<A>(m), et, rhs);
+  else
+    explicit_terms_kernel<A, DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_u<A>(m), et, rhs);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <int DIM, int N>
+dg_status run_explicit_terms(const dg_mesh* m, const ExplTerms& et, int nt, double* rhs,
+                             cudaStream_t s) {
+  return m->fp64_arith ? run_explicit_terms_a<double, DIM, N>(m, et, nt, rhs, s)
+                       : run_explicit_terms_a<df64, DIM, N>(m, et, nt, rhs, s);
+}
+
 template <int DIM, int N>
 dg_status run_explicit(const dg_mesh* m, int mode, double visc, double adv, const double* w,
                        const double* wb, double* rhs, cudaStream_t s) {
@@ -728,12 +943,23 @@ dg_status dg_rhs_momentum(dg_mesh* m, const dg_momentum_rhs* d, double* rhs, voi
   dg_status st = m->affine ? DG_DISPATCH_U(m, run_mass_grad, m, d->mass, d->u_mass, d->f, d->p, rhs, s)
                            : general_mass_grad(m, d->mass, d->u_mass, d->f, d->p, rhs, s);
   if (st != DG_OK) return st;
-  for (int t = 0; t < d->n_terms; ++t) {
-    // a term without advection still needs a field for the shared-memory
-    // staging; the term's own w stands in (multiplied by adv = 0)
+  if (m->affine && d->n_terms > 0) {
+    // all explicit terms in one pass; a term without advection still needs
+    // a field for the shared-memory staging: its own w stands in (times 0)
+    ExplTerms et;
+    for (int t = 0; t < 2; ++t) {
+      const int u = t < d->n_terms ? t : 0;
+      et.visc[t] = t < d->n_terms ? d->visc[t] : 0.0;
+      et.adv[t] = t < d->n_terms ? d->adv[t] : 0.0;
+      et.w[t] = d->w[u];
+      et.wb[t] = d->wbar[u] ? d->wbar[u] : d->w[u];
+    }
+    st = DG_DISPATCH_U(m, run_explicit_terms, m, et, d->n_terms, rhs, s);
+    if (st != DG_OK) return st;
+  }
+  for (int t = 0; t < d->n_terms && !m->affine; ++t) {
     const double* wb = d->wbar[t] ? d->wbar[t] : d->w[t];
-    st = m->affine ? DG_DISPATCH_U(m, run_explicit, m, 0, d->visc[t], d->adv[t], d->w[t], wb, rhs, s)
-                   : general_explicit(m, 0, d->visc[t], d->adv[t], d->w[t], wb, rhs, s);
+    st = general_explicit(m, 0, d->visc[t], d->adv[t], d->w[t], wb, rhs, s);
     if (st != DG_OK) return st;
   }
   bool walls = false;
