@@ -80,18 +80,30 @@ __device__ __forceinline__ df64 df_const(double x) {
   return {h, static_cast<float>(x - static_cast<double>(h))};
 }
 
-// Exact widening of a float to double with integer operations (no FP64-pipe
-// conversion): the sign is kept, the exponent rebiased (127 -> 1023) and the
-// 23 fraction bits moved to the top of the 52.  Zeros are built directly;
-// subnormals, infinities and NaNs take the conversion instruction.
+// Exact widening of a float to double with integer operations only (no
+// FP64-pipe conversion, not even a predicated one): the sign is kept, the
+// exponent rebiased (127 -> 1023) and the 23 fraction bits moved to the top
+// of the 52.  Zeros, subnormals (normalised by their leading one),
+// infinities and NaNs are built the same way.
 __device__ __forceinline__ double df_widen(float f) {
   const unsigned int u = __float_as_uint(f);
   const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned int m = u & 0x7FFFFFu;
   const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sgn);
-  if (e == 0u || e == 0xFFu) return (double)f;
-  const unsigned long long bits =
-      sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  unsigned long long bits;
+  if (e == 0u) {
+    if (m == 0u) {
+      bits = sgn;
+    } else {  // m 2^-149 = 1.f 2^(p-149), p the position of m's leading one
+      const int p = 31 - __clz((int)m);
+      const unsigned long long frac = ((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFull;
+      bits = sgn | ((unsigned long long)(p - 149 + 1023) << 52) | frac;
+    }
+  } else if (e == 0xFFu) {
+    bits = sgn | (0x7FFull << 52) | ((unsigned long long)m << 29);
+  } else {
+    bits = sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  }
   return __longlong_as_double((long long)bits);
 }
 
@@ -99,18 +111,25 @@ __device__ __forceinline__ double df_widen(float f) {
 __device__ __forceinline__ double df_to(df64 a) { return df_widen(a.hi) + df_widen(a.lo); }
 
 // Split of a double into a float pair with integer operations only (no FP64
-// instruction): hi keeps the sign, exponent and leading 23 fraction bits; the
-// remaining 29 fraction bits become lo (truncated to 24 significant bits, a
-// relative error below 2^-48 of x), and one FastTwoSum renormalises the pair.
-// Zero, values outside FP32's normal range, infinities and NaNs take the
-// conversion path above.
+// instruction -- also none that a predicated fallback would issue): hi keeps
+// the sign, exponent and leading 23 fraction bits; the remaining 29 fraction
+// bits become lo (truncated to 24 significant bits, a relative error below
+// 2^-47 of x), and one FastTwoSum renormalises the pair.  The float-float
+// format's exponent range applies: lo is dropped once it would fall below
+// FP32's normal range (|x| < 2^-102: relative error up to 2^-23), the pair
+// is (+-0, 0) below 2^-126 and (+-inf or NaN, 0) from 2^128 on.
 __device__ __forceinline__ df64 df_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FFull);
+  const unsigned int top = (unsigned int)(b >> 32);
+  const unsigned int sign = top & 0x80000000u;
+  const int e = (int)((top >> 20) & 0x7FFu);
   const int ef = e - 1023 + 127;
-  if (ef <= 0 || ef >= 255) return df_from(x);
-  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (ef <= 0) return {__int_as_float((int)sign), 0.0f};
+  if (ef >= 255) {
+    const unsigned int nan = (e == 0x7FF && m != 0ull) ? 0x00400000u : 0u;
+    return {__int_as_float((int)(sign | 0x7F800000u | nan)), 0.0f};
+  }
   const float hi = __int_as_float((int)(sign | ((unsigned int)ef << 23) | (unsigned int)(m >> 29)));
   const unsigned int r = (unsigned int)(m & 0x1FFFFFFFull);
   if (r == 0u) return {hi, 0.0f};
