@@ -49,9 +49,10 @@ import workloads as W  # noqa: E402
 METRIC = "GDoF/s DG operator apply; s per TR-BDF2 step (mixed+learned vs FP64)"
 FP64_PEAK_TFLOPS = 1.253   # measured FP64 FMA throughput of GB300
 FP32_PEAK_TFLOPS = 76.5    # measured FP32 FMA throughput
-# FP64-equivalent ceiling of float-float arithmetic: one multiply-add costs 27
-# FP32-pipe instructions; 152 SMs x 128 lanes x 2.07 GHz / 27 x 2 flop
-FLOAT_FLOAT_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 27 * 2 / 1e12
+# FP64-equivalent ceiling of float-float arithmetic: one fused multiply-add
+# (df_fma) costs 15 FP32-pipe instructions; 152 SMs x 128 lanes x 2.07 GHz
+# / 15 x 2 flop
+FLOAT_FLOAT_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 15 * 2 / 1e12
 
 
 def peaks():

@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const A v = s_u[cl][node_of(N, ax, i, t, DIM)];
-          uin += tb.L[s][i] * v;
-          dnin += tb.dL[s][i] * v;
+          uin = Ar::fma(tb.L[s][i], v, uin);
+          dnin = Ar::fma(tb.dL[s][i], v, dnin);
         }
         dnin = dnin * sgn * hiK;
         A fv = zero, fg = zero;
@@ -177,8 +177,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
 #pragma unroll
           for (int i = 0; i < N; ++i) {
             const A v = Ar::from(__ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]));
-            uout += tb.L[1 - s][i] * v;
-            dnout += tb.dL[1 - s][i] * v;
+            uout = Ar::fma(tb.L[1 - s][i], v, uout);
+            dnout = Ar::fma(tb.dL[1 - s][i], v, dnout);
           }
           dnout = dnout * sgn * hiN;
           const A Cpen = half * pen * (hiK + hiN);
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
               unout = zero;
 #pragma unroll
               for (int i = 0; i < N; ++i) {
-                unin += tb.L[s][i] * s_ub[ax][cl][node_of(N, ax, i, t, DIM)];
+                unin = Ar::fma(tb.L[s][i], s_ub[ax][cl][node_of(N, ax, i, t, DIM)], unin);
                 unout += tb.L[1 - s][i] *
                          Ar::from(__ldg(&ub[((int64_t)ax * a.ncell + nb) * NB + node_of(N, ax, i, t, DIM)]));
               }
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
               unin = zero;
 #pragma unroll
               for (int i = 0; i < N; ++i)
-                unin += tb.L[s][i] * s_ub[ax][cl][node_of(N, ax, i, t, DIM)];
+                unin = Ar::fma(tb.L[s][i], s_ub[ax][cl][node_of(N, ax, i, t, DIM)], unin);
               unin = unin * sgn;
               lam = Ar::abs(unin);
               s_un[cl][fp][0] = unin;

@@ -166,15 +166,15 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const A v = s_u[cl][node_of(N, ax, i, t, DIM)];
-          uin += tb.L[s][i] * v;
-          dnin += tb.dL[s][i] * v;
+          uin = Ar::fma(tb.L[s][i], v, uin);
+          dnin = Ar::fma(tb.dL[s][i], v, dnin);
         }
         if (interior) {
 #pragma unroll
           for (int i = 0; i < N; ++i) {
             const A v = Ar::from(__ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]));
-            uout += tb.L[1 - s][i] * v;
-            dnout += tb.dL[1 - s][i] * v;
+            uout = Ar::fma(tb.L[1 - s][i], v, uout);
+            dnout = Ar::fma(tb.dL[1 - s][i], v, dnout);
           }
         }
         s_t[cl][fp][0] = uin;
@@ -191,9 +191,9 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
 #pragma unroll
             for (int i = 0; i < N; ++i) {
               const int nd = node_of(N, ax, i, t, DIM);
-              wi += tb.L[s][i] * s_ub[r][cl][nd];
+              wi = Ar::fma(tb.L[s][i], s_ub[r][cl][nd], wi);
               if (interior)
-                wo += tb.L[1 - s][i] * Ar::from(__ldg(&ub[((int64_t)r * a.ncell + nb) * NB + nd]));
+                wo = Ar::fma(tb.L[1 - s][i], Ar::from(__ldg(&ub[((int64_t)r * a.ncell + nb) * NB + nd])), wo);
             }
             unin += nr * wi;
             unout += nr * wo;
@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
 #pragma unroll
             for (int m = 0; m < N; ++m) {
               const int q = f * NF + t + (m - tb_) * stride;
-              gi += tb.D[tb_][m] * s_t[cl][q][0];
-              go += tb.D[tb_][m] * s_t[cl][q][1];
+              gi = Ar::fma(tb.D[tb_][m], s_t[cl][q][0], gi);
+              go = Ar::fma(tb.D[tb_][m], s_t[cl][q][1], go);
             }
             dn_in += cown[b] * gi;
             dn_out += cnb[b] * go;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
             const int tg = ii[g2];
 #pragma unroll
             for (int m = 0; m < N; ++m)
-              R += tb.D[m][tg] * s_Q[cl][f * NF + t + (m - tg) * stride][e];
+              R = Ar::fma(tb.D[m][tg], s_Q[cl][f * NF + t + (m - tg) * stride][e], R);
             stride *= N;
             ++e;
           }

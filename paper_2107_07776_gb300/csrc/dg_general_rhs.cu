@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
         A a_in = zero, a_out = zero;
         for (int i = 0; i < N; ++i) {
           const int nd = node_of(N, ax, i, t, DIM);
-          a_in += tb.L[s][i] * s_wb[r][cl][nd];
+          a_in = Ar::fma(tb.L[s][i], s_wb[r][cl][nd], a_in);
           if (MODE == 0 && nb >= 0)
-            a_out += tb.L[1 - s][i] * Ar::from(__ldg(&wb[((int64_t)r * g.ncell + nb) * NB + nd]));
+            a_out = Ar::fma(tb.L[1 - s][i], Ar::from(__ldg(&wb[((int64_t)r * g.ncell + nb) * NB + nd])), a_out);
         }
         wi += nr * a_in;
         wo += nr * a_out;
@@ -179,14 +179,14 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
         A uin = zero, dnin = zero, uout = zero, dnout = zero;
         for (int i = 0; i < N; ++i) {
           const A v = s_u[cl][node_of(N, ax, i, t, DIM)];
-          uin += tb.L[s][i] * v;
-          dnin += tb.dL[s][i] * v;
+          uin = Ar::fma(tb.L[s][i], v, uin);
+          dnin = Ar::fma(tb.dL[s][i], v, dnin);
         }
         if (MODE == 0 && nb >= 0) {
           for (int i = 0; i < N; ++i) {
             const A v = Ar::from(__ldg(&wc[nb * NB + node_of(N, ax, i, t, DIM)]));
-            uout += tb.L[1 - s][i] * v;
-            dnout += tb.dL[1 - s][i] * v;
+            uout = Ar::fma(tb.L[1 - s][i], v, uout);
+            dnout = Ar::fma(tb.dL[1 - s][i], v, dnout);
           }
         }
         s_t[cl][fp][0] = uin;
@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
             A gi = zero, go = zero;
             for (int m = 0; m < N; ++m) {
               const int q = f * NF + t + (m - tb_) * stride;
-              gi += tb.D[tb_][m] * s_t[cl][q][0];
-              go += tb.D[tb_][m] * s_t[cl][q][1];
+              gi = Ar::fma(tb.D[tb_][m], s_t[cl][q][0], gi);
+              go = Ar::fma(tb.D[tb_][m], s_t[cl][q][1], go);
             }
             dn_in += cown[b] * gi;
             dn_out += cnb[b] * go;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
       const int j0 = j % NP, j1 = (j / NP) % NP, j2 = DIM == 3 ? j / (NP * NP) : 0;
       A wgt = mx.I[ii[0]][j0] * mx.I[ii[1]][j1];
       if (DIM == 3) wgt = wgt * mx.I[ii[2]][j2];
-      pu += wgt * s_p[cl][j];
+      pu = Ar::fma(wgt, s_p[cl][j], pu);
     }
     s_pu[cl][node] = pu;
   }
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
           A wgt = tp.L[1 - s][jj[ax]];
           for (int b = 0; b < DIM; ++b)
             if (b != ax) wgt = wgt * mx.I[tb3[b]][jj[b]];
-          pout += wgt * Ar::from(__ldg(&p[nb * NBP + j]));
+          pout = Ar::fma(wgt, Ar::from(__ldg(&p[nb * NBP + j])), pout);
         }
         pav = half * (pin + pout);
       }
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(((CPB * Shape<NP, DIM>::NB + 31) / 32) * 32)
         A uin = zero, uout = zero;
         for (int i = 0; i < N; ++i) {
           const int nd = node_of(N, ax, i, t, DIM);
-          uin += tb.L[s][i] * s_u[r][cl][nd];
+          uin = Ar::fma(tb.L[s][i], s_u[r][cl][nd], uin);
           if (nb >= 0) uout += tb.L[1 - s][i] * Ar::from(__ldg(&uss[((int64_t)r * g.ncell + nb) * NB + nd]));
         }
         acc += Ar::from(gfp[(1 + r) * NF]) * (nb >= 0 ? half * (uin + uout) : uin);
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
       const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
       A wgt = a == 0 ? mx.D[ii[0]][jj[0]] : mx.I[ii[0]][jj[0]];
       for (int b = 1; b < DIM; ++b) wgt = wgt * (b == a ? mx.D[ii[b]][jj[b]] : mx.I[ii[b]][jj[b]]);
-      acc += wgt * s_p[cl][j];
+      acc = Ar::fma(wgt, s_p[cl][j], acc);
     }
     gref[a] = acc;
   }
@@ -530,6 +530,7 @@ template <int DIM, int N, bool VEL, typename R>
 __global__ void gen_diag_kernel(const __grid_constant__ GG g, const __grid_constant__ Tab1D<R> tb,
                                 R mass, R visc, R adv, R pen, const double* __restrict__ ub,
                                 double* __restrict__ diag) {
+  using Ar = Arith<R>;
   using GC = GeomCount<DIM>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
   constexpr int NG = GC::NG;
@@ -592,7 +593,7 @@ __global__ void gen_diag_kernel(const __grid_constant__ GG g, const __grid_const
           R wi = 0, wo = 0;
           for (int i = 0; i < N; ++i) {
             const int nd = node_of(N, ax, i, t, DIM);
-            wi += tb.L[s][i] * (R)ub[((int64_t)r * g.ncell + cell) * NB + nd];
+            wi = Ar::fma(tb.L[s][i], (R)ub[((int64_t)r * g.ncell + cell) * NB + nd], wi);
             if (nb >= 0) wo += tb.L[1 - s][i] * (R)ub[((int64_t)r * g.ncell + nb) * NB + nd];
           }
           const R nr = (R)gfp[(1 + r) * NF];

@@ -151,9 +151,9 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const int nd = nodeof(N, DIM, ax, i, t);
-          uin += tb.L[s][i] * s_u[cl][nd];
-          dnin += tb.dL[s][i] * s_u[cl][nd];
-          wnin += tb.L[s][i] * s_wb[ax][cl][nd];
+          uin = Ar::fma(tb.L[s][i], s_u[cl][nd], uin);
+          dnin = Ar::fma(tb.dL[s][i], s_u[cl][nd], dnin);
+          wnin = Ar::fma(tb.L[s][i], s_wb[ax][cl][nd], wnin);
         }
         dnin = dnin * sgn * hiK;
         wnin = wnin * sgn;
@@ -168,9 +168,9 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
             for (int i = 0; i < N; ++i) {
               const int nd = nodeof(N, DIM, ax, i, t);
               const A v = Ar::from(__ldg(&wc[nb * NB + nd]));
-              uout += tb.L[1 - s][i] * v;
-              dnout += tb.dL[1 - s][i] * v;
-              wnout += tb.L[1 - s][i] * Ar::from(__ldg(&wb[((int64_t)ax * g.ncell + nb) * NB + nd]));
+              uout = Ar::fma(tb.L[1 - s][i], v, uout);
+              dnout = Ar::fma(tb.dL[1 - s][i], v, dnout);
+              wnout = Ar::fma(tb.L[1 - s][i], Ar::from(__ldg(&wb[((int64_t)ax * g.ncell + nb) * NB + nd])), wnout);
             }
             dnout = dnout * sgn * hiN;
             wnout = wnout * sgn;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const int nd = nodeof(N, DIM, ax, i, t);
-          wi += tb.L[s][i] * s_wb[tt][ax][cl][nd];
+          wi = Ar::fma(tb.L[s][i], s_wb[tt][ax][cl][nd], wi);
           if (nb >= 0) wo += tb.L[1 - s][i] * Ar::from(__ldg(&et.wb[tt][((int64_t)ax * g.ncell + nb) * NB + nd]));
         }
         s_wn[tt][cl][fp][0] = wi * sgn;
@@ -340,8 +340,8 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
         for (int i = 0; i < N; ++i) {
           const int nd = nodeof(N, DIM, ax, i, t);
           const A v = s_v[cl][nd];
-          vin += tb.L[s][i] * v;
-          dvin += tb.dL[s][i] * v;
+          vin = Ar::fma(tb.L[s][i], v, vin);
+          dvin = Ar::fma(tb.dL[s][i], v, dvin);
 #pragma unroll
           for (int tt = 0; tt < NT; ++tt) uin[tt] += tb.L[s][i] * s_u[tt][cl][nd];
         }
@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
               uout[tt] += tb.L[1 - s][i] * u;
               v += visc[tt] * u;
             }
-            vout += tb.L[1 - s][i] * v;
-            dvout += tb.dL[1 - s][i] * v;
+            vout = Ar::fma(tb.L[1 - s][i], v, vout);
+            dvout = Ar::fma(tb.dL[1 - s][i], v, dvout);
           }
           dvout = dvout * sgn * hiN;
           A a = zero;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       const int j0 = j % NP, j1 = (j / NP) % NP, j2 = DIM == 3 ? j / (NP * NP) : 0;
       A wgt = mx.I[ii[0]][j0] * mx.I[ii[1]][j1];
       if (DIM == 3) wgt = wgt * mx.I[ii[2]][j2];
-      pu += wgt * s_p[cl][j];
+      pu = Ar::fma(wgt, s_p[cl][j], pu);
     }
     s_pu[cl][node] = pu;
     s_g[cl][node] = W * pu;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
           A wgt = tp.L[1 - s][sel3(ax, jj[0], jj[1], jj[2])];
           for (int b = 0; b < DIM; ++b)
             if (b != ax) wgt = wgt * mx.I[tb3[b]][jj[b]];
-          pout += wgt * Ar::from(__ldg(&p[nb * NBP + j]));
+          pout = Ar::fma(wgt, Ar::from(__ldg(&p[nb * NBP + j])), pout);
         }
         pav = half * (pin + pout);
       }
@@ -630,7 +630,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
       A wgt = b0_or(c == 0, mx.D[ii[0]][jj[0]], mx.I[ii[0]][jj[0]]);
       for (int b = 1; b < DIM; ++b) wgt = wgt * (b == c ? mx.D[ii[b]][jj[b]] : mx.I[ii[b]][jj[b]]);
-      acc += wgt * s_p[cl][j];
+      acc = Ar::fma(wgt, s_p[cl][j], acc);
     }
     ut[((int64_t)c * g.ncell + cell) * NB + node] = Ar::to_d(acc * Ar::from(g.hi[c][ci[c]]));
   }
@@ -643,6 +643,7 @@ template <int DIM, int N, typename R>
 __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb,
                             R mass, R visc, R adv, R pen, int walls,
                             const double* __restrict__ ub, double* __restrict__ diag) {
+  using Ar = Arith<R>;
   constexpr int NB = Sh<N, DIM>::NB;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= g.ncell * NB) return;
@@ -687,7 +688,7 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
       R unin = 0.0;
       if (adv != 0.0) {
         for (int i = 0; i < N; ++i)
-          unin += tb.L[s][i] * (R)ub[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)];
+          unin = Ar::fma(tb.L[s][i], (R)ub[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)], unin);
         unin *= sgn;
       }
       R fv = 0.0, fg = 0.0;
@@ -705,7 +706,7 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
         if (adv != 0.0) {
           R unout = 0.0;
           for (int i = 0; i < N; ++i)
-            unout += tb.L[1 - s][i] * (R)ub[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)];
+            unout = Ar::fma(tb.L[1 - s][i], (R)ub[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)], unout);
           unout *= sgn;
           const R lam = fmax(fabs(unin), fabs(unout));
           fv += adv * (R(0.5) * (uin * unin + uout * unout) + R(0.5) * lam * jump);
