@@ -1,7 +1,7 @@
 """Throughput of one DG operator apply (GDoF/s), the operator half of the
 benchmark metric, for a workload's mesh on one GPU.
 
-python -m paper_2107_07776_gb300.applybench [--workload tgv32]
+python -m paper_2107_07776_gb300.applybench [--workload tgv32] [--cells N ...]
         [--op momentum|poisson] [--precision fp64|fp64_native|fp32]
         [--launches K] [--warmup W] [--profile]
 
@@ -32,6 +32,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="tgv32", choices=sorted(W.WORKLOADS))
     ap.add_argument("--op", default="momentum", choices=["momentum", "poisson"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_native", "fp32"])
+    ap.add_argument("--cells", type=int, nargs="+", default=None,
+                    help="cells per axis (the workload's mesh scaled; default: its own)")
     ap.add_argument("--launches", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true")
@@ -43,6 +45,9 @@ def main(argv=None):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     w = W.WORKLOADS[args.workload]
+    if args.cells:
+        cells = args.cells * w.dim if len(args.cells) == 1 else args.cells
+        w = w.scaled(tuple(cells))
     mesh = b.Mesh.from_workload(w)
     if not args.no_autotune:
         b.dg_autotune(mesh.handle)
