@@ -132,6 +132,21 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def job_rate(total_ms_local: float, steps: int, dofs_per_rank: int, world: int, device=None):
+    """Whole-job throughput of weakly scaled replicas: every rank advances
+    dofs_per_rank DoFs per step, and the job's time is the slowest rank's
+    (max over ranks, one all-reduce after the timed region).  Returns
+    (ms per step, GDoF/s of all ranks together)."""
+    total = float(total_ms_local)
+    if world > 1:
+        import torch
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    ms = total / steps
+    return ms, dofs_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def step_params(b, w, precond, guess, tol=1e-8, f=None):
     prm = b.dg_step_params()
     prm.dt, prm.gamma, prm.extrapolate = w.dt, 0.0, 1
@@ -218,14 +233,8 @@ def run_ours(args, rank, world):
 
     ms, iters, clocks, launches, (s_main, prm_main) = timed_steps(args.solver, args.steps,
                                                                   args.warmup, True)
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
     dofs = mesh.n_dofs_u + mesh.n_dofs_p
-    value = dofs * world / (ms_per_step * 1e-3) / 1e9
+    ms_per_step, value = job_rate(sum(ms), args.steps, dofs, world, dev)
     compare = {}
     for other in SOLVERS:
         if other == args.solver:
