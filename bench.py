@@ -13,7 +13,8 @@ solves and the learned initial guess (trained in an untimed phase of
 --train-steps steps before the warm-up, inference only while timed);
 "mixed": the same with the linearly extrapolated guess; "plain": FP64
 multigrid and the extrapolated guess.  The other solvers' times per step are
-reported in "compare".  Solves stop at a relative residual of 1e-8.
+reported in "compare"; every solver first takes the same --train-steps +
+--warmup untimed steps, so all of them time the same window of the flow.  Solves stop at a relative residual of 1e-8.
 
 Timing: W untimed warm-up steps; K timed steps, each bracketed by CUDA events
 on the launching stream, with a 512 MiB buffer written between steps (L2 is
@@ -190,6 +191,8 @@ def run_ours(args, rank, world):
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     def timed_steps(name, nsteps, nwarm, sample_clocks=False):
+        # every solver takes the same untimed steps (training phase of the
+        # learned guess + warm-up) so all time the same window of the flow
         pc, guess, learned = SOLVERS[name]
         pc, guess = getattr(b, pc), getattr(b, guess)
         s = b.dg_solver_create(mesh.handle, w.Re, w.c)
@@ -197,8 +200,9 @@ def run_ours(args, rank, world):
         prm = step_params(b, w, pc, guess, f=fdev)
         if learned:  # untimed training phase, then inference only
             b.dg_guess_configure(s, enable=1, train=1, systems=1, lr=1e-3, seed=1)
-            for _ in range(args.train_steps):
-                b.trbdf2_step(s, prm, u, p)
+        for _ in range(args.train_steps):
+            b.trbdf2_step(s, prm, u, p)
+        if learned:
             b.dg_guess_configure(s, enable=1, train=0, systems=1, lr=1e-3, seed=1)
         iters = []
         for _ in range(nwarm):
@@ -239,7 +243,7 @@ def run_ours(args, rank, world):
     for other in SOLVERS:
         if other == args.solver:
             continue
-        ms_o, iters_o, _, _, (s_o, _) = timed_steps(other, max(3, args.steps // 2), 3)
+        ms_o, iters_o, _, _, (s_o, _) = timed_steps(other, max(3, args.steps // 2), args.warmup)
         b.dg_solver_destroy(s_o)
         compare[other] = {"ms_per_step": statistics.mean(ms_o),
                           "iterations_per_step": np.array(iters_o).mean(axis=0).round(2).tolist()}
@@ -372,7 +376,7 @@ def main():
     ap.add_argument("--workload", default="tgv32", choices=sorted(W.WORKLOADS))
     ap.add_argument("--solver", default="mixed+learned", choices=sorted(SOLVERS))
     ap.add_argument("--train-steps", type=int, default=40,
-                    help="untimed training steps of the learned guess before warm-up")
+                    help="untimed steps before the warm-up (the learned guess trains on them)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")

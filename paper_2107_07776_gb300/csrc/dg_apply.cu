@@ -57,6 +57,8 @@ struct GeomPtr<double> {
   static const double* face(const dg_mesh* m, bool p) { return p ? m->gfp64 : m->gfu64; }
   static const double* pen(const dg_mesh* m) { return m->gpen64; }
 };
+static const df64* vol_pairs(const dg_mesh* m, bool p) { return p ? m->gvp_df : m->gvu_df; }
+static const df64* face_pairs(const dg_mesh* m, bool p) { return p ? m->gfp_df : m->gfu_df; }
 template <>
 struct GeomPtr<float> {
   static const float* vol(const dg_mesh* m, bool p) { return p ? m->gvp32 : m->gvu32; }
@@ -106,6 +108,9 @@ static dg_status launch_general_op(const dg_mesh* m, bool pressure, T mass, T vi
   a.gv = GeomPtr<T>::vol(m, pressure);
   a.gf = GeomPtr<T>::face(m, pressure);
   a.gpen = GeomPtr<T>::pen(m);
+  a.gv2 = vol_pairs(m, pressure);
+  a.gf2 = face_pairs(m, pressure);
+  a.gpen2 = m->gpen_df;
   a.mass = mass;
   a.visc = visc;
   a.adv = adv;

@@ -47,10 +47,11 @@ __device__ __forceinline__ int node_of(int N, int a, int i, int t, int dim) {
   return a == 0 ? i + N * t : (a == 1 ? t % N + N * (i + N * (t / N)) : t + N * N * i);
 }
 
-// v[ax] for a run-time axis without a local-memory array access
+// v[ax] for a run-time axis without a local-memory array access (the
+// elements are passed by value, so the array itself stays in registers)
 template <int DIM, typename X>
-__device__ __forceinline__ X pick(const X (&v)[DIM], int ax) {
-  return ax == 0 ? v[0] : (ax == 1 || DIM == 2 ? v[1] : v[DIM - 1]);
+__device__ __forceinline__ X pick(int ax, X v0, X v1, X v2) {
+  return ax == 0 ? v0 : (ax == 1 || DIM == 2 ? v1 : v2);
 }
 __device__ __forceinline__ int pick3(int ax, int v0, int v1, int v2) {
   return ax == 0 ? v0 : (ax == 1 ? v1 : v2);

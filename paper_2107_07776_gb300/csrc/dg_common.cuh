@@ -83,6 +83,11 @@ struct dg_mesh {
   float* gfp32 = nullptr;
   double* gpen64 = nullptr; // penalty geometry per cell face
   float* gpen32 = nullptr;
+  dg::df64* gvu_df = nullptr;  // the FP64 terms split into float pairs
+  dg::df64* gfu_df = nullptr;
+  dg::df64* gvp_df = nullptr;
+  dg::df64* gfp_df = nullptr;
+  dg::df64* gpen_df = nullptr;
   bool geom_u = false;      // velocity terms present (not on multigrid levels)
   bool level = false;       // a multigrid level (pressure space only)
   // autotuned tile shape of the operator kernels: variant index per

@@ -22,6 +22,8 @@
 #include "dg_apply_kernel.cuh"
 #include "dg_geom.cuh"
 
+#include <type_traits>
+
 namespace dg {
 
 template <typename T>
@@ -32,6 +34,11 @@ struct GenArgs {
   const T* gv;    // volume terms [cell][field][node]
   const T* gf;    // face terms [cell][face][field][point]
   const T* gpen;  // penalty geometry [cell][face]
+  // the same terms split into float pairs once at setup, read by the
+  // float-float variant instead of splitting a double at every load
+  const df64* gv2;
+  const df64* gf2;
+  const df64* gpen2;
   T mass, visc, adv, pen;
   int walls;      // 1: SIP + LF wall terms (homogeneous Dirichlet); 0: none (Neumann)
   int ncomp;
@@ -41,6 +48,14 @@ struct GenArgs {
   const T* cdinv;
   T cc1, cc2;
 };
+
+// metric term i: from the float-pair copy in float-float arithmetic, else
+// converted from the storage type
+template <typename A, typename T>
+__device__ __forceinline__ A gload(const T* p, const df64* q, int64_t i) {
+  if constexpr (std::is_same<A, df64>::value) return q[i];
+  else return Arith<A>::from(p[i]);
+}
 
 template <int N, int DIM, bool ADV>
 constexpr int gen_smem_words(int cpb) {
@@ -100,10 +115,12 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
     ci[0] = (int)(cell % a.n0);
     ci[1] = (int)((cell / a.n0) % a.n1);
     ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
-    const T* gv = a.gv + cell * (int64_t)NV * NB + node;
+    const int64_t gvo = cell * (int64_t)NV * NB + node;
+    const T* gv = a.gv + gvo;
+    const df64* gv2 = a.gv2 + gvo;
 #pragma unroll
-    for (int f = 0; f < NG; ++f) Gm[f] = Ar::from(gv[f * NB]);
-    Wm = Ar::from(gv[NG * NB]);
+    for (int f = 0; f < NG; ++f) Gm[f] = gload<A>(gv, gv2, f * NB);
+    Wm = gload<A>(gv, gv2, NG * NB);
     if (ADV) {
       A ubn[DIM];
 #pragma unroll
@@ -115,7 +132,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
       for (int b = 0; b < DIM; ++b) {
         A acc = zero;
 #pragma unroll
-        for (int r = 0; r < DIM; ++r) acc += Ar::from(gv[(NG + 1 + b * DIM + r) * NB]) * ubn[r];
+        for (int r = 0; r < DIM; ++r) acc = Ar::fma(gload<A>(gv, gv2, (NG + 1 + b * DIM + r) * NB), ubn[r], acc);
         ut[b] = acc;
       }
     }
@@ -182,11 +199,13 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
         s_dn[cl][fp][0] = dnin;
         s_dn[cl][fp][1] = dnout;
         if (ADV && c == 0) {
-          const T* gfp = a.gf + ((cell * 2 * DIM + f) * (int64_t)NFF) * NF + t;
+          const int64_t gfo = ((cell * 2 * DIM + f) * (int64_t)NFF) * NF + t;
+          const T* gfp = a.gf + gfo;
+          const df64* gfp2 = a.gf2 + gfo;
           A unin = zero, unout = zero;
 #pragma unroll
           for (int r = 0; r < DIM; ++r) {
-            const A nr = Ar::from(gfp[(1 + r) * NF]);
+            const A nr = gload<A>(gfp, gfp2, (1 + r) * NF);
             A wi = zero, wo = zero;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
@@ -213,17 +232,20 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
         const int cax = pick3(ax, ci[0], ci[1], ci[2]);
         const bool interior =
             pick3(ax, a.per0, a.per1, a.per2) || (s ? cax + 1 < pick3(ax, a.n0, a.n1, a.n2) : cax > 0);
-        const T* gfp = a.gf + ((cell * 2 * DIM + f) * (int64_t)NFF) * NF + t;
-        const A dS = Ar::from(gfp[0]);
+        const int64_t gfo = ((cell * 2 * DIM + f) * (int64_t)NFF) * NF + t;
+        const T* gfp = a.gf + gfo;
+        const df64* gfp2 = a.gf2 + gfo;
+        const A dS = gload<A>(gfp, gfp2, 0);
         A cown[DIM], cnb[DIM];
 #pragma unroll
         for (int b = 0; b < DIM; ++b) {
-          cown[b] = Ar::from(gfp[(OFF_C + b) * NF]);
-          cnb[b] = Ar::from(gfp[(OFF_C + DIM + b) * NF]);
+          cown[b] = gload<A>(gfp, gfp2, (OFF_C + b) * NF);
+          cnb[b] = gload<A>(gfp, gfp2, (OFF_C + DIM + b) * NF);
         }
         const A uin = s_t[cl][fp][0], uout = s_t[cl][fp][1];
-        const A cown_ax = pick<DIM>(cown, ax);
-        A dn_in = cown_ax * s_dn[cl][fp][0], dn_out = pick<DIM>(cnb, ax) * s_dn[cl][fp][1];
+        const A cown_ax = pick<DIM>(ax, cown[0], cown[1], cown[DIM - 1]);
+        const A cnb_ax = pick<DIM>(ax, cnb[0], cnb[1], cnb[DIM - 1]);
+        A dn_in = cown_ax * s_dn[cl][fp][0], dn_out = cnb_ax * s_dn[cl][fp][1];
         {
           int stride = 1;
 #pragma unroll
@@ -243,7 +265,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
           }
         }
         A fv = zero, fg = zero;
-        const A sig = pen * Ar::from(a.gpen[cell * 2 * DIM + f]);
+        const A sig = pen * gload<A>(a.gpen, a.gpen2, cell * 2 * DIM + f);
         if (interior) {
           const A jump = uin - uout;
           fv = visc * (sig * jump - half * (dn_in + dn_out));

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dg_df64.cuh"
 #include "dg_geom.cuh"
 
 namespace dg {
@@ -242,6 +243,12 @@ __global__ void penalty_kernel(const __grid_constant__ Lattice g, const double* 
   gpen[gid] = nb < 0 ? ratio[gid] : 0.5 * (ratio[gid] + ratio[nb * 2 * d + 2 * a + (1 - s)]);
 }
 
+__global__ void to_pairs_kernel(int64_t n, const double* __restrict__ a, df64* __restrict__ b) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = df_split(a[k]);
+}
+
 __global__ void to_f32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
@@ -250,9 +257,10 @@ __global__ void to_f32_kernel(int64_t n, const double* __restrict__ a, float* __
 
 unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-dg_status alloc_pair(int64_t n, double** d64, float** d32) {
+dg_status alloc_pair(int64_t n, double** d64, float** d32, df64** ddf) {
   DG_CUDA(cudaMalloc(d64, sizeof(double) * n));
   DG_CUDA(cudaMalloc(d32, sizeof(float) * n));
+  DG_CUDA(cudaMalloc(ddf, sizeof(df64) * n));
   return DG_OK;
 }
 
@@ -261,11 +269,16 @@ dg_status alloc_pair(int64_t n, double** d64, float** d32) {
 void free_geometry(dg_mesh* m) {
   double** p64[] = {&m->gvu64, &m->gfu64, &m->gvp64, &m->gfp64, &m->gpen64};
   float** p32[] = {&m->gvu32, &m->gfu32, &m->gvp32, &m->gfp32, &m->gpen32};
+  df64** pdf[] = {&m->gvu_df, &m->gfu_df, &m->gvp_df, &m->gfp_df, &m->gpen_df};
   for (double** p : p64) {
     cudaFree(*p);
     *p = nullptr;
   }
   for (float** p : p32) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  for (df64** p : pdf) {
     cudaFree(*p);
     *p = nullptr;
   }
@@ -323,12 +336,12 @@ dg_status build_geometry(dg_mesh* m, bool velocity, cudaStream_t s) {
   const int64_t n_pen = m->ncell * 2 * d;
   dg_status st = DG_OK;
   if (velocity) {
-    st = alloc_pair(n_vu, &m->gvu64, &m->gvu32);
-    if (st == DG_OK) st = alloc_pair(n_fu, &m->gfu64, &m->gfu32);
+    st = alloc_pair(n_vu, &m->gvu64, &m->gvu32, &m->gvu_df);
+    if (st == DG_OK) st = alloc_pair(n_fu, &m->gfu64, &m->gfu32, &m->gfu_df);
   }
-  if (st == DG_OK) st = alloc_pair(n_vp, &m->gvp64, &m->gvp32);
-  if (st == DG_OK) st = alloc_pair(n_fp, &m->gfp64, &m->gfp32);
-  if (st == DG_OK) st = alloc_pair(n_pen, &m->gpen64, &m->gpen32);
+  if (st == DG_OK) st = alloc_pair(n_vp, &m->gvp64, &m->gvp32, &m->gvp_df);
+  if (st == DG_OK) st = alloc_pair(n_fp, &m->gfp64, &m->gfp32, &m->gfp_df);
+  if (st == DG_OK) st = alloc_pair(n_pen, &m->gpen64, &m->gpen32, &m->gpen_df);
   if (st != DG_OK) {
     cudaFree(dV);
     cudaFree(ratio);
@@ -352,6 +365,13 @@ dg_status build_geometry(dg_mesh* m, bool velocity, cudaStream_t s) {
   to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_vp, m->gvp64, m->gvp32);
   to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_fp, m->gfp64, m->gfp32);
   to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_pen, m->gpen64, m->gpen32);
+  if (velocity) {
+    to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_vu, m->gvu64, m->gvu_df);
+    to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_fu, m->gfu64, m->gfu_df);
+  }
+  to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_vp, m->gvp64, m->gvp_df);
+  to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_fp, m->gfp64, m->gfp_df);
+  to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_pen, m->gpen64, m->gpen_df);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(dV);

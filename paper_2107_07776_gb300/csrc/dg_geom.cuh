@@ -39,10 +39,9 @@ struct GeomCount {
   static constexpr int NFP = 1 + 2 * DIM;          // pressure face fields: dS, cown, cnb
 };
 
-// index of G[a][b] (a <= b) in the packed upper triangle
-__host__ __device__ constexpr int sym_index(int dim, int a, int b) {
-  return a <= b ? (dim == 3 ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (a == 0 ? b : 2))
-                : sym_index(dim, b, a);
+// index of G[a][b] in the packed upper triangle (row-major, a <= b)
+__host__ __device__ __forceinline__ constexpr int sym_index(int dim, int a, int b) {
+  return (a < b ? a : b) * dim - (a < b ? a : b) * ((a < b ? a : b) - 1) / 2 + (a < b ? b - a : a - b);
 }
 
 // Builds the metric arrays of a non-affine mesh (velocity terms only when

@@ -565,6 +565,9 @@ GuessState::~GuessState() {
       if (p) cudaFree(p);
   if (yout) cudaFree(yout);
   if (target) cudaFree(target);
+  if (xe) cudaFree(xe);
+  if (dvec) cudaFree(dvec);
+  if (rt) cudaFree(rt);
 }
 
 dg_status mlp_forward_backward(int64_t M, int n_in, int hidden, int n_out, const float* weights,

@@ -65,6 +65,12 @@ struct GuessState {
   bool predicted = false;
   double last_loss = 0.0;
   int64_t train_steps = 0;
+  // Helmholtz safeguard: the extrapolated guess, the learned correction and
+  // the residual / operator image used to weight it (pressure-space vectors)
+  double* xe = nullptr;
+  double* dvec = nullptr;
+  double* rt = nullptr;  // [2 n]: b - A xe, then A d
+  int64_t safe_n = 0;
   ~GuessState();
 };
 

@@ -213,9 +213,27 @@ dg_status ensure_net(dg_solver* s, int k, const SysShape& sh) {
   return DG_OK;
 }
 
-// Writes the initial guess of a stage solve into x; *given = 1 when x holds
-// a guess for the solve (else the caller's value stays).
-dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, double* x) {
+// x = xe + theta d with theta = <d, r_e> / <d, A d> read from sc[0..1] (0
+// when d carries no energy): the energy-norm-optimal multiple of the learned
+// correction d on top of the extrapolated guess xe, r_e = b - A xe
+__global__ void theta_axpy_kernel(int64_t n, const double* __restrict__ sc,
+                                  const double* __restrict__ xe, const double* __restrict__ d,
+                                  double* __restrict__ x) {
+  const double den = sc[1];
+  const double th = den > 0.0 ? sc[0] / den : 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    x[k] = xe[k] + th * d[k];
+}
+
+// Writes the initial guess of a stage solve into x (the caller's value
+// stays when there is no history).  For the pressure Helmholtz systems the
+// learned correction is scaled by the multiple that minimises the energy
+// norm of the initial error along it (one line search of CG, two applies of
+// alpha M^p + K), so the learned guess is never worse than the
+// extrapolation in that norm.
+dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, double* x,
+                        double alpha = 0.0) {
   GuessState& G = s->guess;
   G.predicted = false;
   if (mode != DG_GUESS_EXTRAP && mode != DG_GUESS_LEARNED) return DG_OK;
@@ -257,6 +275,29 @@ dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, dou
   if (st != DG_OK) return st;
   G.predicted = true;
   G.sout = sout;
+  if (k == 0 && alpha > 0.0) {
+    const int64_t n = sh.n;
+    if (G.safe_n < n) {
+      for (double** p : {&G.xe, &G.dvec, &G.rt}) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+      }
+      DG_CUDA(cudaMalloc(&G.xe, sizeof(double) * n));
+      DG_CUDA(cudaMalloc(&G.dvec, sizeof(double) * n));
+      DG_CUDA(cudaMalloc(&G.rt, sizeof(double) * 2 * n));
+      G.safe_n = n;
+    }
+    st = guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], nullptr, 0.0, G.xe, s->stream);
+    if (st == DG_OK) st = s->vo.axpby(n, 1.0, x, -1.0, G.xe, G.dvec);
+    if (st == DG_OK) st = dg_apply_poisson(s->mesh, alpha, G.xe, G.rt, s->stream);
+    if (st == DG_OK) st = s->vo.axpby(n, 1.0, rhs, -1.0, G.rt, G.rt);
+    if (st == DG_OK) st = dg_apply_poisson(s->mesh, alpha, G.dvec, G.rt + n, s->stream);
+    if (st == DG_OK) st = s->vo.dots(n, 2, G.dvec, G.rt, n, s->vo.scal);
+    if (st != DG_OK) return st;
+    theta_axpy_kernel<<<1216, 256, 0, s->stream>>>(n, s->vo.scal, G.xe, G.dvec, x);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+  }
   return DG_OK;
 }
 
@@ -491,7 +532,7 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   if (ho.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->p_g, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
   tr.mark(1);
-  STEP(prepare_guess(s, 1, prm->helm.guess, s->rhs_p, s->p_g));
+  STEP(prepare_guess(s, 1, prm->helm.guess, s->rhs_p, s->p_g, alpha1));
   tr.mark(4);
   STEP(dg_solve_stage(s, nullptr, alpha1, nullptr, s->rhs_p, s->p_g, &ho, &info[1]));
   tr.mark(1);
@@ -551,7 +592,7 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
     DG_CUDA(cudaMemcpyAsync(p, s->p_g, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
   // p (in: p^n, no longer needed) receives p^{n+1}
   tr.mark(1);
-  STEP(prepare_guess(s, 3, prm->helm.guess, s->rhs_p, p));
+  STEP(prepare_guess(s, 3, prm->helm.guess, s->rhs_p, p, alpha2));
   tr.mark(4);
   STEP(dg_solve_stage(s, nullptr, alpha2, nullptr, s->rhs_p, p, &ho, &info[3]));
   tr.mark(1);
