@@ -375,7 +375,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tgv32", choices=sorted(W.WORKLOADS))
     ap.add_argument("--solver", default="mixed+learned", choices=sorted(SOLVERS))
-    ap.add_argument("--train-steps", type=int, default=40,
+    ap.add_argument("--train-steps", type=int, default=200,
                     help="untimed steps before the warm-up (the learned guess trains on them)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel")

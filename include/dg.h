@@ -310,6 +310,15 @@ dg_status dg_mlp_forward_backward(int64_t M, int32_t n_in, int32_t hidden, int32
                                   const float* weights, const float* X, const float* T, float* Y,
                                   float* loss, float* grad, void* stream);
 
+/* Inference of the same network (the solver's path once training stops):
+ * Y = f(X), same layout and rounding points as dg_mlp_forward_backward.
+ * With hidden = 128 and n_out <= 128 it runs as one fused kernel that keeps
+ * the BF16 weights in shared memory (when they fit) and chains the four
+ * tensor-core layers per 16-row tile; otherwise layer by layer.  Allocates
+ * its own scratch; synchronous. */
+dg_status dg_mlp_infer(int64_t M, int32_t n_in, int32_t hidden, int32_t n_out,
+                       const float* weights, const float* X, float* Y, void* stream);
+
 /* Set (device pointer, n_dofs_u) or clear (NULL) the stored u^{n-1+gamma}. */
 dg_status dg_solver_set_history(dg_solver* solver, const double* u_hist);
 

@@ -104,6 +104,7 @@ SIGNATURES = {
     "dg_guess_configure": (ctypes.c_int, [c_void_p, P(dg_guess_opts)]),
     "dg_guess_get_stats": (ctypes.c_int, [c_void_p, P(dg_guess_stats)]),
     "dg_mlp_forward_backward": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_void_p, c_void_p, c_void_p, c_void_p, P(ctypes.c_float), c_void_p, c_void_p]),
+    "dg_mlp_infer": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_solver_save": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solver_load": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solve_helmholtz_noalloc": (ctypes.c_int, [c_void_p, ctypes.c_double, c_void_p, c_void_p, P(dg_solve_opts), P(dg_solve_info), c_void_p]),
@@ -307,6 +308,11 @@ def dg_mlp_forward_backward(M: int, n_in: int, hidden: int, n_out: int, weights,
                                         ptr(Y), ctypes.byref(loss), ptr(grad), stream_ptr(stream)),
           "dg_mlp_forward_backward")
     return loss.value
+
+
+def dg_mlp_infer(M: int, n_in: int, hidden: int, n_out: int, weights, X, Y, stream=None) -> None:
+    check(lib().dg_mlp_infer(M, n_in, hidden, n_out, ptr(weights), ptr(X), ptr(Y),
+                             stream_ptr(stream)), "dg_mlp_infer")
 
 
 def dg_solver_save(solver: int, path: str) -> None:

@@ -157,6 +157,129 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __grid_constant__ 
       }
 }
 
+// ---- fused inference: all four layers in one kernel ----
+// Each CTA keeps the whole network (BF16 weights, padded rows) in shared
+// memory and walks over tiles of 16 rows per warp; a warp's activations stay
+// in its own 16 shared-memory rows between layers (only __syncwarp needed),
+// the accumulators in registers (16 column tiles of m16n8).  Same rounding
+// points as the layer-by-layer path: BF16 inputs, weights and hidden
+// activations, FP32 accumulation, bias added after the accumulation.
+struct InferDesc {
+  int64_t M;
+  int n_in, n_out, kp, nop;  // kp: n_in rounded up to 16; nop: n_out rounded up to 8
+  const __nv_bfloat16* X;    // [M x n_in]
+  const __nv_bfloat16* wb;   // W_l[out][in], packed as in Mlp
+  const float* w;            // FP32 master parameters (biases)
+  int64_t woff[4], boff[4];
+  float* y;                  // [M x n_out]
+};
+
+constexpr int kInferHidden = 128;
+constexpr int kInferWarps = 8;
+constexpr int kInferLdh = kInferHidden + 8;  // padded row of a hidden layer
+
+__host__ __device__ inline int64_t infer_smem_elems(int kp, int nop) {
+  const int s1 = kp + 8, sa = (kp > kInferHidden ? kp : kInferHidden) + 8;
+  return (int64_t)kInferHidden * s1 + 2LL * kInferHidden * kInferLdh + (int64_t)nop * kInferLdh +
+         (int64_t)kInferWarps * 16 * sa;
+}
+
+__global__ void __launch_bounds__(kInferWarps * 32) mlp_infer_kernel(const __grid_constant__ InferDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* sm = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  constexpr int H = kInferHidden, LH = kInferLdh;
+  const int s1 = d.kp + 8, sa = (d.kp > H ? d.kp : H) + 8;
+  __nv_bfloat16* W1 = sm;
+  __nv_bfloat16* W2 = W1 + (int64_t)H * s1;
+  __nv_bfloat16* W3 = W2 + (int64_t)H * LH;
+  __nv_bfloat16* W4 = W3 + (int64_t)H * LH;
+  __nv_bfloat16* act = W4 + (int64_t)d.nop * LH;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const __nv_bfloat16 z16 = __float2bfloat16_rn(0.0f);
+  for (int idx = tid; idx < H * d.kp; idx += nthr) {
+    const int n = idx / d.kp, k = idx % d.kp;
+    W1[n * s1 + k] = k < d.n_in ? d.wb[d.woff[0] + (int64_t)n * d.n_in + k] : z16;
+  }
+  // the hidden layers (the bulk of the weights) as 16-byte vectors when their
+  // packed rows are 16-byte aligned, else element by element
+  const bool vec = ((reinterpret_cast<uintptr_t>(d.wb + d.woff[1]) |
+                     reinterpret_cast<uintptr_t>(d.wb + d.woff[2])) & 15u) == 0;
+  if (vec) {
+    for (int idx = tid; idx < H * H / 8; idx += nthr) {
+      const int n = idx / (H / 8), k = (idx % (H / 8)) * 8;
+      *reinterpret_cast<uint4*>(&W2[n * LH + k]) =
+          *reinterpret_cast<const uint4*>(&d.wb[d.woff[1] + (int64_t)n * H + k]);
+      *reinterpret_cast<uint4*>(&W3[n * LH + k]) =
+          *reinterpret_cast<const uint4*>(&d.wb[d.woff[2] + (int64_t)n * H + k]);
+    }
+  } else {
+    for (int idx = tid; idx < H * H; idx += nthr) {
+      const int n = idx / H, k = idx % H;
+      W2[n * LH + k] = d.wb[d.woff[1] + idx];
+      W3[n * LH + k] = d.wb[d.woff[2] + idx];
+    }
+  }
+  for (int idx = tid; idx < d.nop * H; idx += nthr) {
+    const int n = idx / H, k = idx % H;
+    W4[n * LH + k] = n < d.n_out ? d.wb[d.woff[3] + (int64_t)n * H + k] : z16;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  __nv_bfloat16* A = act + (int64_t)warp * 16 * sa;
+  const int64_t tile = 16 * kInferWarps;
+  for (int64_t r0 = (int64_t)blockIdx.x * tile; r0 < d.M; r0 += (int64_t)gridDim.x * tile) {
+    const int64_t wr0 = r0 + warp * 16;
+    for (int idx = lane; idx < 16 * d.kp; idx += 32) {
+      const int rr = idx / d.kp, k = idx % d.kp;
+      const int64_t row = wr0 + rr;
+      A[rr * sa + k] = (row < d.M && k < d.n_in) ? d.X[row * d.n_in + k] : z16;
+    }
+    __syncwarp();
+    for (int l = 0; l < 4; ++l) {
+      const __nv_bfloat16* W = l == 0 ? W1 : (l == 1 ? W2 : (l == 2 ? W3 : W4));
+      const int ldw = l == 0 ? s1 : LH;
+      const int K = l == 0 ? d.kp : H;
+      const int ntiles = l == 3 ? d.nop / 8 : H / 8;
+      float acc[H / 8][4];
+#pragma unroll
+      for (int nt = 0; nt < H / 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[nt][q] = 0.0f;
+      for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t*>(&A[g * sa + k0 + 2 * t]);
+        a[1] = *reinterpret_cast<const uint32_t*>(&A[(g + 8) * sa + k0 + 2 * t]);
+        a[2] = *reinterpret_cast<const uint32_t*>(&A[g * sa + k0 + 2 * t + 8]);
+        a[3] = *reinterpret_cast<const uint32_t*>(&A[(g + 8) * sa + k0 + 2 * t + 8]);
+#pragma unroll
+        for (int nt = 0; nt < H / 8; ++nt) {
+          if (nt >= ntiles) break;
+          uint32_t bq[2];
+          bq[0] = *reinterpret_cast<const uint32_t*>(&W[(nt * 8 + g) * ldw + k0 + 2 * t]);
+          bq[1] = *reinterpret_cast<const uint32_t*>(&W[(nt * 8 + g) * ldw + k0 + 2 * t + 8]);
+          mma_bf16(acc[nt], a, bq);
+        }
+      }
+      __syncwarp();  // every lane has read this layer's input rows
+      const float* bias = d.w + d.boff[l];
+#pragma unroll
+      for (int nt = 0; nt < H / 8; ++nt) {
+        if (nt >= ntiles) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rr = g + (q >> 1) * 8, col = nt * 8 + 2 * t + (q & 1);
+          if (l < 3) {
+            A[rr * sa + col] = __float2bfloat16_rn(silu(acc[nt][q] + bias[col]));
+          } else if (col < d.n_out && wr0 + rr < d.M) {
+            d.y[(wr0 + rr) * d.n_out + col] = acc[nt][q] + bias[col];
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 unsigned gridn(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -252,8 +375,8 @@ __global__ void adam_kernel(int64_t n, float* __restrict__ w, const float* __res
 __global__ void features_kernel(int64_t ncell, int ncomp, int nbc, const double* __restrict__ h0,
                                 const double* __restrict__ h1, const double* __restrict__ h2,
                                 const double* __restrict__ h3, const double* __restrict__ b,
-                                double is0, double is1, double is2, double is3, double isb,
-                                __nv_bfloat16* __restrict__ X) {
+                                const double* __restrict__ dsc, __nv_bfloat16* __restrict__ X) {
+  const double is0 = dsc[0], is1 = dsc[1], is2 = dsc[2], is3 = dsc[3], isb = dsc[4];
   const int nbs = ncomp * nbc;
   const int64_t total = ncell * nbs;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
@@ -298,10 +421,37 @@ __global__ void __launch_bounds__(256) hist_norms_kernel(int64_t n, const double
     for (int j = 0; j < 5; ++j) part[blockIdx.x * 5 + j] = s[j][0];
 }
 
-// x = 2 h0 - h1 + so * y  (y == nullptr: plain extrapolation)
+// block RMS values of the features from the partial sums (one warp per
+// feature block, fixed lane assignment and reduction tree): dsc[0..4] inverse scales, dsc[5] the output scale (the
+// second difference's RMS, else the first's, else the level's), dsc[6] its
+// inverse
+__global__ void __launch_bounds__(160) guess_scales_kernel(int nb, int64_t n, const double* __restrict__ part,
+                                                           double* __restrict__ dsc) {
+  __shared__ double rms[5];
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;  // one warp per block j
+  double a = 0.0;
+  for (int i = lane; i < nb; i += 32) a += part[i * 5 + j];  // fixed assignment and order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) rms[j] = sqrt(a / (double)n);
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    const double r = rms[threadIdx.x];
+    dsc[threadIdx.x] = 1.0 / (r > 0.0 && isfinite(r) ? r : 1.0);
+  }
+  if (threadIdx.x == 0) {
+    const double s0 = rms[0] > 0.0 && isfinite(rms[0]) ? rms[0] : 1.0;
+    const double so = rms[2] > 0.0 ? rms[2] : (rms[1] > 0.0 ? rms[1] : s0);
+    dsc[5] = so;
+    dsc[6] = 1.0 / so;
+  }
+}
+
+// x = 2 h0 - h1 + dsc[5] * y  (y == nullptr: plain extrapolation)
 __global__ void apply_guess_kernel(int64_t ncell, int ncomp, int nbc, const double* __restrict__ h0,
                                    const double* __restrict__ h1, const float* __restrict__ y,
-                                   double so, double* __restrict__ x) {
+                                   const double* __restrict__ dsc, double* __restrict__ x) {
+  const double so = y ? dsc[5] : 0.0;
   const int nbs = ncomp * nbc;
   const int64_t total = ncell * nbs;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
@@ -319,7 +469,8 @@ __global__ void apply_guess_kernel(int64_t ncell, int ncomp, int nbc, const doub
 // t = (x* - (2 h0 - h1)) / so in network layout
 __global__ void target_kernel(int64_t ncell, int ncomp, int nbc, const double* __restrict__ h0,
                               const double* __restrict__ h1, const double* __restrict__ xs,
-                              double iso, float* __restrict__ t) {
+                              const double* __restrict__ dsc, float* __restrict__ t) {
+  const double iso = dsc[6];
   const int nbs = ncomp * nbc;
   const int64_t total = ncell * nbs;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
@@ -437,6 +588,43 @@ dg_status Mlp::reserve(int64_t rows, cudaStream_t s) {
                        (int64_t)n_out * hidden;
   part_cap = 64 * maxw;
   DG_CUDA(cudaMalloc(&part, sizeof(float) * part_cap));
+  return DG_OK;
+}
+
+// Inference only: the fused kernel when the network fits in shared memory
+// (hidden width 128), else the layer-by-layer GEMMs.
+dg_status Mlp::infer(int64_t M, float* y, cudaStream_t s) {
+  const int kp = (n_in + 15) / 16 * 16, nop = (n_out + 7) / 8 * 8;
+  const int64_t bytes = 2 * infer_smem_elems(kp, nop);
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (hidden != kInferHidden || nop > kInferHidden || bytes > max_optin) return forward(M, y, s);
+  if (M <= 0) return DG_OK;
+  DG_CUDA(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  int per_sm = 0;
+  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_kernel, kInferWarps * 32, bytes));
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (M + 16 * kInferWarps - 1) / (16 * kInferWarps);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * std::max(1, per_sm)));
+  InferDesc d;
+  d.M = M;
+  d.n_in = n_in;
+  d.n_out = n_out;
+  d.kp = kp;
+  d.nop = nop;
+  d.X = xb;
+  d.wb = wb;
+  d.w = w;
+  for (int l = 0; l < 4; ++l) {
+    d.woff[l] = woff[l];
+    d.boff[l] = boff[l];
+  }
+  d.y = y;
+  mlp_infer_kernel<<<(unsigned)grid, kInferWarps * 32, bytes, s>>>(d);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
@@ -559,7 +747,7 @@ GuessState::~GuessState() {
   delete net[0];
   delete net[1];
   if (part) cudaFree(part);
-  if (host_part) cudaFreeHost(host_part);
+  if (dsc) cudaFree(dsc);
   for (auto& sl : hist)
     for (double* p : sl)
       if (p) cudaFree(p);
@@ -596,51 +784,63 @@ dg_status mlp_forward_backward(int64_t M, int n_in, int hidden, int n_out, const
   return DG_OK;
 }
 
+dg_status mlp_infer(int64_t M, int n_in, int hidden, int n_out, const float* weights,
+                    const float* X, float* Y, cudaStream_t s) {
+  Mlp net;
+  dg_status st = net.init(n_in, hidden, n_out, 1, s);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemcpyAsync(net.w, weights, sizeof(float) * net.nparam, cudaMemcpyDeviceToDevice, s));
+  st = net.sync_bf16(s);
+  if (st != DG_OK) return st;
+  st = net.reserve(M, s);
+  if (st != DG_OK) return st;
+  f32_to_bf16_rows_kernel<<<gridn(M * n_in), 256, 0, s>>>(M * n_in, X, net.xb); count_launch();
+  DG_CUDA(cudaGetLastError());
+  st = net.infer(M, Y, s);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
 // ------------------------------------------------------------------ solver glue
 dg_status guess_features(Mlp& net, int64_t ncell, int ncomp, int nbc, double* const h[4],
-                         const double* b, double* const scale, double* out_scale, double* part,
-                         double* host_part, cudaStream_t s) {
+                         const double* b, double* part, double* dsc, cudaStream_t s) {
   dg_status st = net.reserve(ncell, s);
   if (st != DG_OK) return st;
   const int64_t n = ncell * ncomp * nbc;
   const int nb = (int)std::min<int64_t>(1216, std::max<int64_t>(1, (n + 1023) / 1024));
   hist_norms_kernel<<<nb, 256, 0, s>>>(n, h[0], h[1], h[2], h[3], b, part); count_launch();
-  DG_CUDA(cudaGetLastError());
-  DG_CUDA(cudaMemcpyAsync(host_part, part, sizeof(double) * 5 * nb, cudaMemcpyDeviceToHost, s));
-  DG_CUDA(cudaStreamSynchronize(s));
-  double rms[5] = {0, 0, 0, 0, 0};
-  for (int i = 0; i < nb; ++i)
-    for (int j = 0; j < 5; ++j) rms[j] += host_part[i * 5 + j];
-  for (int j = 0; j < 5; ++j) {
-    rms[j] = std::sqrt(rms[j] / (double)n);
-    scale[j] = rms[j] > 0.0 && std::isfinite(rms[j]) ? rms[j] : 1.0;
-  }
-  // the correction to the linear extrapolation is of the size of the second
-  // difference; without one (fewer than three distinct levels) fall back to
-  // the first difference, then to the level
-  *out_scale = rms[2] > 0.0 ? rms[2] : (rms[1] > 0.0 ? rms[1] : scale[0]);
-  features_kernel<<<gridn(n), 256, 0, s>>>(ncell, ncomp, nbc, h[0], h[1], h[2], h[3], b,
-                                           1.0 / scale[0], 1.0 / scale[1], 1.0 / scale[2],
-                                           1.0 / scale[3], 1.0 / scale[4], net.xb); count_launch();
+  guess_scales_kernel<<<1, 160, 0, s>>>(nb, n, part, dsc); count_launch();
+  features_kernel<<<gridn(n), 256, 0, s>>>(ncell, ncomp, nbc, h[0], h[1], h[2], h[3], b, dsc,
+                                           net.xb); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 dg_status guess_apply(int64_t ncell, int ncomp, int nbc, const double* h0, const double* h1,
-                      const float* y, double so, double* x, cudaStream_t s) {
-  apply_guess_kernel<<<gridn(ncell * ncomp * nbc), 256, 0, s>>>(ncell, ncomp, nbc, h0, h1, y, so, x); count_launch();
+                      const float* y, const double* dsc, double* x, cudaStream_t s) {
+  apply_guess_kernel<<<gridn(ncell * ncomp * nbc), 256, 0, s>>>(ncell, ncomp, nbc, h0, h1, y, dsc, x); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 dg_status guess_target(int64_t ncell, int ncomp, int nbc, const double* h0, const double* h1,
-                       const double* xs, double so, float* t, cudaStream_t s) {
-  target_kernel<<<gridn(ncell * ncomp * nbc), 256, 0, s>>>(ncell, ncomp, nbc, h0, h1, xs, 1.0 / so, t); count_launch();
+                       const double* xs, const double* dsc, float* t, cudaStream_t s) {
+  target_kernel<<<gridn(ncell * ncomp * nbc), 256, 0, s>>>(ncell, ncomp, nbc, h0, h1, xs, dsc, t); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 }  // namespace dg
+
+extern "C" dg_status dg_mlp_infer(int64_t M, int32_t n_in, int32_t hidden, int32_t n_out,
+                                  const float* weights, const float* X, float* Y, void* stream) {
+  if (M < 1 || n_in < 1 || hidden < 1 || n_out < 1 || !weights || !X || !Y) {
+    dg::set_error("dg_mlp_infer: bad argument");
+    return DG_EINVAL;
+  }
+  return dg::mlp_infer(M, n_in, hidden, n_out, weights, X, Y, reinterpret_cast<cudaStream_t>(stream));
+}
 
 extern "C" dg_status dg_mlp_forward_backward(int64_t M, int32_t n_in, int32_t hidden, int32_t n_out,
                                              const float* weights, const float* X, const float* T,

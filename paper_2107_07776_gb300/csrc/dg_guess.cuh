@@ -40,6 +40,9 @@ struct Mlp {
   dg_status sync_bf16(cudaStream_t s);
   // Y = f(X) for M rows; X given as BF16 in xb (already filled) -> y [M x n_out]
   dg_status forward(int64_t M, float* y, cudaStream_t s);
+  // the same output without keeping activations for a backward pass (one
+  // fused launch when the network fits in shared memory)
+  dg_status infer(int64_t M, float* y, cudaStream_t s);
   // gradients of mean((Y - T)^2) after forward(); loss returned if non-null
   dg_status backward(int64_t M, const float* y, const float* t, double* loss, cudaStream_t s);
   dg_status adam_step(float lr, cudaStream_t s);
@@ -58,10 +61,8 @@ struct GuessState {
   float* yout = nullptr;               // [rows x n_out] network output
   float* target = nullptr;             // [rows x n_out] training target
   int64_t out_cap = 0;
-  double sout = 1.0;                   // output scale of the last prediction
-  double scale[5] = {1, 1, 1, 1, 1};   // input block scales of the last prediction
-  double* part = nullptr;              // norm partials (device) and their host copy
-  double* host_part = nullptr;
+  double* part = nullptr;              // norm partials (device)
+  double* dsc = nullptr;               // device: inverse input scales, output scale, its inverse
   bool predicted = false;
   double last_loss = 0.0;
   int64_t train_steps = 0;
@@ -75,17 +76,19 @@ struct GuessState {
 };
 
 // solver glue: features of one stage system from its history (h[0] newest)
-// and right-hand side (also returns the block scales and the output scale);
-// the guess x = 2 h0 - h1 + sout y; the training target.
+// and right-hand side, with the block scales and the output scale computed
+// on the device into dsc (no host round trip); the guess x = 2 h0 - h1 +
+// dsc[5] y; the training target.
 dg_status guess_features(Mlp& net, int64_t ncell, int ncomp, int nbc, double* const h[4],
-                         const double* b, double* const scale, double* out_scale, double* part,
-                         double* host_part, cudaStream_t s);
+                         const double* b, double* part, double* dsc, cudaStream_t s);
 dg_status guess_apply(int64_t ncell, int ncomp, int nbc, const double* h0, const double* h1,
-                      const float* y, double sx, double* x, cudaStream_t s);
+                      const float* y, const double* dsc, double* x, cudaStream_t s);
 dg_status guess_target(int64_t ncell, int ncomp, int nbc, const double* h0, const double* h1,
-                       const double* xs, double sx, float* t, cudaStream_t s);
+                       const double* xs, const double* dsc, float* t, cudaStream_t s);
 
-// GEMM entry used by the tests' gradient check: see dg_mlp_forward_backward.
+// entries of the tests' checks: see dg_mlp_forward_backward, dg_mlp_infer
+dg_status mlp_infer(int64_t M, int n_in, int hidden, int n_out, const float* weights,
+                    const float* X, float* Y, cudaStream_t s);
 dg_status mlp_forward_backward(int64_t M, int n_in, int hidden, int n_out, const float* weights,
                                const float* X, const float* T, float* Y, float* loss, float* grad,
                                cudaStream_t s);

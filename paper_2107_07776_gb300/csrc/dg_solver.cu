@@ -213,14 +213,15 @@ dg_status ensure_net(dg_solver* s, int k, const SysShape& sh) {
   return DG_OK;
 }
 
-// x = xe + theta d with theta = <d, r_e> / <d, A d> read from sc[0..1] (0
-// when d carries no energy): the energy-norm-optimal multiple of the learned
-// correction d on top of the extrapolated guess xe, r_e = b - A xe
+// x = xe + theta d with theta = (<d, b> - <A d, xe>) / <d, A d> from sc =
+// [<d, A d>, <d, b>, <A d, xe>] (0 when d carries no energy): the energy-
+// norm-optimal multiple of the learned correction d on top of the
+// extrapolated guess xe
 __global__ void theta_axpy_kernel(int64_t n, const double* __restrict__ sc,
                                   const double* __restrict__ xe, const double* __restrict__ d,
                                   double* __restrict__ x) {
-  const double den = sc[1];
-  const double th = den > 0.0 ? sc[0] / den : 0.0;
+  const double den = sc[0];
+  const double th = den > 0.0 ? (sc[1] - sc[2]) / den : 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     x[k] = xe[k] + th * d[k];
@@ -248,17 +249,15 @@ dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, dou
   if (cnt < 2) return DG_OK;
   const int k = (slot & 1) ? 0 : 1;
   const bool use_net = mode == DG_GUESS_LEARNED && G.enable && ((G.systems >> k) & 1) && cnt >= 4;
-  if (!use_net) return guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], nullptr, 0.0, x, s->stream);
+  if (!use_net) return guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], nullptr, nullptr, x, s->stream);
   dg_status st = ensure_net(s, k, sh);
   if (st != DG_OK) return st;
   if (!G.part) {
     DG_CUDA(cudaMalloc(&G.part, sizeof(double) * 5 * 1216));
-    DG_CUDA(cudaMallocHost(&G.host_part, sizeof(double) * 5 * 1216));
+    DG_CUDA(cudaMalloc(&G.dsc, sizeof(double) * 8));
   }
   Mlp& net = *G.net[k];
-  double sout = 1.0;
-  st = guess_features(net, m->ncell, sh.ncomp, sh.nbc, h, rhs, G.scale, &sout, G.part,
-                      G.host_part, s->stream);
+  st = guess_features(net, m->ncell, sh.ncomp, sh.nbc, h, rhs, G.part, G.dsc, s->stream);
   if (st != DG_OK) return st;
   const int64_t need = m->ncell * net.n_out;
   if (need > G.out_cap) {
@@ -269,12 +268,11 @@ dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, dou
     DG_CUDA(cudaMalloc(&G.target, sizeof(float) * need));
     G.out_cap = need;
   }
-  st = net.forward(m->ncell, G.yout, s->stream);
+  st = G.train ? net.forward(m->ncell, G.yout, s->stream) : net.infer(m->ncell, G.yout, s->stream);
   if (st != DG_OK) return st;
-  st = guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], G.yout, sout, x, s->stream);
+  st = guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], G.yout, G.dsc, x, s->stream);
   if (st != DG_OK) return st;
   G.predicted = true;
-  G.sout = sout;
   if (k == 0 && alpha > 0.0) {
     const int64_t n = sh.n;
     if (G.safe_n < n) {
@@ -287,12 +285,16 @@ dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, dou
       DG_CUDA(cudaMalloc(&G.rt, sizeof(double) * 2 * n));
       G.safe_n = n;
     }
-    st = guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], nullptr, 0.0, G.xe, s->stream);
+    // theta = <d, b - A xe> / <d, A d> = (<d, b> - <A d, xe>) / <d, A d> (A
+    // symmetric): one apply, to the correction only
+    st = guess_apply(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], nullptr, nullptr, G.xe, s->stream);
     if (st == DG_OK) st = s->vo.axpby(n, 1.0, x, -1.0, G.xe, G.dvec);
-    if (st == DG_OK) st = dg_apply_poisson(s->mesh, alpha, G.xe, G.rt, s->stream);
-    if (st == DG_OK) st = s->vo.axpby(n, 1.0, rhs, -1.0, G.rt, G.rt);
-    if (st == DG_OK) st = dg_apply_poisson(s->mesh, alpha, G.dvec, G.rt + n, s->stream);
-    if (st == DG_OK) st = s->vo.dots(n, 2, G.dvec, G.rt, n, s->vo.scal);
+    if (st == DG_OK) st = dg_apply_poisson(s->mesh, alpha, G.dvec, G.rt, s->stream);
+    if (st == DG_OK) {
+      DG_CUDA(cudaMemcpyAsync(G.rt + n, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+      st = s->vo.dots(n, 2, G.dvec, G.rt, n, s->vo.scal);       // <d, A d>, <d, b>
+    }
+    if (st == DG_OK) st = s->vo.dots(n, 1, G.rt, G.xe, n, s->vo.scal + 2);  // <A d, xe>
     if (st != DG_OK) return st;
     theta_axpy_kernel<<<1216, 256, 0, s->stream>>>(n, s->vo.scal, G.xe, G.dvec, x);
     count_launch();
@@ -312,7 +314,7 @@ dg_status finish_guess(dg_solver* s, int slot, int mode, const double* xs) {
   if (G.predicted && G.train) {
     const int k = (slot & 1) ? 0 : 1;
     Mlp& net = *G.net[k];
-    dg_status st = guess_target(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], xs, G.sout, G.target, s->stream);
+    dg_status st = guess_target(m->ncell, sh.ncomp, sh.nbc, h[0], h[1], xs, G.dsc, G.target, s->stream);
     if (st != DG_OK) return st;
     double loss;
     st = net.backward(m->ncell, G.yout, G.target, &loss, s->stream);

@@ -52,6 +52,35 @@ def test_network_forward_backward_matches_oracle(n_in, hidden, n_out, M):
         o += n
 
 
+@pytest.mark.parametrize("n_in,hidden,n_out,M", [(40, 128, 8, 3001), (135, 128, 27, 1000),
+                                                 (405, 128, 81, 300), (24, 64, 9, 777)])
+def test_network_inference_matches_oracle(n_in, hidden, n_out, M):
+    """The solver's inference path once training stops: the fused kernel
+    (weights in shared memory, the four tensor-core layers per 16-row tile;
+    hidden 128 when the network fits) or the layer-by-layer GEMMs otherwise,
+    against the oracle's forward with the same BF16 rounding points, and
+    against the training-path forward on the GPU."""
+    from paper_2107_07776_gb300 import binding as b
+    rng = np.random.default_rng(n_in + 1)
+    d = mlp.dims_of(n_in, hidden, n_out)
+    w = []
+    for l in range(4):
+        w.append(rng.uniform(-1, 1, d[l + 1] * d[l]) * math.sqrt(3.0 / d[l]))
+        w.append(rng.uniform(-0.1, 0.1, d[l + 1]))
+    w = np.concatenate(w).astype(np.float32)
+    X = rng.standard_normal((M, n_in)).astype(np.float32)
+    Yr, _, _ = mlp.forward_backward(w.astype(np.float64), X, np.zeros((M, n_out), np.float32),
+                                    n_in, hidden, n_out)
+    dev = lambda a: torch.tensor(a, device="cuda")
+    Yi = torch.empty((M, n_out), dtype=torch.float32, device="cuda")
+    b.dg_mlp_infer(M, n_in, hidden, n_out, dev(w), dev(X), Yi)
+    Yf = torch.empty((M, n_out), dtype=torch.float32, device="cuda")
+    b.dg_mlp_forward_backward(M, n_in, hidden, n_out, dev(w), dev(X), None, Yf, None)
+    rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))
+    assert rel(Yi.cpu().numpy(), Yr) < 5e-3
+    assert rel(Yi.cpu().numpy(), Yf.cpu().numpy()) < 2e-3
+
+
 def _run(b, mesh, w, steps, mode, train_steps, u0, p0, tol=1e-10):
     s = b.dg_solver_create(mesh.handle, w.Re, w.c)
     if mode == b.DG_GUESS_LEARNED:
