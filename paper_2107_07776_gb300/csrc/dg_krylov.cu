@@ -119,6 +119,32 @@ __global__ void cg_update_kernel(int64_t n, double a, const double* __restrict__
   }
 }
 
+// the same update with a = sc[irz] / sc[ipq] read on the device
+__global__ void cg_update_dev_kernel(int64_t n, const double* __restrict__ sc, int irz, int ipq,
+                                     const double* __restrict__ p, const double* __restrict__ q,
+                                     double* __restrict__ x, double* __restrict__ r,
+                                     double* __restrict__ r_old) {
+  const double a = sc[irz] / sc[ipq];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    x[k] += a * p[k];
+    const double rk = r[k];
+    r_old[k] = rk;
+    r[k] = rk - a * q[k];
+  }
+}
+
+// flexible (Polak-Ribiere) direction: p = z + beta p, beta = (<z, r> -
+// <z, r_old>) / rz_old with sc[izr] = <z, r>, sc[izr + 1] = <z, r_old>,
+// sc[irz] = rz_old
+__global__ void cg_direction_kernel(int64_t n, const double* __restrict__ sc, int izr, int irz,
+                                    const double* __restrict__ z, double* __restrict__ p) {
+  const double beta = (sc[izr] - sc[izr + 1]) / sc[irz];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    p[k] = z[k] + beta * p[k];
+}
+
 unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -171,36 +197,52 @@ dg_status VecOps::invert(int64_t n, const double* d, int64_t period, double* out
 // Restarted GMRES(m), right Jacobi preconditioning (x = x0 + D^-1 V y, so the
 // Arnoldi residual is the true residual), classical Gram-Schmidt applied
 // twice (CGS2) through the fused multi-dot / multi-axpy kernels.
+// Restarted GMRES(m) with right Jacobi preconditioning and two classical
+// Gram-Schmidt passes.  Host round trips: one per cycle start (|b| and |r0|
+// together) and one per Arnoldi step (both passes' coefficients and |w| in
+// one copy); the small Hessenberg problem is solved on the host.
+//   hdev: >= 3 * 256 doubles: [0, 256) pass-1 coefficients and y, [256, 512)
+//   pass-2 coefficients, [512] |w|^2.  vo.host_scal: >= 1024 doubles (pinned),
+//   [768, 1024) stages y.
 dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv, const double* b,
                       double* x, double* V /* (m+1) n */, double* w, double* hdev, int m,
                       double tol, int max_iter, double timeout_s, dg_solve_info* info) {
   using clock = std::chrono::steady_clock;
   const auto t0 = clock::now();
-  double bnorm2;
-  dg_status st = vo.dots_host(n, 1, b, b, n, &bnorm2);
-  if (st != DG_OK) return st;
-  const double bnorm = std::sqrt(bnorm2);
   info->iterations = 0;
   info->res0 = info->res_final = 0.0;
-  if (!std::isfinite(bnorm)) return DG_EBREAKDOWN;
-  if (bnorm == 0.0) {
-    DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, vo.stream));
-    return DG_OK;
+  if (m > 255) {
+    set_error("gmres: restart above 255");
+    return DG_EINVAL;
   }
-  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), y(m), hcol(m + 2),
-      hcol2(m + 2);
+  double* const h1 = hdev;
+  double* const h2 = hdev + 256;
+  double* const hw = hdev + 512;
+  double* const hs = vo.host_scal;
+  double* const hy = vo.host_scal + 768;
+  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), hcol(m + 2);
   int it = 0;
   bool first = true;
+  double bnorm = 0.0;
   while (true) {
-    // r = b - A x -> V_0
-    st = A(x, w);
+    // r = b - A x -> V_0, with |b|^2 (first cycle) and |r|^2 in one round trip
+    dg_status st = A(x, w);
     if (st != DG_OK) return st;
     st = vo.axpby(n, 1.0, b, -1.0, w, V);
+    if (st == DG_OK) st = vo.dots(n, 1, V, V, n, vo.scal + 1);
+    if (st == DG_OK && first) st = vo.dots(n, 1, b, b, n, vo.scal);
     if (st != DG_OK) return st;
-    double beta2;
-    st = vo.dots_host(n, 1, V, V, n, &beta2);
-    if (st != DG_OK) return st;
-    double beta = std::sqrt(beta2);
+    DG_CUDA(cudaMemcpyAsync(hs, vo.scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, vo.stream));
+    DG_CUDA(cudaStreamSynchronize(vo.stream));
+    if (first) {
+      bnorm = std::sqrt(hs[0]);
+      if (!std::isfinite(bnorm)) return DG_EBREAKDOWN;
+      if (bnorm == 0.0) {
+        DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, vo.stream));
+        return DG_OK;
+      }
+    }
+    const double beta = std::sqrt(hs[1]);
     if (!std::isfinite(beta)) return DG_EBREAKDOWN;
     if (first) {
       info->res0 = beta;
@@ -227,21 +269,22 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
         st = A(vj, w);
       }
       if (st != DG_OK) return st;
-      // two classical Gram-Schmidt passes
+      // two classical Gram-Schmidt passes on the device, then |w|^2
       for (int pass = 0; pass < 2; ++pass) {
-        st = vo.dots(n, j + 1, w, V, n, hdev);
+        double* hc = pass == 0 ? h1 : h2;
+        st = vo.dots(n, j + 1, w, V, n, hc);
         if (st != DG_OK) return st;
-        multi_axpy_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j + 1, hdev, V, n, w); count_launch();
+        multi_axpy_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j + 1, hc, V, n, w); count_launch();
         DG_CUDA(cudaGetLastError());
-        DG_CUDA(cudaMemcpyAsync(vo.host_scal, hdev, sizeof(double) * (j + 1),
-                                cudaMemcpyDeviceToHost, vo.stream));
-        DG_CUDA(cudaStreamSynchronize(vo.stream));
-        for (int i = 0; i <= j; ++i) (pass == 0 ? hcol : hcol2)[i] = vo.host_scal[i];
       }
-      double hn2;
-      st = vo.dots_host(n, 1, w, w, n, &hn2);
+      st = vo.dots(n, 1, w, w, n, hw);
       if (st != DG_OK) return st;
-      for (int i = 0; i <= j; ++i) hcol[i] += hcol2[i];
+      DG_CUDA(cudaMemcpyAsync(hs, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, vo.stream));
+      DG_CUDA(cudaMemcpyAsync(hs + 256, h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, vo.stream));
+      DG_CUDA(cudaMemcpyAsync(hs + 512, hw, sizeof(double), cudaMemcpyDeviceToHost, vo.stream));
+      DG_CUDA(cudaStreamSynchronize(vo.stream));
+      const double hn2 = hs[512];
+      for (int i = 0; i <= j; ++i) hcol[i] = hs[i] + hs[256 + i];
       hcol[j + 1] = std::sqrt(hn2);
       if (!std::isfinite(hcol[j + 1])) return DG_EBREAKDOWN;
       // Givens rotations
@@ -279,16 +322,17 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
         break;
       }
     }
-    // y = H^-1 g (upper triangular), x += D^-1 V y
+    // y = H^-1 g (upper triangular) in pinned host memory, x += D^-1 V y.  The
+    // copy is asynchronous: the staging area is written again only after the
+    // next cycle's round trip.
     for (int i = j - 1; i >= 0; --i) {
       double s = g[i];
-      for (int l = i + 1; l < j; ++l) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
+      for (int l = i + 1; l < j; ++l) s -= H[(size_t)i * m + l] * hy[l];
+      hy[i] = s / H[(size_t)i * m + i];
     }
-    DG_CUDA(cudaMemcpyAsync(hdev, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, vo.stream));
-    gmres_update_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j, hdev, V, n, dinv, x); count_launch();
+    DG_CUDA(cudaMemcpyAsync(h1, hy, sizeof(double) * j, cudaMemcpyHostToDevice, vo.stream));
+    gmres_update_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j, h1, V, n, dinv, x); count_launch();
     DG_CUDA(cudaGetLastError());
-    DG_CUDA(cudaStreamSynchronize(vo.stream));  // y is host memory
     if (timeout_s > 0 && std::chrono::duration<double>(clock::now() - t0).count() > timeout_s)
       return DG_ETIMEOUT;
     // with two Gram-Schmidt passes the Arnoldi residual tracks the true one,
@@ -301,29 +345,35 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
 // Flexible preconditioned CG (Polak-Ribiere beta = <z, r - r_old>/<z_old, r_old>),
 // robust when the preconditioner varies between iterations (multigrid in
 // reduced precision).  P == nullptr: unpreconditioned.
+// Flexible preconditioned CG.  Its scalars stay on the device: the step
+// length and the direction update read them there, so each iteration needs
+// one host round trip (the residual norm for the stopping test, with <p, A p>
+// for the breakdown test) instead of three.
+//   device scalars (vo.scal): [0] <b, b>  [1] <r, r>  [2] <p, A p>
+//   [3], [4] <z, r>, <z, r_old>  [5], [6] <z, r> of alternate iterations (rz)
 dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const double* b,
                    double* x, double* r, double* r_old, double* z, double* p, double* q,
                    double tol, int max_iter, double timeout_s, dg_solve_info* info) {
   using clock = std::chrono::steady_clock;
   const auto t0 = clock::now();
   info->iterations = 0;
-  double bb;
-  dg_status st = vo.dots_host(n, 1, b, b, n, &bb);
+  double* sc = vo.scal;
+  dg_status st = A(x, q);
   if (st != DG_OK) return st;
-  const double bnorm = std::sqrt(bb);
+  st = vo.axpby(n, 1.0, b, -1.0, q, r);
+  if (st == DG_OK) st = vo.dots(n, 1, b, b, n, sc + 0);
+  if (st == DG_OK) st = vo.dots(n, 1, r, r, n, sc + 1);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemcpyAsync(vo.host_scal, sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, vo.stream));
+  DG_CUDA(cudaStreamSynchronize(vo.stream));
+  const double bnorm = std::sqrt(vo.host_scal[0]);
+  double rr = vo.host_scal[1];
   if (!std::isfinite(bnorm)) return DG_EBREAKDOWN;
   if (bnorm == 0.0) {
     DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, vo.stream));
     info->res0 = info->res_final = 0.0;
     return DG_OK;
   }
-  st = A(x, q);
-  if (st != DG_OK) return st;
-  st = vo.axpby(n, 1.0, b, -1.0, q, r);
-  if (st != DG_OK) return st;
-  double rr;
-  st = vo.dots_host(n, 1, r, r, n, &rr);
-  if (st != DG_OK) return st;
   info->res0 = info->res_final = std::sqrt(rr);
   if (!std::isfinite(rr)) return DG_EBREAKDOWN;
   if (info->res0 <= tol * bnorm) return DG_OK;
@@ -333,23 +383,28 @@ dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const 
   } else {
     DG_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, vo.stream));
   }
-  double rz;
-  st = vo.dots_host(n, 1, z, r, n, &rz);
+  int irz = 5;  // slot of the current <z, r>
+  st = vo.dots(n, 1, z, r, n, sc + irz);
   if (st != DG_OK) return st;
   DG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, vo.stream));
   for (int it = 0; it < max_iter; ++it) {
     st = A(p, q);
     if (st != DG_OK) return st;
-    double pq;
-    st = vo.dots_host(n, 1, p, q, n, &pq);
+    st = vo.dots(n, 1, p, q, n, sc + 2);
     if (st != DG_OK) return st;
-    if (!std::isfinite(pq) || pq <= 0.0) return DG_EBREAKDOWN;
-    const double alpha = rz / pq;
-    cg_update_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, alpha, p, q, x, r, r_old); count_launch();
+    cg_update_dev_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, sc, irz, 2, p, q, x, r, r_old);
+    count_launch();
     DG_CUDA(cudaGetLastError());
-    st = vo.dots_host(n, 1, r, r, n, &rr);
+    st = vo.dots(n, 1, r, r, n, sc + 1);
     if (st != DG_OK) return st;
+    DG_CUDA(cudaMemcpyAsync(vo.host_scal, sc + 1, sizeof(double) * 2, cudaMemcpyDeviceToHost, vo.stream));
+    DG_CUDA(cudaStreamSynchronize(vo.stream));
+    rr = vo.host_scal[0];
+    const double pq = vo.host_scal[1];
     info->iterations = it + 1;
+    // a non-positive <p, A p> means the step just taken was not a CG step:
+    // report the breakdown (x and r hold that step)
+    if (!std::isfinite(pq) || pq <= 0.0) return DG_EBREAKDOWN;
     info->res_final = std::sqrt(rr);
     if (!std::isfinite(rr)) return DG_EBREAKDOWN;
     if (info->res_final <= tol * bnorm) return DG_OK;
@@ -361,18 +416,16 @@ dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const 
     } else {
       DG_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, vo.stream));
     }
-    // <z, r> and <z, r_old> in one pass
-    double zr[2];
-    {
-      // r_old and r are adjacent in the caller's workspace: r_old = r + n
-      st = vo.dots_host(n, 2, z, r, r_old - r, zr);
-      if (st != DG_OK) return st;
-    }
-    const double rz_new = zr[0];
-    const double beta = (zr[0] - zr[1]) / rz;
-    rz = rz_new;
-    st = vo.axpby(n, 1.0, z, beta, p, p);
+    // <z, r> and <z, r_old> in one pass (r_old = r + its distance in the
+    // caller's workspace), then the direction on the device
+    st = vo.dots(n, 2, z, r, r_old - r, sc + 3);
     if (st != DG_OK) return st;
+    cg_direction_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, sc, 3, irz, z, p);
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+    // the new <z, r> becomes the next iteration's rz (alternate slot)
+    irz = irz == 5 ? 6 : 5;
+    DG_CUDA(cudaMemcpyAsync(sc + irz, sc + 3, sizeof(double), cudaMemcpyDeviceToDevice, vo.stream));
   }
   return DG_ENOCONV;
 }

@@ -372,10 +372,10 @@ dg_status dg_solver_create(dg_mesh* m, double Re, double c, dg_solver** out) {
   if (st == DG_OK) st = dalloc(s, &s->cgbuf, 5 * s->np);
   if (st == DG_OK) st = dalloc(s, &s->rhs_p, s->np);
   if (st == DG_OK) st = dalloc(s, &s->p_g, s->np);
-  if (st == DG_OK) st = dalloc(s, &s->hdev, 256);
+  if (st == DG_OK) st = dalloc(s, &s->hdev, 768);
   if (st == DG_OK) st = dalloc(s, &s->vo.partial, 1216 * 256);
   if (st == DG_OK) st = dalloc(s, &s->vo.scal, 256);
-  if (st == DG_OK && cudaMallocHost(&s->vo.host_scal, sizeof(double) * 256) != cudaSuccess) {
+  if (st == DG_OK && cudaMallocHost(&s->vo.host_scal, sizeof(double) * 1024) != cudaSuccess) {
     set_error("dg_solver_create: pinned host scratch");
     st = DG_ENOMEM;
   }
