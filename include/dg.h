@@ -139,11 +139,23 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
 /* Autotuner (a project addition): times the candidate tile shapes (cells per
  * CTA) of this mesh's operator kernels -- pressure Helmholtz, momentum with
  * and without advection, FP64 and FP32 -- with CUDA events on `stream` and
- * keeps the fastest for later applies; results do not depend on the choice.
+ * keeps the fastest for later applies.  Candidates: cells per CTA, a
+ * register cap, and the face-once form (every face evaluated once into a
+ * per-mesh flux scratch, then the cells: a different rounding order, the
+ * same result to FP64 rounding).  A mesh using the face-once form shares
+ * that scratch between its applies, so applies on one tuned mesh from
+ * different streams must not overlap.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
  * Trilinear meshes use one tile shape per kernel: the call records an empty
  * report.  Allocates temporary device buffers; synchronous. */
 dg_status dg_autotune(dg_mesh* mesh, void* stream);
+
+/* Sets the operator kernels' tile variant of this mesh by hand (0..6, the
+ * candidates listed in dg_autotune's report: 0-2 cells per CTA half /
+ * default / double, 3-4 default with 96 / 80 registers, 5-6 face-once
+ * uncapped / 80 registers) for every operator and precision; a face-once
+ * variant allocates the mesh's flux scratch.  Trilinear meshes ignore it. */
+dg_status dg_mesh_set_variant(dg_mesh* mesh, int32_t variant);
 
 /* JSON list of the tuning choices and timings of a mesh ("[]" if untuned),
  * written to buf (host, size bytes). */

@@ -104,6 +104,7 @@ SIGNATURES = {
     "dg_guess_configure": (ctypes.c_int, [c_void_p, P(dg_guess_opts)]),
     "dg_guess_get_stats": (ctypes.c_int, [c_void_p, P(dg_guess_stats)]),
     "dg_mlp_forward_backward": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_void_p, c_void_p, c_void_p, c_void_p, P(ctypes.c_float), c_void_p, c_void_p]),
+    "dg_mesh_set_variant": (ctypes.c_int, [c_void_p, ctypes.c_int32]),
     "dg_mlp_infer": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_solver_save": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "dg_solver_load": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
@@ -185,6 +186,10 @@ def dg_mesh_node_coords(mesh: int, field: int, xyz, stream=None) -> None:
 
 def dg_mesh_set_fp64_arith(mesh: int, mode: int) -> None:
     check(lib().dg_mesh_set_fp64_arith(mesh, mode), "dg_mesh_set_fp64_arith")
+
+
+def dg_mesh_set_variant(mesh: int, variant: int) -> None:
+    check(lib().dg_mesh_set_variant(mesh, variant), "dg_mesh_set_variant")
 
 
 def dg_apply_momentum(mesh: int, co: dg_momentum_coeffs, ubar, src, dst, stream=None) -> None:

@@ -226,6 +226,8 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
   a.cx = a.cr = nullptr;
   a.cdinv = nullptr;
   a.cc1 = a.cc2 = T(0);
+  a.flux = m->split_flux;
+  a.flux_bytes = m->split_flux_bytes;
   if (cheb) {
     a.cheb = 1;
     a.cx = cheb->cx;
@@ -237,6 +239,18 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
   const bool use_adv = !pressure && ubar != nullptr && adv != T(0);
   const int v = m->tune[sizeof(T) == 8 ? 0 : 1][pressure ? 0 : (use_adv ? 2 : 1)];
   return dispatch(m, pressure, v, N, use_adv, a, ubar, src, dst, s);
+}
+
+// face-flux scratch of the face-once variants: 2 values of at most 8 bytes
+// per face point, for every velocity component (covers the pressure space)
+static dg_status alloc_split_flux(dg_mesh* m) {
+  int64_t nface = 0;
+  for (int ax = 0; ax < m->dim; ++ax) nface += faces_of_axis(ax, m->n, m->periodic);
+  const int nfu = m->dim == 3 ? m->nu * m->nu : m->nu, nfp = m->dim == 3 ? m->np * m->np : m->np;
+  const int64_t bytes = nface * 2 * 8 * std::max<int64_t>((int64_t)nfu * m->dim, nfp);
+  DG_CUDA(cudaMalloc(&m->split_flux, bytes));
+  m->split_flux_bytes = bytes;
+  return DG_OK;
 }
 
 // cells per CTA of a tuning variant (reporting)
@@ -258,6 +272,10 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
     m->tune_report = "[]";
     return DG_OK;
   }
+  if (!m->split_flux) {  // face-flux scratch of the face-once variants
+    dg_status st0 = alloc_split_flux(m);
+    if (st0 != DG_OK) return st0;
+  }
   const int64_t nu = m->ncell * m->nbu * m->dim, np = m->ncell * m->nbp;
   void* buf = nullptr;
   const size_t bytes = sizeof(double) * (size_t)(3 * nu + 2 * np);
@@ -272,7 +290,7 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
   const char* opname[3] = {"pressure", "momentum", "momentum+advection"};
   for (int prec = 0; prec < 2 && st == DG_OK; ++prec) {
     for (int op = 0; op < 3 && st == DG_OK; ++op) {
-      float best = 1e30f, times[kTuneVariants] = {0, 0, 0, 0, 0};
+      float best = 1e30f, times[kTuneVariants] = {0, 0, 0, 0, 0, 0, 0};
       int bestv = 1;
       for (int v = 0; v < kTuneVariants && st == DG_OK; ++v) {
         m->tune[prec][op] = v;
@@ -305,17 +323,19 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
         }
       }
       m->tune[prec][op] = bestv;
-      char line[512];
+      char line[768];
       const bool p = op == 0, adv = op == 2;
       auto cp = [&](int v) {
         return prec == 0 ? cpb_for_mesh<double>(m, p, adv, v) : cpb_for_mesh<float>(m, p, adv, v);
       };
       std::snprintf(line, sizeof(line),
                     "%s{\"op\": \"%s\", \"precision\": \"%s\", "
-                    "\"cells_per_cta\": [%d, %d, %d, %d, %d], \"register_cap\": [0, 0, 0, 96, 80], "
-                    "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f], \"chosen_variant\": %d}",
+                    "\"cells_per_cta\": [%d, %d, %d, %d, %d, %d, %d], "
+                    "\"register_cap\": [0, 0, 0, 96, 80, 0, 80], \"face_once\": [0, 0, 0, 0, 0, 1, 1], "
+                    "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f, %.5f, %.5f], \"chosen_variant\": %d}",
                     rep.size() > 1 ? ", " : "", opname[op], prec == 0 ? "f64" : "f32", cp(0), cp(1),
-                    cp(2), cp(3), cp(4), times[0], times[1], times[2], times[3], times[4], bestv);
+                    cp(2), cp(3), cp(4), cp(5), cp(6), times[0], times[1], times[2], times[3], times[4],
+                    times[5], times[6], bestv);
       rep += line;
     }
   }
@@ -341,6 +361,20 @@ template dg_status launch_scalar_op<float>(const dg_mesh*, bool, float, float, f
 using namespace dg;
 
 extern "C" {
+
+dg_status dg_mesh_set_variant(dg_mesh* m, int32_t variant) {
+  if (!m || variant < 0 || variant >= kTuneVariants) {
+    set_error("dg_mesh_set_variant: bad argument");
+    return DG_EINVAL;
+  }
+  if (variant_split(variant) && m->affine && !m->split_flux) {
+    dg_status st = alloc_split_flux(m);
+    if (st != DG_OK) return st;
+  }
+  for (auto& row : m->tune)
+    for (int& v : row) v = variant;
+  return DG_OK;
+}
 
 dg_status dg_apply_momentum(dg_mesh* m, const dg_momentum_coeffs* co, const double* ubar,
                             const double* src, double* dst, void* stream) {

@@ -37,6 +37,9 @@ struct OpArgs {
   T* cr;
   const T* cdinv;
   T cc1, cc2;
+  // face-flux scratch of the face-once variant (null: not available)
+  void* flux;
+  int64_t flux_bytes;
 };
 
 __device__ __forceinline__ int node_of(int N, int a, int i, int t, int dim) {
@@ -68,6 +71,12 @@ __device__ __forceinline__ int tang_of(int a, const int i[3]) {
   }
   return t;
 }
+
+}  // namespace dg
+
+#include "dg_split_kernel.cuh"
+
+namespace dg {
 
 // T: storage type of the vectors (double or float); A: arithmetic type
 // (double, float, or df64 = float-float on the FP32 pipes).
@@ -291,8 +300,12 @@ constexpr int smem_words(int cpb) {
 // default and double the default cells per CTA, each clamped to the 48 KB
 // static shared-memory and 1024-thread limits; variants 3 and 4 take the
 // default cells per CTA with the registers per thread capped at 96 and 80
-// (more resident CTAs per SM, possibly at the price of spills).
-constexpr int kTuneVariants = 5;
+// (more resident CTAs per SM, possibly at the price of spills); variants 5
+// and 6 are the face-once form (face fluxes, then cells) with the default
+// cells per CTA, uncapped and capped at 80 registers.
+constexpr int kTuneVariants = 7;
+
+__host__ __device__ constexpr bool variant_split(int v) { return v >= 5; }
 
 template <typename T, int DIM, int N, bool ADV>
 constexpr int cpb_variant(int v) {
@@ -307,7 +320,7 @@ constexpr int cpb_variant(int v) {
 template <typename T, int DIM, int N, bool ADV>
 constexpr int minb_variant(int v) {
   const int threads = ((cpb_variant<T, DIM, N, ADV>(v) * Shape<N, DIM>::NB + 31) / 32) * 32;
-  const int cap = v == 3 ? 96 : (v == 4 ? 80 : 0);
+  const int cap = v == 3 ? 96 : (v == 4 || v == 6 ? 80 : 0);
   if (cap == 0) return 1;
   const int b = 65536 / (threads * cap);
   return b < 1 ? 1 : b;
@@ -328,11 +341,38 @@ static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<A>& tb, const T* 
   return DG_OK;
 }
 
+template <typename T, typename A, int DIM, int N, bool ADV, int CPB, int MINB>
+static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
+                              T* dst, cudaStream_t s) {
+  const int n[3] = {args.n0, args.n1, args.n2};
+  const int per[3] = {args.per0, args.per1, args.per2};
+  int64_t nface = faces_of_axis(0, n, per) + faces_of_axis(1, n, per);
+  if (DIM == 3) nface += faces_of_axis(2, n, per);
+  const int64_t need = nface * Shape<N, DIM>::NF * 2 * args.ncomp * (int64_t)sizeof(A);
+  if (!args.flux || need > args.flux_bytes) {  // no scratch: the single-kernel form
+    return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(1), 1>(args, tb, ub, src, dst, s);
+  }
+  A* flux = static_cast<A*>(args.flux);
+  const int64_t fthreads = nface * Shape<N, DIM>::NF;
+  face_flux_kernel<T, A, DIM, N, ADV><<<(unsigned)((fthreads + 255) / 256), 256, 0, s>>>(args, tb, src, ub, flux);
+  count_launch();
+  constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
+  const int64_t blocks = (args.ncell + CPB - 1) / CPB;
+  cell_split_kernel<T, A, DIM, N, ADV, CPB, MINB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, flux, dst);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
 template <typename T, typename A, int DIM, int N, bool ADV, int V>
 static dg_status launch_v(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
                           T* dst, cudaStream_t s) {
-  return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V)>(
-      args, tb, ub, src, dst, s);
+  if constexpr (variant_split(V))
+    return launch_split<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V)>(
+        args, tb, ub, src, dst, s);
+  else
+    return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V)>(
+        args, tb, ub, src, dst, s);
 }
 
 template <typename T, typename A, int DIM, int N, bool ADV>
@@ -343,6 +383,8 @@ static dg_status launch_fixed(int variant, const OpArgs<T>& args, const Tab1D<A>
     case 2: return launch_v<T, A, DIM, N, ADV, 2>(args, tb, ub, src, dst, s);
     case 3: return launch_v<T, A, DIM, N, ADV, 3>(args, tb, ub, src, dst, s);
     case 4: return launch_v<T, A, DIM, N, ADV, 4>(args, tb, ub, src, dst, s);
+    case 5: return launch_v<T, A, DIM, N, ADV, 5>(args, tb, ub, src, dst, s);
+    case 6: return launch_v<T, A, DIM, N, ADV, 6>(args, tb, ub, src, dst, s);
     default: return launch_v<T, A, DIM, N, ADV, 1>(args, tb, ub, src, dst, s);
   }
 }

@@ -89,6 +89,10 @@ struct dg_mesh {
   dg::df64* gfp_df = nullptr;
   dg::df64* gpen_df = nullptr;
   bool geom_u = false;      // velocity terms present (not on multigrid levels)
+  // face-flux scratch of the face-once operator variant (allocated by the
+  // autotuner, which is the only way that variant gets chosen)
+  void* split_flux = nullptr;
+  int64_t split_flux_bytes = 0;
   bool level = false;       // a multigrid level (pressure space only)
   // autotuned tile shape of the operator kernels: variant index per
   // [precision: 0 FP64, 1 FP32][operator: 0 pressure, 1 momentum, 2 momentum

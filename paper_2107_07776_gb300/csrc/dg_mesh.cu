@@ -420,6 +420,7 @@ void dg_mesh_destroy(dg_mesh* m) {
     if (m->d_hi32[a]) cudaFree(m->d_hi32[a]);
   }
   if (m->d_status) cudaFree(m->d_status);
+  if (m->split_flux) cudaFree(m->split_flux);
   free_geometry(m);
   delete m;
 }

@@ -1,0 +1,284 @@
+// Face-once variant of the affine operator kernel: the same operator as
+// scalar_op_kernel, in two launches.
+//
+//  1. face_flux_kernel: one thread per face point of every face, each face
+//     once.  It takes both sides' traces and normal derivatives (and the
+//     advecting field's normal traces), forms the SIP + LF flux of Section 3
+//     and stores the pair (F0, G) = (w_t fv, w_t fg) per face point and
+//     component, in the orientation of the face's lower-side cell.  The
+//     upper-side cell sees the antisymmetric pair: its value flux is -F0, and
+//     its normal-derivative coefficient is G times its own inverse extent
+//     (for both sides).  Wall faces store the one-sided flux of their single
+//     cell in the same convention.
+//  2. cell_split_kernel: the volume terms (as in scalar_op_kernel) plus the
+//     stored fluxes of the cell's 2d faces.
+//
+// Every face is evaluated once instead of once per side, which removes
+// about half of the face arithmetic.  The flux pairs make a round trip
+// through L2/HBM: 2 values per face point and component.  Results equal
+// those of the single-kernel variant up to rounding order; each output is
+// still written once, without atomics.
+#pragma once
+
+#include "dg_common.cuh"
+#include "dg_df64.cuh"
+
+namespace dg {
+
+// number of face layers along axis a: periodic n_a, walled n_a + 1
+__host__ __device__ __forceinline__ int face_layers(int n, int per) { return per ? n : n + 1; }
+
+// faces normal to axis a (layers x the other axes' cells)
+__host__ __device__ __forceinline__ int64_t faces_of_axis(int a, const int n[3], const int per[3]) {
+  int64_t f = face_layers(n[a], per[a]);
+  for (int b = 0; b < 3; ++b)
+    if (b != a) f *= n[b];
+  return f;
+}
+
+// linear index of the face at layer l along axis a with the tangential cell
+// coordinates of c (x fastest, the axis a dimension replaced by its layers)
+__device__ __forceinline__ int64_t face_index(int a, int l, const int c[3], const int n[3],
+                                              const int per[3]) {
+  const int d0 = a == 0 ? face_layers(n[0], per[0]) : n[0];
+  const int d1 = a == 1 ? face_layers(n[1], per[1]) : n[1];
+  const int f0 = a == 0 ? l : c[0], f1 = a == 1 ? l : c[1], f2 = a == 2 ? l : c[2];
+  return f0 + (int64_t)d0 * (f1 + (int64_t)d1 * f2);
+}
+
+template <typename T, typename A, int DIM, int N, bool ADV>
+__global__ void __launch_bounds__(256)
+    face_flux_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
+                     const T* __restrict__ src, const T* __restrict__ ub, A* __restrict__ flux) {
+  using Ar = Arith<A>;
+  constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
+  const int n[3] = {a.n0, a.n1, a.n2};
+  const int per[3] = {a.per0, a.per1, a.per2};
+  const int64_t f0 = faces_of_axis(0, n, per), f1 = faces_of_axis(1, n, per);
+  const int64_t f2 = DIM == 3 ? faces_of_axis(2, n, per) : 0;
+  const int64_t nface = f0 + f1 + f2;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nface * NF) return;
+  const int t = (int)(gid % NF);
+  int64_t fg = gid / NF;  // global face index (axis 0 faces, then 1, then 2)
+  int ax;
+  int64_t fl;
+  if (fg < f0) {
+    ax = 0;
+    fl = fg;
+  } else if (fg < f0 + f1) {
+    ax = 1;
+    fl = fg - f0;
+  } else {
+    ax = 2;
+    fl = fg - f0 - f1;
+  }
+  // face coordinates
+  const int d0 = ax == 0 ? face_layers(n[0], per[0]) : n[0];
+  const int d1 = ax == 1 ? face_layers(n[1], per[1]) : n[1];
+  int fc[3];
+  fc[0] = (int)(fl % d0);
+  fc[1] = (int)((fl / d0) % d1);
+  fc[2] = DIM == 3 ? (int)(fl / ((int64_t)d0 * d1)) : 0;
+  const int layer = pick3(ax, fc[0], fc[1], fc[2]);
+  const int nax = pick3(ax, n[0], n[1], n[2]);
+  const bool pax = pick3(ax, per[0], per[1], per[2]) != 0;
+  // cells on both sides (lower side L: the face is its upper face)
+  const int cl_ax = pax ? (layer - 1 + nax) % nax : layer - 1;
+  const int cr_ax = layer;
+  const bool hasL = pax || layer >= 1, hasR = pax || layer < nax;
+  const int64_t cstr = ax == 0 ? 1 : (ax == 1 ? (int64_t)n[0] : (int64_t)n[0] * n[1]);
+  const int64_t cbase = (ax == 0 ? 0 : fc[0]) + (int64_t)n[0] * ((ax == 1 ? 0 : fc[1]) +
+                                                             (int64_t)n[1] * (ax == 2 ? 0 : fc[2]));
+  const int64_t cL = cbase + (int64_t)cl_ax * cstr, cR = cbase + (int64_t)cr_ax * cstr;
+  const T* hiax = ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2);
+  const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
+  const A visc = Ar::from(a.visc), advc = Ar::from(a.adv), pen = Ar::from(a.pen);
+  const A hiL = hasL ? Ar::from(hiax[cl_ax]) : zero, hiR = hasR ? Ar::from(hiax[cr_ax]) : zero;
+  // tangential weight: face quadrature weight times the face measure
+  A wt = Ar::c(1.0);
+  {
+    int tt = t;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      if (b == ax) continue;
+      const T* hb = b == 0 ? a.h0 : (b == 1 ? a.h1 : a.h2);
+      wt = wt * tb.w[tt % N] * Ar::from(hb[pick3(b, fc[0], fc[1], fc[2])]);
+      tt /= N;
+    }
+  }
+  // normal traces of the advecting field along +e_ax
+  A unL = zero, unR = zero;
+  if (ADV) {
+    const T* uba = ub + (int64_t)ax * a.ncell * NB;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int nd = node_of(N, ax, i, t, DIM);
+      if (hasL) unL = Ar::fma(tb.L[1][i], Ar::from(__ldg(&uba[cL * NB + nd])), unL);
+      if (hasR) unR = Ar::fma(tb.L[0][i], Ar::from(__ldg(&uba[cR * NB + nd])), unR);
+    }
+  }
+  for (int c = 0; c < a.ncomp; ++c) {
+    const T* srcc = src + (int64_t)c * a.ncell * NB;
+    A uL = zero, dL = zero, uR = zero, dR = zero;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int nd = node_of(N, ax, i, t, DIM);
+      if (hasL) {
+        const A v = Ar::from(__ldg(&srcc[cL * NB + nd]));
+        uL = Ar::fma(tb.L[1][i], v, uL);
+        dL = Ar::fma(tb.dL[1][i], v, dL);
+      }
+      if (hasR) {
+        const A v = Ar::from(__ldg(&srcc[cR * NB + nd]));
+        uR = Ar::fma(tb.L[0][i], v, uR);
+        dR = Ar::fma(tb.dL[0][i], v, dR);
+      }
+    }
+    A F0 = zero, G = zero;
+    if (hasL && hasR) {  // interior face, from the lower cell's side (normal +e_ax)
+      const A dnL = dL * hiL, dnR = dR * hiR;
+      const A Cpen = half * pen * (hiL + hiR);
+      const A jump = uL - uR;
+      A fv = visc * (Cpen * jump - half * (dnL + dnR));
+      const A fgr = -(half * visc * jump);
+      if (ADV) {
+        const A lam = Ar::max(Ar::abs(unL), Ar::abs(unR));
+        fv += advc * (half * (uL * unL + uR * unR) + half * lam * jump);
+      }
+      F0 = wt * fv;
+      G = wt * fgr;
+    } else if (a.walls) {
+      // one-sided wall flux of the single cell (normal -e_ax below, +e_ax above)
+      const bool low = hasR;  // the wall is the lower face of cell R
+      const A uin = low ? uR : uL;
+      const A dnin = low ? -(dR * hiR) : dL * hiL;
+      const A sig = pen * (low ? hiR : hiL);
+      A fv = visc * (two * sig * uin - dnin);
+      const A fgr = -(visc * uin);
+      if (ADV) fv += advc * Ar::abs(low ? -unR : unL) * uin;
+      // stored so that the reader's rule (value flux -F0 below / +F0 above,
+      // derivative coefficient G times its inverse extent) reproduces it
+      F0 = low ? -(wt * fv) : wt * fv;
+      G = low ? -(wt * fgr) : wt * fgr;
+    }
+    A* fo = flux + ((c * nface + fg) * NF + t) * 2;
+    fo[0] = F0;
+    fo[1] = G;
+  }
+}
+
+template <typename T, typename A, int DIM, int N, bool ADV, int CPB, int MINB>
+__global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MINB)
+    cell_split_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
+                      const T* __restrict__ src, const T* __restrict__ ub,
+                      const A* __restrict__ flux, T* __restrict__ dst) {
+  using Ar = Arith<A>;
+  constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
+  __shared__ A s_u[CPB][NB];
+  __shared__ A s_q[DIM][CPB][NB];
+  const int tid = threadIdx.x;
+  const int cl = tid / NB, node = tid - (tid / NB) * NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < a.ncell;
+  const A zero = Ar::c(0.0);
+  const A mass = Ar::from(a.mass), visc = Ar::from(a.visc), advc = Ar::from(a.adv);
+  const int n[3] = {a.n0, a.n1, a.n2};
+  const int per[3] = {a.per0, a.per1, a.per2};
+  const int64_t f0 = faces_of_axis(0, n, per), f1 = faces_of_axis(1, n, per);
+  const int64_t f2 = DIM == 3 ? faces_of_axis(2, n, per) : 0;
+  const int64_t nface = f0 + f1 + f2;
+  int ci[3] = {0, 0, 0};
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  A W = zero, ubn[DIM];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) ubn[b] = zero;
+  if (active) {
+    ci[0] = (int)(cell % a.n0);
+    ci[1] = (int)((cell / a.n0) % a.n1);
+    ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
+    h[0] = Ar::from(a.h0[ci[0]]);
+    h[1] = Ar::from(a.h1[ci[1]]);
+    hi[0] = Ar::from(a.hi0[ci[0]]);
+    hi[1] = Ar::from(a.hi1[ci[1]]);
+    if (DIM == 3) {
+      h[2] = Ar::from(a.h2[ci[2]]);
+      hi[2] = Ar::from(a.hi2[ci[2]]);
+    }
+    W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
+    if (DIM == 3) W = W * tb.w[ii[2]] * h[2];
+    if (ADV) {
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) ubn[b] = Ar::from(ub[((int64_t)b * a.ncell + cell) * NB + node]);
+    }
+  }
+  // face indices of this node's 2d face points (the same for every component)
+  int64_t fpos[2 * DIM];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    const int t = tang_of<N, DIM>(b, ii);
+    const int64_t foff = b == 0 ? 0 : (b == 1 ? f0 : f0 + f1);
+    const int cb = ci[b], nb_ = n[b];
+    const int lo = cb, hi_l = per[b] ? (cb + 1) % nb_ : cb + 1;
+    fpos[2 * b] = (foff + face_index(b, lo, ci, n, per)) * NF + t;
+    fpos[2 * b + 1] = (foff + face_index(b, hi_l, ci, n, per)) * NF + t;
+  }
+  for (int c = 0; c < a.ncomp; ++c) {
+    const T* srcc = src + (int64_t)c * a.ncell * NB;
+    if (active) s_u[cl][node] = Ar::from(srcc[cell * NB + node]);
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A du = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          du = Ar::fma(tb.D[ii[b]][m], s_u[cl][j[0] + N * (j[1] + N * j[2])], du);
+        }
+        A q = visc * du * hi[b];
+        if (ADV) q -= advc * s_u[cl][node] * ubn[b];
+        s_q[b][cl][node] = W * q;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      A y = mass * W * s_u[cl][node];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A acc = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          acc = Ar::fma(tb.D[m][ii[b]], s_q[b][cl][j[0] + N * (j[1] + N * j[2])], acc);
+        }
+        y = Ar::fma(acc, hi[b], y);
+        const A* fl = flux + (int64_t)c * nface * NF * 2;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const A* fp = fl + fpos[2 * b + s] * 2;
+          const A F0 = fp[0], G = fp[1];
+          y = Ar::fma(s ? F0 : -F0, tb.L[s][ii[b]], y);
+          y = Ar::fma(G * hi[b], tb.dL[s][ii[b]], y);
+        }
+      }
+      const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
+      const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
+      if (a.cheb) {
+        const T dk = srcc[cell * NB + node];
+        a.cx[o] += dk;
+        const T rk = a.cr[o] - a.cdinv[o] * yt;
+        a.cr[o] = rk;
+        dst[o] = a.cc1 * dk + a.cc2 * rk;
+      } else {
+        dst[o] = yt;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace dg

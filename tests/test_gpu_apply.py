@@ -101,6 +101,43 @@ def test_momentum_apply_matches_oracle(ci, fp64_arith):
     assert rel_err(y32.double().cpu().numpy(), ref) < 2e-5
 
 
+@pytest.mark.parametrize("variant", [5, 6])
+@pytest.mark.parametrize("ci", [i for i, c in enumerate(CASES) if c[6] != 2])
+def test_face_once_variants_match_oracle(ci, variant):
+    """The face-once form (every face's flux once into a scratch, then the
+    cells) in float-float, native FP64 and FP32, against the oracle."""
+    from paper_2107_07776_gb300 import binding as b
+    gm, om = meshes(CASES[ci])
+    b.dg_mesh_set_variant(gm.handle, variant)
+    d = om.dim
+    x = W.random_vector(d * om.n_u, 200 + ci)
+    ub = W.random_vector(d * om.n_u, 300 + ci)
+    mass, visc, adv = 1.0 / (b.GAMMA * 0.01), 1.0 / 200.0, 0.5
+    M, A, C = om.assemble("mass_u"), om.assemble("sipg_u"), om.assemble("adv_u", ub)
+    ref_u = np.concatenate([mass * M.apply(x[i * om.n_u:(i + 1) * om.n_u])
+                            + visc * A.apply(x[i * om.n_u:(i + 1) * om.n_u])
+                            + adv * C.apply(x[i * om.n_u:(i + 1) * om.n_u]) for i in range(d)])
+    xp = W.random_vector(om.n_p, 100 + ci)
+    ref_p = 2.9 * om.assemble("mass_p").apply(xp) + om.assemble("sipg_p").apply(xp)
+    co = b.momentum_coeffs(mass, visc, adv)
+    for arith in (0, 1):
+        b.dg_mesh_set_fp64_arith(gm.handle, arith)
+        y = torch.empty(d * om.n_u, dtype=torch.float64, device="cuda")
+        b.dg_apply_momentum(gm.handle, co, dev(ub), dev(x), y)
+        yp = torch.empty(om.n_p, dtype=torch.float64, device="cuda")
+        b.dg_apply_poisson(gm.handle, 2.9, dev(xp), yp)
+        torch.cuda.synchronize()
+        assert rel_err(y.cpu().numpy(), ref_u) < 1e-12, arith
+        assert rel_err(yp.cpu().numpy(), ref_p) < 1e-12, arith
+    y32 = torch.empty(d * om.n_u, dtype=torch.float32, device="cuda")
+    b.dg_apply_momentum_f32(gm.handle, co, dev(ub, torch.float32), dev(x, torch.float32), y32)
+    yp32 = torch.empty(om.n_p, dtype=torch.float32, device="cuda")
+    b.dg_apply_poisson_f32(gm.handle, 2.9, dev(xp, torch.float32), yp32)
+    torch.cuda.synchronize()
+    assert rel_err(y32.double().cpu().numpy(), ref_u) < 2e-5
+    assert rel_err(yp32.double().cpu().numpy(), ref_p) < 2e-5
+
+
 def test_node_coords_match_oracle():
     for case in CASES:
         gm, om = meshes(case)

@@ -38,13 +38,20 @@ def test_autotune_keeps_results_and_reports(dim, n, k):
     rep = json.loads(b.dg_autotune_report(gm.handle))
     assert len(rep) == 6
     for r in rep:
-        assert len(r["cells_per_cta"]) == len(r["ms"]) == len(r["register_cap"]) == 5
-        assert 0 <= r["chosen_variant"] < 5
+        assert len(r["cells_per_cta"]) == len(r["ms"]) == len(r["register_cap"]) == 7
+        assert len(r["face_once"]) == 7
+        assert 0 <= r["chosen_variant"] < 7
         assert r["ms"][r["chosen_variant"]] == min(r["ms"])
         assert all(t > 0 for t in r["ms"])
     after = apply_all()
+    # the cell-centric variants give identical bits whatever the tile; the
+    # face-once variants evaluate each face once, a different rounding order
+    face_once = any(r["face_once"][r["chosen_variant"]] for r in rep)
     for a, c in zip(before, after):
-        assert torch.equal(a, c)
+        if face_once:
+            assert ((a - c).abs().max() / a.abs().max()).item() < (1e-12 if a.dtype == torch.float64 else 2e-5)
+        else:
+            assert torch.equal(a, c)
 
 
 def test_multigrid_levels_of_a_tuned_mesh():
