@@ -11,6 +11,7 @@
 #include "dg_common.cuh"
 #include "dg_df64.cuh"
 #include "dg_geom.cuh"
+#include "dg_faces.cuh"
 
 namespace dg {
 
@@ -406,6 +407,226 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
 }
 
 // ------------------------------------------------------------------
+// Face-once form of the explicit terms (used when the mesh's momentum
+// operator runs in the face-once form and its flux scratch exists): one
+// thread per face point of every face computes the central flux once, in the
+// orientation of the face's lower-side cell (the flux is antisymmetric, so
+// the upper-side cell takes -F0); the cell kernel adds the volume terms and
+// the stored fluxes.  Wall faces store their single cell's flux in the same
+// convention.
+template <typename A, int DIM, int N, int NT>
+__global__ void __launch_bounds__(256)
+    explicit_face_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
+                         const __grid_constant__ ExplTerms et, A* __restrict__ flux) {
+  using Ar = Arith<A>;
+  constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF;
+  const int64_t f0 = faces_of_axis(0, g.n, g.per), f1 = faces_of_axis(1, g.n, g.per);
+  const int64_t f2 = DIM == 3 ? faces_of_axis(2, g.n, g.per) : 0;
+  const int64_t nface = f0 + f1 + f2;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nface * NF) return;
+  const int t = (int)(gid % NF);
+  const int64_t fg = gid / NF;
+  const int ax = fg < f0 ? 0 : (fg < f0 + f1 ? 1 : 2);
+  const int64_t fl = fg - (ax == 0 ? 0 : (ax == 1 ? f0 : f0 + f1));
+  const int d0 = ax == 0 ? face_layers(g.n[0], g.per[0]) : g.n[0];
+  const int d1 = ax == 1 ? face_layers(g.n[1], g.per[1]) : g.n[1];
+  const int fc[3] = {(int)(fl % d0), (int)((fl / d0) % d1), DIM == 3 ? (int)(fl / ((int64_t)d0 * d1)) : 0};
+  const int layer = sel3(ax, fc[0], fc[1], fc[2]);
+  const int nax = sel3(ax, g.n[0], g.n[1], g.n[2]);
+  const bool pax = sel3(ax, g.per[0], g.per[1], g.per[2]) != 0;
+  const int cl_ax = pax ? (layer - 1 + nax) % nax : layer - 1;
+  const int cr_ax = layer;
+  const bool hasL = pax || layer >= 1, hasR = pax || layer < nax;
+  const int64_t cstr = ax == 0 ? 1 : (ax == 1 ? (int64_t)g.n[0] : (int64_t)g.n[0] * g.n[1]);
+  const int64_t cbase = (ax == 0 ? 0 : fc[0]) +
+                        (int64_t)g.n[0] * ((ax == 1 ? 0 : fc[1]) + (int64_t)g.n[1] * (ax == 2 ? 0 : fc[2]));
+  const int64_t cL = cbase + (int64_t)cl_ax * cstr, cR = cbase + (int64_t)cr_ax * cstr;
+  const double* hiax = sel3(ax, g.hi[0], g.hi[1], g.hi[2]);
+  const A zero = Ar::c(0.0), half = Ar::c(0.5);
+  const A hiL = hasL ? Ar::from(hiax[cl_ax]) : zero, hiR = hasR ? Ar::from(hiax[cr_ax]) : zero;
+  A visc[NT], adv[NT];
+#pragma unroll
+  for (int tt = 0; tt < NT; ++tt) {
+    visc[tt] = Ar::from(et.visc[tt]);
+    adv[tt] = Ar::from(et.adv[tt]);
+  }
+  A wt = Ar::c(1.0);
+  {
+    int tt = t;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      if (b == ax) continue;
+      wt = wt * tb.w[tt % N] * Ar::from(g.h[b][fc[b]]);
+      tt /= N;
+    }
+  }
+  // advecting fields' traces along +e_ax
+  A wnL[NT], wnR[NT];
+#pragma unroll
+  for (int tt = 0; tt < NT; ++tt) {
+    A l = zero, r = zero;
+    const double* wa = et.wb[tt] + (int64_t)ax * g.ncell * NB;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int nd = nodeof(N, DIM, ax, i, t);
+      if (hasL) l = Ar::fma(tb.L[1][i], Ar::from(__ldg(&wa[cL * NB + nd])), l);
+      if (hasR) r = Ar::fma(tb.L[0][i], Ar::from(__ldg(&wa[cR * NB + nd])), r);
+    }
+    wnL[tt] = l;
+    wnR[tt] = r;
+  }
+  for (int c = 0; c < DIM; ++c) {
+    A vL = zero, dvL = zero, vR = zero, dvR = zero, uL[NT], uR[NT];
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt) uL[tt] = uR[tt] = zero;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int nd = nodeof(N, DIM, ax, i, t);
+      A vl = zero, vr = zero;
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) {
+        const double* wc = et.w[tt] + (int64_t)c * g.ncell * NB;
+        if (hasL) {
+          const A u = Ar::from(__ldg(&wc[cL * NB + nd]));
+          uL[tt] = Ar::fma(tb.L[1][i], u, uL[tt]);
+          vl = Ar::fma(visc[tt], u, vl);
+        }
+        if (hasR) {
+          const A u = Ar::from(__ldg(&wc[cR * NB + nd]));
+          uR[tt] = Ar::fma(tb.L[0][i], u, uR[tt]);
+          vr = Ar::fma(visc[tt], u, vr);
+        }
+      }
+      vL = Ar::fma(tb.L[1][i], vl, vL);
+      dvL = Ar::fma(tb.dL[1][i], vl, dvL);
+      vR = Ar::fma(tb.L[0][i], vr, vR);
+      dvR = Ar::fma(tb.dL[0][i], vr, dvR);
+    }
+    A F0 = zero;
+    if (hasL && hasR) {
+      A a = zero;
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) a += adv[tt] * (uL[tt] * wnL[tt] + uR[tt] * wnR[tt]);
+      F0 = wt * (half * (dvL * hiL + dvR * hiR - a));
+    } else if (hasR) {  // lower wall of cell R (outward normal -e_ax)
+      A a = zero;
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) a += adv[tt] * uR[tt] * wnR[tt];
+      F0 = -(wt * (a - dvR * hiR));
+    } else {  // upper wall of cell L
+      A a = zero;
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) a += adv[tt] * uL[tt] * wnL[tt];
+      F0 = wt * (dvL * hiL - a);
+    }
+    flux[(c * nface + fg) * NF + t] = F0;
+  }
+}
+
+template <typename A, int DIM, int N, int NT, int CPB>
+__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
+    explicit_cell_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
+                         const __grid_constant__ ExplTerms et, const A* __restrict__ flux,
+                         double* __restrict__ rhs) {
+  using Ar = Arith<A>;
+  constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF;
+  __shared__ A s_v[CPB][NB];
+  __shared__ A s_q[DIM][CPB][NB];
+  const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < g.ncell;
+  const A zero = Ar::c(0.0);
+  A visc[NT], adv[NT];
+#pragma unroll
+  for (int tt = 0; tt < NT; ++tt) {
+    visc[tt] = Ar::from(et.visc[tt]);
+    adv[tt] = Ar::from(et.adv[tt]);
+  }
+  const int64_t f0 = faces_of_axis(0, g.n, g.per), f1 = faces_of_axis(1, g.n, g.per);
+  const int64_t nface = f0 + f1 + (DIM == 3 ? faces_of_axis(2, g.n, g.per) : 0);
+  int ci[3] = {0, 0, 0};
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
+  A W = zero, wbn[NT][DIM];
+  if (active) {
+    cell_coords(g, cell, ci);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      h[b] = Ar::from(g.h[b][ci[b]]);
+      hi[b] = Ar::from(g.hi[b][ci[b]]);
+    }
+    W = Ar::c(1.0);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) W = W * tb.w[ii[b]] * h[b];
+  }
+#pragma unroll
+  for (int tt = 0; tt < NT; ++tt)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b)
+      wbn[tt][b] = active ? Ar::from(et.wb[tt][((int64_t)b * g.ncell + cell) * NB + node]) : zero;
+  int64_t fpos[2 * DIM];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    const int t = tangof(N, DIM, b, ii);
+    const int64_t foff = b == 0 ? 0 : (b == 1 ? f0 : f0 + f1);
+    const int hi_l = g.per[b] ? (ci[b] + 1) % g.n[b] : ci[b] + 1;
+    fpos[2 * b] = (foff + face_index(b, ci[b], ci, g.n, g.per)) * NF + t;
+    fpos[2 * b + 1] = (foff + face_index(b, hi_l, ci, g.n, g.per)) * NF + t;
+  }
+  for (int c = 0; c < DIM; ++c) {
+    A u[NT];
+    if (active) {
+      A v = zero;
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) {
+        u[tt] = Ar::from(et.w[tt][((int64_t)c * g.ncell + cell) * NB + node]);
+        v = Ar::fma(visc[tt], u[tt], v);
+      }
+      s_v[cl][node] = v;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A dv = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          dv = Ar::fma(tb.D[ii[b]][m], s_v[cl][j[0] + N * (j[1] + N * j[2])], dv);
+        }
+        A q = -(dv * hi[b]);
+#pragma unroll
+        for (int tt = 0; tt < NT; ++tt) q += adv[tt] * u[tt] * wbn[tt][b];
+        s_q[b][cl][node] = W * q;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      A y = zero;
+      const A* fl = flux + (int64_t)c * nface * NF;
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        A acc = zero;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          acc = Ar::fma(tb.D[m][ii[b]], s_q[b][cl][j[0] + N * (j[1] + N * j[2])], acc);
+        }
+        y = Ar::fma(acc, hi[b], y);
+        const A F0lo = fl[fpos[2 * b]], F0hi = fl[fpos[2 * b + 1]];
+        y = Ar::fma(-F0lo, tb.L[0][ii[b]], y);
+        y = Ar::fma(F0hi, tb.L[1][ii[b]], y);
+      }
+      rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += Ar::to_d(y);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------
 // rhs = mass M u_mass + M f + G p (G the DG pressure gradient of Eq. rhs1);
 // writes (does not accumulate).  N velocity, NP pressure nodes per direction.
 template <typename A, int DIM, int N, int NP, int CPB>
@@ -781,6 +1002,27 @@ dg_status run_explicit_terms_a(const dg_mesh* m, const ExplTerms& et, int nt, do
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  int64_t nface = 0;
+  for (int ax = 0; ax < DIM; ++ax) nface += faces_of_axis(ax, m->n, m->periodic);
+  const int64_t need = nface * Sh<N, DIM>::NF * DIM * (int64_t)sizeof(A);
+  const bool face_once = (m->tune[0][2] >= 5 || m->tune[0][1] >= 5) && m->split_flux &&
+                         need <= m->split_flux_bytes;
+  if (face_once) {
+    A* flux = static_cast<A*>(m->split_flux);
+    const Grid g = make_grid<DIM>(m);
+    const unsigned fb = (unsigned)((nface * Sh<N, DIM>::NF + 255) / 256);
+    if (nt == 2) {
+      explicit_face_kernel<A, DIM, N, 2><<<fb, 256, 0, s>>>(g, tab_u<A>(m), et, flux);
+      explicit_cell_kernel<A, DIM, N, 2, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), et, flux, rhs);
+    } else {
+      explicit_face_kernel<A, DIM, N, 1><<<fb, 256, 0, s>>>(g, tab_u<A>(m), et, flux);
+      explicit_cell_kernel<A, DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), et, flux, rhs);
+    }
+    count_launch();
+    count_launch();
+    DG_CUDA(cudaGetLastError());
+    return DG_OK;
+  }
   if (nt == 2)
     explicit_terms_kernel<A, DIM, N, 2, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_u<A>(m), et, rhs);
   else

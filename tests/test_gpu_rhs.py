@@ -44,10 +44,15 @@ def rel_err(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("ci", range(len(CASES)))
-def test_momentum_rhs(ci):
+@pytest.mark.parametrize("ci,variant", [(i, None) for i in range(len(CASES))] +
+                         [(i, 5) for i, c in enumerate(CASES) if c[6] != 2])
+def test_momentum_rhs(ci, variant):
+    """variant 5: the mesh runs the face-once form, which the explicit terms
+    follow (every face's central flux once, then the cells)."""
     from paper_2107_07776_gb300 import binding as b
     gm, om = meshes(CASES[ci])
+    if variant is not None:
+        b.dg_mesh_set_variant(gm.handle, variant)
     d, nu = om.dim, om.n_u
     rs = lambda s, n: W.random_vector(n, 1000 * ci + s)
     um, w0, w1, wb0, wb1, uD, ub, f = (rs(i, d * nu) for i in range(8))
