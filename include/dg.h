@@ -230,6 +230,8 @@ typedef struct {
   int32_t precond;      /* DG_PC_*: momentum takes NONE/JACOBI, Helmholtz any */
   int32_t guess;        /* DG_GUESS_* */
   double timeout_s;     /* wall-clock limit, <= 0: none */
+  int32_t mg_degree;    /* Chebyshev degree of the multigrid smoother (pre and
+                           post, every level); <= 0: the default, 5 */
 } dg_solve_opts;
 
 typedef struct {

@@ -49,7 +49,7 @@ class dg_solve_opts(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int32), ("tol_rel", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("guess", ctypes.c_int32),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("mg_degree", ctypes.c_int32)]
 
 
 class dg_solve_info(ctypes.Structure):
@@ -353,10 +353,10 @@ def momentum_coeffs(mass: float, visc: float, adv: float) -> dg_momentum_coeffs:
 
 def solve_opts(system: int, tol: float = 1e-8, max_iter: int = 500, restart: int = 30,
                precond: int = DG_PC_JACOBI, guess: int = DG_GUESS_ZERO,
-               timeout_s: float = 0.0) -> dg_solve_opts:
+               timeout_s: float = 0.0, mg_degree: int = 0) -> dg_solve_opts:
     o = dg_solve_opts()
     o.system, o.tol_rel, o.max_iter, o.restart = system, tol, max_iter, restart
-    o.precond, o.guess, o.timeout_s = precond, guess, timeout_s
+    o.precond, o.guess, o.timeout_s, o.mg_degree = precond, guess, timeout_s, mg_degree
     return o
 
 

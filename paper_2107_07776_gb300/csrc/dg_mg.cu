@@ -9,7 +9,7 @@
 //   transfer cell-local DG embedding: prolongation evaluates the coarse
 //            polynomial at the fine nodes (exact: the coarse space is a
 //            subspace), restriction is its transpose;
-//   smoother Chebyshev iteration of degree 4 on D^-1 A over
+//   smoother Chebyshev iteration of degree 5 (an option) on D^-1 A over
 //            [lambda_max/20, 1.1 lambda_max], lambda_max from 15 Lanczos
 //            (Jacobi-CG) steps, each step after the first one fused launch;
 //   coarse   the coarsest level (at most 2048 DoFs) is solved exactly by a
@@ -694,6 +694,14 @@ dg_status MultiGrid<T>::apply_direct(const double* r, double* z) {
   cvt_back_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, L.x, z); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
+}
+
+template <typename T>
+void MultiGrid<T>::set_degree(int degree) {
+  if (degree < 1) degree = 5;
+  if (degree == smooth_degree) return;
+  drop_graphs(-1);
+  smooth_degree = degree;
 }
 
 // slot < 0: all

@@ -59,7 +59,7 @@ struct MultiGrid {
   double alpha = 0.0;
   double cache_alpha[2] = {0, 0};
   int cur = 0, next_slot = 0;
-  int smooth_degree = 4;
+  int smooth_degree = 5;
   double* part = nullptr;
   double* host_part = nullptr;
   double* diag = nullptr;
@@ -81,6 +81,8 @@ struct MultiGrid {
   ~MultiGrid();
   dg_status build(dg_mesh* fine, cudaStream_t s);
   dg_status set_alpha(double alpha);
+  // Chebyshev degree of the smoother (drops the recorded cycles on a change)
+  void set_degree(int degree);
   // z = V-cycle(r) for an FP64 residual r of the finest level
   dg_status apply(const double* r, double* z);
 

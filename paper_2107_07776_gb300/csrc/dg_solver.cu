@@ -130,6 +130,7 @@ dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double*
           return st;
         }
       }
+      s->mg32->set_degree(o->mg_degree);
       st = s->mg32->set_alpha(alpha);
     } else {
       if (!s->mg64) {
@@ -142,6 +143,7 @@ dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double*
           return st;
         }
       }
+      s->mg64->set_degree(o->mg_degree);
       st = s->mg64->set_alpha(alpha);
     }
     if (st != DG_OK) return st;
