@@ -36,6 +36,10 @@ dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const 
                    double tol, int max_iter, double timeout_s, dg_solve_info* info);
 
 dg_status poisson_diagonal(const dg_mesh* m, double alpha, double* diag, cudaStream_t s);
+// ut = M^-1 P p (the projection's broken pressure gradient); when out is not
+// null also out = base + tau (ut - sub) in the same pass (sub may be null).
+dg_status project_fused(const dg_mesh* m, const double* p, double* ut, const double* base,
+                        double tau, const double* sub, double* out, cudaStream_t s);
 dg_status momentum_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co, const double* ub,
                                  double* diag, cudaStream_t s);
 

@@ -70,6 +70,13 @@ __device__ __forceinline__ int64_t neighbour(const Grid& g, const int ci[3], int
   return cell + (int64_t)(cn - ca) * stride;
 }
 
+// coordinate along axis a of the neighbour across face s (periodic wrap;
+// only meaningful where neighbour() is not -1), without a division
+__device__ __forceinline__ int neighbour_coord(const Grid& g, const int ci[3], int a, int s) {
+  const int ca = sel3(a, ci[0], ci[1], ci[2]), na = sel3(a, g.n[0], g.n[1], g.n[2]);
+  return s ? (ca + 1 == na ? 0 : ca + 1) : (ca == 0 ? na - 1 : ca - 1);
+}
+
 __device__ __forceinline__ void cell_coords(const Grid& g, int64_t cell, int ci[3]) {
   ci[0] = (int)(cell % g.n[0]);
   ci[1] = (int)((cell / g.n[0]) % g.n[1]);
@@ -161,9 +168,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
         A fv = zero, fg = zero;
         if (MODE == 0) {
           if (nb >= 0) {
-            int nc3[3];
-            cell_coords(g, nb, nc3);
-            const A hiN = Ar::from(sel3(ax, g.hi[0], g.hi[1], g.hi[2])[sel3(ax, nc3[0], nc3[1], nc3[2])]);
+            const A hiN = Ar::from(sel3(ax, g.hi[0], g.hi[1], g.hi[2])[neighbour_coord(g, ci, ax, s)]);
             A uout = zero, dnout = zero, wnout = zero;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
@@ -349,9 +354,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
         dvin = dvin * sgn * hiK;
         A fv;
         if (nb >= 0) {
-          int nc3[3];
-          cell_coords(g, nb, nc3);
-          const A hiN = Ar::from(sel3(ax, g.hi[0], g.hi[1], g.hi[2])[sel3(ax, nc3[0], nc3[1], nc3[2])]);
+          const A hiN = Ar::from(sel3(ax, g.hi[0], g.hi[1], g.hi[2])[neighbour_coord(g, ci, ax, s)]);
           A vout = zero, dvout = zero, uout[NT];
 #pragma unroll
           for (int tt = 0; tt < NT; ++tt) uout[tt] = zero;
@@ -629,6 +632,10 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 // ------------------------------------------------------------------
 // rhs = mass M u_mass + M f + G p (G the DG pressure gradient of Eq. rhs1);
 // writes (does not accumulate).  N velocity, NP pressure nodes per direction.
+// p reaches the velocity nodes by sum factorisation (the value table one
+// axis at a time; exact, Q_{k-1} lies in Q_k); the face average {{p}} is
+// formed in the pressure basis of the face (own and neighbour trace, NP
+// values along the normal each) and then interpolated to the face points.
 template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     mass_grad_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
@@ -637,10 +644,14 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
                      const double* __restrict__ p, double* __restrict__ rhs) {
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
-  constexpr int NBP = Sh<NP, DIM>::NB;
+  constexpr int NBP = Sh<NP, DIM>::NB, NPF = Sh<NP, DIM>::NF;
+  constexpr int SA = DIM == 3 ? N * NP * NP : N * NP;  // after the axis-0 interpolation
+  constexpr int SB = DIM == 3 ? N * N * NP : 1;        // after the axis-1 interpolation (3D)
   __shared__ A s_p[CPB][NBP];
+  __shared__ A s_a[CPB][SA];
+  __shared__ A s_b[CPB][SB];
   __shared__ A s_g[CPB][NB];
-  __shared__ A s_pu[CPB][NB];
+  __shared__ A s_t[CPB][2 * DIM * NPF];  // {{p}} per face, pressure tangential basis
   __shared__ A s_f[CPB][NFP];
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
@@ -654,54 +665,82 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     for (int b = 0; b < DIM; ++b) h[b] = Ar::from(g.h[b][ci[b]]);
     W = Ar::c(1.0);
     for (int b = 0; b < DIM; ++b) W = W * tb.w[ii[b]] * h[b];
-    if (p && node < NBP) s_p[cl][node] = Ar::from(p[cell * NBP + node]);
-  }
-  __syncthreads();
-  if (active && p) {
-    // p at the velocity nodes (exact: Q_{k-1} lies in Q_k)
-    A pu = zero;
-    for (int j = 0; j < NBP; ++j) {
-      const int j0 = j % NP, j1 = (j / NP) % NP, j2 = DIM == 3 ? j / (NP * NP) : 0;
-      A wgt = mx.I[ii[0]][j0] * mx.I[ii[1]][j1];
-      if (DIM == 3) wgt = wgt * mx.I[ii[2]][j2];
-      pu = Ar::fma(wgt, s_p[cl][j], pu);
+    if (p) {
+      if (node < NBP) s_p[cl][node] = Ar::from(p[cell * NBP + node]);
+      for (int idx = node; idx < 2 * DIM * NPF; idx += NB) {
+        const int fc = idx / NPF, t = idx % NPF, ax = fc >> 1, s = fc & 1;
+        A pin = zero;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          pin = Ar::fma(tp.L[s][j], Ar::from(__ldg(&p[cell * NBP + nodeof(NP, DIM, ax, j, t)])), pin);
+        A pav = pin;
+        const int64_t nb = neighbour(g, ci, ax, s);
+        if (nb >= 0) {
+          A pout = zero;
+#pragma unroll
+          for (int j = 0; j < NP; ++j)
+            pout = Ar::fma(tp.L[1 - s][j], Ar::from(__ldg(&p[nb * NBP + nodeof(NP, DIM, ax, j, t)])), pout);
+          pav = half * (pin + pout);
+        }
+        s_t[cl][idx] = pav;
+      }
     }
-    s_pu[cl][node] = pu;
-    s_g[cl][node] = W * pu;
   }
   __syncthreads();
   if (active && p) {
-    for (int fp = node; fp < NFP; fp += NB) {
+    for (int idx = node; idx < SA; idx += NB) {  // axis 0
+      const int i0 = idx % N, rest = idx / N;
+      A av = zero;
+#pragma unroll
+      for (int j0 = 0; j0 < NP; ++j0) av = Ar::fma(mx.I[i0][j0], s_p[cl][j0 + NP * rest], av);
+      s_a[cl][idx] = av;
+    }
+    for (int fp = node; fp < NFP; fp += NB) {  // - w |face| n {{p}} at the face points
       const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
       const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
-      const int64_t nb = neighbour(g, ci, ax, s);
-      A wt = Ar::c(1.0);
-      int tb3[3] = {0, 0, 0};
-      {
-        int tt = t;
-        for (int b = 0; b < DIM; ++b) {
-          if (b == ax) continue;
-          tb3[b] = tt % N;
-          wt = wt * tb.w[tt % N] * h[b];
-          tt /= N;
+      const int ta = t % N, tb2 = DIM == 3 ? t / N : 0;
+      const int ba = ax == 0 ? 1 : 0, bb = ax == 2 ? 1 : 2;
+      A wt = tb.w[ta] * sel3(ba, h[0], h[1], h[2]);
+      if (DIM == 3) wt = wt * tb.w[tb2] * sel3(bb, h[0], h[1], h[2]);
+      A pv = zero;
+      if (DIM == 3) {
+#pragma unroll
+        for (int b2 = 0; b2 < NP; ++b2) {
+          A r = zero;
+#pragma unroll
+          for (int a2 = 0; a2 < NP; ++a2) r = Ar::fma(mx.I[ta][a2], s_t[cl][fc * NPF + a2 + NP * b2], r);
+          pv = Ar::fma(mx.I[tb2][b2], r, pv);
         }
+      } else {
+#pragma unroll
+        for (int a2 = 0; a2 < NP; ++a2) pv = Ar::fma(mx.I[ta][a2], s_t[cl][fc * NPF + a2], pv);
       }
-      A pin = zero;
-      for (int i = 0; i < N; ++i) pin += tb.L[s][i] * s_pu[cl][nodeof(N, DIM, ax, i, t)];
-      A pav = pin;
-      if (nb >= 0) {
-        A pout = zero;
-        for (int j = 0; j < NBP; ++j) {
-          const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
-          A wgt = tp.L[1 - s][sel3(ax, jj[0], jj[1], jj[2])];
-          for (int b = 0; b < DIM; ++b)
-            if (b != ax) wgt = wgt * mx.I[tb3[b]][jj[b]];
-          pout = Ar::fma(wgt, Ar::from(__ldg(&p[nb * NBP + j])), pout);
-        }
-        pav = half * (pin + pout);
-      }
-      s_f[cl][fp] = -(wt * sgn * pav);
+      s_f[cl][fp] = -(wt * sgn * pv);
     }
+  }
+  __syncthreads();
+  if (DIM == 3) {
+    if (active && p) {
+      for (int idx = node; idx < SB; idx += NB) {  // axis 1
+        const int i0 = idx % N, i1 = (idx / N) % N, j2 = idx / (N * N);
+        A bv = zero;
+#pragma unroll
+        for (int j1 = 0; j1 < NP; ++j1) bv = Ar::fma(mx.I[i1][j1], s_a[cl][i0 + N * (j1 + NP * j2)], bv);
+        s_b[cl][idx] = bv;
+      }
+    }
+    __syncthreads();
+  }
+  if (active && p) {  // last axis: p at the velocity nodes
+    A pu = zero;
+    if (DIM == 3) {
+#pragma unroll
+      for (int j2 = 0; j2 < NP; ++j2) pu = Ar::fma(mx.I[ii[2]][j2], s_b[cl][ii[0] + N * (ii[1] + N * j2)], pu);
+    } else {
+#pragma unroll
+      for (int j1 = 0; j1 < NP; ++j1) pu = Ar::fma(mx.I[ii[1]][j1], s_a[cl][ii[0] + N * j1], pu);
+    }
+    s_g[cl][node] = W * pu;
   }
   __syncthreads();
   if (active) {
@@ -713,13 +752,12 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       if (p) {
         A acc = zero;
         for (int m = 0; m < N; ++m) {
-          int j[3] = {ii[0], ii[1], ii[2]};
-          j[c] = m;
-          acc += tb.D[m][ii[c]] * s_g[cl][j[0] + N * (j[1] + N * j[2])];
+          const int j0 = c == 0 ? m : ii[0], j1 = c == 1 ? m : ii[1], j2 = c == 2 ? m : ii[2];
+          acc = Ar::fma(tb.D[m][sel3(c, ii[0], ii[1], ii[2])], s_g[cl][j0 + N * (j1 + N * j2)], acc);
         }
         y += acc * Ar::from(g.hi[c][ci[c]]);
         const int t = tangof(N, DIM, c, ii);
-        for (int s = 0; s < 2; ++s) y += s_f[cl][(2 * c + s) * NF + t] * tb.L[s][ii[c]];
+        for (int s = 0; s < 2; ++s) y += s_f[cl][(2 * c + s) * NF + t] * tb.L[s][sel3(c, ii[0], ii[1], ii[2])];
       }
       rhs[o] = Ar::to_d(y);
     }
@@ -729,7 +767,12 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 // ------------------------------------------------------------------
 // rhs_p = alpha M^p p_old + (1/tau) sum_c D_c uss_c, one thread per pressure
 // node; D the DG divergence of Eq. weakform_p_1, integrated with the
-// velocity rule.
+// velocity rule.  Cell term by sum factorisation over the transposed
+// pressure-to-velocity tables: component 0 takes D^T along axis 0 and I^T
+// along the others, and so on; partial sums that meet the same remaining
+// tables are added before they are contracted further.  Face term: the
+// quadrature-weighted normal flux w |face| n {{u}} is tested against the
+// pressure basis, tangential axes first.
 template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
     pressure_rhs_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
@@ -738,46 +781,54 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
                         const double* __restrict__ p_old, double* __restrict__ rhs) {
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
-  constexpr int NBP = Sh<NP, DIM>::NB;
-  __shared__ A s_u[DIM][CPB][NB];
-  __shared__ A s_f[CPB][NFP];
+  constexpr int NBP = Sh<NP, DIM>::NB, NPF = Sh<NP, DIM>::NF;
+  constexpr int SX = DIM == 3 ? NP * N * N : NP * N;  // after the axis-0 contraction
+  constexpr int SY = DIM == 3 ? NP * NP * N : 1;      // after the axis-1 contraction (3D)
+  __shared__ A s_u[DIM][CPB][NB];         // W hi_c u_c at the velocity nodes
+  __shared__ A s_f[CPB][NFP];             // w |face| n {{u}} at the face points
+  __shared__ A s_F[CPB][2 * DIM * NPF];   // the same tested in the tangential pressure basis
+  __shared__ A s_x[DIM][CPB][SX];
+  __shared__ A s_y[2][CPB][SY];
   const int tid = threadIdx.x, cl = tid / NBP, node = tid % NBP;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
   const A zero = Ar::c(0.0), half = Ar::c(0.5);
   int ci[3] = {0, 0, 0};
-  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
+  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hiv[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
   if (active) {
     cell_coords(g, cell, ci);
-    for (int b = 0; b < DIM; ++b) h[b] = Ar::from(g.h[b][ci[b]]);
+    for (int b = 0; b < DIM; ++b) {
+      h[b] = Ar::from(g.h[b][ci[b]]);
+      hiv[b] = Ar::from(g.hi[b][ci[b]]);
+    }
     for (int idx = node; idx < DIM * NB; idx += NBP) {
       const int c = idx / NB, nd = idx % NB;
-      s_u[c][cl][nd] = Ar::from(uss[((int64_t)c * g.ncell + cell) * NB + nd]);
+      const int q0 = nd % N, q1 = (nd / N) % N, q2 = DIM == 3 ? nd / (N * N) : 0;
+      A Wq = tb.w[q0] * h[0] * tb.w[q1] * h[1];
+      if (DIM == 3) Wq = Wq * tb.w[q2] * h[2];
+      s_u[c][cl][nd] = Wq * sel3(c, hiv[0], hiv[1], hiv[2]) *
+                       Ar::from(uss[((int64_t)c * g.ncell + cell) * NB + nd]);
     }
-  }
-  __syncthreads();
-  if (active) {
     for (int fp = node; fp < NFP; fp += NBP) {
       const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
       const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
       const int64_t nb = neighbour(g, ci, ax, s);
-      A wt = Ar::c(1.0);
-      {
-        int tt = t;
-        for (int b = 0; b < DIM; ++b) {
-          if (b == ax) continue;
-          wt = wt * tb.w[tt % N] * h[b];
-          tt /= N;
-        }
-      }
+      const int ta = t % N, tb2 = DIM == 3 ? t / N : 0;
+      const int ba = ax == 0 ? 1 : 0, bb = ax == 2 ? 1 : 2;
+      A wt = tb.w[ta] * sel3(ba, h[0], h[1], h[2]);
+      if (DIM == 3) wt = wt * tb.w[tb2] * sel3(bb, h[0], h[1], h[2]);
       A uin = zero;
-      for (int i = 0; i < N; ++i) uin += tb.L[s][i] * s_u[ax][cl][nodeof(N, DIM, ax, i, t)];
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        uin = Ar::fma(tb.L[s][i], Ar::from(__ldg(&uss[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)])),
+                      uin);
       A uav = uin;
       if (nb >= 0) {
         A uout = zero;
+#pragma unroll
         for (int i = 0; i < N; ++i)
-          uout += tb.L[1 - s][i] *
-                  Ar::from(__ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)]));
+          uout = Ar::fma(tb.L[1 - s][i],
+                         Ar::from(__ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)])), uout);
         uav = half * (uin + uout);
       }
       s_f[cl][fp] = wt * sgn * uav;
@@ -785,93 +836,225 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
   }
   __syncthreads();
   if (active) {
-    const int pi[3] = {node % NP, (node / NP) % NP, DIM == 3 ? node / (NP * NP) : 0};
-    A Wp = Ar::c(1.0), hiv[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
-    for (int b = 0; b < DIM; ++b) {
-      Wp = Wp * tp.w[pi[b]] * h[b];
-      hiv[b] = Ar::from(g.hi[b][ci[b]]);
-    }
-    A acc = zero;
-    // cell term: sum over velocity quadrature points of W u_c d_c psi_i
-    for (int q = 0; q < NB; ++q) {
-      const int qq[3] = {q % N, (q / N) % N, DIM == 3 ? q / (N * N) : 0};
-      A Wq = Ar::c(1.0), v[DIM];
-      for (int b = 0; b < DIM; ++b) {
-        Wq = Wq * tb.w[qq[b]] * h[b];
-        v[b] = mx.I[qq[b]][pi[b]];
+    for (int idx = node; idx < SX; idx += NBP) {  // axis 0
+      const int p0 = idx % NP, rest = idx / NP;
+      A x[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) x[c] = zero;
+#pragma unroll
+      for (int q0 = 0; q0 < N; ++q0) {
+        x[0] = Ar::fma(mx.D[q0][p0], s_u[0][cl][q0 + N * rest], x[0]);
+#pragma unroll
+        for (int c = 1; c < DIM; ++c) x[c] = Ar::fma(mx.I[q0][p0], s_u[c][cl][q0 + N * rest], x[c]);
       }
-      for (int c = 0; c < DIM; ++c) {
-        A dpsi = mx.D[qq[c]][pi[c]] * hiv[c];
-        for (int b = 0; b < DIM; ++b)
-          if (b != c) dpsi = dpsi * v[b];
-        acc += Wq * s_u[c][cl][q] * dpsi;
-      }
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) s_x[c][cl][idx] = x[c];
     }
-    // face term: - sum_faces sum_t w_t {{u}}.n psi_i
-    for (int fc = 0; fc < 2 * DIM; ++fc) {
-      const int ax = fc >> 1, s = fc & 1;
-      for (int t = 0; t < NF; ++t) {
-        A psi = tp.L[s][sel3(ax, pi[0], pi[1], pi[2])];
-        int tt = t;
-        for (int b = 0; b < DIM; ++b) {
-          if (b == ax) continue;
-          psi = psi * mx.I[tt % N][pi[b]];
-          tt /= N;
+    for (int idx = node; idx < 2 * DIM * NPF; idx += NBP) {  // face fluxes, tangential axes
+      const int fc = idx / NPF, t = idx % NPF, a2 = t % NP, b2 = DIM == 3 ? t / NP : 0;
+      A F = zero;
+      if (DIM == 3) {
+#pragma unroll
+        for (int tb2 = 0; tb2 < N; ++tb2) {
+          A r = zero;
+#pragma unroll
+          for (int ta = 0; ta < N; ++ta) r = Ar::fma(mx.I[ta][a2], s_f[cl][fc * NF + ta + N * tb2], r);
+          F = Ar::fma(mx.I[tb2][b2], r, F);
         }
-        acc -= s_f[cl][fc * NF + t] * psi;
+      } else {
+#pragma unroll
+        for (int ta = 0; ta < N; ++ta) F = Ar::fma(mx.I[ta][a2], s_f[cl][fc * NF + ta], F);
+      }
+      s_F[cl][idx] = F;
+    }
+  }
+  __syncthreads();
+  if (DIM == 3) {
+    if (active) {
+      for (int idx = node; idx < SY; idx += NBP) {  // axis 1: (x0, x2 with I^T; x1 with D^T)
+        const int p0 = idx % NP, p1 = (idx / NP) % NP, q2 = idx / (NP * NP);
+        A y0 = zero, y1 = zero;
+#pragma unroll
+        for (int q1 = 0; q1 < N; ++q1) {
+          const int q = p0 + NP * (q1 + N * q2);
+          y0 = Ar::fma(mx.I[q1][p1], s_x[0][cl][q], y0);
+          y0 = Ar::fma(mx.D[q1][p1], s_x[1][cl][q], y0);
+          y1 = Ar::fma(mx.I[q1][p1], s_x[DIM - 1][cl][q], y1);
+        }
+        s_y[0][cl][idx] = y0;
+        s_y[1][cl][idx] = y1;
       }
     }
-    rhs[cell * NBP + node] =
-        Ar::to_d(Ar::from(alpha_d) * Wp * Ar::from(p_old[cell * NBP + node]) + Ar::from(inv_tau_d) * acc);
+    __syncthreads();
   }
+  if (!active) return;
+  const int pi[3] = {node % NP, (node / NP) % NP, DIM == 3 ? node / (NP * NP) : 0};
+  A acc = zero;
+  if (DIM == 3) {  // axis 2: I^T on (x0 + x1 so far), D^T on x2
+#pragma unroll
+    for (int q2 = 0; q2 < N; ++q2) {
+      const int q = pi[0] + NP * (pi[1] + NP * q2);
+      acc = Ar::fma(mx.I[q2][pi[2]], s_y[0][cl][q], acc);
+      acc = Ar::fma(mx.D[q2][pi[2]], s_y[1][cl][q], acc);
+    }
+  } else {  // axis 1 in 2D: I^T on x0, D^T on x1
+#pragma unroll
+    for (int q1 = 0; q1 < N; ++q1) {
+      const int q = pi[0] + NP * q1;
+      acc = Ar::fma(mx.I[q1][pi[1]], s_x[0][cl][q], acc);
+      acc = Ar::fma(mx.D[q1][pi[1]], s_x[DIM - 1][cl][q], acc);
+    }
+  }
+  // face term: - sum_faces (tested flux) L_s(normal index)
+#pragma unroll
+  for (int fc = 0; fc < 2 * DIM; ++fc) {
+    const int ax = fc >> 1, s = fc & 1;
+    acc = Ar::fma(-tp.L[s][sel3(ax, pi[0], pi[1], pi[2])], s_F[cl][fc * NPF + tangof(NP, DIM, ax, pi)], acc);
+  }
+  A Wp = Ar::c(1.0);
+  for (int b = 0; b < DIM; ++b) Wp = Wp * tp.w[pi[b]] * h[b];
+  rhs[cell * NBP + node] =
+      Ar::to_d(Ar::from(alpha_d) * Wp * Ar::from(p_old[cell * NBP + node]) + Ar::from(inv_tau_d) * acc);
 }
 
 // ------------------------------------------------------------------
 // u~_c = M^-1 P_c p: the broken gradient of p at the velocity nodes (exact
-// on affine cells, where M is diagonal and P_c p = W d_c p at the nodes).
+// on affine cells, where M is diagonal and P_c p = W d_c p at the nodes), by
+// sum factorisation: the pressure-to-velocity tables applied one axis at a
+// time (value table I or derivative table D per axis), sharing the partial
+// contractions between the components.  Optional fused update (out != null):
+// out = base + tau (u~ - sub) (sub may be null), the stage updates of
+// Section 2 (u** = u* + tau u~old, u = u* - tau (u~new - u~old)).
 template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     project_kernel(const __grid_constant__ Grid g, const __grid_constant__ MixTab<A> mx,
-                   const double* __restrict__ p, double* __restrict__ ut) {
+                   const double* __restrict__ p, double* __restrict__ ut,
+                   const double* __restrict__ base, double tau, const double* __restrict__ sub,
+                   double* __restrict__ out) {
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NBP = Sh<NP, DIM>::NB;
+  constexpr int SA = DIM == 3 ? N * NP * NP : N * NP;  // after the axis-0 contraction
+  constexpr int SB = DIM == 3 ? N * N * NP : 1;        // after the axis-1 contraction (3D)
   __shared__ A s_p[CPB][NBP];
+  __shared__ A s_a[2][CPB][SA];   // I0 p, D0 p
+  __shared__ A s_b[3][CPB][SB];   // I1 I0 p, D1 I0 p, I1 D0 p
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
+  const A zero = Ar::c(0.0);
   if (active && node < NBP) s_p[cl][node] = Ar::from(p[cell * NBP + node]);
   __syncthreads();
+  if (active) {  // axis 0
+    for (int idx = node; idx < SA; idx += NB) {
+      const int i0 = idx % N, rest = idx / N;  // rest = j1 (+ NP j2)
+      A av = zero, bv = zero;
+#pragma unroll
+      for (int j0 = 0; j0 < NP; ++j0) {
+        const A pv = s_p[cl][j0 + NP * rest];
+        av = Ar::fma(mx.I[i0][j0], pv, av);
+        bv = Ar::fma(mx.D[i0][j0], pv, bv);
+      }
+      s_a[0][cl][idx] = av;
+      s_a[1][cl][idx] = bv;
+    }
+  }
+  __syncthreads();
+  if (DIM == 3) {
+    if (active) {  // axis 1
+      for (int idx = node; idx < SB; idx += NB) {
+        const int i0 = idx % N, i1 = (idx / N) % N, j2 = idx / (N * N);
+        A ai = zero, ad = zero, bi = zero;
+#pragma unroll
+        for (int j1 = 0; j1 < NP; ++j1) {
+          const int q = i0 + N * (j1 + NP * j2);
+          ai = Ar::fma(mx.I[i1][j1], s_a[0][cl][q], ai);
+          ad = Ar::fma(mx.D[i1][j1], s_a[0][cl][q], ad);
+          bi = Ar::fma(mx.I[i1][j1], s_a[1][cl][q], bi);
+        }
+        s_b[0][cl][idx] = ai;
+        s_b[1][cl][idx] = ad;
+        s_b[2][cl][idx] = bi;
+      }
+    }
+    __syncthreads();
+  }
   if (!active) return;
   int ci[3];
   cell_coords(g, cell, ci);
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  for (int c = 0; c < DIM; ++c) {
-    A acc = Ar::c(0.0);
-    for (int j = 0; j < NBP; ++j) {
-      const int jj[3] = {j % NP, (j / NP) % NP, DIM == 3 ? j / (NP * NP) : 0};
-      A wgt = b0_or(c == 0, mx.D[ii[0]][jj[0]], mx.I[ii[0]][jj[0]]);
-      for (int b = 1; b < DIM; ++b) wgt = wgt * (b == c ? mx.D[ii[b]][jj[b]] : mx.I[ii[b]][jj[b]]);
-      acc = Ar::fma(wgt, s_p[cl][j], acc);
+  A uc[DIM];
+  if (DIM == 3) {  // axis 2: x-derivative (I2 I1 D0), y (I2 D1 I0), z (D2 I1 I0)
+    A u0 = zero, u1 = zero, u2 = zero;
+#pragma unroll
+    for (int j2 = 0; j2 < NP; ++j2) {
+      const int q = ii[0] + N * (ii[1] + N * j2);
+      u0 = Ar::fma(mx.I[ii[2]][j2], s_b[2][cl][q], u0);
+      u1 = Ar::fma(mx.I[ii[2]][j2], s_b[1][cl][q], u1);
+      u2 = Ar::fma(mx.D[ii[2]][j2], s_b[0][cl][q], u2);
     }
-    ut[((int64_t)c * g.ncell + cell) * NB + node] = Ar::to_d(acc * Ar::from(g.hi[c][ci[c]]));
+    uc[0] = u0;
+    uc[1] = u1;
+    uc[DIM - 1] = u2;
+  } else {  // axis 1 in 2D: x (I1 D0), y (D1 I0)
+    A u0 = zero, u1 = zero;
+#pragma unroll
+    for (int j1 = 0; j1 < NP; ++j1) {
+      const int q = ii[0] + N * j1;
+      u0 = Ar::fma(mx.I[ii[1]][j1], s_a[1][cl][q], u0);
+      u1 = Ar::fma(mx.D[ii[1]][j1], s_a[0][cl][q], u1);
+    }
+    uc[0] = u0;
+    uc[DIM - 1] = u1;
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t o = ((int64_t)c * g.ncell + cell) * NB + node;
+    const double v = Ar::to_d(uc[c] * Ar::from(g.hi[c][ci[c]]));
+    ut[o] = v;
+    if (out) out[o] = base[o] + tau * (sub ? v - sub[o] : v);
   }
 }
 
 // ------------------------------------------------------------------
 // Diagonal of mass M + visc A + adv C(ubar) (walls = 1) or of
 // alpha M^p + K (walls = 0, adv = 0), one thread per node.
-template <int DIM, int N, typename R>
-__global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb,
-                            R mass, R visc, R adv, R pen, int walls,
-                            const double* __restrict__ ub, double* __restrict__ diag) {
+template <int DIM, int N, typename R, int CPB>
+__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
+    diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb, R mass, R visc, R adv,
+                R pen, int walls, const double* __restrict__ ub, double* __restrict__ diag) {
   using Ar = Arith<R>;
-  constexpr int NB = Sh<N, DIM>::NB;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= g.ncell * NB) return;
-  const int64_t cell = gid / NB;
-  const int node = (int)(gid % NB);
-  int ci[3];
-  cell_coords(g, cell, ci);
+  constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
+  // normal advecting velocity on each face point, own and neighbour trace,
+  // evaluated once per cell (each is shared by the N nodes of its line)
+  __shared__ R s_in[CPB][NFP];
+  __shared__ R s_out[CPB][NFP];
+  const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < g.ncell;
+  int ci[3] = {0, 0, 0};
+  if (active) cell_coords(g, cell, ci);
+  if (adv != R(0.0)) {
+    if (active) {
+      for (int fp = node; fp < NFP; fp += NB) {
+        const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
+        const R sgn = s ? R(1.0) : R(-1.0);
+        const double* ua = ub + (int64_t)ax * g.ncell * NB;
+        R unin = 0.0, unout = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) unin = Ar::fma(tb.L[s][i], (R)__ldg(&ua[cell * NB + nodeof(N, DIM, ax, i, t)]), unin);
+        const int64_t nb = neighbour(g, ci, ax, s);
+        if (nb >= 0) {
+#pragma unroll
+          for (int i = 0; i < N; ++i)
+            unout = Ar::fma(tb.L[1 - s][i], (R)__ldg(&ua[nb * NB + nodeof(N, DIM, ax, i, t)]), unout);
+        }
+        s_in[cl][fp] = sgn * unin;
+        s_out[cl][fp] = sgn * unout;
+      }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
   R h[3] = {1, 1, 1}, hi[3] = {1, 1, 1};
   for (int b = 0; b < DIM; ++b) {
@@ -894,7 +1077,7 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
       acc += Wat(j) * dm * dm;
     }
     d += visc * acc;
-    if (adv != 0.0) d -= adv * W * (R)ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] * hi[b];
+    if (adv != R(0.0)) d -= adv * W * (R)ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] * hi[b];
   }
   for (int ax = 0; ax < DIM; ++ax) {
     const int t = tangof(N, DIM, ax, ii);
@@ -906,17 +1089,10 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
       const int64_t nb = neighbour(g, ci, ax, s);
       const R hiK = hi[ax];
       const R uin = tb.L[s][ii[ax]], dnin = sgn * tb.dL[s][ii[ax]] * hiK;
-      R unin = 0.0;
-      if (adv != 0.0) {
-        for (int i = 0; i < N; ++i)
-          unin = Ar::fma(tb.L[s][i], (R)ub[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)], unin);
-        unin *= sgn;
-      }
+      const R unin = adv != R(0.0) ? s_in[cl][(2 * ax + s) * NF + t] : R(0.0);
       R fv = 0.0, fg = 0.0;
       if (nb >= 0) {
-        int nc3[3];
-        cell_coords(g, nb, nc3);
-        const R hiN = (R)g.hi[ax][nc3[ax]];
+        const R hiN = (R)g.hi[ax][neighbour_coord(g, ci, ax, s)];
         // a one-cell period makes the cell its own neighbour
         const R uout = nb == cell ? tb.L[1 - s][ii[ax]] : R(0.0);
         const R dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] * hiN : R(0.0);
@@ -924,11 +1100,8 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
         const R jump = uin - uout;
         fv = visc * (R(-0.5) * (dnin + dnout) + C * jump);
         fg = R(-0.5) * visc * jump;
-        if (adv != 0.0) {
-          R unout = 0.0;
-          for (int i = 0; i < N; ++i)
-            unout = Ar::fma(tb.L[1 - s][i], (R)ub[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)], unout);
-          unout *= sgn;
+        if (adv != R(0.0)) {
+          const R unout = s_out[cl][(2 * ax + s) * NF + t];
           const R lam = fmax(fabs(unin), fabs(unout));
           fv += adv * (R(0.5) * (uin * unin + uout * unout) + R(0.5) * lam * jump);
         }
@@ -939,7 +1112,7 @@ __global__ void diag_kernel(const __grid_constant__ Grid g, const __grid_constan
       d += wt * (fv * tb.L[s][ii[ax]] + fg * sgn * tb.dL[s][ii[ax]] * hiK);
     }
   }
-  diag[gid] = (double)d;
+  diag[cell * NB + node] = (double)d;
 }
 
 template <int DIM>
@@ -1088,35 +1261,39 @@ dg_status run_pressure_rhs(const dg_mesh* m, double alpha, double inv_tau, const
 }
 
 template <typename A, int DIM, int N>
-dg_status run_project_a(const dg_mesh* m, const double* p, double* ut, cudaStream_t s) {
+dg_status run_project_a(const dg_mesh* m, const double* p, double* ut, const double* base,
+                        double tau, const double* sub, double* out, cudaStream_t s) {
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  project_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_mix<A>(m), p, ut);
+  project_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_mix<A>(m), p,
+                                                                   ut, base, tau, sub, out);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 template <int DIM, int N>
-dg_status run_project(const dg_mesh* m, const double* p, double* ut, cudaStream_t s) {
-  return m->fp64_arith ? run_project_a<double, DIM, N>(m, p, ut, s)
-                       : run_project_a<df64, DIM, N>(m, p, ut, s);
+dg_status run_project(const dg_mesh* m, const double* p, double* ut, const double* base,
+                      double tau, const double* sub, double* out, cudaStream_t s) {
+  return m->fp64_arith ? run_project_a<double, DIM, N>(m, p, ut, base, tau, sub, out, s)
+                       : run_project_a<df64, DIM, N>(m, p, ut, base, tau, sub, out, s);
 }
 
 template <int DIM, int N>
 dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, double adv,
                    const double* ub, double* diag, cudaStream_t s, bool fp32 = false) {
-  const int64_t total = m->ncell * Sh<N, DIM>::NB;
-  const unsigned blocks = (unsigned)((total + 255) / 256);
+  constexpr int CPB = cpb_for<N, DIM>();
+  constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
+  const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
   if (fp32)
-    diag_kernel<DIM, N, float><<<blocks, 256, 0, s>>>(
+    diag_kernel<DIM, N, float, CPB><<<blocks, threads, 0, s>>>(
         make_grid<DIM>(m), pressure ? m->tp32 : m->tu32, (float)mass, (float)visc, (float)adv,
         (float)(N * N), pressure ? 0 : 1, ub, diag);
   else
-    diag_kernel<DIM, N, double><<<blocks, 256, 0, s>>>(make_grid<DIM>(m), pressure ? m->tp64 : m->tu64,
-                                                       mass, visc, adv, (double)(N * N),
-                                                       pressure ? 0 : 1, ub, diag);
+    diag_kernel<DIM, N, double, CPB><<<blocks, threads, 0, s>>>(
+        make_grid<DIM>(m), pressure ? m->tp64 : m->tu64, mass, visc, adv, (double)(N * N),
+        pressure ? 0 : 1, ub, diag);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -1140,6 +1317,37 @@ dg_status momentum_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co,
                                  double* diag, cudaStream_t s) {
   if (!m->affine) return general_diag(m, false, co->mass, co->visc, co->adv, ub, diag, true, s);
   return DG_DISPATCH_U(m, run_diag, m, false, co->mass, co->visc, co->adv, ub, diag, s, true);
+}
+
+// out = base + tau (ut - sub) elementwise (sub may be null)
+__global__ void __launch_bounds__(256)
+    update_kernel(int64_t n, const double* __restrict__ base, double tau, const double* __restrict__ ut,
+                  const double* __restrict__ sub, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = base[i] + tau * (sub ? ut[i] - sub[i] : ut[i]);
+}
+
+dg_status axpby_update(int64_t n, const double* base, double tau, const double* ut, const double* sub,
+                       double* out, cudaStream_t s) {
+  const int64_t want = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
+  update_kernel<<<blocks, 256, 0, s>>>(n, base, tau, ut, sub, out);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// internal entry used by the solver: u~ = M^-1 P p into ut, and optionally
+// out = base + tau (u~ - sub) in the same pass
+dg_status project_fused(const dg_mesh* m, const double* p, double* ut, const double* base,
+                        double tau, const double* sub, double* out, cudaStream_t s) {
+  if (!m->affine) {
+    dg_status st = general_project(m, p, ut, s);
+    if (st != DG_OK || !out) return st;
+    // trilinear cells: the update as a separate pass
+    return axpby_update(m->ncell * m->nbu * m->dim, base, tau, ut, sub, out, s);
+  }
+  return DG_DISPATCH_U(m, run_project, m, p, ut, base, tau, sub, out, s);
 }
 
 // internal entry used by the solver: diagonal of a pressure-space operator
@@ -1221,8 +1429,7 @@ dg_status dg_project_gradient(dg_mesh* m, const double* p, double* ut, void* str
     set_error("dg_project_gradient: bad argument");
     return DG_EINVAL;
   }
-  if (!m->affine) return general_project(m, p, ut, as_stream(stream));
-  return DG_DISPATCH_U(m, run_project, m, p, ut, as_stream(stream));
+  return project_fused(m, p, ut, nullptr, 0.0, nullptr, nullptr, as_stream(stream));
 }
 
 dg_status dg_rhs_pressure(dg_mesh* m, double alpha, double tau, const double* uss,

@@ -530,8 +530,8 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(3);
   // ---------------- stage 1: projection (Eq. helmholtz2a) ---------------
   const double tau1 = g * dt, alpha1 = 1.0 / (s->c * s->c * tau1 * tau1);
-  STEP(dg_project_gradient(m, p, s->ut_old, st_));
-  STEP(vo.axpby(nu, 1.0, s->ustar, tau1, s->ut_old, s->uss));
+  // u~(p^n) into ut_old, u** = u* + tau u~(p^n) in the same pass
+  STEP(project_fused(m, p, s->ut_old, s->ustar, tau1, nullptr, s->uss, st_));
   STEP(dg_rhs_pressure(m, alpha1, tau1, s->uss, p, s->rhs_p, st_));
   if (ho.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(s->p_g, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
@@ -542,10 +542,8 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(1);
   STEP(finish_guess(s, 1, prm->helm.guess, s->p_g));
   tr.mark(3);
-  STEP(dg_project_gradient(m, s->p_g, s->ut_new, st_));
-  // u^{n+g} = u* - tau (u~new - u~old)
-  STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
-  STEP(vo.axpby(nu, 1.0, s->ustar, -tau1, s->ut_new, s->u_g));
+  // u~(p^{n+g}) into ut_new and u^{n+g} = u* - tau (u~new - u~old)
+  STEP(project_fused(m, s->p_g, s->ut_new, s->ustar, -tau1, s->ut_old, s->u_g, st_));
   tr.mark(0);
   // ---------------- stage 2: momentum predictor (Eq. second_stage) ------
   if (prm->extrapolate) {
@@ -589,8 +587,8 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(3);
   // ---------------- stage 2: projection (Eq. helmholtz3a) ---------------
   const double tau2 = (1.0 - g) * dt, alpha2 = 1.0 / (s->c * s->c * tau2 * tau2);
-  STEP(dg_project_gradient(m, s->p_g, s->ut_old, st_));
-  STEP(vo.axpby(nu, 1.0, s->ustar, tau2, s->ut_old, s->uss));
+  // u~(p^{n+g}) is stage 1's ut_new (p^{n+g} has not changed since)
+  STEP(vo.axpby(nu, 1.0, s->ustar, tau2, s->ut_new, s->uss));
   STEP(dg_rhs_pressure(m, alpha2, tau2, s->uss, s->p_g, s->rhs_p, st_));
   if (ho.guess != DG_GUESS_ZERO)
     DG_CUDA(cudaMemcpyAsync(p, s->p_g, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
@@ -602,11 +600,10 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(1);
   STEP(finish_guess(s, 3, prm->helm.guess, p));
   tr.mark(3);
-  STEP(dg_project_gradient(m, p, s->ut_new, st_));
-  STEP(vo.axpby(nu, 1.0, s->ut_new, -1.0, s->ut_old, s->ut_new));
   // history u^{n+g} before u is overwritten with u^{n+1}
   DG_CUDA(cudaMemcpyAsync(s->u_hist, s->u_g, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
-  STEP(vo.axpby(nu, 1.0, s->ustar, -tau2, s->ut_new, u));
+  // u~(p^{n+1}) into ut_old (free now) and u^{n+1} = u* - tau (u~(p^{n+1}) - u~(p^{n+g}))
+  STEP(project_fused(m, p, s->ut_old, s->ustar, -tau2, s->ut_new, u, st_));
   tr.mark(5);
   DG_CUDA(cudaStreamSynchronize(st_));
   tr.finish();
