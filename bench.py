@@ -198,6 +198,8 @@ def run_ours(args, rank, world):
         # every solver takes the same untimed steps (training phase of the
         # learned guess + warm-up) so all time the same window of the flow
         pc, guess, learned, deg = SOLVERS[name]
+        if name == args.solver and args.mg_degree:
+            deg = args.mg_degree
         pc, guess = getattr(b, pc), getattr(b, guess)
         s = b.dg_solver_create(mesh.handle, w.Re, w.c)
         u, p = u0.clone(), p0.clone()
@@ -427,6 +429,8 @@ def main():
                     help="ncu DRAM bytes per launch of the dominant kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--mg-degree", type=int, default=0,
+                    help="Chebyshev degree of the multigrid smoother for --solver (0: its default)")
     ap.add_argument("--profile-step", action="store_true",
                     help="bracket the first timed step with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -473,7 +477,7 @@ def main():
             "data": "synthetic", "config": cfg, "clocks": r["clocks"], "e2e": r["e2e"],
             "gpu_launches": r["gpu_launches"], "iterations_per_step": r["iterations"],
             "compare": r["compare"], "apply": r["apply"], "roofline": r["roofline"],
-            "autotune": r["autotune"], "mg_degree": SOLVERS[args.solver][3], "cpu_baseline": cb}
+            "autotune": r["autotune"], "mg_degree": args.mg_degree or SOLVERS[args.solver][3], "cpu_baseline": cb}
     print(json.dumps(line))
 
 

@@ -16,7 +16,13 @@
  *    space Q_k and k per direction for the pressure space Q_{k-1} (Section 3).
  *  - Work is enqueued on the caller's stream (`stream` is a cudaStream_t, NULL
  *    = legacy default stream).  Calls that return iteration counts or
- *    residuals synchronise that stream before returning.
+ *    residuals synchronise that stream before returning.  The solver calls
+ *    (dg_solve_stage, trbdf2_step, dg_solver_set_history) run on the solver's
+ *    own non-blocking stream instead: each first waits for the work enqueued
+ *    on the legacy default stream (and so on every blocking stream) and
+ *    synchronises before it returns.  Kernels are launched with programmatic
+ *    dependent launch on non-default streams (DG_PDL=0 in the environment
+ *    turns it off).
  *  - Errors come back as dg_status; dg_last_error() gives a message for the
  *    calling thread.  No C++ exception crosses the ABI and no kernel traps:
  *    device-side failures set a device status word checked at call end.
@@ -245,7 +251,7 @@ typedef struct {
 dg_status dg_solver_create(dg_mesh* mesh, double Re, double c, dg_solver** out);
 void dg_solver_destroy(dg_solver* solver);
 
-/* Solve one stage system on the solver's stream:
+/* Solve one stage system on the solver's stream (see the stream note above):
  *   system MOMENTUM:  (co) applied per component with advecting field ubar,
  *                     rhs and x have n_dofs_u doubles (all components);
  *   system HELMHOLTZ: (alpha M^p + K), rhs and x have n_dofs_p doubles.

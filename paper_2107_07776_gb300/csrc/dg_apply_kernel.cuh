@@ -75,6 +75,7 @@ __device__ __forceinline__ int tang_of(int a, const int i[3]) {
 }  // namespace dg
 
 #include "dg_split_kernel.cuh"
+#include "dg_q1_kernel.cuh"
 
 namespace dg {
 
@@ -84,6 +85,7 @@ template <typename T, typename A, int DIM, int N, bool ADV, int CPB, int MINB = 
 __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MINB)
     scalar_op_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
                      const T* __restrict__ src, const T* __restrict__ ub, T* __restrict__ dst) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF, NFP = Shape<N, DIM>::NFP;
   __shared__ A s_u[CPB][NB];
@@ -105,9 +107,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
   A W = zero;
   if (active) {
-    ci[0] = (int)(cell % a.n0);
-    ci[1] = (int)((cell / a.n0) % a.n1);
-    ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
+    lex_coords(cell, a.n0, a.n1, ci);
     h[0] = Ar::from(a.h0[ci[0]]);
     h[1] = Ar::from(a.h1[ci[1]]);
     hi[0] = Ar::from(a.hi0[ci[0]]);
@@ -302,10 +302,10 @@ constexpr int smem_words(int cpb) {
 // default cells per CTA with the registers per thread capped at 96 and 80
 // (more resident CTAs per SM, possibly at the price of spills); variants 5
 // and 6 are the face-once form (face fluxes, then cells) with the default
-// cells per CTA, uncapped and capped at 80 registers.
-constexpr int kTuneVariants = 7;
-
-__host__ __device__ constexpr bool variant_split(int v) { return v >= 5; }
+// cells per CTA, uncapped and capped at 80 registers; variant 7 is the
+// thread-per-cell Q1 kernel (3D scalar operators without advection on two
+// points per direction; elsewhere it runs as variant 1).
+// (kTuneVariants, variant_split and variant_q1 are in dg_common.cuh.)
 
 template <typename T, int DIM, int N, bool ADV>
 constexpr int cpb_variant(int v) {
@@ -335,7 +335,7 @@ static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<A>& tb, const T* 
     set_error("operator apply: grid too large");
     return DG_EINVAL;
   }
-  scalar_op_kernel<T, A, DIM, N, ADV, CPB, MINB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst);
+  launch(scalar_op_kernel<T, A, DIM, N, ADV, CPB, MINB>, (unsigned)blocks, threads, 0, s, args, tb, src, ub, dst);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -354,11 +354,25 @@ static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T
   }
   A* flux = static_cast<A*>(args.flux);
   const int64_t fthreads = nface * Shape<N, DIM>::NF;
-  face_flux_kernel<T, A, DIM, N, ADV><<<(unsigned)((fthreads + 255) / 256), 256, 0, s>>>(args, tb, src, ub, flux);
+  launch(face_flux_kernel<T, A, DIM, N, ADV>, (unsigned)((fthreads + 255) / 256), 256, 0, s, args, tb, src, ub, flux);
   count_launch();
   constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
   const int64_t blocks = (args.ncell + CPB - 1) / CPB;
-  cell_split_kernel<T, A, DIM, N, ADV, CPB, MINB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, flux, dst);
+  launch(cell_split_kernel<T, A, DIM, N, ADV, CPB, MINB>, (unsigned)blocks, threads, 0, s, args, tb, src, ub, flux, dst);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+template <typename T, typename A>
+static dg_status launch_q1(const OpArgs<T>& args, const Tab1D<A>& tb, const T* src, T* dst,
+                           cudaStream_t s) {
+  const int64_t blocks = (args.ncell + 127) / 128;
+  if (blocks > 0x7fffffff) {
+    set_error("operator apply: grid too large");
+    return DG_EINVAL;
+  }
+  launch(q1_cell_kernel<T, A>, (unsigned)blocks, 128, 0, s, args, tb, src, dst);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -367,7 +381,12 @@ static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T
 template <typename T, typename A, int DIM, int N, bool ADV, int V>
 static dg_status launch_v(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
                           T* dst, cudaStream_t s) {
-  if constexpr (variant_split(V))
+  if constexpr (variant_q1(V)) {
+    if constexpr (N == 2 && DIM == 3 && !ADV) {
+      if (args.ncomp == 1) return launch_q1<T, A>(args, tb, src, dst, s);
+    }
+    return launch_v<T, A, DIM, N, ADV, 1>(args, tb, ub, src, dst, s);
+  } else if constexpr (variant_split(V))
     return launch_split<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V)>(
         args, tb, ub, src, dst, s);
   else
@@ -385,6 +404,7 @@ static dg_status launch_fixed(int variant, const OpArgs<T>& args, const Tab1D<A>
     case 4: return launch_v<T, A, DIM, N, ADV, 4>(args, tb, ub, src, dst, s);
     case 5: return launch_v<T, A, DIM, N, ADV, 5>(args, tb, ub, src, dst, s);
     case 6: return launch_v<T, A, DIM, N, ADV, 6>(args, tb, ub, src, dst, s);
+    case 7: return launch_v<T, A, DIM, N, ADV, 7>(args, tb, ub, src, dst, s);
     default: return launch_v<T, A, DIM, N, ADV, 1>(args, tb, ub, src, dst, s);
   }
 }

@@ -12,6 +12,60 @@
 
 namespace dg {
 
+// Programmatic dependent launch.  Every kernel of the library begins with
+// pdl_entry(): griddepcontrol.wait returns once the kernels before it on the
+// stream have completed and their writes are visible (at once when the launch
+// carried no PDL attribute); launch_dependents then lets the next kernel's
+// blocks be placed on free SM slots while this one still runs, so that the
+// launch latency of back-to-back small kernels overlaps the tail of the one
+// before.  Nothing reads or writes global memory before the wait.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// (i, j, k) of a lexicographic cell index on an n0 x n1 x n2 box, in 32-bit
+// integer division while the index fits (several times cheaper than 64-bit)
+__device__ __forceinline__ void lex_coords(int64_t cell, int n0, int n1, int ci[3]) {
+  if (cell <= 0x7fffffffLL) {
+    const unsigned c = (unsigned)cell, q = c / (unsigned)n0;
+    ci[0] = (int)(c - q * (unsigned)n0);
+    ci[1] = (int)(q % (unsigned)n1);
+    ci[2] = (int)(q / (unsigned)n1);
+  } else {
+    const int64_t q = cell / n0;
+    ci[0] = (int)(cell - q * n0);
+    ci[1] = (int)(q % n1);
+    ci[2] = (int)(q / n1);
+  }
+}
+
+// The PDL attribute is set unless DG_PDL=0 in the environment, and never on
+// the legacy default stream.
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed =
+      (pdl_enabled() && s != nullptr && s != cudaStreamLegacy) ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Operator-kernel variants chosen by the autotuner: 0-4 cell-centric tile
+// shapes, 5-6 face-once, 7 thread-per-cell Q1.
+constexpr int kTuneVariants = 8;
+__host__ __device__ constexpr bool variant_split(int v) { return v == 5 || v == 6; }
+__host__ __device__ constexpr bool variant_q1(int v) { return v == 7; }
+
 constexpr int kMaxN = 8;  // nodes per direction supported by the 1D tables
 
 // 1D tables of the nodal Lagrange basis on the n Gauss-Legendre points of

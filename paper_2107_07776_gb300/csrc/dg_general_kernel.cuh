@@ -80,6 +80,7 @@ template <typename T, typename A, int DIM, int N, bool ADV, bool VEL, int CPB>
 __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
     general_op_kernel(const __grid_constant__ GenArgs<T> a, const __grid_constant__ Tab1D<A> tb,
                       const T* __restrict__ src, const T* __restrict__ ub, T* __restrict__ dst) {
+  pdl_entry();
   using Ar = Arith<A>;
   using GC = GeomCount<DIM>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF, NFP = Shape<N, DIM>::NFP;
@@ -112,9 +113,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
 #pragma unroll
   for (int b = 0; b < DIM; ++b) ut[b] = zero;
   if (active) {
-    ci[0] = (int)(cell % a.n0);
-    ci[1] = (int)((cell / a.n0) % a.n1);
-    ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
+    lex_coords(cell, a.n0, a.n1, ci);
     const int64_t gvo = cell * (int64_t)NV * NB + node;
     const T* gv = a.gv + gvo;
     const df64* gv2 = a.gv2 + gvo;
@@ -348,7 +347,7 @@ dg_status launch_general_fixed(const GenArgs<T>& args, const Tab1D<A>& tb, const
     set_error("operator apply: grid too large");
     return DG_EINVAL;
   }
-  general_op_kernel<T, A, DIM, N, ADV, VEL, CPB><<<(unsigned)blocks, threads, 0, s>>>(args, tb, src, ub, dst);
+  launch(general_op_kernel<T, A, DIM, N, ADV, VEL, CPB>, (unsigned)blocks, threads, 0, s, args, tb, src, ub, dst);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;

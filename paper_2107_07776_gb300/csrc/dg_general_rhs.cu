@@ -43,9 +43,7 @@ GG make_gg(const dg_mesh* m) {
 }
 
 __device__ __forceinline__ void coords(const GG& g, int64_t cell, int ci[3]) {
-  ci[0] = (int)(cell % g.n[0]);
-  ci[1] = (int)((cell / g.n[0]) % g.n[1]);
-  ci[2] = (int)(cell / ((int64_t)g.n[0] * g.n[1]));
+  lex_coords(cell, g.n[0], g.n[1], ci);
 }
 
 __device__ __forceinline__ int64_t nbr(const GG& g, const int ci[3], int a, int s) {
@@ -91,6 +89,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
     gen_explicit_kernel(const __grid_constant__ GG g, const __grid_constant__ Tab1D<A> tb,
                         double visc_d, double adv_d, double pen_d, const double* __restrict__ w,
                         const double* __restrict__ wb, double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   using GC = GeomCount<DIM>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF, NFP = Shape<N, DIM>::NFP;
@@ -286,6 +285,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
                          double mass_d, const double* __restrict__ u_mass,
                          const double* __restrict__ f, const double* __restrict__ p,
                          double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   using GC = GeomCount<DIM>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF, NFP = Shape<N, DIM>::NFP;
@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(((CPB * Shape<NP, DIM>::NB + 31) / 32) * 32)
                             const __grid_constant__ Tab1D<A> tp, const __grid_constant__ MixTab<A> mx,
                             double alpha_d, double inv_tau_d, const double* __restrict__ uss,
                             const double* __restrict__ p_old, double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   using GC = GeomCount<DIM>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF, NFP = Shape<N, DIM>::NFP;
@@ -490,6 +491,7 @@ template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
     gen_project_kernel(const __grid_constant__ GG g, const __grid_constant__ MixTab<A> mx,
                        const double* __restrict__ p, double* __restrict__ ut) {
+  pdl_entry();
   using Ar = Arith<A>;
   using GC = GeomCount<DIM>;
   constexpr int NB = Shape<N, DIM>::NB, NBP = Shape<NP, DIM>::NB;
@@ -530,6 +532,7 @@ template <int DIM, int N, bool VEL, typename R>
 __global__ void gen_diag_kernel(const __grid_constant__ GG g, const __grid_constant__ Tab1D<R> tb,
                                 R mass, R visc, R adv, R pen, const double* __restrict__ ub,
                                 double* __restrict__ diag) {
+  pdl_entry();
   using Ar = Arith<R>;
   using GC = GeomCount<DIM>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
@@ -636,9 +639,9 @@ dg_status run_explicit(const dg_mesh* m, int mode, double visc, double adv, cons
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
   const double pen = (double)(N * N);
   if (mode == 0)
-    gen_explicit_kernel<A, DIM, N, 0, CPB><<<blocks, threads, 0, s>>>(make_gg(m), tabu<A>(m), visc, adv, pen, w, wb, rhs);
+    launch(gen_explicit_kernel<A, DIM, N, 0, CPB>, blocks, threads, 0, s, make_gg(m), tabu<A>(m), visc, adv, pen, w, wb, rhs);
   else
-    gen_explicit_kernel<A, DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(make_gg(m), tabu<A>(m), visc, adv, pen, w, wb, rhs);
+    launch(gen_explicit_kernel<A, DIM, N, 1, CPB>, blocks, threads, 0, s, make_gg(m), tabu<A>(m), visc, adv, pen, w, wb, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -650,7 +653,7 @@ dg_status run_mass_grad(const dg_mesh* m, double mass, const double* um, const d
   constexpr int CPB = rhs_cpb<N, DIM>();
   constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  gen_mass_grad_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(
+  launch(gen_mass_grad_kernel<A, DIM, N, N - 1, CPB>, blocks, threads, 0, s, 
       make_gg(m), tabu<A>(m), tabp<A>(m), tabmix<A>(m), mass, um, f, p, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
@@ -664,7 +667,7 @@ dg_status run_pressure_rhs(const dg_mesh* m, double alpha, double inv_tau, const
   constexpr int CPB = rhs_cpb<NP, DIM>();
   constexpr int threads = ((CPB * Shape<NP, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  gen_pressure_rhs_kernel<A, DIM, N, NP, CPB><<<blocks, threads, 0, s>>>(
+  launch(gen_pressure_rhs_kernel<A, DIM, N, NP, CPB>, blocks, threads, 0, s, 
       make_gg(m), tabu<A>(m), tabp<A>(m), tabmix<A>(m), alpha, inv_tau, uss, p_old, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
@@ -676,7 +679,7 @@ dg_status run_project(const dg_mesh* m, const double* p, double* ut, cudaStream_
   constexpr int CPB = rhs_cpb<N, DIM>();
   constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  gen_project_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_gg(m), tabmix<A>(m), p, ut);
+  launch(gen_project_kernel<A, DIM, N, N - 1, CPB>, blocks, threads, 0, s, make_gg(m), tabmix<A>(m), p, ut);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -689,10 +692,10 @@ dg_status run_diag(const dg_mesh* m, double mass, double visc, double adv, const
   const unsigned blocks = (unsigned)((total + 255) / 256);
   const double pen = VEL ? (double)((m->k + 1) * (m->k + 1)) : (double)(m->k * m->k);
   if (fp32)
-    gen_diag_kernel<DIM, N, VEL, float><<<blocks, 256, 0, s>>>(
+    launch(gen_diag_kernel<DIM, N, VEL, float>, blocks, 256, 0, s, 
         make_gg(m), VEL ? m->tu32 : m->tp32, (float)mass, (float)visc, (float)adv, (float)pen, ub, diag);
   else
-    gen_diag_kernel<DIM, N, VEL, double><<<blocks, 256, 0, s>>>(
+    launch(gen_diag_kernel<DIM, N, VEL, double>, blocks, 256, 0, s, 
         make_gg(m), VEL ? m->tu64 : m->tp64, mass, visc, adv, pen, ub, diag);
   count_launch();
   DG_CUDA(cudaGetLastError());

@@ -97,6 +97,7 @@ struct Rule {
 // volume terms at the nodes of a space with n points per direction
 __global__ void volume_kernel(const __grid_constant__ Lattice g, const __grid_constant__ Rule q,
                               bool with_b, int nfield, double* __restrict__ out) {
+  pdl_entry();
   const int d = g.dim, n = q.n;
   const int nb = d == 3 ? n * n * n : n * n;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,6 +132,7 @@ __global__ void volume_kernel(const __grid_constant__ Lattice g, const __grid_co
 // face terms at the face points of a space with n points per direction
 __global__ void face_kernel(const __grid_constant__ Lattice g, const __grid_constant__ Rule q,
                             bool with_n, int nfield, double* __restrict__ out) {
+  pdl_entry();
   const int d = g.dim, n = q.n;
   const int nf = d == 3 ? n * n : n;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -187,6 +189,7 @@ __global__ void face_kernel(const __grid_constant__ Lattice g, const __grid_cons
 // |Gamma_f| / |K| per cell face by the rule q
 __global__ void ratio_kernel(const __grid_constant__ Lattice g, const __grid_constant__ Rule q,
                              double* __restrict__ ratio) {
+  pdl_entry();
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   const int d = g.dim, n = q.n;
@@ -232,6 +235,7 @@ __global__ void ratio_kernel(const __grid_constant__ Lattice g, const __grid_con
 
 __global__ void penalty_kernel(const __grid_constant__ Lattice g, const double* __restrict__ ratio,
                                double* __restrict__ gpen) {
+  pdl_entry();
   const int d = g.dim;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= g.ncell * 2 * d) return;
@@ -244,12 +248,14 @@ __global__ void penalty_kernel(const __grid_constant__ Lattice g, const double* 
 }
 
 __global__ void to_pairs_kernel(int64_t n, const double* __restrict__ a, df64* __restrict__ b) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     b[k] = df_split(a[k]);
 }
 
 __global__ void to_f32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     b[k] = (float)a[k];
@@ -350,28 +356,28 @@ dg_status build_geometry(dg_mesh* m, bool velocity, cudaStream_t s) {
   }
   const int T = 128;
   if (velocity) {
-    volume_kernel<<<blocks_for(m->ncell * m->nbu, T), T, 0, s>>>(g, ru, true, nvu_f, m->gvu64);
-    face_kernel<<<blocks_for(m->ncell * 2 * d * nfu, T), T, 0, s>>>(g, ru, true, nfu_f, m->gfu64);
+    launch(volume_kernel, blocks_for(m->ncell * m->nbu, T), T, 0, s, g, ru, true, nvu_f, m->gvu64);
+    launch(face_kernel, blocks_for(m->ncell * 2 * d * nfu, T), T, 0, s, g, ru, true, nfu_f, m->gfu64);
   }
-  volume_kernel<<<blocks_for(m->ncell * m->nbp, T), T, 0, s>>>(g, rp, false, nvp_f, m->gvp64);
-  face_kernel<<<blocks_for(m->ncell * 2 * d * nfp, T), T, 0, s>>>(g, rp, false, nfp_f, m->gfp64);
-  ratio_kernel<<<blocks_for(m->ncell, T), T, 0, s>>>(g, rm, ratio);
-  penalty_kernel<<<blocks_for(n_pen, T), T, 0, s>>>(g, ratio, m->gpen64);
+  launch(volume_kernel, blocks_for(m->ncell * m->nbp, T), T, 0, s, g, rp, false, nvp_f, m->gvp64);
+  launch(face_kernel, blocks_for(m->ncell * 2 * d * nfp, T), T, 0, s, g, rp, false, nfp_f, m->gfp64);
+  launch(ratio_kernel, blocks_for(m->ncell, T), T, 0, s, g, rm, ratio);
+  launch(penalty_kernel, blocks_for(n_pen, T), T, 0, s, g, ratio, m->gpen64);
   const int conv_blocks = 1216;
   if (velocity) {
-    to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_vu, m->gvu64, m->gvu32);
-    to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_fu, m->gfu64, m->gfu32);
+    launch(to_f32_kernel, conv_blocks, 256, 0, s, n_vu, m->gvu64, m->gvu32);
+    launch(to_f32_kernel, conv_blocks, 256, 0, s, n_fu, m->gfu64, m->gfu32);
   }
-  to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_vp, m->gvp64, m->gvp32);
-  to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_fp, m->gfp64, m->gfp32);
-  to_f32_kernel<<<conv_blocks, 256, 0, s>>>(n_pen, m->gpen64, m->gpen32);
+  launch(to_f32_kernel, conv_blocks, 256, 0, s, n_vp, m->gvp64, m->gvp32);
+  launch(to_f32_kernel, conv_blocks, 256, 0, s, n_fp, m->gfp64, m->gfp32);
+  launch(to_f32_kernel, conv_blocks, 256, 0, s, n_pen, m->gpen64, m->gpen32);
   if (velocity) {
-    to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_vu, m->gvu64, m->gvu_df);
-    to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_fu, m->gfu64, m->gfu_df);
+    launch(to_pairs_kernel, conv_blocks, 256, 0, s, n_vu, m->gvu64, m->gvu_df);
+    launch(to_pairs_kernel, conv_blocks, 256, 0, s, n_fu, m->gfu64, m->gfu_df);
   }
-  to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_vp, m->gvp64, m->gvp_df);
-  to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_fp, m->gfp64, m->gfp_df);
-  to_pairs_kernel<<<conv_blocks, 256, 0, s>>>(n_pen, m->gpen64, m->gpen_df);
+  launch(to_pairs_kernel, conv_blocks, 256, 0, s, n_vp, m->gvp64, m->gvp_df);
+  launch(to_pairs_kernel, conv_blocks, 256, 0, s, n_fp, m->gfp64, m->gfp_df);
+  launch(to_pairs_kernel, conv_blocks, 256, 0, s, n_pen, m->gpen64, m->gpen_df);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(dV);

@@ -67,6 +67,7 @@ __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
 // C[M x N] = A[M x K] B[K x N] (+ bias, activation); 64 x 64 tile per CTA,
 // 4 warps of 32 x 32, K steps of 32 staged in shared memory as BF16.
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __grid_constant__ GemmDesc d) {
+  pdl_entry();
   __shared__ __align__(16) __nv_bfloat16 As[64][40];
   __shared__ __align__(16) __nv_bfloat16 Bs[64][40];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
@@ -175,16 +176,19 @@ struct InferDesc {
 };
 
 constexpr int kInferHidden = 128;
-constexpr int kInferWarps = 8;
 constexpr int kInferLdh = kInferHidden + 8;  // padded row of a hidden layer
 
-__host__ __device__ inline int64_t infer_smem_elems(int kp, int nop) {
+// shared memory of the fused inference kernel with `warps` warps: the four
+// weight matrices plus a 16-row activation tile per warp
+__host__ __device__ inline int64_t infer_smem_elems(int kp, int nop, int warps) {
   const int s1 = kp + 8, sa = (kp > kInferHidden ? kp : kInferHidden) + 8;
   return (int64_t)kInferHidden * s1 + 2LL * kInferHidden * kInferLdh + (int64_t)nop * kInferLdh +
-         (int64_t)kInferWarps * 16 * sa;
+         (int64_t)warps * 16 * sa;
 }
 
+template <int kInferWarps>
 __global__ void __launch_bounds__(kInferWarps * 32) mlp_infer_kernel(const __grid_constant__ InferDesc d) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* sm = reinterpret_cast<__nv_bfloat16*>(smem_raw);
   constexpr int H = kInferHidden, LH = kInferLdh;
@@ -226,13 +230,29 @@ __global__ void __launch_bounds__(kInferWarps * 32) mlp_infer_kernel(const __gri
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
   __nv_bfloat16* A = act + (int64_t)warp * 16 * sa;
+  const bool vecx = d.n_in % 8 == 0 && (reinterpret_cast<uintptr_t>(d.X) & 15u) == 0;
   const int64_t tile = 16 * kInferWarps;
   for (int64_t r0 = (int64_t)blockIdx.x * tile; r0 < d.M; r0 += (int64_t)gridDim.x * tile) {
     const int64_t wr0 = r0 + warp * 16;
-    for (int idx = lane; idx < 16 * d.kp; idx += 32) {
-      const int rr = idx / d.kp, k = idx % d.kp;
-      const int64_t row = wr0 + rr;
-      A[rr * sa + k] = (row < d.M && k < d.n_in) ? d.X[row * d.n_in + k] : z16;
+    if (vecx) {  // rows of 8-element multiples: 16-byte chunks, never across rows
+      const int cpr = d.n_in / 8;
+      for (int idx = lane; idx < 16 * cpr; idx += 32) {
+        const int rr = idx / cpr, k = (idx % cpr) * 8;
+        const int64_t row = wr0 + rr;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < d.M) v = *reinterpret_cast<const uint4*>(&d.X[row * d.n_in + k]);
+        *reinterpret_cast<uint4*>(&A[rr * sa + k]) = v;
+      }
+      for (int idx = lane; idx < 16 * (d.kp - d.n_in); idx += 32) {
+        const int rr = idx / (d.kp - d.n_in), k = d.n_in + idx % (d.kp - d.n_in);
+        A[rr * sa + k] = z16;
+      }
+    } else {
+      for (int idx = lane; idx < 16 * d.kp; idx += 32) {
+        const int rr = idx / d.kp, k = idx % d.kp;
+        const int64_t row = wr0 + rr;
+        A[rr * sa + k] = (row < d.M && k < d.n_in) ? d.X[row * d.n_in + k] : z16;
+      }
     }
     __syncwarp();
     for (int l = 0; l < 4; ++l) {
@@ -290,6 +310,7 @@ unsigned gridn(int64_t n) {
 // out[i] = sum_z part[z * n + i], fixed order
 __global__ void split_reduce_kernel(int64_t n, int nz, const float* __restrict__ part,
                                     float* __restrict__ out) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.0f;
@@ -302,6 +323,7 @@ __global__ void split_reduce_kernel(int64_t n, int nz, const float* __restrict__
 __global__ void __launch_bounds__(256) out_grad_kernel(int64_t n, float scale, const float* __restrict__ y,
                                                        const float* __restrict__ t, float* __restrict__ dz,
                                                        double* __restrict__ part) {
+  pdl_entry();
   __shared__ double s[256];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -322,6 +344,7 @@ __global__ void __launch_bounds__(256) out_grad_kernel(int64_t n, float scale, c
 // dz = dh * silu'(z); dzb = bf16(dz)
 __global__ void silu_back_kernel(int64_t n, const float* __restrict__ dh, const float* __restrict__ z,
                                  float* __restrict__ dz) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float zz = z[i];
@@ -331,6 +354,7 @@ __global__ void silu_back_kernel(int64_t n, const float* __restrict__ dh, const 
 }
 
 __global__ void to_bf16_kernel(int64_t n, const float* __restrict__ a, __nv_bfloat16* __restrict__ b) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = __float2bfloat16_rn(a[i]);
@@ -339,6 +363,7 @@ __global__ void to_bf16_kernel(int64_t n, const float* __restrict__ a, __nv_bflo
 // column sums of a row-major [rows x cols] matrix, one block per column
 __global__ void __launch_bounds__(256) col_sum_kernel(int64_t rows, int cols, const float* __restrict__ a,
                                                       float* __restrict__ out) {
+  pdl_entry();
   __shared__ float s[256];
   const int c = blockIdx.x;
   float acc = 0.0f;
@@ -355,6 +380,7 @@ __global__ void __launch_bounds__(256) col_sum_kernel(int64_t rows, int cols, co
 __global__ void adam_kernel(int64_t n, float* __restrict__ w, const float* __restrict__ g,
                             float* __restrict__ m1, float* __restrict__ m2, float lr, float b1,
                             float b2, float eps, float c1, float c2) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
@@ -376,6 +402,7 @@ __global__ void features_kernel(int64_t ncell, int ncomp, int nbc, const double*
                                 const double* __restrict__ h1, const double* __restrict__ h2,
                                 const double* __restrict__ h3, const double* __restrict__ b,
                                 const double* __restrict__ dsc, __nv_bfloat16* __restrict__ X) {
+  pdl_entry();
   const double is0 = dsc[0], is1 = dsc[1], is2 = dsc[2], is3 = dsc[3], isb = dsc[4];
   const int nbs = ncomp * nbc;
   const int64_t total = ncell * nbs;
@@ -402,6 +429,7 @@ __global__ void __launch_bounds__(256) hist_norms_kernel(int64_t n, const double
                                                          const double* __restrict__ h3,
                                                          const double* __restrict__ b,
                                                          double* __restrict__ part) {
+  pdl_entry();
   __shared__ double s[5][256];
   double a[5] = {0, 0, 0, 0, 0};
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -427,6 +455,7 @@ __global__ void __launch_bounds__(256) hist_norms_kernel(int64_t n, const double
 // inverse
 __global__ void __launch_bounds__(160) guess_scales_kernel(int nb, int64_t n, const double* __restrict__ part,
                                                            double* __restrict__ dsc) {
+  pdl_entry();
   __shared__ double rms[5];
   const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;  // one warp per block j
   double a = 0.0;
@@ -451,6 +480,7 @@ __global__ void __launch_bounds__(160) guess_scales_kernel(int nb, int64_t n, co
 __global__ void apply_guess_kernel(int64_t ncell, int ncomp, int nbc, const double* __restrict__ h0,
                                    const double* __restrict__ h1, const float* __restrict__ y,
                                    const double* __restrict__ dsc, double* __restrict__ x) {
+  pdl_entry();
   const double so = y ? dsc[5] : 0.0;
   const int nbs = ncomp * nbc;
   const int64_t total = ncell * nbs;
@@ -470,6 +500,7 @@ __global__ void apply_guess_kernel(int64_t ncell, int ncomp, int nbc, const doub
 __global__ void target_kernel(int64_t ncell, int ncomp, int nbc, const double* __restrict__ h0,
                               const double* __restrict__ h1, const double* __restrict__ xs,
                               const double* __restrict__ dsc, float* __restrict__ t) {
+  pdl_entry();
   const double iso = dsc[6];
   const int nbs = ncomp * nbc;
   const int64_t total = ncell * nbs;
@@ -485,6 +516,7 @@ __global__ void target_kernel(int64_t ncell, int ncomp, int nbc, const double* _
 
 __global__ void f32_to_bf16_rows_kernel(int64_t n, const float* __restrict__ a,
                                         __nv_bfloat16* __restrict__ b) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = __float2bfloat16_rn(a[i]);
@@ -500,7 +532,7 @@ dg_status gemm(const GemmDesc& d0, int64_t ksplit, cudaStream_t s) {
     set_error("learned guess: GEMM grid too large");
     return DG_EINVAL;
   }
-  gemm_bf16_kernel<<<grid, 128, 0, s>>>(d); count_launch();
+  launch(gemm_bf16_kernel, grid, 128, 0, s, d); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -559,12 +591,13 @@ dg_status Mlp::init(int ni, int h, int no, uint64_t seed, cudaStream_t s) {
   DG_CUDA(cudaMalloc(&loss_part, sizeof(double) * 1216));
   dg_status stt = sync_bf16(s);
   if (stt != DG_OK) return stt;
-  DG_CUDA(cudaStreamSynchronize(s));  // hw dies here
+  // hw is a host buffer that goes out of scope on return: the copy must finish
+  DG_CUDA(cudaStreamSynchronize(s));
   return DG_OK;
 }
 
 dg_status Mlp::sync_bf16(cudaStream_t s) {
-  f32_to_bf16_rows_kernel<<<gridn(nparam), 256, 0, s>>>(nparam, w, wb); count_launch();
+  launch(f32_to_bf16_rows_kernel, gridn(nparam), 256, 0, s, nparam, w, wb); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -595,18 +628,22 @@ dg_status Mlp::reserve(int64_t rows, cudaStream_t s) {
 // (hidden width 128), else the layer-by-layer GEMMs.
 dg_status Mlp::infer(int64_t M, float* y, cudaStream_t s) {
   const int kp = (n_in + 15) / 16 * 16, nop = (n_out + 7) / 8 * 8;
-  const int64_t bytes = 2 * infer_smem_elems(kp, nop);
-  int dev = 0, max_optin = 0;
+  int dev = 0, max_optin = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // 16 warps per CTA (one CTA per SM covers 16 x 16 rows per SM and pass)
+  // when their activation tiles fit next to the weights, else 8
+  const int64_t bytes16 = 2 * infer_smem_elems(kp, nop, 16), bytes8 = 2 * infer_smem_elems(kp, nop, 8);
+  const int warps = bytes16 <= max_optin ? 16 : 8;
+  const int64_t bytes = warps == 16 ? bytes16 : bytes8;
   if (hidden != kInferHidden || nop > kInferHidden || bytes > max_optin) return forward(M, y, s);
   if (M <= 0) return DG_OK;
-  DG_CUDA(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  void (*kern)(InferDesc) = warps == 16 ? mlp_infer_kernel<16> : mlp_infer_kernel<8>;
+  DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   int per_sm = 0;
-  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_kernel, kInferWarps * 32, bytes));
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = (M + 16 * kInferWarps - 1) / (16 * kInferWarps);
+  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, bytes));
+  const int64_t tiles = (M + 16 * warps - 1) / (16 * warps);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * std::max(1, per_sm)));
   InferDesc d;
   d.M = M;
@@ -622,7 +659,7 @@ dg_status Mlp::infer(int64_t M, float* y, cudaStream_t s) {
     d.boff[l] = boff[l];
   }
   d.y = y;
-  mlp_infer_kernel<<<(unsigned)grid, kInferWarps * 32, bytes, s>>>(d);
+  launch(kern, (unsigned)grid, warps * 32, bytes, s, d);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -666,11 +703,11 @@ dg_status Mlp::forward(int64_t M, float* y, cudaStream_t s) {
 dg_status Mlp::backward(int64_t M, const float* y, const float* t, double* loss, cudaStream_t s) {
   const int64_t nout = M * n_out;
   const int nb = (int)std::min<int64_t>(1216, std::max<int64_t>(1, (nout + 1023) / 1024));
-  out_grad_kernel<<<nb, 256, 0, s>>>(nout, (float)(2.0 / (double)nout), y, t, dz, loss_part); count_launch();
+  launch(out_grad_kernel, nb, 256, 0, s, nout, (float)(2.0 / (double)nout), y, t, dz, loss_part); count_launch();
   DG_CUDA(cudaGetLastError());
   for (int l = 3; l >= 0; --l) {
     const int64_t no = dims[l + 1], ni = dims[l];
-    to_bf16_kernel<<<gridn(M * no), 256, 0, s>>>(M * no, dz, dzb); count_launch();
+    launch(to_bf16_kernel, gridn(M * no), 256, 0, s, M * no, dz, dzb); count_launch();
     // dW_l[out][in] = sum_m dz[m][out] h_{l-1}[m][in], rows split for parallelism
     int64_t ksplit = std::min<int64_t>(64, std::max<int64_t>(1, M / 2048));
     while (ksplit > 1 && ksplit * no * ni > part_cap) --ksplit;
@@ -696,9 +733,9 @@ dg_status Mlp::backward(int64_t M, const float* y, const float* t, double* loss,
     dg_status st = gemm(d, ksplit, s);
     if (st != DG_OK) return st;
     if (nz > 1) {
-      split_reduce_kernel<<<gridn(no * ni), 256, 0, s>>>(no * ni, (int)nz, part, g + woff[l]); count_launch();
+      launch(split_reduce_kernel, gridn(no * ni), 256, 0, s, no * ni, (int)nz, part, g + woff[l]); count_launch();
     }
-    col_sum_kernel<<<(unsigned)no, 256, 0, s>>>(M, (int)no, dz, g + boff[l]); count_launch();
+    launch(col_sum_kernel, (unsigned)no, 256, 0, s, M, (int)no, dz, g + boff[l]); count_launch();
     DG_CUDA(cudaGetLastError());
     if (l == 0) break;
     // dh[m][in] = sum_out dz[m][out] W_l[out][in]
@@ -720,7 +757,7 @@ dg_status Mlp::backward(int64_t M, const float* y, const float* t, double* loss,
     e.scn = 1;
     st = gemm(e, 1, s);
     if (st != DG_OK) return st;
-    silu_back_kernel<<<gridn(M * ni), 256, 0, s>>>(M * ni, dh, z[l - 1], dz); count_launch();
+    launch(silu_back_kernel, gridn(M * ni), 256, 0, s, M * ni, dh, z[l - 1], dz); count_launch();
     DG_CUDA(cudaGetLastError());
   }
   if (loss) {
@@ -738,7 +775,7 @@ dg_status Mlp::adam_step(float lr, cudaStream_t s) {
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = (float)(1.0 / (1.0 - std::pow((double)b1, (double)adam_t)));
   const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, (double)adam_t)));
-  adam_kernel<<<gridn(nparam), 256, 0, s>>>(nparam, w, g, m1, m2, lr, b1, b2, 1e-8f, c1, c2); count_launch();
+  launch(adam_kernel, gridn(nparam), 256, 0, s, nparam, w, g, m1, m2, lr, b1, b2, 1e-8f, c1, c2); count_launch();
   DG_CUDA(cudaGetLastError());
   return sync_bf16(s);
 }
@@ -769,7 +806,7 @@ dg_status mlp_forward_backward(int64_t M, int n_in, int hidden, int n_out, const
   if (st != DG_OK) return st;
   st = net.reserve(M, s);
   if (st != DG_OK) return st;
-  f32_to_bf16_rows_kernel<<<gridn(M * n_in), 256, 0, s>>>(M * n_in, X, net.xb); count_launch();
+  launch(f32_to_bf16_rows_kernel, gridn(M * n_in), 256, 0, s, M * n_in, X, net.xb); count_launch();
   DG_CUDA(cudaGetLastError());
   st = net.forward(M, Y, s);
   if (st != DG_OK) return st;
@@ -794,7 +831,7 @@ dg_status mlp_infer(int64_t M, int n_in, int hidden, int n_out, const float* wei
   if (st != DG_OK) return st;
   st = net.reserve(M, s);
   if (st != DG_OK) return st;
-  f32_to_bf16_rows_kernel<<<gridn(M * n_in), 256, 0, s>>>(M * n_in, X, net.xb); count_launch();
+  launch(f32_to_bf16_rows_kernel, gridn(M * n_in), 256, 0, s, M * n_in, X, net.xb); count_launch();
   DG_CUDA(cudaGetLastError());
   st = net.infer(M, Y, s);
   if (st != DG_OK) return st;
@@ -809,9 +846,9 @@ dg_status guess_features(Mlp& net, int64_t ncell, int ncomp, int nbc, double* co
   if (st != DG_OK) return st;
   const int64_t n = ncell * ncomp * nbc;
   const int nb = (int)std::min<int64_t>(1216, std::max<int64_t>(1, (n + 1023) / 1024));
-  hist_norms_kernel<<<nb, 256, 0, s>>>(n, h[0], h[1], h[2], h[3], b, part); count_launch();
-  guess_scales_kernel<<<1, 160, 0, s>>>(nb, n, part, dsc); count_launch();
-  features_kernel<<<gridn(n), 256, 0, s>>>(ncell, ncomp, nbc, h[0], h[1], h[2], h[3], b, dsc,
+  launch(hist_norms_kernel, nb, 256, 0, s, n, h[0], h[1], h[2], h[3], b, part); count_launch();
+  launch(guess_scales_kernel, 1, 160, 0, s, nb, n, part, dsc); count_launch();
+  launch(features_kernel, gridn(n), 256, 0, s, ncell, ncomp, nbc, h[0], h[1], h[2], h[3], b, dsc,
                                            net.xb); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -819,14 +856,14 @@ dg_status guess_features(Mlp& net, int64_t ncell, int ncomp, int nbc, double* co
 
 dg_status guess_apply(int64_t ncell, int ncomp, int nbc, const double* h0, const double* h1,
                       const float* y, const double* dsc, double* x, cudaStream_t s) {
-  apply_guess_kernel<<<gridn(ncell * ncomp * nbc), 256, 0, s>>>(ncell, ncomp, nbc, h0, h1, y, dsc, x); count_launch();
+  launch(apply_guess_kernel, gridn(ncell * ncomp * nbc), 256, 0, s, ncell, ncomp, nbc, h0, h1, y, dsc, x); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 dg_status guess_target(int64_t ncell, int ncomp, int nbc, const double* h0, const double* h1,
                        const double* xs, const double* dsc, float* t, cudaStream_t s) {
-  target_kernel<<<gridn(ncell * ncomp * nbc), 256, 0, s>>>(ncell, ncomp, nbc, h0, h1, xs, dsc, t); count_launch();
+  launch(target_kernel, gridn(ncell * ncomp * nbc), 256, 0, s, ncell, ncomp, nbc, h0, h1, xs, dsc, t); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }

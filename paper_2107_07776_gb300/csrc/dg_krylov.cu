@@ -24,10 +24,18 @@ int red_blocks(int64_t n) {
   return (int)b;
 }
 
-// partial[blk * nv + i] = sum over this block's range of w * V_i
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[blk * nv + i] = sum over this block's range of w * V_i (fixed
+// per-thread order, fixed block tree)
 __global__ void __launch_bounds__(kRedThreads)
     multi_dot_kernel(int64_t n, int nv, const double* __restrict__ w, const double* __restrict__ V,
                      int64_t ldv, double* __restrict__ partial) {
+  pdl_entry();
   __shared__ double s[kRedThreads];
   for (int i = 0; i < nv; ++i) {
     const double* v = V + (int64_t)i * ldv;
@@ -49,22 +57,27 @@ __global__ void __launch_bounds__(kRedThreads)
 // out[i] = sum_blk partial[blk * nv + i], fixed order (one block per i)
 __global__ void __launch_bounds__(kRedThreads)
     reduce_kernel(int nblk, int nv, const double* __restrict__ partial, double* __restrict__ out) {
-  __shared__ double s[kRedThreads];
-  const int i = blockIdx.x;
+  pdl_entry();
+  constexpr int kWarps = kRedThreads / 32;
+  __shared__ double s[kWarps];
+  const int i = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[(int64_t)b * nv + i];
-  s[threadIdx.x] = acc;
+  acc = warp_sum(acc);
+  if (lane == 0) s[warp] = acc;
   __syncthreads();
-  for (int st = kRedThreads / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) t += s[q];
+    out[i] = t;
   }
-  if (threadIdx.x == 0) out[i] = s[0];
 }
 
 // w -= sum_i h[i] V_i  (h on the device)
 __global__ void multi_axpy_kernel(int64_t n, int nv, const double* __restrict__ h,
                                   const double* __restrict__ V, int64_t ldv, double* __restrict__ w) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     double acc = w[k];
@@ -77,6 +90,7 @@ __global__ void multi_axpy_kernel(int64_t n, int nv, const double* __restrict__ 
 __global__ void gmres_update_kernel(int64_t n, int nv, const double* __restrict__ y,
                                     const double* __restrict__ V, int64_t ldv,
                                     const double* __restrict__ dinv, double* __restrict__ x) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
@@ -87,6 +101,7 @@ __global__ void gmres_update_kernel(int64_t n, int nv, const double* __restrict_
 
 __global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b,
                              const double* __restrict__ y, double* __restrict__ z) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     z[k] = a * x[k] + (b == 0.0 ? 0.0 : b * y[k]);
@@ -94,6 +109,7 @@ __global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, 
 
 __global__ void mul_kernel(int64_t n, const double* __restrict__ d, const double* __restrict__ x,
                            double* __restrict__ z) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     z[k] = d[k] * x[k];
@@ -101,6 +117,7 @@ __global__ void mul_kernel(int64_t n, const double* __restrict__ d, const double
 
 __global__ void inv_kernel(int64_t n, const double* __restrict__ d, int64_t period,
                            double* __restrict__ out) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     out[k] = 1.0 / d[k % period];
@@ -110,6 +127,7 @@ __global__ void inv_kernel(int64_t n, const double* __restrict__ d, int64_t peri
 __global__ void cg_update_kernel(int64_t n, double a, const double* __restrict__ p,
                                  const double* __restrict__ q, double* __restrict__ x,
                                  double* __restrict__ r, double* __restrict__ r_old) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     x[k] += a * p[k];
@@ -124,6 +142,7 @@ __global__ void cg_update_dev_kernel(int64_t n, const double* __restrict__ sc, i
                                      const double* __restrict__ p, const double* __restrict__ q,
                                      double* __restrict__ x, double* __restrict__ r,
                                      double* __restrict__ r_old) {
+  pdl_entry();
   const double a = sc[irz] / sc[ipq];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -139,6 +158,7 @@ __global__ void cg_update_dev_kernel(int64_t n, const double* __restrict__ sc, i
 // sc[irz] = rz_old
 __global__ void cg_direction_kernel(int64_t n, const double* __restrict__ sc, int izr, int irz,
                                     const double* __restrict__ z, double* __restrict__ p) {
+  pdl_entry();
   const double beta = (sc[izr] - sc[izr + 1]) / sc[irz];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
@@ -158,8 +178,8 @@ unsigned grid_for(int64_t n) {
 dg_status VecOps::dots(int64_t n, int nv, const double* w, const double* V, int64_t ldv,
                        double* out_dev) {
   const int nb = red_blocks(n);
-  multi_dot_kernel<<<nb, kRedThreads, 0, stream>>>(n, nv, w, V, ldv, partial); count_launch();
-  reduce_kernel<<<nv, kRedThreads, 0, stream>>>(nb, nv, partial, out_dev); count_launch();
+  launch(multi_dot_kernel, nb, kRedThreads, 0, stream, n, nv, w, V, ldv, partial); count_launch();
+  launch(reduce_kernel, nv, kRedThreads, 0, stream, nb, nv, partial, out_dev); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -176,19 +196,19 @@ dg_status VecOps::dots_host(int64_t n, int nv, const double* w, const double* V,
 
 dg_status VecOps::axpby(int64_t n, double a, const double* x, double b, const double* y,
                         double* z) {
-  axpby_kernel<<<grid_for(n), 256, 0, stream>>>(n, a, x, b, y, z); count_launch();
+  launch(axpby_kernel, grid_for(n), 256, 0, stream, n, a, x, b, y, z); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 dg_status VecOps::mul(int64_t n, const double* d, const double* x, double* z) {
-  mul_kernel<<<grid_for(n), 256, 0, stream>>>(n, d, x, z); count_launch();
+  launch(mul_kernel, grid_for(n), 256, 0, stream, n, d, x, z); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 dg_status VecOps::invert(int64_t n, const double* d, int64_t period, double* out) {
-  inv_kernel<<<grid_for(n), 256, 0, stream>>>(n, d, period, out); count_launch();
+  launch(inv_kernel, grid_for(n), 256, 0, stream, n, d, period, out); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -274,7 +294,7 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
         double* hc = pass == 0 ? h1 : h2;
         st = vo.dots(n, j + 1, w, V, n, hc);
         if (st != DG_OK) return st;
-        multi_axpy_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j + 1, hc, V, n, w); count_launch();
+        launch(multi_axpy_kernel, grid_for(n), 256, 0, vo.stream, n, j + 1, hc, V, n, w); count_launch();
         DG_CUDA(cudaGetLastError());
       }
       st = vo.dots(n, 1, w, w, n, hw);
@@ -303,10 +323,6 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
       g[j] = cs[j] * g[j];
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
       const double hnext = std::sqrt(hn2);
-      if (hnext > 0.0) {
-        st = vo.axpby(n, 1.0 / hnext, w, 0.0, nullptr, vj1);
-        if (st != DG_OK) return st;
-      }
       info->iterations = it + 1;
       info->res_final = std::fabs(g[j + 1]);
       if (std::fabs(g[j + 1]) <= tol * bnorm || hnext == 0.0) {
@@ -315,6 +331,10 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
         done = true;
         break;
       }
+      // v_{j+1} = w / |w| only when the cycle goes on (a converged cycle
+      // never reads it)
+      st = vo.axpby(n, 1.0 / hnext, w, 0.0, nullptr, vj1);
+      if (st != DG_OK) return st;
       if (timeout_s > 0 &&
           std::chrono::duration<double>(clock::now() - t0).count() > timeout_s) {
         ++j;
@@ -331,7 +351,7 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
       hy[i] = s / H[(size_t)i * m + i];
     }
     DG_CUDA(cudaMemcpyAsync(h1, hy, sizeof(double) * j, cudaMemcpyHostToDevice, vo.stream));
-    gmres_update_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, j, h1, V, n, dinv, x); count_launch();
+    launch(gmres_update_kernel, grid_for(n), 256, 0, vo.stream, n, j, h1, V, n, dinv, x); count_launch();
     DG_CUDA(cudaGetLastError());
     if (timeout_s > 0 && std::chrono::duration<double>(clock::now() - t0).count() > timeout_s)
       return DG_ETIMEOUT;
@@ -392,7 +412,7 @@ dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const 
     if (st != DG_OK) return st;
     st = vo.dots(n, 1, p, q, n, sc + 2);
     if (st != DG_OK) return st;
-    cg_update_dev_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, sc, irz, 2, p, q, x, r, r_old);
+    launch(cg_update_dev_kernel, grid_for(n), 256, 0, vo.stream, n, sc, irz, 2, p, q, x, r, r_old);
     count_launch();
     DG_CUDA(cudaGetLastError());
     st = vo.dots(n, 1, r, r, n, sc + 1);
@@ -420,7 +440,7 @@ dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const 
     // caller's workspace), then the direction on the device
     st = vo.dots(n, 2, z, r, r_old - r, sc + 3);
     if (st != DG_OK) return st;
-    cg_direction_kernel<<<grid_for(n), 256, 0, vo.stream>>>(n, sc, 3, irz, z, p);
+    launch(cg_direction_kernel, grid_for(n), 256, 0, vo.stream, n, sc, 3, irz, z, p);
     count_launch();
     DG_CUDA(cudaGetLastError());
     // the new <z, r> becomes the next iteration's rz (alternate slot)

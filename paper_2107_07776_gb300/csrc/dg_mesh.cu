@@ -22,6 +22,14 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_kernel_launches{0};
 
 void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("DG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 void count_launches(int64_t n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_kernel_launches.load(std::memory_order_relaxed); }
 

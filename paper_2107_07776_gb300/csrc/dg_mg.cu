@@ -52,18 +52,21 @@ void lagrange_at(const double* xs, int n, double x, double* out) {
 
 template <typename T>
 __global__ void cvt_kernel(int64_t n, const double* __restrict__ a, T* __restrict__ b) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     b[k] = (T)a[k];
 }
 template <typename T>
 __global__ void cvt_back_kernel(int64_t n, const T* __restrict__ a, double* __restrict__ b) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     b[k] = (double)a[k];
 }
 template <typename T>
 __global__ void inv_diag_kernel(int64_t n, const double* __restrict__ d, T* __restrict__ dinv) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     dinv[k] = (T)(1.0 / d[k]);
@@ -73,6 +76,7 @@ template <typename T>
 __global__ void cheb_init_kernel(int64_t n, const T* __restrict__ b, const T* __restrict__ t,
                                  const T* __restrict__ dinv, T inv_theta, T* __restrict__ r,
                                  T* __restrict__ d) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const T rk = dinv[k] * (t ? b[k] - t[k] : b[k]);
@@ -84,6 +88,7 @@ __global__ void cheb_init_kernel(int64_t n, const T* __restrict__ b, const T* __
 template <typename T>
 __global__ void cheb_step_kernel(int64_t n, T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
                                  const T* __restrict__ t, const T* __restrict__ dinv, T c1, T c2) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const T dk = d[k];
@@ -95,6 +100,7 @@ __global__ void cheb_step_kernel(int64_t n, T* __restrict__ x, T* __restrict__ d
 }
 template <typename T>
 __global__ void add_kernel(int64_t n, const T* __restrict__ d, T* __restrict__ x) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     x[k] += d[k];
@@ -102,6 +108,7 @@ __global__ void add_kernel(int64_t n, const T* __restrict__ d, T* __restrict__ x
 template <typename T>
 __global__ void sub_kernel(int64_t n, const T* __restrict__ b, const T* __restrict__ t,
                            T* __restrict__ r) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     r[k] = b[k] - t[k];
@@ -109,6 +116,7 @@ __global__ void sub_kernel(int64_t n, const T* __restrict__ b, const T* __restri
 // I = identity (n x n)
 template <typename T>
 __global__ void identity_kernel(int64_t n, T* __restrict__ I) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n * n;
        k += (int64_t)gridDim.x * blockDim.x)
     I[k] = (k / n == k % n) ? T(1) : T(0);
@@ -118,6 +126,7 @@ __global__ void identity_kernel(int64_t n, T* __restrict__ I) {
 template <typename T>
 __global__ void __launch_bounds__(256) dense_matvec_kernel(int n, const T* __restrict__ Ainv,
                                                            const T* __restrict__ b, T* __restrict__ x) {
+  pdl_entry();
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= n) return;
   const T* a = Ainv + (int64_t)row * n;
@@ -130,6 +139,7 @@ __global__ void __launch_bounds__(256) dense_matvec_kernel(int n, const T* __res
 // deterministic pseudo-random start vector in [-1, 1] (splitmix64 hash)
 template <typename T>
 __global__ void hash_fill_kernel(int64_t n, T* __restrict__ x) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     uint64_t z = (uint64_t)k + 0x9E3779B97F4A7C15ull;
@@ -143,6 +153,7 @@ __global__ void hash_fill_kernel(int64_t n, T* __restrict__ x) {
 template <typename T>
 __global__ void __launch_bounds__(256) dot_kernel(int64_t n, const T* __restrict__ a,
                                                   const T* __restrict__ b, double* __restrict__ part) {
+  pdl_entry();
   __shared__ double s[256];
   double acc = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -160,6 +171,7 @@ __global__ void __launch_bounds__(256) dot_kernel(int64_t n, const T* __restrict
 template <typename T>
 __global__ void prolong_add_kernel(const __grid_constant__ Transfer tr, int64_t nfine_dofs,
                                    const T* __restrict__ xc, T* __restrict__ xf) {
+  pdl_entry();
   const int nbf = tr.dim == 3 ? tr.nf * tr.nf * tr.nf : tr.nf * tr.nf;
   const int nbc = tr.dim == 3 ? tr.nc * tr.nc * tr.nc : tr.nc * tr.nc;
   // grid-stride: the launch grid is capped (grid1), levels can be larger
@@ -193,6 +205,7 @@ __global__ void prolong_add_kernel(const __grid_constant__ Transfer tr, int64_t 
 template <typename T>
 __global__ void restrict_part_kernel(const __grid_constant__ Transfer tr, int64_t ncc, int nchild,
                                      const T* __restrict__ rf, T* __restrict__ part) {
+  pdl_entry();
   const int nbf = tr.dim == 3 ? tr.nf * tr.nf * tr.nf : tr.nf * tr.nf;
   const int nbc = tr.dim == 3 ? tr.nc * tr.nc * tr.nc : tr.nc * tr.nc;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,6 +238,7 @@ __global__ void restrict_part_kernel(const __grid_constant__ Transfer tr, int64_
 template <typename T>
 __global__ void restrict_sum_kernel(int64_t ncoarse_dofs, int nbc, int nchild,
                                     const T* __restrict__ part, T* __restrict__ bc) {
+  pdl_entry();
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= ncoarse_dofs) return;
   const int64_t cc = gid / nbc;
@@ -369,7 +383,7 @@ template <typename T>
 dg_status MultiGrid<T>::dot(int64_t n, const T* a, const T* b, double* out) {
   int64_t nb = (n + 1023) / 1024;
   nb = std::max<int64_t>(1, std::min<int64_t>(nb, 1216));
-  dot_kernel<T><<<(unsigned)nb, 256, 0, stream>>>(n, a, b, part); count_launch();
+  launch(dot_kernel<T>, (unsigned)nb, 256, 0, stream, n, a, b, part); count_launch();
   DG_CUDA(cudaGetLastError());
   DG_CUDA(cudaMemcpyAsync(host_part, part, sizeof(double) * nb, cudaMemcpyDeviceToHost, stream));
   DG_CUDA(cudaStreamSynchronize(stream));
@@ -391,8 +405,8 @@ dg_status MultiGrid<T>::estimate(int l, int slot, int steps, double* lo, double*
   T *r = L.r, *z = L.x, *p = L.d, *q = L.t;
   double rz;
   dg_status st;
-  hash_fill_kernel<T><<<grid1(n), 256, 0, stream>>>(n, r); count_launch();  // r = b
-  cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, r, nullptr, dinv, (T)1, z, p); count_launch();  // z = p = D^-1 r
+  launch(hash_fill_kernel<T>, grid1(n), 256, 0, stream, n, r); count_launch();  // r = b
+  launch(cheb_init_kernel<T>, grid1(n), 256, 0, stream, n, r, nullptr, dinv, (T)1, z, p); count_launch();  // z = p = D^-1 r
   st = dot(n, r, z, &rz);
   if (st != DG_OK) return st;
   double a_prev = 0.0, b_prev = 0.0;
@@ -433,6 +447,7 @@ template <typename T>
 __global__ void lanczos_update_kernel(int64_t n, T a, const T* __restrict__ q,
                                       const T* __restrict__ dinv, T* __restrict__ r,
                                       T* __restrict__ z) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const T rk = r[k] - a * q[k];
@@ -442,6 +457,7 @@ __global__ void lanczos_update_kernel(int64_t n, T a, const T* __restrict__ q,
 }
 template <typename T>
 __global__ void lanczos_dir_kernel(int64_t n, T b, const T* __restrict__ z, T* __restrict__ p) {
+  pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
     p[k] = z[k] + b * p[k];
@@ -449,11 +465,11 @@ __global__ void lanczos_dir_kernel(int64_t n, T b, const T* __restrict__ z, T* _
 
 template <typename T>
 void MultiGrid<T>::lanczos_update(int64_t n, T a, const T* q, const T* dinv, T* r, T* z) {
-  lanczos_update_kernel<T><<<grid1(n), 256, 0, stream>>>(n, a, q, dinv, r, z); count_launch();
+  launch(lanczos_update_kernel<T>, grid1(n), 256, 0, stream, n, a, q, dinv, r, z); count_launch();
 }
 template <typename T>
 void MultiGrid<T>::lanczos_dir(int64_t n, T b, const T* z, T* p) {
-  lanczos_dir_kernel<T><<<grid1(n), 256, 0, stream>>>(n, b, z, p); count_launch();
+  launch(lanczos_dir_kernel<T>, grid1(n), 256, 0, stream, n, b, z, p); count_launch();
 }
 
 template <typename T>
@@ -476,7 +492,7 @@ dg_status MultiGrid<T>::set_alpha(double a) {
     MGLevel<T>& L = lv[l];
     dg_status st = poisson_diagonal(L.mesh, a, diag, stream);
     if (st != DG_OK) return st;
-    inv_diag_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, diag, L.dinv[slot]); count_launch();
+    launch(inv_diag_kernel<T>, grid1(L.n), 256, 0, stream, L.n, diag, L.dinv[slot]); count_launch();
     DG_CUDA(cudaGetLastError());
     const bool coarsest = l + 1 == lv.size();
     double lo, hi;
@@ -537,12 +553,12 @@ dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
   double rho = 1.0 / sigma;
   dg_status st;
   if (x_zero) {
-    cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.b, nullptr, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
+    launch(cheb_init_kernel<T>, grid1(n), 256, 0, stream, n, L.b, nullptr, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
     DG_CUDA(cudaMemsetAsync(L.x, 0, sizeof(T) * n, stream));
   } else {
     st = level_apply<T>(L, alpha, L.x, L.t, stream);
     if (st != DG_OK) return st;
-    cheb_init_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.b, L.t, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
+    launch(cheb_init_kernel<T>, grid1(n), 256, 0, stream, n, L.b, L.t, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
   }
   int swaps = 0;
   for (int k = 0; k + 1 < degree; ++k) {
@@ -556,7 +572,7 @@ dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
     ++swaps;
     rho = rho_new;
   }
-  add_kernel<T><<<grid1(n), 256, 0, stream>>>(n, L.d, L.x); count_launch();
+  launch(add_kernel<T>, grid1(n), 256, 0, stream, n, L.d, L.x); count_launch();
   DG_CUDA(cudaGetLastError());
   if (swaps & 1) {  // the direction is consumed: give every call the same buffers
     T* tmp = L.d;
@@ -576,7 +592,7 @@ dg_status MultiGrid<T>::coarse_inverse(int slot) {
   T *I = nullptr, *Acol = nullptr;
   DG_CUDA(cudaMalloc(&I, sizeof(T) * n * n));
   DG_CUDA(cudaMalloc(&Acol, sizeof(T) * n * n));
-  identity_kernel<T><<<grid1(n * n), 256, 0, stream>>>(n, I); count_launch();
+  launch(identity_kernel<T>, grid1(n * n), 256, 0, stream, n, I); count_launch();
   dg_status st = DG_OK;
   for (int64_t j = 0; j < n && st == DG_OK; ++j)
     st = level_apply<T>(L, alpha, I + j * n, Acol + j * n, stream);
@@ -636,7 +652,8 @@ dg_status MultiGrid<T>::coarse_inverse(int slot) {
     }
   }
   cudaError_t e = cudaMemcpyAsync(L.ainv[slot], ht.data(), sizeof(T) * n * n, cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // ht dies here
+  // ht is a host buffer that goes out of scope on return: the copy must finish
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   cudaFree(Acol);
   if (e != cudaSuccess) return cuda_fail(e, "coarse inverse");
   return DG_OK;
@@ -648,7 +665,7 @@ dg_status MultiGrid<T>::vcycle(int l) {
   if (l + 1 == (int)lv.size()) {
     MGLevel<T>& Lc = lv[l];
     if (Lc.ainv[cur]) {
-      dense_matvec_kernel<T><<<(unsigned)((Lc.n + 7) / 8), 256, 0, stream>>>((int)Lc.n, Lc.ainv[cur],
+      launch(dense_matvec_kernel<T>, (unsigned)((Lc.n + 7) / 8), 256, 0, stream, (int)Lc.n, Lc.ainv[cur],
                                                                               Lc.b, Lc.x);
       count_launch();
       DG_CUDA(cudaGetLastError());
@@ -662,7 +679,7 @@ dg_status MultiGrid<T>::vcycle(int l) {
   if (st != DG_OK) return st;
   st = level_apply<T>(L, alpha, L.x, L.t, stream);
   if (st != DG_OK) return st;
-  sub_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, L.b, L.t, L.r); count_launch();
+  launch(sub_kernel<T>, grid1(L.n), 256, 0, stream, L.n, L.b, L.t, L.r); count_launch();
   {
     const Transfer& t = tr[l];
     int nchild = 1;
@@ -672,15 +689,15 @@ dg_status MultiGrid<T>::vcycle(int l) {
     const int64_t ncc = C.n / nbc, nterm = C.n * nchild;
     // the fine level's spare direction buffer holds the partial sums
     // (nchild * coarse DoFs = fine cells * coarse nodes <= fine DoFs)
-    restrict_part_kernel<T><<<(unsigned)((nterm + 255) / 256), 256, 0, stream>>>(t, ncc, nchild, L.r, L.d2);
+    launch(restrict_part_kernel<T>, (unsigned)((nterm + 255) / 256), 256, 0, stream, t, ncc, nchild, L.r, L.d2);
     count_launch();
-    restrict_sum_kernel<T><<<(unsigned)((C.n + 255) / 256), 256, 0, stream>>>(C.n, nbc, nchild, L.d2, C.b);
+    launch(restrict_sum_kernel<T>, (unsigned)((C.n + 255) / 256), 256, 0, stream, C.n, nbc, nchild, L.d2, C.b);
     count_launch();
   }
   DG_CUDA(cudaGetLastError());
   st = vcycle(l + 1);
   if (st != DG_OK) return st;
-  prolong_add_kernel<T><<<grid1(L.n), 256, 0, stream>>>(tr[l], L.n, C.x, L.x); count_launch();
+  launch(prolong_add_kernel<T>, grid1(L.n), 256, 0, stream, tr[l], L.n, C.x, L.x); count_launch();
   DG_CUDA(cudaGetLastError());
   return chebyshev(l, smooth_degree, false);
 }
@@ -688,10 +705,10 @@ dg_status MultiGrid<T>::vcycle(int l) {
 template <typename T>
 dg_status MultiGrid<T>::apply_direct(const double* r, double* z) {
   MGLevel<T>& L = lv[0];
-  cvt_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, r, L.b); count_launch();
+  launch(cvt_kernel<T>, grid1(L.n), 256, 0, stream, L.n, r, L.b); count_launch();
   dg_status st = vcycle(0);
   if (st != DG_OK) return st;
-  cvt_back_kernel<T><<<grid1(L.n), 256, 0, stream>>>(L.n, L.x, z); count_launch();
+  launch(cvt_back_kernel<T>, grid1(L.n), 256, 0, stream, L.n, L.x, z); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }

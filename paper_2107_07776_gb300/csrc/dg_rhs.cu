@@ -78,9 +78,7 @@ __device__ __forceinline__ int neighbour_coord(const Grid& g, const int ci[3], i
 }
 
 __device__ __forceinline__ void cell_coords(const Grid& g, int64_t cell, int ci[3]) {
-  ci[0] = (int)(cell % g.n[0]);
-  ci[1] = (int)((cell / g.n[0]) % g.n[1]);
-  ci[2] = (int)(cell / ((int64_t)g.n[0] * g.n[1]));
+  lex_coords(cell, g.n[0], g.n[1], ci);
 }
 
 // All kernels below keep FP64 storage and compute in the arithmetic type A:
@@ -96,6 +94,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     explicit_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
                     double visc_d, double adv_d, double pen_d, const double* __restrict__ w,
                     const double* __restrict__ wb, double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
   __shared__ A s_u[CPB][NB];
@@ -239,6 +238,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
                                   expl_minb<N, DIM>(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32))
     explicit_terms_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
                           const __grid_constant__ ExplTerms et, double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
   __shared__ A s_u[NT][CPB][NB];
@@ -421,6 +421,7 @@ template <typename A, int DIM, int N, int NT>
 __global__ void __launch_bounds__(256)
     explicit_face_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
                          const __grid_constant__ ExplTerms et, A* __restrict__ flux) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF;
   const int64_t f0 = faces_of_axis(0, g.n, g.per), f1 = faces_of_axis(1, g.n, g.per);
@@ -434,7 +435,8 @@ __global__ void __launch_bounds__(256)
   const int64_t fl = fg - (ax == 0 ? 0 : (ax == 1 ? f0 : f0 + f1));
   const int d0 = ax == 0 ? face_layers(g.n[0], g.per[0]) : g.n[0];
   const int d1 = ax == 1 ? face_layers(g.n[1], g.per[1]) : g.n[1];
-  const int fc[3] = {(int)(fl % d0), (int)((fl / d0) % d1), DIM == 3 ? (int)(fl / ((int64_t)d0 * d1)) : 0};
+  int fc[3];
+  lex_coords(fl, d0, d1, fc);
   const int layer = sel3(ax, fc[0], fc[1], fc[2]);
   const int nax = sel3(ax, g.n[0], g.n[1], g.n[2]);
   const bool pax = sel3(ax, g.per[0], g.per[1], g.per[2]) != 0;
@@ -532,6 +534,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     explicit_cell_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
                          const __grid_constant__ ExplTerms et, const A* __restrict__ flux,
                          double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF;
   __shared__ A s_v[CPB][NB];
@@ -642,6 +645,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
                      const __grid_constant__ Tab1D<A> tp, const __grid_constant__ MixTab<A> mx,
                      double mass_d, const double* __restrict__ u_mass, const double* __restrict__ f,
                      const double* __restrict__ p, double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
   constexpr int NBP = Sh<NP, DIM>::NB, NPF = Sh<NP, DIM>::NF;
@@ -779,6 +783,7 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
                         const __grid_constant__ Tab1D<A> tp, const __grid_constant__ MixTab<A> mx,
                         double alpha_d, double inv_tau_d, const double* __restrict__ uss,
                         const double* __restrict__ p_old, double* __restrict__ rhs) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
   constexpr int NBP = Sh<NP, DIM>::NB, NPF = Sh<NP, DIM>::NF;
@@ -931,6 +936,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
                    const double* __restrict__ p, double* __restrict__ ut,
                    const double* __restrict__ base, double tau, const double* __restrict__ sub,
                    double* __restrict__ out) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NBP = Sh<NP, DIM>::NB;
   constexpr int SA = DIM == 3 ? N * NP * NP : N * NP;  // after the axis-0 contraction
@@ -1022,6 +1028,7 @@ template <int DIM, int N, typename R, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb, R mass, R visc, R adv,
                 R pen, int walls, const double* __restrict__ ub, double* __restrict__ diag) {
+  pdl_entry();
   using Ar = Arith<R>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
   // normal advecting velocity on each face point, own and neighbour trace,
@@ -1161,9 +1168,9 @@ dg_status run_explicit_a(const dg_mesh* m, int mode, double visc, double adv, co
   const Grid g = make_grid<DIM>(m);
   const double pen = (double)(N * N);
   if (mode == 0)
-    explicit_kernel<A, DIM, N, 0, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), visc, adv, pen, w, wb, rhs);
+    launch(explicit_kernel<A, DIM, N, 0, CPB>, blocks, threads, 0, s, g, tab_u<A>(m), visc, adv, pen, w, wb, rhs);
   else
-    explicit_kernel<A, DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), visc, adv, pen, w, wb, rhs);
+    launch(explicit_kernel<A, DIM, N, 1, CPB>, blocks, threads, 0, s, g, tab_u<A>(m), visc, adv, pen, w, wb, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -1178,18 +1185,18 @@ dg_status run_explicit_terms_a(const dg_mesh* m, const ExplTerms& et, int nt, do
   int64_t nface = 0;
   for (int ax = 0; ax < DIM; ++ax) nface += faces_of_axis(ax, m->n, m->periodic);
   const int64_t need = nface * Sh<N, DIM>::NF * DIM * (int64_t)sizeof(A);
-  const bool face_once = (m->tune[0][2] >= 5 || m->tune[0][1] >= 5) && m->split_flux &&
+  const bool face_once = (variant_split(m->tune[0][2]) || variant_split(m->tune[0][1])) && m->split_flux &&
                          need <= m->split_flux_bytes;
   if (face_once) {
     A* flux = static_cast<A*>(m->split_flux);
     const Grid g = make_grid<DIM>(m);
     const unsigned fb = (unsigned)((nface * Sh<N, DIM>::NF + 255) / 256);
     if (nt == 2) {
-      explicit_face_kernel<A, DIM, N, 2><<<fb, 256, 0, s>>>(g, tab_u<A>(m), et, flux);
-      explicit_cell_kernel<A, DIM, N, 2, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), et, flux, rhs);
+      launch(explicit_face_kernel<A, DIM, N, 2>, fb, 256, 0, s, g, tab_u<A>(m), et, flux);
+      launch(explicit_cell_kernel<A, DIM, N, 2, CPB>, blocks, threads, 0, s, g, tab_u<A>(m), et, flux, rhs);
     } else {
-      explicit_face_kernel<A, DIM, N, 1><<<fb, 256, 0, s>>>(g, tab_u<A>(m), et, flux);
-      explicit_cell_kernel<A, DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(g, tab_u<A>(m), et, flux, rhs);
+      launch(explicit_face_kernel<A, DIM, N, 1>, fb, 256, 0, s, g, tab_u<A>(m), et, flux);
+      launch(explicit_cell_kernel<A, DIM, N, 1, CPB>, blocks, threads, 0, s, g, tab_u<A>(m), et, flux, rhs);
     }
     count_launch();
     count_launch();
@@ -1197,9 +1204,9 @@ dg_status run_explicit_terms_a(const dg_mesh* m, const ExplTerms& et, int nt, do
     return DG_OK;
   }
   if (nt == 2)
-    explicit_terms_kernel<A, DIM, N, 2, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_u<A>(m), et, rhs);
+    launch(explicit_terms_kernel<A, DIM, N, 2, CPB>, blocks, threads, 0, s, make_grid<DIM>(m), tab_u<A>(m), et, rhs);
   else
-    explicit_terms_kernel<A, DIM, N, 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_u<A>(m), et, rhs);
+    launch(explicit_terms_kernel<A, DIM, N, 1, CPB>, blocks, threads, 0, s, make_grid<DIM>(m), tab_u<A>(m), et, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -1225,7 +1232,7 @@ dg_status run_mass_grad_a(const dg_mesh* m, double mass, const double* um, const
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  mass_grad_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(
+  launch(mass_grad_kernel<A, DIM, N, N - 1, CPB>, blocks, threads, 0, s, 
       make_grid<DIM>(m), tab_u<A>(m), tab_p<A>(m), tab_mix<A>(m), mass, um, f, p, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
@@ -1246,7 +1253,7 @@ dg_status run_pressure_rhs_a(const dg_mesh* m, double alpha, double inv_tau, con
   constexpr int CPB = cpb_for<NP, DIM>();
   constexpr int threads = ((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  pressure_rhs_kernel<A, DIM, N, NP, CPB><<<blocks, threads, 0, s>>>(
+  launch(pressure_rhs_kernel<A, DIM, N, NP, CPB>, blocks, threads, 0, s, 
       make_grid<DIM>(m), tab_u<A>(m), tab_p<A>(m), tab_mix<A>(m), alpha, inv_tau, uss, p_old, rhs);
   count_launch();
   DG_CUDA(cudaGetLastError());
@@ -1266,7 +1273,7 @@ dg_status run_project_a(const dg_mesh* m, const double* p, double* ut, const dou
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
-  project_kernel<A, DIM, N, N - 1, CPB><<<blocks, threads, 0, s>>>(make_grid<DIM>(m), tab_mix<A>(m), p,
+  launch(project_kernel<A, DIM, N, N - 1, CPB>, blocks, threads, 0, s, make_grid<DIM>(m), tab_mix<A>(m), p,
                                                                    ut, base, tau, sub, out);
   count_launch();
   DG_CUDA(cudaGetLastError());
@@ -1287,11 +1294,11 @@ dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, do
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
   if (fp32)
-    diag_kernel<DIM, N, float, CPB><<<blocks, threads, 0, s>>>(
+    launch(diag_kernel<DIM, N, float, CPB>, blocks, threads, 0, s, 
         make_grid<DIM>(m), pressure ? m->tp32 : m->tu32, (float)mass, (float)visc, (float)adv,
         (float)(N * N), pressure ? 0 : 1, ub, diag);
   else
-    diag_kernel<DIM, N, double, CPB><<<blocks, threads, 0, s>>>(
+    launch(diag_kernel<DIM, N, double, CPB>, blocks, threads, 0, s, 
         make_grid<DIM>(m), pressure ? m->tp64 : m->tu64, mass, visc, adv, (double)(N * N),
         pressure ? 0 : 1, ub, diag);
   count_launch();
@@ -1323,6 +1330,7 @@ dg_status momentum_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co,
 __global__ void __launch_bounds__(256)
     update_kernel(int64_t n, const double* __restrict__ base, double tau, const double* __restrict__ ut,
                   const double* __restrict__ sub, double* __restrict__ out) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = base[i] + tau * (sub ? ut[i] - sub[i] : ut[i]);
 }
@@ -1331,7 +1339,7 @@ dg_status axpby_update(int64_t n, const double* base, double tau, const double* 
                        double* out, cudaStream_t s) {
   const int64_t want = (n + 255) / 256;
   const unsigned blocks = (unsigned)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
-  update_kernel<<<blocks, 256, 0, s>>>(n, base, tau, ut, sub, out);
+  launch(update_kernel, blocks, 256, 0, s, n, base, tau, ut, sub, out);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;

@@ -14,7 +14,11 @@
 struct dg_solver {
   dg_mesh* mesh = nullptr;
   double Re = 1.0, c = 1e3;
-  cudaStream_t stream = nullptr;  // legacy default stream
+  // the solver's own non-blocking stream: every call first waits for the work
+  // the caller has enqueued on the legacy default stream (join_caller) and
+  // synchronises this stream before it returns
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr;
   dg::VecOps vo;
   int64_t nu = 0, np = 0, nus = 0;  // velocity (all comps), pressure, one component
   int m_alloc = 0;
@@ -43,6 +47,12 @@ struct dg_solver {
 
 namespace dg {
 namespace {
+
+dg_status join_caller(dg_solver* s) {
+  DG_CUDA(cudaEventRecord(s->ev_in, cudaStreamLegacy));
+  DG_CUDA(cudaStreamWaitEvent(s->stream, s->ev_in, 0));
+  return DG_OK;
+}
 
 dg_status dalloc(dg_solver* s, double** p, int64_t n) {
   cudaError_t e = cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1));
@@ -222,6 +232,7 @@ dg_status ensure_net(dg_solver* s, int k, const SysShape& sh) {
 __global__ void theta_axpy_kernel(int64_t n, const double* __restrict__ sc,
                                   const double* __restrict__ xe, const double* __restrict__ d,
                                   double* __restrict__ x) {
+  pdl_entry();
   const double den = sc[0];
   const double th = den > 0.0 ? (sc[1] - sc[2]) / den : 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -298,7 +309,7 @@ dg_status prepare_guess(dg_solver* s, int slot, int mode, const double* rhs, dou
     }
     if (st == DG_OK) st = s->vo.dots(n, 1, G.rt, G.xe, n, s->vo.scal + 2);  // <A d, xe>
     if (st != DG_OK) return st;
-    theta_axpy_kernel<<<1216, 256, 0, s->stream>>>(n, s->vo.scal, G.xe, G.dvec, x);
+    launch(theta_axpy_kernel, 1216, 256, 0, s->stream, n, s->vo.scal, G.xe, G.dvec, x);
     count_launch();
     DG_CUDA(cudaGetLastError());
   }
@@ -363,8 +374,13 @@ dg_status dg_solver_create(dg_mesh* m, double Re, double c, dg_solver** out) {
   s->nus = m->ncell * m->nbu;
   s->nu = s->nus * m->dim;
   s->np = m->ncell * m->nbp;
-  s->vo.stream = s->stream;
   dg_status st = DG_OK;
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("dg_solver_create: stream or event creation failed");
+    st = DG_ECUDA;
+  }
+  s->vo.stream = s->stream;
   double** vecs_u[] = {&s->w, &s->dinv_u, &s->ub, &s->ustar, &s->ut_old, &s->ut_new, &s->uss,
                        &s->rhs_u, &s->u_g, &s->u_hist, &s->fcomb};
   for (double** v : vecs_u)
@@ -394,7 +410,7 @@ dg_status dg_solver_create(dg_mesh* m, double Re, double c, dg_solver** out) {
 
 void dg_solver_destroy(dg_solver* s) {
   if (!s) return;
-  cudaStreamSynchronize(s->stream);
+  if (s->stream) cudaStreamSynchronize(s->stream);
   delete s->mg32;
   delete s->mg64;
   for (int i = 0; i < 24; ++i)
@@ -402,6 +418,8 @@ void dg_solver_destroy(dg_solver* s) {
   for (void* a : s->allocs)
     if (a) cudaFree(a);
   if (s->vo.host_scal) cudaFreeHost(s->vo.host_scal);
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
 
@@ -416,7 +434,11 @@ dg_status dg_solve_stage(dg_solver* s, const dg_momentum_coeffs* co, double alph
     info->status = DG_EINVAL;
     return DG_EINVAL;
   }
-  dg_status st;
+  dg_status st = join_caller(s);
+  if (st != DG_OK) {
+    info->status = st;
+    return st;
+  }
   if (o->system == DG_SYS_MOMENTUM) {
     if (!co || (co->adv != 0.0 && !ubar)) {
       set_error("dg_solve_stage: momentum solve needs coefficients and ubar");
@@ -448,6 +470,8 @@ dg_status dg_solver_set_history(dg_solver* s, const double* u_hist) {
     s->has_hist = false;
     return DG_OK;
   }
+  dg_status st = join_caller(s);
+  if (st != DG_OK) return st;
   DG_CUDA(cudaMemcpyAsync(s->u_hist, u_hist, sizeof(double) * s->nu, cudaMemcpyDeviceToDevice,
                           s->stream));
   DG_CUDA(cudaStreamSynchronize(s->stream));
@@ -463,6 +487,7 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   }
   if (!check_opts(&prm->mom, "trbdf2_step") || !check_opts(&prm->helm, "trbdf2_step"))
     return DG_EINVAL;
+  if (join_caller(s) != DG_OK) return DG_ECUDA;
   dg_solve_info loc[4];
   if (!info) info = loc;
   std::memset(info, 0, sizeof(dg_solve_info) * 4);

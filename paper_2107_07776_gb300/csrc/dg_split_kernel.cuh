@@ -30,6 +30,7 @@ template <typename T, typename A, int DIM, int N, bool ADV>
 __global__ void __launch_bounds__(256)
     face_flux_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
                      const T* __restrict__ src, const T* __restrict__ ub, A* __restrict__ flux) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
   const int n[3] = {a.n0, a.n1, a.n2};
@@ -57,9 +58,7 @@ __global__ void __launch_bounds__(256)
   const int d0 = ax == 0 ? face_layers(n[0], per[0]) : n[0];
   const int d1 = ax == 1 ? face_layers(n[1], per[1]) : n[1];
   int fc[3];
-  fc[0] = (int)(fl % d0);
-  fc[1] = (int)((fl / d0) % d1);
-  fc[2] = DIM == 3 ? (int)(fl / ((int64_t)d0 * d1)) : 0;
+  lex_coords(fl, d0, d1, fc);
   const int layer = pick3(ax, fc[0], fc[1], fc[2]);
   const int nax = pick3(ax, n[0], n[1], n[2]);
   const bool pax = pick3(ax, per[0], per[1], per[2]) != 0;
@@ -153,6 +152,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
     cell_split_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
                       const T* __restrict__ src, const T* __restrict__ ub,
                       const A* __restrict__ flux, T* __restrict__ dst) {
+  pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
   __shared__ A s_u[CPB][NB];
@@ -175,9 +175,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
 #pragma unroll
   for (int b = 0; b < DIM; ++b) ubn[b] = zero;
   if (active) {
-    ci[0] = (int)(cell % a.n0);
-    ci[1] = (int)((cell / a.n0) % a.n1);
-    ci[2] = DIM == 3 ? (int)(cell / ((int64_t)a.n0 * a.n1)) : 0;
+    lex_coords(cell, a.n0, a.n1, ci);
     h[0] = Ar::from(a.h0[ci[0]]);
     h[1] = Ar::from(a.h1[ci[1]]);
     hi[0] = Ar::from(a.hi0[ci[0]]);

@@ -138,6 +138,59 @@ def test_face_once_variants_match_oracle(ci, variant):
     assert rel_err(yp32.double().cpu().numpy(), ref_p) < 2e-5
 
 
+@pytest.mark.parametrize("ci", [i for i, c in enumerate(CASES) if c[0] == 3 and c[5] == 2 and c[6] != 2])
+def test_q1_thread_per_cell_variant_matches_oracle(ci):
+    """Variant 7 (one thread per Q1 cell) for the pressure operator in
+    float-float, native FP64 and FP32 against the oracle; the momentum
+    operator (not Q1 scalar) runs its fallback and stays exact."""
+    from paper_2107_07776_gb300 import binding as b
+    gm, om = meshes(CASES[ci])
+    b.dg_mesh_set_variant(gm.handle, 7)
+    xp = W.random_vector(om.n_p, 700 + ci)
+    ref_p = 2.9 * om.assemble("mass_p").apply(xp) + om.assemble("sipg_p").apply(xp)
+    for arith in (0, 1):
+        b.dg_mesh_set_fp64_arith(gm.handle, arith)
+        yp = torch.empty(om.n_p, dtype=torch.float64, device="cuda")
+        b.dg_apply_poisson(gm.handle, 2.9, dev(xp), yp)
+        torch.cuda.synchronize()
+        assert rel_err(yp.cpu().numpy(), ref_p) < 1e-12, arith
+    yp32 = torch.empty(om.n_p, dtype=torch.float32, device="cuda")
+    b.dg_apply_poisson_f32(gm.handle, 2.9, dev(xp, torch.float32), yp32)
+    torch.cuda.synchronize()
+    assert rel_err(yp32.double().cpu().numpy(), ref_p) < 2e-5
+    d = om.dim
+    x = W.random_vector(d * om.n_u, 800 + ci)
+    ref_u = np.concatenate([3.0 * om.assemble("mass_u").apply(x[i * om.n_u:(i + 1) * om.n_u])
+                            + 0.01 * om.assemble("sipg_u").apply(x[i * om.n_u:(i + 1) * om.n_u])
+                            for i in range(d)])
+    y = torch.empty(d * om.n_u, dtype=torch.float64, device="cuda")
+    b.dg_apply_momentum(gm.handle, b.momentum_coeffs(3.0, 0.01, 0.0), None, dev(x), y)
+    torch.cuda.synchronize()
+    assert rel_err(y.cpu().numpy(), ref_u) < 1e-12
+
+
+def test_q1_thread_per_cell_variant_in_multigrid():
+    """The Chebyshev-fused epilogue of variant 7: an FP32-multigrid
+    Helmholtz solve on a Q2/Q1 mesh whose operators all run variant 7
+    converges to the same solution as with the default variant."""
+    from paper_2107_07776_gb300 import binding as b
+    sols = []
+    for variant in (1, 7):
+        gm = b.Mesh(3, (8, 6, 8), (0, 0, 0), (1.0, 0.8, 1.0), (True, False, True), 2)
+        b.dg_mesh_set_variant(gm.handle, variant)
+        s = b.dg_solver_create(gm.handle, 100.0, 1e3)
+        try:
+            rhs = torch.tensor(W.random_vector(gm.n_dofs_p, 5), device="cuda")
+            x = torch.zeros_like(rhs)
+            o = b.solve_opts(b.DG_SYS_HELMHOLTZ, tol=1e-11, max_iter=100, precond=b.DG_PC_MG_FP32)
+            info = b.dg_solve_stage(s, None, 2.9, None, rhs, x, o)
+            assert info.status == 0 and info.iterations < 30
+            sols.append(x.cpu().numpy())
+        finally:
+            b.dg_solver_destroy(s)
+    assert rel_err(sols[1], sols[0]) < 1e-9
+
+
 def test_node_coords_match_oracle():
     for case in CASES:
         gm, om = meshes(case)
