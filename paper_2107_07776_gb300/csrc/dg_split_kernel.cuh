@@ -26,6 +26,16 @@
 
 namespace dg {
 
+// asynchronous global-to-shared copy of BYTES (4, 8 or 16; both addresses
+// aligned to it), its commit and the wait for all of the thread's copies
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T, typename A, int DIM, int N, bool ADV>
 __global__ void __launch_bounds__(256)
     face_flux_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
@@ -157,6 +167,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
   __shared__ A s_u[CPB][NB];
   __shared__ A s_q[DIM][CPB][NB];
+  __shared__ __align__(16) A s_fl[CPB][NB][2 * DIM][2];
   const int tid = threadIdx.x;
   const int cl = tid / NB, node = tid - (tid / NB) * NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
@@ -204,6 +215,15 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   }
   for (int c = 0; c < a.ncomp; ++c) {
     const T* srcc = src + (int64_t)c * a.ncell * NB;
+    // this component's flux pairs (F0, G) at the node's 2d face points,
+    // copied asynchronously into the thread's own shared-memory slots first,
+    // so that their latency overlaps the cell-term phase
+    if (active) {
+      const A* fl = flux + (int64_t)c * nface * NF * 2;
+#pragma unroll
+      for (int q = 0; q < 2 * DIM; ++q) cp_async<2 * sizeof(A)>(&s_fl[cl][node][q][0], fl + fpos[q] * 2);
+    }
+    cp_async_commit();
     if (active) s_u[cl][node] = Ar::from(srcc[cell * NB + node]);
     __syncthreads();
     if (active) {
@@ -234,11 +254,10 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
           acc = Ar::fma(tb.D[m][ii[b]], s_q[b][cl][j[0] + N * (j[1] + N * j[2])], acc);
         }
         y = Ar::fma(acc, hi[b], y);
-        const A* fl = flux + (int64_t)c * nface * NF * 2;
+        if (b == 0) cp_async_wait_all();  // the thread's own copies (no barrier needed)
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const A* fp = fl + fpos[2 * b + s] * 2;
-          const A F0 = fp[0], G = fp[1];
+          const A F0 = s_fl[cl][node][2 * b + s][0], G = s_fl[cl][node][2 * b + s][1];
           y = Ar::fma(s ? F0 : -F0, tb.L[s][ii[b]], y);
           y = Ar::fma(G * hi[b], tb.dL[s][ii[b]], y);
         }
