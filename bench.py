@@ -63,8 +63,7 @@ FLOAT_FLOAT_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 15 * 2 / 1e12
 # the bench's launch configuration; to be re-captured whenever the kernel
 # changes
 # (face-once form: flux kernel + cell kernel of one apply)
-NCU_TRAFFIC_BYTES = {"tgv32": 42625024 + 6534400 + 85311488 + 7347712,
-                     "channel": 2718136832 + 1346348800 + 2775603200 + 665124608}
+NCU_TRAFFIC_BYTES = {"tgv32": 42662656 + 7026688 + 85345536 + 7072256}
 
 
 def peaks():

@@ -39,6 +39,16 @@ __device__ __forceinline__ void lex_coords(int64_t cell, int n0, int n1, int ci[
   }
 }
 
+// asynchronous global-to-shared copy of BYTES (4, 8 or 16; both addresses
+// aligned to it), its commit and the wait for all of the thread's copies
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // The PDL attribute is set unless DG_PDL=0 in the environment, and never on
 // the legacy default stream.
 bool pdl_enabled();

@@ -26,16 +26,6 @@
 
 namespace dg {
 
-// asynchronous global-to-shared copy of BYTES (4, 8 or 16; both addresses
-// aligned to it), its commit and the wait for all of the thread's copies
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
 template <typename T, typename A, int DIM, int N, bool ADV>
 __global__ void __launch_bounds__(256)
     face_flux_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
