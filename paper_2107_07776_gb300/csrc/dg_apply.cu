@@ -331,7 +331,7 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
       char line[1024];
       const bool p = op == 0, adv = op == 2;
       auto cp = [&](int v) {
-        if (variant_q1(v)) return 128;  // one thread per cell, 128 threads per CTA
+        if (variant_q1(v)) return 64;  // two threads per cell, 128 threads per CTA
         return prec == 0 ? cpb_for_mesh<double>(m, p, adv, v) : cpb_for_mesh<float>(m, p, adv, v);
       };
       std::snprintf(line, sizeof(line),

@@ -367,7 +367,7 @@ static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T
 template <typename T, typename A>
 static dg_status launch_q1(const OpArgs<T>& args, const Tab1D<A>& tb, const T* src, T* dst,
                            cudaStream_t s) {
-  const int64_t blocks = (args.ncell + 127) / 128;
+  const int64_t blocks = (2 * args.ncell + 127) / 128;  // two threads per cell
   if (blocks > 0x7fffffff) {
     set_error("operator apply: grid too large");
     return DG_EINVAL;

@@ -1,17 +1,20 @@
 // Scalar operator alpha M + visc K_SIP on Q1 elements (two Gauss points per
 // direction, 3D, no advection: the pressure space of Q2/Q1 and every
-// multigrid level after p-coarsening), one thread per cell.  With N = 2 a
+// multigrid level after p-coarsening), two threads per cell.  With N = 2 a
 // cell's 8 values, each face's 4 points and the 2 nodes on each normal line
-// are compile-time indices, so the whole cell lives in registers: the cell
-// term (sum factorisation, axis by axis), then the 6 faces one after
-// another (the neighbour's 8 values, the SIP flux of Eqs. weakform_p_1 and
-// the penalty of Eq. penconst1 at the 4 face points, lifted back onto the 2
-// nodes of each normal line), then the plain or Chebyshev epilogue.  The
-// arithmetic is term by term that of scalar_op_kernel, in the same order.
+// are compile-time indices, so the cell lives in registers.  Thread h of a
+// lane pair owns the 4 nodes of the z-layer i2 = h: it evaluates the x and y
+// derivative terms and the x and y faces of its layer alone, the z
+// derivative and the z face on its side (s = h) for the whole cell, and
+// trades the halves that belong to its partner by warp shuffles.  Terms
+// follow scalar_op_kernel (the SIP flux of Eqs. weakform_p_1, the penalty
+// of Eq. penconst1) and are added to each node in the same order.
 #pragma once
 
 #include "dg_common.cuh"
 #include "dg_df64.cuh"
+
+#include <type_traits>
 
 namespace dg {
 
@@ -43,22 +46,52 @@ __host__ __device__ constexpr int q1_node(int ax, int i, int t) {
   return ax == 0 ? i + 2 * t : (ax == 1 ? (t & 1) + 2 * i + 4 * (t >> 1) : t + 4 * i);
 }
 
+template <typename A>
+__device__ __forceinline__ A shfl_pair(A v) {
+  if constexpr (sizeof(A) == 8 && !std::is_same<A, double>::value) {  // float-float
+    v.hi = __shfl_xor_sync(0xffffffffu, v.hi, 1);
+    v.lo = __shfl_xor_sync(0xffffffffu, v.lo, 1);
+    return v;
+  } else {
+    return __shfl_xor_sync(0xffffffffu, v, 1);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void q1_load4(const T* __restrict__ p, bool vec, T out[4]) {
+  if (vec) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+      out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    } else {
+      const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+      const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+      out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = __ldg(p + i);
+  }
+}
+
 template <typename T, typename A>
 __global__ void __launch_bounds__(128)
     q1_cell_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
                    const T* __restrict__ src, T* __restrict__ dst) {
   pdl_entry();
   using Ar = Arith<A>;
-  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= a.ncell) return;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = (int)(gt & 1);  // the thread's z-layer
+  // pairs are whole (2 ncell threads); threads past the end compute the last
+  // cell again so that every lane takes part in the shuffles, and store nothing
+  const bool active = (gt >> 1) < a.ncell;
+  const int64_t cell = active ? (gt >> 1) : a.ncell - 1;
   const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
   const A mass = Ar::from(a.mass), visc = Ar::from(a.visc), pen = Ar::from(a.pen);
   int ci[3];
   lex_coords(cell, a.n0, a.n1, ci);
-  const A h[3] = {Ar::from(a.h0[ci[0]]), Ar::from(a.h1[ci[1]]), Ar::from(a.h2[ci[2]])};
+  const A h3[3] = {Ar::from(a.h0[ci[0]]), Ar::from(a.h1[ci[1]]), Ar::from(a.h2[ci[2]])};
   const A hi[3] = {Ar::from(a.hi0[ci[0]]), Ar::from(a.hi1[ci[1]]), Ar::from(a.hi2[ci[2]])};
-  // 16-byte vector access when every base pointer allows it (a cell's 8
-  // values then start on a 32- or 64-byte boundary)
   uintptr_t align = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst);
   if (a.cheb)
     align |= reinterpret_cast<uintptr_t>(a.cx) | reinterpret_cast<uintptr_t>(a.cr) |
@@ -66,43 +99,71 @@ __global__ void __launch_bounds__(128)
   const bool vec = (align & 15u) == 0;
   T ut[8];
   q1_load<T, A>(src + cell * 8, vec, ut);
-  A u[8], W[8], y[8];
+  A u[8];
 #pragma unroll
-  for (int nd = 0; nd < 8; ++nd) {
-    u[nd] = Ar::from(ut[nd]);
-    W[nd] = tb.w[nd & 1] * tb.w[(nd >> 1) & 1] * h[0] * h[1] * tb.w[nd >> 2] * h[2];
-    y[nd] = mass * W[nd] * u[nd];
+  for (int nd = 0; nd < 8; ++nd) u[nd] = Ar::from(ut[nd]);
+  // own nodes nd = 4 h + k (k = i0 + 2 i1), picked by selects (a run-time
+  // index into u would put it in local memory)
+  A uo[4], W[4], y[4];
+  T uto[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uo[k] = h ? u[4 + k] : u[k];
+    uto[k] = h ? ut[4 + k] : ut[k];
+    W[k] = tb.w[k & 1] * tb.w[k >> 1] * h3[0] * h3[1] * tb.w[h] * h3[2];
+    y[k] = mass * W[k] * uo[k];
   }
-  // cell term: y += hi_b D_b^T (W visc hi_b D_b u), axis by axis
+  // x and y derivative terms within the layer
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    A q[8];
+  for (int b = 0; b < 2; ++b) {
+    A q[4];
 #pragma unroll
-    for (int nd = 0; nd < 8; ++nd) {
-      const int ib = (nd >> b) & 1, lo = nd & ~(1 << b), up = lo | (1 << b);
+    for (int k = 0; k < 4; ++k) {
+      const int ib = (k >> b) & 1, lo = k & ~(1 << b), up = lo | (1 << b);
       A du = zero;
-      du += tb.D[ib][0] * u[lo];
-      du += tb.D[ib][1] * u[up];
-      q[nd] = W[nd] * (visc * du * hi[b]);
+      du += tb.D[ib][0] * uo[lo];
+      du += tb.D[ib][1] * uo[up];
+      q[k] = W[k] * (visc * du * hi[b]);
     }
 #pragma unroll
-    for (int nd = 0; nd < 8; ++nd) {
-      const int ib = (nd >> b) & 1, lo = nd & ~(1 << b), up = lo | (1 << b);
+    for (int k = 0; k < 4; ++k) {
+      const int ib = (k >> b) & 1, lo = k & ~(1 << b), up = lo | (1 << b);
       A acc = zero;
       acc += tb.D[0][ib] * q[lo];
       acc += tb.D[1][ib] * q[up];
-      y[nd] += acc * hi[b];
+      y[k] += acc * hi[b];
     }
   }
-  // faces, in the order of the cell-centric kernel's lifting (axis, side)
+  // z derivative: q on the own layer, the partner's layer by shuffle
+  {
+    A qo[4], qp[4];
 #pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
+    for (int k = 0; k < 4; ++k) {
+      A du = zero;
+      du += tb.D[h][0] * u[k];
+      du += tb.D[h][1] * u[4 + k];
+      qo[k] = W[k] * (visc * du * hi[2]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qp[k] = shfl_pair(qo[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const A q0 = h == 0 ? qo[k] : qp[k], q1 = h == 0 ? qp[k] : qo[k];
+      A acc = zero;
+      acc += tb.D[0][h] * q0;
+      acc += tb.D[1][h] * q1;
+      y[k] += acc * hi[2];
+    }
+  }
+  // x and y faces: the layer's 2 points on each
+#pragma unroll
+  for (int ax = 0; ax < 2; ++ax) {
     const int cax = ci[ax];
-    const int nax = ax == 0 ? a.n0 : (ax == 1 ? a.n1 : a.n2);
-    const int per = ax == 0 ? a.per0 : (ax == 1 ? a.per1 : a.per2);
-    const int64_t cstr = ax == 0 ? 1 : (ax == 1 ? (int64_t)a.n0 : (int64_t)a.n0 * a.n1);
-    const T* hiax = ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2);
-    const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;  // tangential axes
+    const int nax = ax == 0 ? a.n0 : a.n1;
+    const int per = ax == 0 ? a.per0 : a.per1;
+    const int64_t cstr = ax == 0 ? 1 : (int64_t)a.n0;
+    const T* hiax = ax == 0 ? a.hi0 : a.hi1;
+    const int b0 = ax == 0 ? 1 : 0;  // tangential axes b0 and z
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
@@ -115,26 +176,27 @@ __global__ void __launch_bounds__(128)
       if (!interior && !a.walls) continue;  // Neumann: no face terms
       const A hiK = hi[ax];
       A hiN = zero;
-      T vt[8];
+      T vt[4];  // the neighbour's layer h
       if (interior) {
         hiN = Ar::from(hiax[cn]);
-        q1_load<T, A>(src + (cell + (int64_t)(cn - cax) * cstr) * 8, vec, vt);
+        q1_load4<T>(src + (cell + (int64_t)(cn - cax) * cstr) * 8 + 4 * h, vec, vt);
       }
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int n0 = q1_node(ax, 0, t), n1 = q1_node(ax, 1, t);
+      for (int j = 0; j < 2; ++j) {
+        // layer-local nodes on the normal line through tangential index j
+        const int k0 = ax == 0 ? 2 * j : j, k1 = ax == 0 ? 2 * j + 1 : j + 2;
         A wt = Ar::c(1.0);
-        wt = wt * tb.w[t & 1] * h[b0];
-        wt = wt * tb.w[t >> 1] * h[b1];
+        wt = wt * tb.w[j] * h3[b0];
+        wt = wt * tb.w[h] * h3[2];
         A uin = zero, dnin = zero;
-        uin = Ar::fma(tb.L[s][0], u[n0], uin);
-        dnin = Ar::fma(tb.dL[s][0], u[n0], dnin);
-        uin = Ar::fma(tb.L[s][1], u[n1], uin);
-        dnin = Ar::fma(tb.dL[s][1], u[n1], dnin);
+        uin = Ar::fma(tb.L[s][0], uo[k0], uin);
+        dnin = Ar::fma(tb.dL[s][0], uo[k0], dnin);
+        uin = Ar::fma(tb.L[s][1], uo[k1], uin);
+        dnin = Ar::fma(tb.dL[s][1], uo[k1], dnin);
         dnin = dnin * sgn * hiK;
         A fv, fg;
         if (interior) {
-          const A v0 = Ar::from(vt[n0]), v1 = Ar::from(vt[n1]);
+          const A v0 = Ar::from(vt[k0]), v1 = Ar::from(vt[k1]);
           A uout = zero, dnout = zero;
           uout = Ar::fma(tb.L[1 - s][0], v0, uout);
           dnout = Ar::fma(tb.dL[1 - s][0], v0, dnout);
@@ -151,36 +213,108 @@ __global__ void __launch_bounds__(128)
           fg = -(visc * uin);
         }
         const A f0 = wt * fv, f1 = wt * fg * sgn * hiK;
-        y[n0] += f0 * tb.L[s][0] + f1 * tb.dL[s][0];
-        y[n1] += f0 * tb.L[s][1] + f1 * tb.dL[s][1];
+        y[k0] += f0 * tb.L[s][0] + f1 * tb.dL[s][0];
+        y[k1] += f0 * tb.L[s][1] + f1 * tb.dL[s][1];
       }
     }
   }
-  const int64_t o = cell * 8;
-  T yt[8];
+  // z faces: this thread evaluates side s = h at all 4 points; the lift onto
+  // the partner's layer is traded by shuffle, and each node adds side 0 first
+  {
+    const int s = h;
+    const A sgn = s ? Ar::c(1.0) : Ar::c(-1.0);
+    int cn = ci[2] + (s ? 1 : -1);
+    bool interior = true;
+    if (cn < 0 || cn >= a.n2) {
+      if (a.per2) cn = cn < 0 ? a.n2 - 1 : 0;
+      else interior = false;
+    }
+    const bool any = interior || a.walls;
+    const A hiK = hi[2];
+    A hiN = zero;
+    T vt[8];
+    if (interior) {
+      hiN = Ar::from(a.hi2[cn]);
+      q1_load<T, A>(src + (cell + (int64_t)(cn - ci[2]) * a.n0 * (int64_t)a.n1) * 8, vec, vt);
+    }
+    A c_own[4], c_par[4];
 #pragma unroll
-  for (int nd = 0; nd < 8; ++nd) yt[nd] = sizeof(T) == 8 ? (T)Ar::to_d(y[nd]) : (T)Ar::to_f(y[nd]);
+    for (int t = 0; t < 4; ++t) {
+      c_own[t] = zero;
+      c_par[t] = zero;
+      if (any) {
+        A wt = Ar::c(1.0);
+        wt = wt * tb.w[t & 1] * h3[0];
+        wt = wt * tb.w[t >> 1] * h3[1];
+        A uin = zero, dnin = zero;
+        uin = Ar::fma(tb.L[s][0], u[t], uin);
+        dnin = Ar::fma(tb.dL[s][0], u[t], dnin);
+        uin = Ar::fma(tb.L[s][1], u[4 + t], uin);
+        dnin = Ar::fma(tb.dL[s][1], u[4 + t], dnin);
+        dnin = dnin * sgn * hiK;
+        A fv, fg;
+        if (interior) {
+          const A v0 = Ar::from(vt[t]), v1 = Ar::from(vt[4 + t]);
+          A uout = zero, dnout = zero;
+          uout = Ar::fma(tb.L[1 - s][0], v0, uout);
+          dnout = Ar::fma(tb.dL[1 - s][0], v0, dnout);
+          uout = Ar::fma(tb.L[1 - s][1], v1, uout);
+          dnout = Ar::fma(tb.dL[1 - s][1], v1, dnout);
+          dnout = dnout * sgn * hiN;
+          const A Cpen = half * pen * (hiK + hiN);
+          const A jump = uin - uout;
+          fv = visc * (Cpen * jump - half * (dnin + dnout));
+          fg = -(half * visc * jump);
+        } else {
+          const A sig = pen * hiK;
+          fv = visc * (two * sig * uin - dnin);
+          fg = -(visc * uin);
+        }
+        const A f0 = wt * fv, f1 = wt * fg * sgn * hiK;
+        // node t (layer 0) takes index 0 of the normal line, node 4 + t index 1
+        const A c0 = f0 * tb.L[s][0] + f1 * tb.dL[s][0];
+        const A c1 = f0 * tb.L[s][1] + f1 * tb.dL[s][1];
+        c_own[t] = h == 0 ? c0 : c1;
+        c_par[t] = h == 0 ? c1 : c0;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const A from_partner = shfl_pair(c_par[t]);  // the partner's side, lifted onto this layer
+      if (h == 0) {
+        y[t] += c_own[t];
+        y[t] += from_partner;
+      } else {
+        y[t] += from_partner;
+        y[t] += c_own[t];
+      }
+    }
+  }
+  if (!active) return;
+  const int64_t o = cell * 8 + 4 * h;
+  T yt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) yt[k] = sizeof(T) == 8 ? (T)Ar::to_d(y[k]) : (T)Ar::to_f(y[k]);
   if (a.cheb) {
     // x += d; r -= dinv y; dst = c1 d + c2 r
 #pragma unroll
-    for (int nd = 0; nd < 8; ++nd) {
-      const T dk = ut[nd];
-      a.cx[o + nd] += dk;
-      const T rk = a.cr[o + nd] - a.cdinv[o + nd] * yt[nd];
-      a.cr[o + nd] = rk;
-      dst[o + nd] = a.cc1 * dk + a.cc2 * rk;
+    for (int k = 0; k < 4; ++k) {
+      const T dk = uto[k];
+      a.cx[o + k] += dk;
+      const T rk = a.cr[o + k] - a.cdinv[o + k] * yt[k];
+      a.cr[o + k] = rk;
+      dst[o + k] = a.cc1 * dk + a.cc2 * rk;
     }
   } else if (vec) {
     if constexpr (sizeof(T) == 4) {
       reinterpret_cast<float4*>(dst + o)[0] = make_float4(yt[0], yt[1], yt[2], yt[3]);
-      reinterpret_cast<float4*>(dst + o)[1] = make_float4(yt[4], yt[5], yt[6], yt[7]);
     } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(dst + o)[q] = make_double2(yt[2 * q], yt[2 * q + 1]);
+      reinterpret_cast<double2*>(dst + o)[0] = make_double2(yt[0], yt[1]);
+      reinterpret_cast<double2*>(dst + o)[1] = make_double2(yt[2], yt[3]);
     }
   } else {
 #pragma unroll
-    for (int nd = 0; nd < 8; ++nd) dst[o + nd] = yt[nd];
+    for (int k = 0; k < 4; ++k) dst[o + k] = yt[k];
   }
 }
 
