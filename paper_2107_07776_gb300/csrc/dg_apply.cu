@@ -292,10 +292,14 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
     for (int op = 0; op < 3 && st == DG_OK; ++op) {
       float best = 1e30f, times[kTuneVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
       int bestv = 1;
-      // the thread-per-cell Q1 kernel exists for the 3D pressure operator on
-      // two points per direction only (elsewhere variant 7 would time
-      // variant 1 again): not timed, reported as 0
-      const bool q1_ok = op == 0 && m->dim == 3 && m->np == 2;
+      // the two-threads-per-cell Q1 kernel exists for the 3D pressure
+      // operator on two points per direction only (elsewhere variant 7 would
+      // time variant 1 again), and is a candidate in FP32 only: its
+      // float-float form is instruction-heavy (8.4 k instructions per warp
+      // on tgv32) and wins back-to-back with a warm instruction cache (28 vs
+      // 31 us) but loses inside the step, between other kernels (49 vs
+      // 31 us cold).  Not timed: reported as 0.
+      const bool q1_ok = op == 0 && m->dim == 3 && m->np == 2 && prec == 1;
       for (int v = 0; v < kTuneVariants && st == DG_OK; ++v) {
         if (variant_q1(v) && !q1_ok) continue;
         m->tune[prec][op] = v;
