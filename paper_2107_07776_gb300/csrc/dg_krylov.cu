@@ -74,6 +74,45 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
+// block sums of a 256-thread block's values in the fixed tree of
+// multi_dot_kernel (s: the block's shared scratch)
+__device__ __forceinline__ double block_tree_sum(double v, double* s) {
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = kRedThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  const double t = s[0];
+  __syncthreads();
+  return t;
+}
+
+// r = b - q with this block's partial sums of <b, b> and <r, r> in one pass
+// (partial[blk * 2 + 0, 1]); the same per-thread order and block tree as
+// multi_dot_kernel, so the sums equal those of two separate inner products
+__global__ void __launch_bounds__(kRedThreads)
+    residual_norms_kernel(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
+                          double* __restrict__ r, double* __restrict__ partial) {
+  pdl_entry();
+  __shared__ double s[kRedThreads];
+  double bb = 0.0, rr = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double bk = b[k];
+    const double rk = 1.0 * bk + (-1.0) * q[k];
+    r[k] = rk;
+    bb += bk * bk;
+    rr += rk * rk;
+  }
+  bb = block_tree_sum(bb, s);
+  rr = block_tree_sum(rr, s);
+  if (threadIdx.x == 0) {
+    partial[(int64_t)blockIdx.x * 2] = bb;
+    partial[(int64_t)blockIdx.x * 2 + 1] = rr;
+  }
+}
+
 // w -= sum_i h[i] V_i  (h on the device)
 __global__ void multi_axpy_kernel(int64_t n, int nv, const double* __restrict__ h,
                                   const double* __restrict__ V, int64_t ldv, double* __restrict__ w) {
@@ -137,20 +176,28 @@ __global__ void cg_update_kernel(int64_t n, double a, const double* __restrict__
   }
 }
 
-// the same update with a = sc[irz] / sc[ipq] read on the device
-__global__ void cg_update_dev_kernel(int64_t n, const double* __restrict__ sc, int irz, int ipq,
-                                     const double* __restrict__ p, const double* __restrict__ q,
-                                     double* __restrict__ x, double* __restrict__ r,
-                                     double* __restrict__ r_old) {
+// the same update with a = sc[irz] / sc[ipq] read on the device, and this
+// block's partial sum of the new <r, r> (multi_dot_kernel's order and tree)
+__global__ void __launch_bounds__(kRedThreads)
+    cg_update_dev_kernel(int64_t n, const double* __restrict__ sc, int irz, int ipq,
+                         const double* __restrict__ p, const double* __restrict__ q,
+                         double* __restrict__ x, double* __restrict__ r, double* __restrict__ r_old,
+                         double* __restrict__ partial) {
   pdl_entry();
+  __shared__ double s[kRedThreads];
   const double a = sc[irz] / sc[ipq];
+  double rr = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     x[k] += a * p[k];
     const double rk = r[k];
     r_old[k] = rk;
-    r[k] = rk - a * q[k];
+    const double rn = rk - a * q[k];
+    r[k] = rn;
+    rr += rn * rn;
   }
+  rr = block_tree_sum(rr, s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = rr;
 }
 
 // flexible (Polak-Ribiere) direction: p = z + beta p, beta = (<z, r> -
@@ -180,6 +227,15 @@ dg_status VecOps::dots(int64_t n, int nv, const double* w, const double* V, int6
   const int nb = red_blocks(n);
   launch(multi_dot_kernel, nb, kRedThreads, 0, stream, n, nv, w, V, ldv, partial); count_launch();
   launch(reduce_kernel, nv, kRedThreads, 0, stream, nb, nv, partial, out_dev); count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status VecOps::residual_norms(int64_t n, const double* b, const double* q, double* r,
+                                 double* out_dev) {
+  const int nb = red_blocks(n);
+  launch(residual_norms_kernel, nb, kRedThreads, 0, stream, n, b, q, r, partial); count_launch();
+  launch(reduce_kernel, 2, kRedThreads, 0, stream, nb, 2, partial, out_dev); count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -248,9 +304,7 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
     // r = b - A x -> V_0, with |b|^2 (first cycle) and |r|^2 in one round trip
     dg_status st = A(x, w);
     if (st != DG_OK) return st;
-    st = vo.axpby(n, 1.0, b, -1.0, w, V);
-    if (st == DG_OK) st = vo.dots(n, 1, V, V, n, vo.scal + 1);
-    if (st == DG_OK && first) st = vo.dots(n, 1, b, b, n, vo.scal);
+    st = vo.residual_norms(n, b, w, V, vo.scal);  // V_0 = b - A x, |b|^2, |V_0|^2
     if (st != DG_OK) return st;
     DG_CUDA(cudaMemcpyAsync(hs, vo.scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, vo.stream));
     DG_CUDA(cudaStreamSynchronize(vo.stream));
@@ -380,9 +434,7 @@ dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const 
   double* sc = vo.scal;
   dg_status st = A(x, q);
   if (st != DG_OK) return st;
-  st = vo.axpby(n, 1.0, b, -1.0, q, r);
-  if (st == DG_OK) st = vo.dots(n, 1, b, b, n, sc + 0);
-  if (st == DG_OK) st = vo.dots(n, 1, r, r, n, sc + 1);
+  st = vo.residual_norms(n, b, q, r, sc + 0);  // r = b - A x, <b, b>, <r, r>
   if (st != DG_OK) return st;
   DG_CUDA(cudaMemcpyAsync(vo.host_scal, sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, vo.stream));
   DG_CUDA(cudaStreamSynchronize(vo.stream));
@@ -412,11 +464,15 @@ dg_status cg_solve(VecOps& vo, int64_t n, const LinOp& A, const LinOp* P, const 
     if (st != DG_OK) return st;
     st = vo.dots(n, 1, p, q, n, sc + 2);
     if (st != DG_OK) return st;
-    launch(cg_update_dev_kernel, grid_for(n), 256, 0, vo.stream, n, sc, irz, 2, p, q, x, r, r_old);
-    count_launch();
-    DG_CUDA(cudaGetLastError());
-    st = vo.dots(n, 1, r, r, n, sc + 1);
-    if (st != DG_OK) return st;
+    {  // x += a p, r_old = r, r -= a q, and <r, r>
+      const int nb = red_blocks(n);
+      launch(cg_update_dev_kernel, nb, kRedThreads, 0, vo.stream, n, sc, irz, 2, p, q, x, r, r_old,
+             vo.partial);
+      count_launch();
+      launch(reduce_kernel, 1, kRedThreads, 0, vo.stream, nb, 1, vo.partial, sc + 1);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+    }
     DG_CUDA(cudaMemcpyAsync(vo.host_scal, sc + 1, sizeof(double) * 2, cudaMemcpyDeviceToHost, vo.stream));
     DG_CUDA(cudaStreamSynchronize(vo.stream));
     rr = vo.host_scal[0];

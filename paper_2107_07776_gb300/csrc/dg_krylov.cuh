@@ -18,6 +18,8 @@ struct VecOps {
   double* host_scal = nullptr;  // pinned host, >= 64 doubles
   dg_status dots(int64_t n, int nv, const double* w, const double* V, int64_t ldv,
                  double* out_dev);
+  // r = b - q with <b, b> and <r, r> into out_dev[0, 1] (one pass)
+  dg_status residual_norms(int64_t n, const double* b, const double* q, double* r, double* out_dev);
   dg_status dots_host(int64_t n, int nv, const double* w, const double* V, int64_t ldv,
                       double* out_host);
   dg_status axpby(int64_t n, double a, const double* x, double b, const double* y, double* z);
@@ -42,5 +44,8 @@ dg_status project_fused(const dg_mesh* m, const double* p, double* ut, const dou
                         double tau, const double* sub, double* out, cudaStream_t s);
 dg_status momentum_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co, const double* ub,
                                  double* diag, cudaStream_t s);
+// affine meshes: 1/diag of the momentum operator for every component at once
+dg_status momentum_inv_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co, const double* ub,
+                                     double* dinv, cudaStream_t s);
 
 }  // namespace dg

@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 template <int DIM, int N, typename R, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb, R mass, R visc, R adv,
-                R pen, int walls, const double* __restrict__ ub, double* __restrict__ diag) {
+                R pen, int walls, const double* __restrict__ ub, double* __restrict__ diag, int inv_copies) {
   pdl_entry();
   using Ar = Arith<R>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
@@ -1119,7 +1119,12 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       d += wt * (fv * tb.L[s][ii[ax]] + fg * sgn * tb.dL[s][ii[ax]] * hiK);
     }
   }
-  diag[cell * NB + node] = (double)d;
+  if (inv_copies > 0) {  // the Jacobi scaling itself, 1/d, for each of inv_copies components
+    const double id = 1.0 / (double)d;
+    for (int c = 0; c < inv_copies; ++c) diag[((int64_t)c * g.ncell + cell) * NB + node] = id;
+  } else {
+    diag[cell * NB + node] = (double)d;
+  }
 }
 
 template <int DIM>
@@ -1289,18 +1294,18 @@ dg_status run_project(const dg_mesh* m, const double* p, double* ut, const doubl
 
 template <int DIM, int N>
 dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, double adv,
-                   const double* ub, double* diag, cudaStream_t s, bool fp32 = false) {
+                   const double* ub, double* diag, cudaStream_t s, bool fp32 = false, int inv_copies = 0) {
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
   if (fp32)
     launch(diag_kernel<DIM, N, float, CPB>, blocks, threads, 0, s, 
         make_grid<DIM>(m), pressure ? m->tp32 : m->tu32, (float)mass, (float)visc, (float)adv,
-        (float)(N * N), pressure ? 0 : 1, ub, diag);
+        (float)(N * N), pressure ? 0 : 1, ub, diag, inv_copies);
   else
     launch(diag_kernel<DIM, N, double, CPB>, blocks, threads, 0, s, 
         make_grid<DIM>(m), pressure ? m->tp64 : m->tu64, mass, visc, adv, (double)(N * N),
-        pressure ? 0 : 1, ub, diag);
+        pressure ? 0 : 1, ub, diag, inv_copies);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -1324,6 +1329,18 @@ dg_status momentum_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co,
                                  double* diag, cudaStream_t s) {
   if (!m->affine) return general_diag(m, false, co->mass, co->visc, co->adv, ub, diag, true, s);
   return DG_DISPATCH_U(m, run_diag, m, false, co->mass, co->visc, co->adv, ub, diag, s, true);
+}
+
+// internal entry used by the solver on affine meshes: the momentum Jacobi
+// scaling 1/diag for all components in one pass (FP32 diagonal arithmetic,
+// as above)
+dg_status momentum_inv_diagonal_fp32(const dg_mesh* m, const dg_momentum_coeffs* co, const double* ub,
+                                     double* dinv, cudaStream_t s) {
+  if (!m->affine) {
+    set_error("momentum_inv_diagonal_fp32: affine meshes only");
+    return DG_EINVAL;
+  }
+  return DG_DISPATCH_U(m, run_diag, m, false, co->mass, co->visc, co->adv, ub, dinv, s, true, m->dim);
 }
 
 // out = base + tau (ut - sub) elementwise (sub may be null)

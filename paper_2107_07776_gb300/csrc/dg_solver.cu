@@ -93,9 +93,12 @@ dg_status solve_momentum(dg_solver* s, const dg_momentum_coeffs* co, const doubl
   dg_status st;
   const double* dinv = nullptr;
   if (o->precond == DG_PC_JACOBI) {
-    st = momentum_diagonal_fp32(m, co, ubar, s->diag_s, s->stream);
-    if (st != DG_OK) return st;
-    st = s->vo.invert(s->nu, s->diag_s, s->nus, s->dinv_u);
+    if (m->affine) {  // diagonal and its inverse in one pass
+      st = momentum_inv_diagonal_fp32(m, co, ubar, s->dinv_u, s->stream);
+    } else {
+      st = momentum_diagonal_fp32(m, co, ubar, s->diag_s, s->stream);
+      if (st == DG_OK) st = s->vo.invert(s->nu, s->diag_s, s->nus, s->dinv_u);
+    }
     if (st != DG_OK) return st;
     dinv = s->dinv_u;
   } else if (o->precond != DG_PC_NONE) {
