@@ -46,7 +46,7 @@ typedef enum {
   DG_ENOCONV = 4,       /* Krylov solve hit max_iter above tolerance */
   DG_EBREAKDOWN = 5,    /* non-finite residual or Krylov breakdown */
   DG_ETIMEOUT = 6,      /* solve exceeded its wall-clock limit */
-  DG_EUNSUPPORTED = 7   /* valid request this build does not implement */
+  DG_EUNSUPPORTED = 7   /* valid request that the library does not implement */
 } dg_status;
 
 typedef struct dg_mesh dg_mesh;     /* geometry, 1D tables, MG hierarchy */
