@@ -162,22 +162,9 @@ __global__ void inv_kernel(int64_t n, const double* __restrict__ d, int64_t peri
     out[k] = 1.0 / d[k % period];
 }
 
-// CG update: x += a p; r_old = r; r -= a q
-__global__ void cg_update_kernel(int64_t n, double a, const double* __restrict__ p,
-                                 const double* __restrict__ q, double* __restrict__ x,
-                                 double* __restrict__ r, double* __restrict__ r_old) {
-  pdl_entry();
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    x[k] += a * p[k];
-    const double rk = r[k];
-    r_old[k] = rk;
-    r[k] = rk - a * q[k];
-  }
-}
-
-// the same update with a = sc[irz] / sc[ipq] read on the device, and this
-// block's partial sum of the new <r, r> (multi_dot_kernel's order and tree)
+// CG update x += a p, r_old = r, r -= a q with a = sc[irz] / sc[ipq] read on
+// the device, and this block's partial sum of the new <r, r>
+// (multi_dot_kernel's order and tree)
 __global__ void __launch_bounds__(kRedThreads)
     cg_update_dev_kernel(int64_t n, const double* __restrict__ sc, int irz, int ipq,
                          const double* __restrict__ p, const double* __restrict__ q,

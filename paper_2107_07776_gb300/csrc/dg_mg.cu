@@ -84,20 +84,6 @@ __global__ void cheb_init_kernel(int64_t n, const T* __restrict__ b, const T* __
     d[k] = rk * inv_theta;
   }
 }
-// x += d; r -= dinv .* t; d = c1 d + c2 r
-template <typename T>
-__global__ void cheb_step_kernel(int64_t n, T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
-                                 const T* __restrict__ t, const T* __restrict__ dinv, T c1, T c2) {
-  pdl_entry();
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const T dk = d[k];
-    x[k] += dk;
-    const T rk = r[k] - dinv[k] * t[k];
-    r[k] = rk;
-    d[k] = c1 * dk + c2 * rk;
-  }
-}
 template <typename T>
 __global__ void add_kernel(int64_t n, const T* __restrict__ d, T* __restrict__ x) {
   pdl_entry();
