@@ -37,6 +37,8 @@ def main(argv=None):
     ap.add_argument("--launches", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="run this kernel variant (0-7) for every operator instead of the tuned choice")
     ap.add_argument("--profile", action="store_true")
     args = ap.parse_args(argv)
 
@@ -51,6 +53,8 @@ def main(argv=None):
     mesh = b.Mesh.from_workload(w)
     if not args.no_autotune:
         b.dg_autotune(mesh.handle)
+    if args.variant is not None:
+        b.dg_mesh_set_variant(mesh.handle, args.variant)
     b.dg_mesh_set_fp64_arith(mesh.handle, 1 if args.precision == "fp64_native" else 0)
     dt = torch.float32 if args.precision == "fp32" else torch.float64
     g = b.GAMMA
