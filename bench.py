@@ -381,8 +381,9 @@ def oracle_step_rate(w, budget_s: float = 15.0, n_small: int = 4):
             "kind": "oracle", "ms_per_step": dt * 1e3,
             "sample": f"{steps} oracle TR-BDF2 steps on the {'x'.join(map(str, ws.n))} mesh of "
                       f"the same workload ({dofs} DoFs; constant operators assembled once in "
-                      f"{setup:.1f} s, not timed; per step: advection assembly and sparse LU "
-                      f"solves to machine precision)"}
+                      f"{setup:.1f} s, not timed; per step: advection assembly on the OpenMP "
+                      f"threads and sparse LU solves to machine precision, which SuperLU runs on "
+                      f"one thread)"}
 
 
 def oracle_apply_rate(w, n_small: int = 16, budget_s: float = 5.0):
