@@ -92,12 +92,21 @@ class Stepper:
     """
 
     def __init__(self, mesh: Mesh, Re: float, c: float = 1e3, g: float = GAMMA,
-                 tol: float = 1e-13, extrapolate: bool = True):
+                 tol: float = 1e-13, extrapolate: bool = True, fixed_point: int = 0,
+                 fixed_point_tol: float = 1e-10):
         self.mesh, self.Re, self.c, self.g, self.tol = mesh, Re, c, g, tol
         # extrapolate=False lags the advecting field (ubar_1 = u^n, ubar_2 =
         # u^{n+g}); the extrapolated fields lose stability near C = 1 on the
         # Taylor-Green test, where the paper's table uses C = 1.63.
         self.extrapolate = extrapolate
+        # fixed_point > 0: the fully nonlinear momentum stages of Section 2
+        # (the advecting field of the implicit advection term is the unknown
+        # itself, found by at most fixed_point Picard iterations that start
+        # from the field above and stop when the relative change of the
+        # iterate drops below fixed_point_tol); the explicit advection term of
+        # stage 1 is then advected by u^n
+        self.fixed_point, self.fixed_point_tol = fixed_point, fixed_point_tol
+        self.fixed_point_iterations = [0, 0]  # of the last step, per stage
         d = mesh.dim
         self.M = mesh.csr("mass_u")
         self.A = mesh.csr("sipg_u")
@@ -165,6 +174,25 @@ class Stepper:
                                x0=None if x0 is None else x0[i])
                          for i in range(self.mesh.dim)])
 
+    def solve_stage(self, co: MomentumCoeffs, ubar0, rhs_of, stage: int):
+        """The momentum predictor of one stage: linear with the advecting
+        field ubar0, or (fixed_point > 0) Picard iterations on the field.
+        rhs_of(ubar) gives the stage's right-hand side for the current field
+        (only the Dirichlet data terms depend on it)."""
+        ubar = ubar0
+        u_new = self.solve_momentum(self.momentum_matrix(co, ubar), rhs_of(ubar))
+        it = 1
+        while it < max(1, self.fixed_point):
+            ubar = u_new
+            u_next = self.solve_momentum(self.momentum_matrix(co, ubar), rhs_of(ubar))
+            change = np.linalg.norm(u_next - u_new) / max(np.linalg.norm(u_next), 1e-300)
+            u_new = u_next
+            it += 1
+            if change < self.fixed_point_tol:
+                break
+        self.fixed_point_iterations[stage] = it
+        return u_new
+
     def pressure_stage(self, ustar, p_old, alpha, tau, x0=None):
         ut_old = self.projection(p_old)
         uss = ustar + tau * ut_old
@@ -186,12 +214,14 @@ class Stepper:
         ub1 = extrapolate_stage1(u, u_hist, g) if self.extrapolate else u
         co1 = MomentumCoeffs(1.0 / (g * dt), 1.0 / (2.0 * Re), 0.5)
         rhs = np.stack([co1.mass * (self.M @ u[i]) for i in range(d)])
-        rhs += self.explicit_rhs([(co1.visc, co1.adv, u, ub1)], p)
-        rhs += self.dirichlet_rhs(co1, ub1, None if uD is None else uD(t + g * dt))
+        # the explicit advection term is advected by ubar_1, or by u^n in the
+        # fully nonlinear form
+        rhs += self.explicit_rhs([(co1.visc, co1.adv, u, u if self.fixed_point else ub1)], p)
         if f is not None:
             fc = 0.5 * (f(t) + f(t + g * dt))
             rhs += np.stack([self.M @ fc[i] for i in range(d)])
-        ustar = self.solve_momentum(self.momentum_matrix(co1, ub1), rhs)
+        uD1 = None if uD is None else uD(t + g * dt)
+        ustar = self.solve_stage(co1, ub1, lambda ub: rhs + self.dirichlet_rhs(co1, ub, uD1), 0)
         # ---- stage 1 pressure (Eqs. helmholtz2a, helmholtz_1) ----
         alpha1 = 1.0 / (c * c * g * g * dt * dt)
         u_g, p_g = self.pressure_stage(ustar, p, alpha1, g * dt)
@@ -200,11 +230,11 @@ class Stepper:
         co2 = MomentumCoeffs(1.0 / ((1.0 - g) * dt), a33 / Re, a33)
         rhs = np.stack([co2.mass * (self.M @ u_g[i]) for i in range(d)])
         rhs += self.explicit_rhs([(a32 / Re, a32, u_g, u_g), (a31 / Re, a31, u, u)], p_g)
-        rhs += self.dirichlet_rhs(co2, ub2, None if uD is None else uD(t + dt))
         if f is not None:
             fc = a31 * f(t) + a32 * f(t + g * dt) + a33 * f(t + dt)
             rhs += np.stack([self.M @ fc[i] for i in range(d)])
-        ustar2 = self.solve_momentum(self.momentum_matrix(co2, ub2), rhs)
+        uD2 = None if uD is None else uD(t + dt)
+        ustar2 = self.solve_stage(co2, ub2, lambda ub: rhs + self.dirichlet_rhs(co2, ub, uD2), 1)
         # ---- stage 2 pressure (Eqs. helmholtz3a, helmholtz_2) ----
         alpha2 = 1.0 / (c * c * (1.0 - g) ** 2 * dt * dt)
         u_new, p_new = self.pressure_stage(ustar2, p_g, alpha2, (1.0 - g) * dt)

@@ -19,18 +19,23 @@ from oracle.dg import Mesh
 from oracle.trbdf2 import GAMMA, Stepper, interpolate, l2_error
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "tg_q2q1_paper.txt")
+GOLD_C3 = os.path.join(os.path.dirname(__file__), "golden", "tg_q2q1_c3_paper.txt")
 
 
-def run_tg(N, k, dt, T, Re, extrapolate=True):
+def run_tg(N, k, dt, T, Re, extrapolate=True, fixed_point=0, its=None):
     m = Mesh(2, [N, N], [0, 0], [2 * math.pi] * 2, [True, True], k)
-    st = Stepper(m, Re, extrapolate=extrapolate)
+    st = Stepper(m, Re, extrapolate=extrapolate, fixed_point=fixed_point, fixed_point_tol=1e-6)
     u = interpolate(m, lambda x, y: W.paper_tg_u(x, y, 0.0, Re))
     p = interpolate(m, lambda x, y: W.paper_tg_p(x, y, 0.0, Re), p_space=True)
     uh = interpolate(m, lambda x, y: W.paper_tg_u(x, y, -(1 - GAMMA) * dt, Re))
     t = 0.0
     pint0 = (st.Mp @ p).sum()
-    for _ in range(int(round(T / dt))):
+    # the C = 3 table's time steps do not divide T: take ceil(T / dt) steps
+    nsteps = int(round(T / dt)) if fixed_point == 0 else math.ceil(T / dt - 1e-9)
+    for _ in range(nsteps):
         u, p, uh = st.step(u, p, uh, t, dt)
+        if its is not None:
+            its.append(tuple(st.fixed_point_iterations))
         t += dt
     e2 = n2 = 0.0
     for i in range(2):
@@ -105,3 +110,45 @@ def test_tg2d_workload_tracks_exact_decay():
         t += w.dt
     err = max(l2_error(m, u[i], lambda x, y, i=i: W.tg2d_u(x, y, t, nu)[i]) for i in range(2))
     assert err < 0.05
+
+
+# ---- fully nonlinear momentum stages (fixed point iterations, Section 2) ----
+def _gold_c3():
+    rows = [l.split() for l in open(GOLD_C3) if l.strip() and not l.startswith("#")]
+    return [(float(a), int(b), float(c), float(d)) for a, b, c, d in rows]
+
+
+@pytest.mark.parametrize("row", [_gold_c3()[0], pytest.param(_gold_c3()[1], marks=pytest.mark.slow)])
+def test_fixed_point_stages_paper_table_c3(row):
+    """At C = 3 the paper iterates the momentum predictors to a fixed point
+    (the implicit advecting field is the unknown itself); the oracle's
+    fully nonlinear stages land in the band of the paper's table."""
+    dt, N, eu_paper, ep_paper = row
+    its = []
+    eu, ep, dp = run_tg(N, 2, dt, 3.2, 100.0, extrapolate=False, fixed_point=200, its=its)
+    assert eu_paper / 2 < eu < eu_paper * 2, eu
+    assert ep_paper / 3 < ep < ep_paper * 3, ep
+    assert abs(dp) < 1e-7
+    assert all(i < 200 for st in its for i in st), its   # converged before the cap
+
+
+def test_fully_nonlinear_form_is_more_accurate_at_c3():
+    """The paper's remark on larger Courant numbers: at C = 3 the fixed-point
+    form is more accurate than both linearised advecting fields."""
+    dt, N = 1.18, 8
+    e_fp = run_tg(N, 2, dt, 3.2, 100.0, extrapolate=False, fixed_point=200)[0]
+    e_lag = run_tg(N, 2, dt, 3.54, 100.0, extrapolate=False)[0]
+    e_ext = run_tg(N, 2, dt, 3.54, 100.0, extrapolate=True)[0]
+    assert e_fp < e_lag and e_fp < e_ext, (e_fp, e_lag, e_ext)
+
+
+def test_fixed_point_of_a_steady_field_is_reached_at_once():
+    """A field with no advection (u = 0, p = 0) is its own fixed point: the
+    second iterate does not change, so the iteration stops after two solves."""
+    m = Mesh(2, [4, 4], [0, 0], [2 * math.pi] * 2, [True, True], 2)
+    st = Stepper(m, 100.0, extrapolate=False, fixed_point=50, fixed_point_tol=1e-12)
+    u = np.zeros((2, m.n_u))
+    p = np.zeros(m.n_p)
+    u1, p1, _ = st.step(u, p, u.copy(), 0.0, 0.1)
+    assert np.abs(u1).max() == 0.0 and np.abs(p1).max() == 0.0
+    assert st.fixed_point_iterations == [2, 2]
