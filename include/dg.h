@@ -146,9 +146,11 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * CTA) of this mesh's operator kernels -- pressure Helmholtz, momentum with
  * and without advection, FP64 and FP32 -- with CUDA events on `stream` and
  * keeps the fastest for later applies.  Candidates: cells per CTA, a
- * register cap, and the face-once form (every face evaluated once into a
+ * register cap, the face-once form (every face evaluated once into a
  * per-mesh flux scratch, then the cells: a different rounding order, the
- * same result to FP64 rounding).  A mesh using the face-once form shares
+ * same result to FP64 rounding) and, for the FP32 3D pressure operator on
+ * two points per direction, two threads per Q1 cell with the cell in
+ * registers (again the same result up to rounding order).  A mesh using the face-once form shares
  * that scratch between its applies, so applies on one tuned mesh from
  * different streams must not overlap.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
@@ -156,11 +158,14 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * report.  Allocates temporary device buffers; synchronous. */
 dg_status dg_autotune(dg_mesh* mesh, void* stream);
 
-/* Sets the operator kernels' tile variant of this mesh by hand (0..6, the
+/* Sets the operator kernels' tile variant of this mesh by hand (0..7, the
  * candidates listed in dg_autotune's report: 0-2 cells per CTA half /
  * default / double, 3-4 default with 96 / 80 registers, 5-6 face-once
- * uncapped / 80 registers) for every operator and precision; a face-once
- * variant allocates the mesh's flux scratch.  Trilinear meshes ignore it. */
+ * uncapped / 80 registers, 7 two threads per Q1 cell -- 3D scalar
+ * operators without advection on two points per direction, in every
+ * precision; other operators run variant 1 instead) for every operator and
+ * precision; a face-once variant allocates the mesh's flux scratch.
+ * Trilinear meshes ignore it. */
 dg_status dg_mesh_set_variant(dg_mesh* mesh, int32_t variant);
 
 /* JSON list of the tuning choices and timings of a mesh ("[]" if untuned),
