@@ -150,8 +150,9 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * per-mesh flux scratch, then the cells: a different rounding order, the
  * same result to FP64 rounding) and, for the FP32 3D pressure operator on
  * two points per direction, two threads per Q1 cell with the cell in
- * registers (again the same result up to rounding order).  A mesh using the face-once form shares
- * that scratch between its applies, so applies on one tuned mesh from
+ * registers (again the same result up to rounding order).  A mesh using
+ * the face-once form shares that scratch between its applies, so applies
+ * on one tuned mesh from
  * different streams must not overlap.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
  * Trilinear meshes use one tile shape per kernel: the call records an empty
