@@ -152,8 +152,7 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * two points per direction, two threads per Q1 cell with the cell in
  * registers (again the same result up to rounding order).  A mesh using
  * the face-once form shares that scratch between its applies, so applies
- * on one tuned mesh from
- * different streams must not overlap.
+ * on one tuned mesh from different streams must not overlap.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
  * Trilinear meshes use one tile shape per kernel: the call records an empty
  * report.  Allocates temporary device buffers; synchronous. */
