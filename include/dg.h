@@ -186,7 +186,9 @@ dg_status dg_autotune_report(const dg_mesh* mesh, char* buf, int64_t size);
  * E_v: unpenalised viscous form -int grad w : grad v + sum_E {{grad w}}:<<v>>
  * E_a: central advective form +int (w x wbar) : grad v - sum_E {{w x wbar}}:<<v>>
  * G:   DG pressure gradient int p div v - sum_E {{p}} [[v]]
- * B_v, B_a: boundary data terms of Eq. rhs1 (SIP and LF with the trace of uD).
+ * B_v, B_a: boundary data terms of Eq. rhs1 (SIP and LF with the trace of uD;
+ *        the LF speed on walls is |ubar . n|, the paper's mirror-state speed
+ *        for tangential data u_D . n = 0, see dg_step_params).
  * All faces of the skeleton take part in E_v, E_a, G (boundary averages are
  * interior traces).  All fields device pointers; u_mass, w[t], wbar[t], uD,
  * ubar, f have n_dofs_u doubles, p has n_dofs_p; rhs must alias none. */
@@ -270,8 +272,14 @@ dg_status dg_solve_stage(dg_solver* solver, const dg_momentum_coeffs* co, double
  * extrapolated advecting fields (linear to t^{n+gamma/2} from u^n and
  * u^{n-1+gamma}; linear to t^{n+1} from u^{n+gamma} and u^n), 0 = lagged
  * (u^n, u^{n+gamma}).  uD_*: Dirichlet data as velocity-layout nodal fields
- * whose wall traces are the data, or NULL (homogeneous).  f_*: forcing at
- * velocity nodes at t^n, t^{n+gamma}, t^{n+1}, or NULL. */
+ * whose wall traces are the data, or NULL (homogeneous).  Walls are
+ * impermeable: the data must be tangential, u_D . n = 0 on every wall
+ * (no-slip walls, moving lids).  There the Lax-Friedrichs speed of the
+ * paper's boundary flux (Section 3: the mirror state 2 u_D - ubar+, speed
+ * max(|ubar+ . n|, |(2 u_D - ubar+) . n|)) is |ubar+ . n|, which is what the
+ * operators use; inflow and outflow data are not supported and are not
+ * checked.  f_*: forcing at velocity nodes at t^n, t^{n+gamma}, t^{n+1}, or
+ * NULL. */
 typedef struct {
   double dt, gamma;
   int32_t extrapolate;

@@ -25,8 +25,10 @@
  *    refinement.
  *  - quadrature: Gauss-Legendre with k+1 points per direction for velocity
  *    and mixed forms, k points for pressure-only forms; faces likewise.
- *  - boundary LF speed lambda = |ubar+ . n|, which equals
- *    max(|ubar+ . n|, |(2 u_D - ubar+) . n|) whenever u_D . n = 0 (walls).
+ *  - boundary LF speed lambda = |ubar+ . n|, which equals the mirror-state
+ *    speed max(|ubar+ . n|, |(2 u_D - ubar+) . n|) whenever u_D . n = 0;
+ *    walls are impermeable (the step refuses data with a normal
+ *    component), so this is the paper's boundary flux wherever it is used.
  *  - boundary averages are interior traces (Section 3, definition of the
  *    average on boundary faces).
  */

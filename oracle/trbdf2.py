@@ -24,7 +24,13 @@ Readings (where the paper is silent or inconsistent):
     weights: (f^n + f^{n+g})/2 in stage 1 and a31 f^n + a32 f^{n+g} + a33
     f^{n+1} in stage 2;
   * Dirichlet data u_D is a velocity-layout nodal field whose boundary
-    traces are the data.
+    traces are the data;
+  * walls are impermeable: u_D . n = 0 on every wall (no-slip walls and
+    moving lids).  There the boundary Lax-Friedrichs speed of the mirror
+    state, max(|ubar+ . n|, |(2 u_D - ubar+) . n|) (Section 3, the flux
+    "taking boundary conditions into account"), equals |ubar+ . n|, the
+    speed the assembled forms use; data with a normal component (inflow
+    or outflow boundaries) is refused rather than given another reading.
 Systems are solved by sparse LU (small) or scipy CG/GMRES to a relative
 residual of 1e-13 (large); mass solves are per-cell dense solves.
 """
@@ -38,7 +44,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .dg import Mesh
+from .dg import Mesh, gauss_legendre, lagrange
 
 GAMMA = 2.0 - math.sqrt(2.0)
 
@@ -82,6 +88,29 @@ def solve(A: sp.spmatrix, b: np.ndarray, spd: bool, tol: float = 1e-13, x0=None,
     if info != 0:
         raise RuntimeError(f"oracle solve did not converge ({info})")
     return x
+
+
+def wall_normal_trace(mesh: Mesh, uD: np.ndarray) -> float:
+    """Largest |u_D . n| over the wall faces of the structured box, from the
+    traces of the nodal field u_D (shape (dim, n_u)).  The walls are the
+    planes x_a = lo_a, hi_a for every mapping built here (the tanh grading
+    keeps them and the sine perturbation vanishes on the boundary), so n =
+    -e_a or +e_a and the normal component is the trace of component a."""
+    d, k = mesh.dim, mesh.degree
+    nodes = gauss_legendre(k + 1)[0]
+    ends = [lagrange(nodes, 0.0)[0], lagrange(nodes, 1.0)[0]]
+    shape = [mesh.n[a] for a in reversed(range(d))] + [k + 1] * d
+    worst = 0.0
+    for a in range(d):
+        if mesh.periodic[a]:
+            continue
+        comp = np.asarray(uD[a]).reshape(shape)  # (cells z,y,x, nodes z,y,x)
+        cax, nax = d - 1 - a, 2 * d - 1 - a
+        for s, l in ((0, ends[0]), (1, ends[1])):
+            layer = np.take(comp, 0 if s == 0 else mesh.n[a] - 1, axis=cax)
+            tr = np.tensordot(layer, l, axes=([nax - 1], [0]))
+            worst = max(worst, float(np.abs(tr).max()))
+    return worst
 
 
 class Stepper:
@@ -201,6 +230,15 @@ class Stepper:
         ut_new = self.projection(p_new)
         return ustar - tau * (ut_new - ut_old), p_new
 
+    def _wall_data(self, uD: np.ndarray) -> np.ndarray:
+        """The Dirichlet data of a stage, after checking that it is
+        tangential on every wall (the impermeable-wall reading above)."""
+        uD = np.asarray(uD)
+        tol = 1e-10 * max(1.0, float(np.abs(uD).max()))
+        if self.walls and wall_normal_trace(self.mesh, uD) > tol:
+            raise ValueError("Dirichlet data must satisfy u_D . n = 0 on the walls")
+        return uD
+
     # the step ----------------------------------------------------------
     def step(self, u: np.ndarray, p: np.ndarray, u_hist: np.ndarray, t: float, dt: float,
              uD: Optional[Callable[[float], np.ndarray]] = None,
@@ -220,7 +258,7 @@ class Stepper:
         if f is not None:
             fc = 0.5 * (f(t) + f(t + g * dt))
             rhs += np.stack([self.M @ fc[i] for i in range(d)])
-        uD1 = None if uD is None else uD(t + g * dt)
+        uD1 = None if uD is None else self._wall_data(uD(t + g * dt))
         ustar = self.solve_stage(co1, ub1, lambda ub: rhs + self.dirichlet_rhs(co1, ub, uD1), 0)
         # ---- stage 1 pressure (Eqs. helmholtz2a, helmholtz_1) ----
         alpha1 = 1.0 / (c * c * g * g * dt * dt)
@@ -233,7 +271,7 @@ class Stepper:
         if f is not None:
             fc = a31 * f(t) + a32 * f(t + g * dt) + a33 * f(t + dt)
             rhs += np.stack([self.M @ fc[i] for i in range(d)])
-        uD2 = None if uD is None else uD(t + dt)
+        uD2 = None if uD is None else self._wall_data(uD(t + dt))
         ustar2 = self.solve_stage(co2, ub2, lambda ub: rhs + self.dirichlet_rhs(co2, ub, uD2), 1)
         # ---- stage 2 pressure (Eqs. helmholtz3a, helmholtz_2) ----
         alpha2 = 1.0 / (c * c * (1.0 - g) ** 2 * dt * dt)

@@ -105,7 +105,7 @@ def test_tg2d_workload_steps_match_oracle():
 @pytest.mark.parametrize("extrapolate", [1, 0])
 def test_walled_step_with_data_and_forcing_matches_oracle(extrapolate, geom):
     """3D, periodic in x, Dirichlet walls in y and z with time-dependent
-    wall data and forcing, on a tanh-graded mesh (Q2) or on sine-perturbed
+    tangential wall data and forcing, on a tanh-graded mesh (Q2) or on sine-perturbed
     trilinear cells (Q3): 3 steps compared."""
     from paper_2107_07776_gb300 import binding as b
     n, lo, hi, per = (3, 4, 3), (0, 0, 0), (2.0, 1.0, 1.0), (True, False, False)
@@ -113,8 +113,13 @@ def test_walled_step_with_data_and_forcing_matches_oracle(extrapolate, geom):
     gm = b.Mesh(3, n, lo, hi, per, k, mp, tuple(prm))
     om = OMesh(3, list(n), list(lo), list(hi), list(per), k, map=mp, map_param=prm)
     X = om.node_coords()
-    uD = lambda t: np.stack([np.sin(X[1] + t) * (1 + X[2]), 0.3 * np.cos(X[0] * math.pi),
-                             0.1 * X[1] * (1 + t)])
+    # impermeable walls (u_D . n = 0): u_y vanishes on the y walls and u_z on
+    # the z walls, and both traces are exact in the nodal space (degree <= 2
+    # per reference direction on either mapping), while the tangential
+    # components vary along the walls
+    uD = lambda t: np.stack([np.sin(X[1] + t) * (1 + X[2]),
+                             0.3 * X[1] * (1 - X[1]) * (1 + 0.5 * X[0]) * (1 + t),
+                             0.1 * X[2] * (1 - X[2]) * (1 + X[1]) * (1 + t)])
     f = lambda t: (1 + t) * W.mms_forcing(*X)
     rng = np.random.default_rng(3)
     u0 = rng.standard_normal((3, om.n_u)) * 0.1

@@ -217,3 +217,96 @@ def test_graded_mesh_is_tanh_law():
     eta = np.arange(n + 1) / n
     ycut = 0.5 * (1 - np.tanh(beta * (1 - 2 * eta)) / math.tanh(beta))
     np.testing.assert_allclose(vol, 0.5 * np.diff(ycut), rtol=1e-13)
+
+
+# --------------------------------------------------------- LF dissipation (Eq. trilinear)
+def _two_cells(dim, k=2, hx=1.0):
+    n = [2, 1, 1][:dim]
+    return Mesh(dim, n, [0] * dim, [2 * hx, 1.0, 1.0][:dim], [False] * dim, k)
+
+
+def _piecewise_field(m, left, right):
+    """Advecting field constant on each of the two cells (x-component only):
+    left on cell 0, right on cell 1, zero y/z components."""
+    ub = np.zeros((m.dim, m.n_u))
+    ub[0, : m.nb_u] = left
+    ub[0, m.nb_u:] = right
+    return ub.reshape(-1)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_lf_flux_self_term_two_cells(dim):
+    """u = 1 on the left unit cell, 0 on the right, ubar = (a, 0) left and
+    (b, 0) right (|a| != |b|).  With the test function on the left cell:
+    the volume term vanishes (grad v = 0); the interior face at x = 1
+    (outward normal +x) gives 1/2 u ubar.n + lambda/2 [[u]] with lambda =
+    max(|a|, |b|); the wall x = 0 gives lambda_wall u v with lambda_wall =
+    |ubar.n| = |a|; the other walls have ubar.n = 0.  Face measures are 1:
+        u^T C u = a/2 + max(|a|, |b|)/2 + |a|.
+    lambda instead of lambda/2 on interior faces, min for max, or another
+    wall speed all change the value."""
+    a, b = 0.3, -0.8
+    m = _two_cells(dim)
+    C = m.csr("adv_u", _piecewise_field(m, a, b))
+    u = np.zeros(m.n_u)
+    u[: m.nb_u] = 1.0
+    assert abs(u @ (C @ u) - (a / 2 + max(abs(a), abs(b)) / 2 + abs(a))) < 1e-13
+    # swap the speeds: the max now comes from the row cell's own side
+    C2 = m.csr("adv_u", _piecewise_field(m, b, a))
+    assert abs(u @ (C2 @ u) - (b / 2 + max(abs(a), abs(b)) / 2 + abs(b))) < 1e-13
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_lf_flux_coupling_term_two_cells(dim):
+    """Row of the right cell (test v = 1 there), trial u = 1 on the left cell:
+    only the shared face couples them.  From the right cell the outward
+    normal is -x, the neighbour's flux is 1/2 u_L (ubar_L.n) = -a/2 and the
+    dissipation -lambda/2 u_L with lambda = max(|a|, |b|):
+        v^T C u = -a/2 - max(|a|, |b|)/2."""
+    a, b = 0.3, -0.8
+    m = _two_cells(dim)
+    C = m.csr("adv_u", _piecewise_field(m, a, b))
+    u = np.zeros(m.n_u)
+    u[: m.nb_u] = 1.0
+    v = np.zeros(m.n_u)
+    v[m.nb_u:] = 1.0
+    assert abs(v @ (C @ u) - (-a / 2 - max(abs(a), abs(b)) / 2)) < 1e-13
+
+
+def test_lf_wall_speed_uses_normal_component():
+    """One unit square, ubar = (a, c) constant, u = v = 1: the volume term
+    vanishes and each wall contributes |ubar.n| times its length:
+    2|a| + 2|c|."""
+    a, c = 0.45, -0.2
+    m = Mesh(2, [1, 1], [0, 0], [1, 1], [False, False], 2)
+    ub = np.concatenate([np.full(m.n_u, a), np.full(m.n_u, c)])
+    u = np.ones(m.n_u)
+    assert abs(u @ (m.csr("adv_u", ub) @ u) - (2 * abs(a) + 2 * abs(c))) < 1e-13
+
+
+# --------------------------------------------------------- pressure penalty (Eq. weakform_p_1)
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("hx", [1.0, 0.5])
+def test_pressure_penalty_jump_two_cells(k, hx):
+    """p = 1 on the left of two cells of width hx (height 1), 0 on the right:
+    no gradients, so p^T K p is the penalty of the shared face alone,
+    C_p |Gamma| with C_p = (sigma+ + sigma-)/2, sigma = k^2 |Gamma|/|K| and k
+    the VELOCITY degree: k^2 / hx.  The pressure degree (k-1)^2 or the
+    velocity penalty (k+1)^2 give other values.  The coupling entry is
+    -k^2 / hx, and homogeneous Neumann walls add nothing."""
+    m = Mesh(2, [2, 1], [0, 0], [2 * hx, 1.0], [False, False], k)
+    p = np.zeros(m.n_p)
+    p[: m.nb_p] = 1.0
+    q = np.zeros(m.n_p)
+    q[m.nb_p:] = 1.0
+    K = m.csr("sipg_p")
+    assert abs(p @ (K @ p) - k * k / hx) < 1e-12
+    assert abs(q @ (K @ p) + k * k / hx) < 1e-12
+
+
+def test_pressure_penalty_jump_3d():
+    """The same in 3D with unit cubes: k^2 |Gamma|^2 / |K| = 4."""
+    m = Mesh(3, [2, 1, 1], [0, 0, 0], [2, 1, 1], [False] * 3, 2)
+    p = np.zeros(m.n_p)
+    p[: m.nb_p] = 1.0
+    assert abs(p @ (m.csr("sipg_p") @ p) - 4.0) < 1e-12

@@ -152,3 +152,35 @@ def test_fixed_point_of_a_steady_field_is_reached_at_once():
     u1, p1, _ = st.step(u, p, u.copy(), 0.0, 0.1)
     assert np.abs(u1).max() == 0.0 and np.abs(p1).max() == 0.0
     assert st.fixed_point_iterations == [2, 2]
+
+
+# ------------------------------------------------------ impermeable walls
+def test_wall_normal_trace_of_polynomial_data():
+    """Traces of a nodal field at the walls: u_y = y + 2 and u_z = 3 z - 1 on
+    [0,2]x[0,1]x[0,1.5] (x periodic) are exact in Q2, so the largest normal
+    trace is max(|2|, |3|, |-1|, |3.5|) = 3.5 (u_y at y = 1 is 3, u_z at
+    z = 1.5 is 3.5)."""
+    from oracle.trbdf2 import wall_normal_trace
+    m = Mesh(3, [2, 3, 2], [0, 0, 0], [2.0, 1.0, 1.5], [True, False, False], 2)
+    x, y, z = m.node_coords()
+    uD = np.stack([10.0 + 0 * x, y + 2.0, 3.0 * z - 1.0])
+    assert abs(wall_normal_trace(m, uD) - 3.5) < 1e-12
+    # the x component is tangential to every wall of this mesh
+    uD[1] = y * (1 - y)
+    uD[2] = z * (1.5 - z)
+    assert wall_normal_trace(m, uD) < 1e-13
+
+
+def test_stepper_refuses_data_with_a_normal_component():
+    """The boundary Lax-Friedrichs speed is |ubar+ . n|, the mirror state's
+    max(|ubar+ . n|, |(2 u_D - ubar+) . n|) when u_D . n = 0: data with a
+    normal component is refused, tangential data is accepted."""
+    m = Mesh(2, [2, 2], [0, 0], [1.0, 1.0], [True, False], 2)
+    st = Stepper(m, 10.0, c=10.0)
+    x, y = m.node_coords()
+    u = np.zeros((2, m.n_u))
+    p = np.zeros(m.n_p)
+    with pytest.raises(ValueError):
+        st.step(u, p, u, 0.0, 0.01, uD=lambda t: np.stack([0 * x, 0.1 + 0 * y]))
+    un, _, _ = st.step(u, p, u, 0.0, 0.01, uD=lambda t: np.stack([0.1 + 0 * x, y * (1 - y)]))
+    assert np.abs(un).max() > 0.0
