@@ -19,7 +19,8 @@
  *    residuals synchronise that stream before returning.  The solver calls
  *    (dg_solve_stage, trbdf2_step, dg_solver_set_history) run on the solver's
  *    own non-blocking stream instead: each first waits for the work enqueued
- *    on the legacy default stream (and so on every blocking stream) and
+ *    on the caller's stream -- the one named by dg_solver_set_stream, by
+ *    default the legacy default stream (and so every blocking stream) -- and
  *    synchronises before it returns.  Kernels are launched with programmatic
  *    dependent launch on non-default streams (DG_PDL=0 in the environment
  *    turns it off).
@@ -352,6 +353,14 @@ dg_status dg_mlp_forward_backward(int64_t M, int32_t n_in, int32_t hidden, int32
 dg_status dg_mlp_infer(int64_t M, int32_t n_in, int32_t hidden, int32_t n_out,
                        const float* weights, const float* X, float* Y, void* stream);
 
+/* The caller's stream (a cudaStream_t; NULL = the legacy default stream, the
+ * default): every later solver call (dg_solve_stage, trbdf2_step,
+ * dg_solver_set_history) first waits for the work enqueued on it, so inputs
+ * filled on a non-blocking stream (a framework's side stream, a per-thread
+ * default stream) are complete before the solver reads them.  The solver
+ * still computes on its own stream and synchronises it before returning. */
+dg_status dg_solver_set_stream(dg_solver* solver, void* stream);
+
 /* Set (device pointer, n_dofs_u) or clear (NULL) the stored u^{n-1+gamma}. */
 dg_status dg_solver_set_history(dg_solver* solver, const double* u_hist);
 
@@ -381,8 +390,9 @@ dg_status dg_solver_load(dg_solver* solver, const char* path);
  * that loads the library, held until exit), so systems with more than
  * 262144 pressure DoFs are rejected with DG_EINVAL.  The first call on a
  * device looks up that array's device address; make it before any stream
- * capture.  Calls share the array: calls that overlap on the GPU race and
- * must be serialised by the caller.  info (host) may be NULL. */
+ * capture.  The mesh's device must be current (DG_EINVAL otherwise).  Calls
+ * share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  info (host) may be NULL. */
 dg_status dg_solve_helmholtz_noalloc(dg_mesh* mesh, double alpha, const double* rhs, double* x,
                                      const dg_solve_opts* opts, dg_solve_info* info,
                                      void* stream);

@@ -99,6 +99,7 @@ SIGNATURES = {
     "dg_solve_stage": (ctypes.c_int, [c_void_p, P(dg_momentum_coeffs), ctypes.c_double, c_void_p, c_void_p, c_void_p, P(dg_solve_opts), P(dg_solve_info)]),
     "trbdf2_step": (ctypes.c_int, [c_void_p, P(dg_step_params), c_void_p, c_void_p, P(dg_solve_info)]),
     "dg_solver_set_history": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_solver_set_stream": (ctypes.c_int, [c_void_p, c_void_p]),
     "dg_solver_set_tracing": (ctypes.c_int, [c_void_p, ctypes.c_int32]),
     "dg_solver_get_trace": (ctypes.c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_int64)]),
     "dg_guess_configure": (ctypes.c_int, [c_void_p, P(dg_guess_opts)]),
@@ -276,6 +277,10 @@ def trbdf2_step(solver: int, params: dg_step_params, u, p):
 
 def dg_solver_set_history(solver: int, u_hist) -> None:
     check(lib().dg_solver_set_history(solver, ptr(u_hist)), "dg_solver_set_history")
+
+
+def dg_solver_set_stream(solver: int, stream=None) -> None:
+    check(lib().dg_solver_set_stream(solver, stream_ptr(stream)), "dg_solver_set_stream")
 
 
 def dg_solver_set_tracing(solver: int, on: int) -> None:

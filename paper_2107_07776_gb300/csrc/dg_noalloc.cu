@@ -12,7 +12,8 @@
 // name as a device address (it is a host-side stand-in), so the first call on
 // each device looks the address up with cudaGetSymbolAddress while that
 // device is current and caches it; make that first call before any stream
-// capture.  Every call shares the array and it keeps the previous call's
+// capture.  The mesh's device must be the current device (DG_EINVAL
+// otherwise), so the scratch, the mesh and the caller's arrays are on one GPU.  Every call shares the array and it keeps the previous call's
 // contents: each solve writes every scratch value before reading it, so
 // nothing needs clearing, but calls whose work overlaps on the GPU (other
 // streams, other host threads) race on the array and must be serialised by
@@ -35,12 +36,18 @@ __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
 
-// device address of the scratch array on the current device (set-up once per
-// device, with that device current)
-dg_status scratch_address(double** out) {
+// device address of the scratch array on the mesh's device, which must be
+// the current one (set-up once per device, with that device current)
+dg_status scratch_address(int mesh_device, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return dg::cuda_fail(e, "dg_solve_helmholtz_noalloc: cudaGetDevice");
+  if (dev != mesh_device) {
+    dg::set_error("dg_solve_helmholtz_noalloc: the current device (" + std::to_string(dev) +
+                  ") is not the mesh's device (" + std::to_string(mesh_device) +
+                  "); make the mesh's device current first");
+    return DG_EINVAL;
+  }
   if (dev < 0 || dev >= kMaxDevices) {
     dg::set_error("dg_solve_helmholtz_noalloc: device index out of range");
     return DG_EINVAL;
@@ -92,7 +99,7 @@ extern "C" dg_status dg_solve_helmholtz_noalloc(dg_mesh* m, double alpha, const 
     return DG_EINVAL;
   }
   double* base = nullptr;
-  dg_status st = scratch_address(&base);
+  dg_status st = scratch_address(m->device, &base);
   if (st != DG_OK) {
     info->status = st;
     return st;
@@ -116,7 +123,11 @@ extern "C" dg_status dg_solve_helmholtz_noalloc(dg_mesh* m, double alpha, const 
   const LinOp* P = nullptr;
   if (o->guess == DG_GUESS_ZERO) {
     cudaError_t e = cudaMemsetAsync(x, 0, sizeof(double) * n, s);
-    if (e != cudaSuccess) return cuda_fail(e, "dg_solve_helmholtz_noalloc");
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "dg_solve_helmholtz_noalloc");
+      info->status = st;
+      return st;
+    }
   }
   if (o->precond == DG_PC_JACOBI) {
     st = poisson_diagonal(m, alpha, dinv, s);

@@ -15,9 +15,11 @@ struct dg_solver {
   dg_mesh* mesh = nullptr;
   double Re = 1.0, c = 1e3;
   // the solver's own non-blocking stream: every call first waits for the work
-  // the caller has enqueued on the legacy default stream (join_caller) and
+  // the caller has enqueued on the caller's stream (join_caller; the legacy
+  // default stream unless dg_solver_set_stream named another) and
   // synchronises this stream before it returns
   cudaStream_t stream = nullptr;
+  cudaStream_t caller = nullptr;  // nullptr: cudaStreamLegacy
   cudaEvent_t ev_in = nullptr;
   dg::VecOps vo;
   int64_t nu = 0, np = 0, nus = 0;  // velocity (all comps), pressure, one component
@@ -49,7 +51,7 @@ namespace dg {
 namespace {
 
 dg_status join_caller(dg_solver* s) {
-  DG_CUDA(cudaEventRecord(s->ev_in, cudaStreamLegacy));
+  DG_CUDA(cudaEventRecord(s->ev_in, s->caller ? s->caller : cudaStreamLegacy));
   DG_CUDA(cudaStreamWaitEvent(s->stream, s->ev_in, 0));
   return DG_OK;
 }
@@ -462,6 +464,15 @@ dg_status dg_solve_stage(dg_solver* s, const dg_momentum_coeffs* co, double alph
   if (st == DG_ETIMEOUT) set_error("dg_solve_stage: wall-clock limit reached");
   info->status = st;
   return st;
+}
+
+dg_status dg_solver_set_stream(dg_solver* s, void* stream) {
+  if (!s) {
+    set_error("dg_solver_set_stream: null solver");
+    return DG_EINVAL;
+  }
+  s->caller = as_stream(stream);
+  return DG_OK;
 }
 
 dg_status dg_solver_set_history(dg_solver* s, const double* u_hist) {

@@ -101,6 +101,43 @@ def test_tg2d_workload_steps_match_oracle():
         b.dg_solver_destroy(s)
 
 
+def test_step_waits_for_inputs_filled_on_the_callers_stream():
+    """u, p and the history are filled on a non-blocking torch stream behind
+    a ~25 ms spin, and the solver is told that stream (dg_solver_set_stream):
+    its calls must wait for those copies, and the first two steps still
+    match the oracle."""
+    from paper_2107_07776_gb300 import binding as b
+    w = W.TG2D
+    gm = b.Mesh.from_workload(w)
+    om = OMesh(2, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree)
+    nu = 1.0 / w.Re
+    u0 = interpolate(om, lambda x, y: W.tg2d_u(x, y, 0.0, nu)).reshape(-1)
+    p0 = interpolate(om, lambda x, y: W.tg2d_p(x, y, 0.0, nu), p_space=True)
+    uh0 = interpolate(om, lambda x, y: W.tg2d_u(x, y, -(1 - GAMMA) * w.dt, nu)).reshape(-1)
+    hosts = [torch.tensor(v).pin_memory() for v in (u0, p0, uh0)]
+    u, p, uh = (torch.full(h.shape, float("nan"), dtype=torch.float64, device="cuda")
+                for h in hosts)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    s = b.dg_solver_create(gm.handle, w.Re, w.c)
+    try:
+        b.dg_solver_set_stream(s, side)
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(50_000_000)
+            for d, h in zip((u, p, uh), hosts):
+                d.copy_(h, non_blocking=True)
+        b.dg_solver_set_history(s, uh)
+        st = Stepper(om, w.Re, c=w.c)
+        ou, op, ouh = u0.reshape(2, -1), p0, uh0.reshape(2, -1)
+        for n in range(2):
+            b.trbdf2_step(s, step_params(b, w.dt), u, p)
+            ou, op, ouh = st.step(ou, op, ouh, n * w.dt, w.dt)
+            assert rel_l2(u.cpu().numpy(), ou.reshape(-1)) < 1e-8, n
+            assert rel_l2(p.cpu().numpy(), op) < 1e-8, n
+    finally:
+        b.dg_solver_destroy(s)
+
+
 @pytest.mark.parametrize("geom", ["graded", "trilinear"])
 @pytest.mark.parametrize("extrapolate", [1, 0])
 def test_walled_step_with_data_and_forcing_matches_oracle(extrapolate, geom):
