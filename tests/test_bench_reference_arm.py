@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.mark.slow
 def test_reference_arm_prints_one_contract_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                          "--oracle-budget", "2"],
                          cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
@@ -23,9 +24,14 @@ def test_reference_arm_prints_one_contract_line():
     assert d["unit"] == "GDoF/s" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["config"]["workload"].startswith("tgv32")
+    # the mesh the oracle ran (a sample of the channel workload), measured
+    # there: no extrapolation to the benchmark's size
+    assert d["config"]["workload"].startswith("channel") and "sample" in d["config"]["workload"]
+    assert d["ms_per_step"] == pytest.approx(d["cpu_baseline"]["ms_per_step"])
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    # the assembled momentum apply at the full 32^3 Taylor-Green size
+    assert cb["apply"]["value"] > 0 and "32x32x32" in cb["apply"]["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

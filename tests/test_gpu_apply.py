@@ -250,6 +250,57 @@ def test_full_size_workload_sampled_cells(wname, fp64_arith):
         assert rel_err(yu[i][cells].reshape(-1), ref) < 1e-12
 
 
+@pytest.mark.parametrize("tuning", ["autotune", 5, 6, 7])
+@pytest.mark.parametrize("wname", ["tgv32", "channel"])
+def test_full_size_benchmark_variants_sampled_cells(wname, tuning):
+    """The kernels the benchmark times, at full size: after dg_autotune (the
+    benchmark's own call) or with the face-once variants (5, 6: every face's
+    flux once into the mesh's scratch, then the cells) and the
+    two-threads-per-Q1-cell variant (7) forced.  64 sampled cells of the
+    float-float FP64 applies at 1e-12, and of the FP32 Poisson apply (the
+    multigrid's finest operator) at 2e-5, against the oracle's rows."""
+    from paper_2107_07776_gb300 import binding as b
+    w = W.WORKLOADS[wname]
+    gm = b.Mesh.from_workload(w)
+    if tuning == "autotune":
+        b.dg_autotune(gm.handle)
+        assert b.dg_autotune_report(gm.handle) != "[]"
+    else:
+        b.dg_mesh_set_variant(gm.handle, tuning)
+    om = OMesh(w.dim, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree,
+               map=w.map, map_param=list(w.map_param))
+    rng = np.random.default_rng(17)
+    N = om.n_cells
+    n0, n1 = w.n[0], w.n[1]
+    cells = np.unique(np.concatenate([[0, N - 1, n0 - 1, n0 * (n1 - 1), N - n0],
+                                      rng.integers(0, N, 59)]))
+    alpha = 1.0 / (w.c ** 2 * (b.GAMMA * w.dt) ** 2)
+    xp = W.random_vector(om.n_p, 21)
+    refp = alpha * om.assemble("mass_p", cells=cells).apply(xp) + \
+        om.assemble("sipg_p", cells=cells).apply(xp)
+    y = torch.empty(om.n_p, dtype=torch.float64, device="cuda")
+    b.dg_apply_poisson(gm.handle, alpha, dev(xp), y)
+    assert rel_err(y.cpu().numpy().reshape(N, -1)[cells].reshape(-1), refp) < 1e-12
+    y32 = torch.empty(om.n_p, dtype=torch.float32, device="cuda")
+    b.dg_apply_poisson_f32(gm.handle, alpha, torch.tensor(xp, dtype=torch.float32,
+                                                          device="cuda"), y32)
+    assert rel_err(y32.double().cpu().numpy().reshape(N, -1)[cells].reshape(-1), refp) < 2e-5
+    X = gm.node_coords(0).cpu().numpy()
+    ub = W.initial_state(w, X, gm.node_coords(1).cpu().numpy())[0].reshape(-1)
+    xu = W.random_vector(3 * om.n_u, 22)
+    mass, visc, adv = 1.0 / (b.GAMMA * w.dt), 1.0 / (2 * w.Re), 0.5
+    yu = torch.empty(3 * om.n_u, dtype=torch.float64, device="cuda")
+    b.dg_apply_momentum(gm.handle, b.momentum_coeffs(mass, visc, adv), dev(ub), dev(xu), yu)
+    yu = yu.cpu().numpy().reshape(3, N, -1)
+    Mb = om.assemble("mass_u", cells=cells)
+    Ab = om.assemble("sipg_u", cells=cells)
+    Cb = om.assemble("adv_u", ub, cells=cells)
+    for i in range(3):
+        xi = xu[i * om.n_u:(i + 1) * om.n_u]
+        ref = mass * Mb.apply(xi) + visc * Ab.apply(xi) + adv * Cb.apply(xi)
+        assert rel_err(yu[i][cells].reshape(-1), ref) < 1e-12
+
+
 def test_bad_arguments_are_rejected():
     from paper_2107_07776_gb300 import binding as b
     gm, om = meshes(CASES[0])

@@ -101,6 +101,46 @@ def test_tg2d_workload_steps_match_oracle():
         b.dg_solver_destroy(s)
 
 
+@pytest.mark.parametrize("tuning", ["autotune", 6, 7])
+def test_periodic_3d_taylor_green_benchmark_path_matches_oracle(tuning):
+    """The benchmark's solver path on the 3D periodic Taylor-Green vortex
+    (Section 4.1's Taylor-Green case; 32^3 in the benchmark, 4^3 here):
+    Q2/Q1, an autotuned (or face-once / two-threads-per-Q1-cell) mesh, the
+    FP32 multigrid Helmholtz preconditioner and the learned initial guess
+    (training on, both nets), 6 steps each compared with the oracle.  Both
+    sides solve to 1e-13, so the mixed-precision preconditioner and the
+    guess change the path, not the answer (1e-8 relative L2)."""
+    from paper_2107_07776_gb300 import binding as b
+    w = W.TGV32.scaled((4, 4, 4), Re=400.0, dt=0.02)
+    gm = b.Mesh.from_workload(w)
+    if tuning == "autotune":
+        b.dg_autotune(gm.handle)
+    else:
+        b.dg_mesh_set_variant(gm.handle, tuning)
+    om = OMesh(3, list(w.n), list(w.lo), list(w.hi), list(w.periodic), w.degree)
+    X, Xp = om.node_coords(), om.node_coords(True)
+    u0, p0 = W.initial_state(w, X, Xp)
+    st = Stepper(om, w.Re, c=w.c)
+    s = b.dg_solver_create(gm.handle, w.Re, w.c)
+    try:
+        b.dg_guess_configure(s, enable=1, train=1, systems=3)
+        u, p = dev(u0.reshape(-1)), dev(p0)
+        ou, op, ouh = u0, p0, u0
+        prm = step_params(b, w.dt)
+        prm.mom = opts(b, b.DG_SYS_MOMENTUM, guess=b.DG_GUESS_LEARNED)
+        prm.helm = opts(b, b.DG_SYS_HELMHOLTZ, precond=b.DG_PC_MG_FP32,
+                        guess=b.DG_GUESS_LEARNED)
+        for n in range(6):
+            info = b.trbdf2_step(s, prm, u, p)
+            assert all(i.status == 0 for i in info)
+            ou, op, ouh = st.step(ou, op, ouh, n * w.dt, w.dt)
+            assert rel_l2(u.cpu().numpy(), ou.reshape(-1)) < 1e-8, n
+            assert rel_l2(p.cpu().numpy(), op) < 1e-8, n
+        assert b.dg_guess_get_stats(s).train_steps > 0
+    finally:
+        b.dg_solver_destroy(s)
+
+
 def test_step_waits_for_inputs_filled_on_the_callers_stream():
     """u, p and the history are filled on a non-blocking torch stream behind
     a ~25 ms spin, and the solver is told that stream (dg_solver_set_stream):
