@@ -290,7 +290,24 @@ typedef struct {
   const double* f_ng;
   const double* f_n1;
   dg_solve_opts mom, helm;
+  /* Fully nonlinear momentum stages (Section 2, the fixed-point alternative
+   * to the linearised advecting fields, needed at larger Courant numbers):
+   * fixed_point <= 1 takes one linear solve per stage with the advecting
+   * field above; fixed_point = K > 1 takes at most K Picard solves, each with
+   * the previous solve's velocity as advecting field (the first one starts
+   * from the field above), stopping once the relative 2-norm change of the
+   * iterate ||u_k - u_{k-1}|| / ||u_k|| drops below fixed_point_tol.  The
+   * explicit advection term of stage 1 is then advected by u^n, as in the
+   * fully implicit trapezoidal stage.  The stage's dg_solve_info sums the
+   * Krylov iterations of its Picard solves (res0 of the first, res_final of
+   * the last); dg_solver_get_fixed_point gives the Picard counts. */
+  int32_t fixed_point;
+  double fixed_point_tol;
 } dg_step_params;
+
+/* Picard solves taken by each momentum stage of the last trbdf2_step
+ * (iterations[0] stage 1, [1] stage 2; 1 without fixed-point iterations). */
+dg_status dg_solver_get_fixed_point(const dg_solver* solver, int32_t iterations[2]);
 
 /* One TR-BDF2 step (Section 2, Eqs. first_stage ... helmholtz3a; algebraic
  * form of Section 3): u (n_dofs_u) in u^n, out u^{n+1}; p (n_dofs_p) in p^n,

@@ -122,8 +122,11 @@ class Stepper:
 
     def __init__(self, mesh: Mesh, Re: float, c: float = 1e3, g: float = GAMMA,
                  tol: float = 1e-13, extrapolate: bool = True, fixed_point: int = 0,
-                 fixed_point_tol: float = 1e-10):
+                 fixed_point_tol: float = 1e-10, direct_max: int = 60000):
         self.mesh, self.Re, self.c, self.g, self.tol = mesh, Re, c, g, tol
+        # systems up to direct_max unknowns are solved by sparse LU, larger
+        # ones by Jacobi-preconditioned CG / GMRES to the relative residual tol
+        self.direct_max = direct_max
         # extrapolate=False lags the advecting field (ubar_1 = u^n, ubar_2 =
         # u^{n+g}); the extrapolated fields lose stability near C = 1 on the
         # Taylor-Green test, where the paper's table uses C = 1.63.
@@ -200,7 +203,7 @@ class Stepper:
 
     def solve_momentum(self, Amat, rhs, x0=None):
         return np.stack([solve(Amat, rhs[i], spd=False, tol=self.tol,
-                               x0=None if x0 is None else x0[i])
+                               x0=None if x0 is None else x0[i], direct_max=self.direct_max)
                          for i in range(self.mesh.dim)])
 
     def solve_stage(self, co: MomentumCoeffs, ubar0, rhs_of, stage: int):
@@ -226,7 +229,8 @@ class Stepper:
         ut_old = self.projection(p_old)
         uss = ustar + tau * ut_old
         rhs = self.pressure_rhs(uss, p_old, alpha, tau)
-        p_new = solve(self.helmholtz_matrix(alpha), rhs, spd=True, tol=self.tol, x0=x0)
+        p_new = solve(self.helmholtz_matrix(alpha), rhs, spd=True, tol=self.tol, x0=x0,
+                      direct_max=self.direct_max)
         ut_new = self.projection(p_new)
         return ustar - tau * (ut_new - ut_old), p_new
 

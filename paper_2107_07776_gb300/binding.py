@@ -72,7 +72,8 @@ class dg_step_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("extrapolate", ctypes.c_int32), ("uD_stage1", c_void_p),
                 ("uD_stage2", c_void_p), ("f_n", c_void_p), ("f_ng", c_void_p),
-                ("f_n1", c_void_p), ("mom", dg_solve_opts), ("helm", dg_solve_opts)]
+                ("f_n1", c_void_p), ("mom", dg_solve_opts), ("helm", dg_solve_opts),
+                ("fixed_point", ctypes.c_int32), ("fixed_point_tol", ctypes.c_double)]
 
 
 # name -> (restype, argtypes); the list mirrors include/dg.h
@@ -100,6 +101,7 @@ SIGNATURES = {
     "trbdf2_step": (ctypes.c_int, [c_void_p, P(dg_step_params), c_void_p, c_void_p, P(dg_solve_info)]),
     "dg_solver_set_history": (ctypes.c_int, [c_void_p, c_void_p]),
     "dg_solver_set_stream": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_solver_get_fixed_point": (ctypes.c_int, [c_void_p, P(ctypes.c_int32)]),
     "dg_solver_set_tracing": (ctypes.c_int, [c_void_p, ctypes.c_int32]),
     "dg_solver_get_trace": (ctypes.c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_int64)]),
     "dg_guess_configure": (ctypes.c_int, [c_void_p, P(dg_guess_opts)]),
@@ -281,6 +283,12 @@ def dg_solver_set_history(solver: int, u_hist) -> None:
 
 def dg_solver_set_stream(solver: int, stream=None) -> None:
     check(lib().dg_solver_set_stream(solver, stream_ptr(stream)), "dg_solver_set_stream")
+
+
+def dg_solver_get_fixed_point(solver: int):
+    it = (ctypes.c_int32 * 2)()
+    check(lib().dg_solver_get_fixed_point(solver, it), "dg_solver_get_fixed_point")
+    return [it[0], it[1]]
 
 
 def dg_solver_set_tracing(solver: int, on: int) -> None:

@@ -2,6 +2,7 @@
 // first_stage, helmholtz2a, second_stage, helmholtz3a; algebraic form at the
 // end of Section 3).  Every vector operation of the step runs in the
 // library's kernels on the solver's stream; the host sequences them.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +37,7 @@ struct dg_solver {
          *rhs_u = nullptr, *u_g = nullptr, *u_hist = nullptr, *fcomb = nullptr;
   double *rhs_p = nullptr, *p_g = nullptr;
   bool has_hist = false;
+  int fp_iters[2] = {1, 1};  // Picard solves of the last step's momentum stages
   std::vector<void*> allocs;
   dg::MultiGrid<float>* mg32 = nullptr;   // built on first use
   dg::MultiGrid<double>* mg64 = nullptr;
@@ -358,12 +360,69 @@ dg_status finish_guess(dg_solver* s, int slot, int mode, const double* xs) {
   return DG_OK;
 }
 
+// Momentum predictor of one stage (Eqs. first_stage / second_stage): one
+// linear solve with the advecting field in s->ub, or, with fixed_point = K >
+// 1, up to K Picard solves, each advected by the previous iterate (the fully
+// nonlinear stage), until the relative change of the iterate is below
+// fixed_point_tol.  The right-hand side depends on the advecting field only
+// through the Dirichlet data's Lax-Friedrichs term, so it is rebuilt only
+// when there is wall data.  x = s->ustar holds the guess on entry.
+dg_status momentum_stage(dg_solver* s, const dg_step_params* prm, int stage,
+                         const dg_momentum_coeffs* co, const dg_momentum_rhs* rd,
+                         const dg_solve_opts* mo, dg_solve_info* info) {
+  dg_status st = dg_solve_stage(s, co, 0.0, s->ub, s->rhs_u, s->ustar, mo, info);
+  s->fp_iters[stage] = 1;
+  if (st != DG_OK || prm->fixed_point <= 1) return st;
+  dg_solve_opts o = *mo;
+  o.guess = DG_GUESS_GIVEN;  // each Picard solve starts from the previous iterate
+  const int64_t nu = s->nu;
+  int it = 1;
+  while (it < prm->fixed_point) {
+    DG_CUDA(cudaMemcpyAsync(s->ub, s->ustar, sizeof(double) * nu, cudaMemcpyDeviceToDevice,
+                            s->stream));
+    if (rd->uD) {
+      st = dg_rhs_momentum(s->mesh, rd, s->rhs_u, s->stream);
+      if (st != DG_OK) return st;
+    }
+    dg_solve_info inf;
+    st = dg_solve_stage(s, co, 0.0, s->ub, s->rhs_u, s->ustar, &o, &inf);
+    info->iterations += inf.iterations;
+    info->res_final = inf.res_final;
+    info->status = inf.status;
+    ++it;
+    if (st != DG_OK) break;
+    double dd[2];
+    st = s->vo.axpby(nu, 1.0, s->ustar, -1.0, s->ub, s->w);
+    if (st == DG_OK) st = s->vo.dots_host(nu, 1, s->w, s->w, nu, dd);
+    if (st == DG_OK) st = s->vo.dots_host(nu, 1, s->ustar, s->ustar, nu, dd + 1);
+    if (st != DG_OK) break;
+    if (!std::isfinite(dd[0])) {
+      set_error("trbdf2_step: fixed-point iteration diverged");
+      st = DG_EBREAKDOWN;
+      break;
+    }
+    if (std::sqrt(dd[0]) < prm->fixed_point_tol * std::max(std::sqrt(dd[1]), 1e-300)) break;
+  }
+  s->fp_iters[stage] = it;
+  return st;
+}
+
 }  // namespace
 }  // namespace dg
 
 using namespace dg;
 
 extern "C" {
+
+dg_status dg_solver_get_fixed_point(const dg_solver* s, int32_t it[2]) {
+  if (!s || !it) {
+    set_error("dg_solver_get_fixed_point: bad argument");
+    return DG_EINVAL;
+  }
+  it[0] = s->fp_iters[0];
+  it[1] = s->fp_iters[1];
+  return DG_OK;
+}
 
 dg_status dg_solver_create(dg_mesh* m, double Re, double c, dg_solver** out) {
   if (!m || !out || !(Re > 0.0) || !(c > 0.0)) {
@@ -501,6 +560,10 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   }
   if (!check_opts(&prm->mom, "trbdf2_step") || !check_opts(&prm->helm, "trbdf2_step"))
     return DG_EINVAL;
+  if (prm->fixed_point > 1 && !(prm->fixed_point_tol > 0.0)) {
+    set_error("trbdf2_step: fixed_point > 1 needs fixed_point_tol > 0");
+    return DG_EINVAL;
+  }
   if (join_caller(s) != DG_OK) return DG_ECUDA;
   dg_solve_info loc[4];
   if (!info) info = loc;
@@ -547,7 +610,9 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   r1.visc[0] = co1.visc;
   r1.adv[0] = co1.adv;
   r1.w[0] = u;
-  r1.wbar[0] = s->ub;
+  // the explicit advection is advected by ubar_1, or by u^n itself in the
+  // fully nonlinear form
+  r1.wbar[0] = prm->fixed_point > 1 ? u : s->ub;
   r1.p = p;
   r1.uD = prm->uD_stage1;
   r1.dir_visc = co1.visc;
@@ -563,7 +628,7 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(1);
   STEP(prepare_guess(s, 0, prm->mom.guess, s->rhs_u, s->ustar));
   tr.mark(2);
-  STEP(dg_solve_stage(s, &co1, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[0]));
+  STEP(momentum_stage(s, prm, 0, &co1, &r1, &mo, &info[0]));
   tr.mark(1);
   STEP(finish_guess(s, 0, prm->mom.guess, s->ustar));
   tr.mark(3);
@@ -620,7 +685,7 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(1);
   STEP(prepare_guess(s, 2, prm->mom.guess, s->rhs_u, s->ustar));
   tr.mark(2);
-  STEP(dg_solve_stage(s, &co2, 0.0, s->ub, s->rhs_u, s->ustar, &mo, &info[2]));
+  STEP(momentum_stage(s, prm, 1, &co2, &r2, &mo, &info[2]));
   tr.mark(1);
   STEP(finish_guess(s, 2, prm->mom.guess, s->ustar));
   tr.mark(3);

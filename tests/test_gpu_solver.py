@@ -141,6 +141,67 @@ def test_periodic_3d_taylor_green_benchmark_path_matches_oracle(tuning):
         b.dg_solver_destroy(s)
 
 
+def test_fully_nonlinear_stages_match_oracle_at_c3():
+    """Section 2's fully nonlinear momentum stages (Picard iterations on the
+    implicit advecting field), which the paper needs at larger Courant
+    numbers: the 8x8 Q2/Q1 Taylor-Green vortex at C = 3 (dt = 1.18, the
+    first row of Section 4.1's C = 3 table; ceil(3.2/dt) = 3 steps), lagged
+    starting fields, Picard to a relative change of 1e-10 on both sides.
+    Every step matches the oracle at 1e-8, the Picard counts agree (to one
+    iteration at the stopping threshold), and the final velocity error lies
+    in the table's band (factor 2 of 0.39)."""
+    from paper_2107_07776_gb300 import binding as b
+    from oracle.trbdf2 import l2_error
+    N, dt, Re = 8, 1.18, 100.0
+    om = OMesh(2, [N, N], [0, 0], [2 * math.pi] * 2, [True, True], 2)
+    gm = b.Mesh(2, (N, N), (0, 0), (2 * math.pi, 2 * math.pi), (True, True), 2)
+    st = Stepper(om, Re, extrapolate=False, fixed_point=400, fixed_point_tol=1e-10)
+    ou = interpolate(om, lambda x, y: W.paper_tg_u(x, y, 0.0, Re))
+    op = interpolate(om, lambda x, y: W.paper_tg_p(x, y, 0.0, Re), p_space=True)
+    ouh = ou
+    s = b.dg_solver_create(gm.handle, Re, 1e3)
+    try:
+        u, p = dev(ou.reshape(-1)), dev(op)
+        prm = step_params(b, dt, extrapolate=0)
+        prm.fixed_point, prm.fixed_point_tol = 400, 1e-10
+        t = 0.0
+        for n in range(3):
+            info = b.trbdf2_step(s, prm, u, p)
+            assert all(i.status == 0 for i in info)
+            ou, op, ouh = st.step(ou, op, ouh, t, dt)
+            t += dt
+            its = b.dg_solver_get_fixed_point(s)
+            assert all(abs(a - c) <= 1 for a, c in zip(its, st.fixed_point_iterations)), \
+                (its, st.fixed_point_iterations)
+            assert min(its) > 2
+            assert rel_l2(u.cpu().numpy(), ou.reshape(-1)) < 1e-8, n
+            assert rel_l2(p.cpu().numpy(), op) < 1e-8, n
+        ug = u.cpu().numpy().reshape(2, -1)
+        e2 = n2 = 0.0
+        for i in range(2):
+            ex = lambda x, y, i=i: W.paper_tg_u(x, y, t, Re)[i]
+            e2 += l2_error(om, ug[i], ex, relative=False) ** 2
+            n2 += l2_error(om, 0 * ug[i], ex, relative=False) ** 2
+        assert 0.39 / 2 < math.sqrt(e2 / n2) < 0.39 * 2
+    finally:
+        b.dg_solver_destroy(s)
+
+
+def test_fixed_point_option_is_validated():
+    from paper_2107_07776_gb300 import binding as b
+    gm = b.Mesh(2, (4, 4), (0, 0), (1.0, 1.0), (True, True), 2)
+    s = b.dg_solver_create(gm.handle, 10.0, 1e3)
+    try:
+        u = torch.zeros(gm.n_dofs_u, dtype=torch.float64, device="cuda")
+        p = torch.zeros(gm.n_dofs_p, dtype=torch.float64, device="cuda")
+        prm = step_params(b, 0.1)
+        prm.fixed_point, prm.fixed_point_tol = 5, 0.0
+        with pytest.raises(b.DGError):
+            b.trbdf2_step(s, prm, u, p)
+    finally:
+        b.dg_solver_destroy(s)
+
+
 def test_step_waits_for_inputs_filled_on_the_callers_stream():
     """u, p and the history are filled on a non-blocking torch stream behind
     a ~25 ms spin, and the solver is told that stream (dg_solver_set_stream):

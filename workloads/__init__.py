@@ -17,6 +17,12 @@ Workloads (the paper's hot-path problems, all synthetic, no dataset):
   tgv48     tgv32 at 48^3 over 400 steps (learned initial guess).
   channel   [0,4]x[0,1]x[0,1], 256x64x64, tanh wall grading (beta 1.5) in y, z,
             Q2/Q1, Re 5000, parabolic profile + seeded 1% perturbation.
+  abc       3D periodic cube [0,2pi]^3, 8^3 hexes, Q2/Q1, Re 1, the
+            Arnold-Beltrami-Childress flow u = (sin z + cos y, sin x + cos z,
+            sin y + cos x) e^{-t/Re} with p = -(sin x cos z + sin y cos x +
+            sin z cos y) e^{-2t/Re}, dt 0.32 (C = 1.63), T = 3.2 (10 steps);
+            refined by doubling the cells and halving dt (hyperbolic scaling)
+            or quartering it (parabolic scaling, mu = 2).
 """
 from __future__ import annotations
 
@@ -76,7 +82,10 @@ CHANNEL = Workload("channel", 3, (256, 64, 64), (0.0,) * 3, (4.0, 1.0, 1.0),
                    (True, False, False), 2, Re=5000.0, dt=5e-4, steps=50, map=1,
                    map_param=(0.0, 1.5, 1.5))
 
-WORKLOADS = {w.name: w for w in (TG2D, TGV32, MMS64, TGV48, CHANNEL)}
+ABC = Workload("abc", 3, (8, 8, 8), (0.0,) * 3, (TWO_PI,) * 3, (True,) * 3, 2,
+               Re=1.0, dt=0.32, steps=10)
+
+WORKLOADS = {w.name: w for w in (TG2D, TGV32, MMS64, TGV48, CHANNEL, ABC)}
 
 
 # ---------------------------------------------------------------- fields
@@ -113,6 +122,23 @@ def tgv3d_u(x, y, z):
 
 def tgv3d_p(x, y, z):
     return (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0) / 16.0
+
+
+def abc_u(x, y, z, t=0.0, Re=1.0):
+    """Arnold-Beltrami-Childress flow (A = B = C = 1) of Section 4.1: a
+    Beltrami field (curl u = u), so u.grad u = grad |u|^2/2 and the viscous
+    term decays it like e^{-t/Re}."""
+    e = math.exp(-t / Re)
+    return np.stack([(np.sin(z) + np.cos(y)) * e, (np.sin(x) + np.cos(z)) * e,
+                     (np.sin(y) + np.cos(x)) * e])
+
+
+def abc_p(x, y, z, t=0.0, Re=1.0):
+    """Its pressure, -|u|^2/2 up to a constant.  Section 4.1 prints the
+    spatial part without a time factor; the exact solution of the equations
+    decays like |u|^2, e^{-2t/Re} (the reading taken here)."""
+    return -(np.sin(x) * np.cos(z) + np.sin(y) * np.cos(x) + np.sin(z) * np.cos(y)) * \
+        math.exp(-2.0 * t / Re)
 
 
 def channel_u0(x, y, z, seed: int = 1, amp: float = 0.01):
@@ -182,6 +208,8 @@ def initial_state(w: Workload, X, Xp):
         return tg2d_u(*X, 0.0, 1.0 / w.Re), tg2d_p(*Xp, 0.0, 1.0 / w.Re)
     if w.name == "channel":
         return channel_u0(*X), np.zeros(Xp.shape[1])
+    if w.name == "abc":
+        return abc_u(*X, 0.0, w.Re), abc_p(*Xp, 0.0, w.Re)
     return np.zeros((w.dim, X.shape[1])), np.zeros(Xp.shape[1])
 
 
