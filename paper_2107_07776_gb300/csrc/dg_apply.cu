@@ -170,6 +170,43 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
                                        const T* ubar, const T* src, T* dst, int ncomp,
                                        const OpArgs<T>* cheb, cudaStream_t s);
 
+// out[i] = x[i] split into a float pair (hi, lo), stored in the bits of a
+// double slot: two values per thread and iteration (16-byte loads and
+// stores when both pointers allow it), grid-stride over 152 x 8 CTAs
+__global__ void __launch_bounds__(256) presplit_kernel(int64_t n, const double* __restrict__ x,
+                                                       double* __restrict__ out) {
+  pdl_entry();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+  if (vec) {
+    const int64_t n2 = n / 2;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(x) + k);
+      const df64 a = df_split(v.x), b = df_split(v.y);
+      reinterpret_cast<float4*>(out)[k] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      const df64 a = df_split(x[n - 1]);
+      reinterpret_cast<float2*>(out)[n - 1] = make_float2(a.hi, a.lo);
+    }
+  } else {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+      const df64 a = df_split(x[k]);
+      reinterpret_cast<float2*>(out)[k] = make_float2(a.hi, a.lo);
+    }
+  }
+}
+
+static dg_status presplit(int64_t n, const double* x, double* out, cudaStream_t s) {
+  if (n <= 0) return DG_OK;
+  int64_t blocks = (n / 2 + 255) / 256;
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 8));
+  launch(presplit_kernel, (unsigned)blocks, 256, 0, s, n, x, out);
+  count_launch();
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
 template <typename T>
 dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T adv, const T* ubar,
                            const T* src, T* dst, int ncomp, cudaStream_t s) {
@@ -236,9 +273,47 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
     a.cc1 = cheb->cc1;
     a.cc2 = cheb->cc2;
   }
+  a.csrc = src;
   const bool use_adv = !pressure && ubar != nullptr && adv != T(0);
   const int v = m->tune[sizeof(T) == 8 ? 0 : 1][pressure ? 0 : (use_adv ? 2 : 1)];
+  if constexpr (sizeof(T) == 8) {
+    if (m->fp64_arith == 0) {  // float-float kernels read pre-split inputs
+      dg_mesh* mm = const_cast<dg_mesh*>(m);
+      const int64_t nsrc = (int64_t)ncomp * m->ncell * (pressure ? m->nbp : m->nbu);
+      if (!m->ps_src || (use_adv && !m->ps_ub)) {
+        set_error("operator apply: float-float split buffers missing on this mesh");
+        return DG_EINVAL;
+      }
+      dg_status st = presplit(nsrc, src, m->ps_src, s);
+      if (st != DG_OK) return st;
+      const T* ub_ps = nullptr;
+      if (use_adv) {
+        if (!(m->ub_keep == ubar && m->ub_split_of == ubar)) {
+          st = presplit((int64_t)m->dim * m->ncell * m->nbu, ubar, m->ps_ub, s);
+          if (st != DG_OK) return st;
+          mm->ub_split_of = ubar;
+        }
+        ub_ps = m->ps_ub;
+      }
+      for (int ax = 0; ax < 3; ++ax) {
+        const T* hp = m->d_hdf[ax];
+        const T* hip = m->d_hidf[ax];
+        (ax == 0 ? a.h0 : (ax == 1 ? a.h1 : a.h2)) = hp;
+        (ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2)) = hip;
+      }
+      a.mass = (T)pack_pair((double)a.mass);
+      a.visc = (T)pack_pair((double)a.visc);
+      a.adv = (T)pack_pair((double)a.adv);
+      a.pen = (T)pack_pair((double)a.pen);
+      return dispatch(m, pressure, v, N, use_adv, a, ub_ps, m->ps_src, dst, s);
+    }
+  }
   return dispatch(m, pressure, v, N, use_adv, a, ubar, src, dst, s);
+}
+
+void keep_presplit_ubar(dg_mesh* m, const double* ubar) {
+  m->ub_keep = ubar;
+  m->ub_split_of = nullptr;
 }
 
 // face-flux scratch of the face-once variants: 2 values of at most 8 bytes

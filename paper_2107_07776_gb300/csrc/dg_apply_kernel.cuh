@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdio>
+#include <type_traits>
 
 #include "dg_common.cuh"
 #include "dg_df64.cuh"
@@ -40,7 +41,25 @@ struct OpArgs {
   // face-flux scratch of the face-once variant (null: not available)
   void* flux;
   int64_t flux_bytes;
+  // the caller's source vector in its storage type (the Chebyshev update
+  // reads it; the kernels' src may be a pre-split copy)
+  const T* csrc;
 };
+
+// Float-float kernels on FP64 storage (T = double, A = df64) receive every
+// FP64 input pre-split: the source vector and advecting field as float
+// pairs in double-sized slots (one split pass per apply instead of one split
+// per read), the cell extents from the mesh's float-float copies and the
+// scalar coefficients split on the host.  ld_val reads a storage value in
+// the arithmetic type either way.
+template <typename T, typename A>
+constexpr bool kPreSplit = std::is_same<T, double>::value && std::is_same<A, df64>::value;
+
+template <typename T, typename A>
+__device__ __forceinline__ A ld_val(T v) {
+  if constexpr (kPreSplit<T, A>) return df_bits(v);
+  else return Arith<A>::from(v);
+}
 
 __device__ __forceinline__ int node_of(int N, int a, int i, int t, int dim) {
   // node index with coordinate i along axis a and tangential index t (the
@@ -99,8 +118,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < a.ncell;
   const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
-  const A mass = Ar::from(a.mass), visc = Ar::from(a.visc), advc = Ar::from(a.adv),
-          pen = Ar::from(a.pen);
+  const A mass = ld_val<T, A>(a.mass), visc = ld_val<T, A>(a.visc), advc = ld_val<T, A>(a.adv),
+          pen = ld_val<T, A>(a.pen);
 
   int ci[3] = {0, 0, 0};
   A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
@@ -108,24 +127,24 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   A W = zero;
   if (active) {
     lex_coords(cell, a.n0, a.n1, ci);
-    h[0] = Ar::from(a.h0[ci[0]]);
-    h[1] = Ar::from(a.h1[ci[1]]);
-    hi[0] = Ar::from(a.hi0[ci[0]]);
-    hi[1] = Ar::from(a.hi1[ci[1]]);
+    h[0] = ld_val<T, A>(a.h0[ci[0]]);
+    h[1] = ld_val<T, A>(a.h1[ci[1]]);
+    hi[0] = ld_val<T, A>(a.hi0[ci[0]]);
+    hi[1] = ld_val<T, A>(a.hi1[ci[1]]);
     if (DIM == 3) {
-      h[2] = Ar::from(a.h2[ci[2]]);
-      hi[2] = Ar::from(a.hi2[ci[2]]);
+      h[2] = ld_val<T, A>(a.h2[ci[2]]);
+      hi[2] = ld_val<T, A>(a.hi2[ci[2]]);
     }
     W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
     if (DIM == 3) W = W * tb.w[ii[2]] * h[2];
     if (ADV) {
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) s_ub[b][cl][node] = Ar::from(ub[((int64_t)b * a.ncell + cell) * NB + node]);
+      for (int b = 0; b < DIM; ++b) s_ub[b][cl][node] = ld_val<T, A>(ub[((int64_t)b * a.ncell + cell) * NB + node]);
     }
   }
   for (int c = 0; c < a.ncomp; ++c) {
     const T* srcc = src + (int64_t)c * a.ncell * NB;
-    if (active) s_u[cl][node] = Ar::from(srcc[cell * NB + node]);
+    if (active) s_u[cl][node] = ld_val<T, A>(srcc[cell * NB + node]);
     __syncthreads();
     if (active) {
       // ---- cell integrand at this node: W * (visc grad u - adv u ubar) ----
@@ -182,11 +201,11 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
         dnin = dnin * sgn * hiK;
         A fv = zero, fg = zero;
         if (interior) {
-          const A hiN = Ar::from(hiax[cn]);
+          const A hiN = ld_val<T, A>(hiax[cn]);
           A uout = zero, dnout = zero;
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const A v = Ar::from(__ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]));
+            const A v = ld_val<T, A>(__ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]));
             uout = Ar::fma(tb.L[1 - s][i], v, uout);
             dnout = Ar::fma(tb.dL[1 - s][i], v, dnout);
           }
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
               for (int i = 0; i < N; ++i) {
                 unin = Ar::fma(tb.L[s][i], s_ub[ax][cl][node_of(N, ax, i, t, DIM)], unin);
                 unout += tb.L[1 - s][i] *
-                         Ar::from(__ldg(&ub[((int64_t)ax * a.ncell + nb) * NB + node_of(N, ax, i, t, DIM)]));
+                         ld_val<T, A>(__ldg(&ub[((int64_t)ax * a.ncell + nb) * NB + node_of(N, ax, i, t, DIM)]));
               }
               unin = unin * sgn;
               unout = unout * sgn;
@@ -270,7 +289,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
       if (a.cheb) {
-        const T dk = srcc[cell * NB + node];
+        const T dk = a.csrc[o];
         a.cx[o] += dk;
         const T rk = a.cr[o] - a.cdinv[o] * yt;
         a.cr[o] = rk;

@@ -157,6 +157,18 @@ struct dg_mesh {
   // autotuner, which is the only way that variant gets chosen)
   void* split_flux = nullptr;
   int64_t split_flux_bytes = 0;
+  // float-float applies (affine meshes): the source vector and advecting
+  // field split into float pairs once per apply (double-sized slots), and
+  // float-float copies of the cell extents, allocated with the mesh
+  double* ps_src = nullptr;         // max(dim * nbu, nbp) * ncell slots
+  double* ps_ub = nullptr;          // dim * nbu * ncell slots (not on multigrid levels)
+  double* d_hdf[3] = {nullptr, nullptr, nullptr};
+  double* d_hidf[3] = {nullptr, nullptr, nullptr};
+  // advecting field whose split copy may be reused while the caller keeps
+  // it unchanged (the solver around its Krylov iterations), and the field
+  // the copy in ps_ub was made from
+  const double* ub_keep = nullptr;
+  const double* ub_split_of = nullptr;
   bool level = false;       // a multigrid level (pressure space only)
   // autotuned tile shape of the operator kernels: variant index per
   // [precision: 0 FP64, 1 FP32][operator: 0 pressure, 1 momentum, 2 momentum
@@ -193,6 +205,14 @@ dg_status make_level_mesh(const dg_mesh* fine, const int coarsen[3], int degree_
                           dg_mesh** out);
 
 dg_status autotune_mesh(dg_mesh* m, cudaStream_t s);
+
+// The advecting field `ubar` stays unchanged until the next call (nullptr:
+// no such promise): float-float momentum applies with it split it once.
+void keep_presplit_ubar(dg_mesh* m, const double* ubar);
+
+// host-side split of a double into a float pair, packed in a double's bits
+// (the layout df_bits reads)
+double pack_pair(double x);
 
 // launchers (dg_apply.cu)
 template <typename T>

@@ -69,6 +69,55 @@ __device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) {
   return df_fast_two_sum(s.hi, t);
 }
 
+// Compensated accumulation of float-float products (the Dot2 scheme of
+// Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005, carried to float-float operands): the leading parts of
+// the products are summed with TwoSum, and every rounding error -- the exact
+// product errors (one FMA), the cross terms hi*lo and the TwoSum errors --
+// goes into one FP32 error word; one FastTwoSum at the end.  12 FP32
+// operations per product instead of 15 for a chain of df_fma, with an error
+// of a few units of 2^-48 of the sum of the terms' magnitudes (the order of
+// the error the chain has).
+struct DfAcc {
+  float s, e;
+};
+
+__device__ __forceinline__ DfAcc acc_of(df64 c) { return {c.hi, c.lo}; }
+
+// first product of an empty sum (no TwoSum needed)
+__device__ __forceinline__ DfAcc acc_prod(df64 x, df64 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return {p, e};
+}
+
+__device__ __forceinline__ void acc_fma(DfAcc& a, df64 x, df64 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const df64 t = df_two_sum(a.s, p);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, e));
+}
+
+__device__ __forceinline__ void acc_add(DfAcc& a, df64 x) {
+  const df64 t = df_two_sum(a.s, x.hi);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, x.lo));
+}
+
+__device__ __forceinline__ df64 acc_value(const DfAcc& a) { return df_fast_two_sum(a.s, a.e); }
+
+// A float-float value stored in 8 bytes of a double-typed array (the
+// pre-split copies the FP64 operator kernels read): the bits are the pair.
+__device__ __forceinline__ df64 df_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return {__uint_as_float((unsigned int)(b & 0xffffffffull)), __uint_as_float((unsigned int)(b >> 32))};
+}
+
 __device__ __forceinline__ df64 operator+(df64 a, df64 b) { return df_add(a, b); }
 __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ df64 operator-(df64 a) { return df_neg(a); }

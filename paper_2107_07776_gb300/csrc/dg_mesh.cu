@@ -6,6 +6,7 @@
 // affine cells).  Points come from Newton's method on the Legendre
 // polynomial; basis values and derivatives from barycentric Lagrange
 // interpolation (Berrut & Trefethen, SIAM Review 46, 2004).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -281,7 +282,44 @@ dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "mesh status word");
   if (!m->affine) return build_geometry(m, !m->level, s);
+  // float-float applies: split copies of the extents and the per-apply
+  // split buffers of the source vector and advecting field
+  for (int a = 0; a < 3; ++a) {
+    const int na = m->n[a];
+    std::vector<double> hp(na), hip(na);
+    for (int i = 0; i < na; ++i) {
+      const double h = m->vx[a][i + 1] - m->vx[a][i];
+      hp[i] = pack_pair(h);
+      hip[i] = pack_pair(1.0 / h);
+    }
+    e = cudaMalloc(&m->d_hdf[a], sizeof(double) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_hidf[a], sizeof(double) * na);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_hdf[a], hp.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->d_hidf[a], hip.data(), sizeof(double) * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mesh upload (float-float extents)");
+  }
+  const int64_t nps = (m->level ? (int64_t)m->nbp : std::max<int64_t>((int64_t)m->dim * m->nbu, m->nbp)) *
+                      m->ncell;
+  e = cudaMalloc(&m->ps_src, sizeof(double) * nps);
+  if (e == cudaSuccess && !m->level)
+    e = cudaMalloc(&m->ps_ub, sizeof(double) * (int64_t)m->dim * m->nbu * m->ncell);
+  if (e != cudaSuccess) return cuda_fail(e, "mesh float-float split buffers");
   return DG_OK;
+}
+
+double pack_pair(double x) {
+  const float hi = (float)x;
+  const float lo = (float)(x - (double)hi);
+  uint32_t a, b;
+  std::memcpy(&a, &hi, 4);
+  std::memcpy(&b, &lo, 4);
+  const uint64_t bits = (uint64_t)a | ((uint64_t)b << 32);
+  double d;
+  std::memcpy(&d, &bits, 8);
+  return d;
 }
 
 // Mesh of a coarser multigrid level: axes with coarsen[a] set keep every
@@ -429,6 +467,12 @@ void dg_mesh_destroy(dg_mesh* m) {
   }
   if (m->d_status) cudaFree(m->d_status);
   if (m->split_flux) cudaFree(m->split_flux);
+  for (int a = 0; a < 3; ++a) {
+    if (m->d_hdf[a]) cudaFree(m->d_hdf[a]);
+    if (m->d_hidf[a]) cudaFree(m->d_hidf[a]);
+  }
+  if (m->ps_src) cudaFree(m->ps_src);
+  if (m->ps_ub) cudaFree(m->ps_ub);
   free_geometry(m);
   delete m;
 }

@@ -87,11 +87,11 @@ __global__ void __launch_bounds__(128)
   const bool active = (gt >> 1) < a.ncell;
   const int64_t cell = active ? (gt >> 1) : a.ncell - 1;
   const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
-  const A mass = Ar::from(a.mass), visc = Ar::from(a.visc), pen = Ar::from(a.pen);
+  const A mass = ld_val<T, A>(a.mass), visc = ld_val<T, A>(a.visc), pen = ld_val<T, A>(a.pen);
   int ci[3];
   lex_coords(cell, a.n0, a.n1, ci);
-  const A h3[3] = {Ar::from(a.h0[ci[0]]), Ar::from(a.h1[ci[1]]), Ar::from(a.h2[ci[2]])};
-  const A hi[3] = {Ar::from(a.hi0[ci[0]]), Ar::from(a.hi1[ci[1]]), Ar::from(a.hi2[ci[2]])};
+  const A h3[3] = {ld_val<T, A>(a.h0[ci[0]]), ld_val<T, A>(a.h1[ci[1]]), ld_val<T, A>(a.h2[ci[2]])};
+  const A hi[3] = {ld_val<T, A>(a.hi0[ci[0]]), ld_val<T, A>(a.hi1[ci[1]]), ld_val<T, A>(a.hi2[ci[2]])};
   uintptr_t align = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst);
   if (a.cheb)
     align |= reinterpret_cast<uintptr_t>(a.cx) | reinterpret_cast<uintptr_t>(a.cr) |
@@ -101,15 +101,13 @@ __global__ void __launch_bounds__(128)
   q1_load<T, A>(src + cell * 8, vec, ut);
   A u[8];
 #pragma unroll
-  for (int nd = 0; nd < 8; ++nd) u[nd] = Ar::from(ut[nd]);
+  for (int nd = 0; nd < 8; ++nd) u[nd] = ld_val<T, A>(ut[nd]);
   // own nodes nd = 4 h + k (k = i0 + 2 i1), picked by selects (a run-time
   // index into u would put it in local memory)
   A uo[4], W[4], y[4];
-  T uto[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     uo[k] = h ? u[4 + k] : u[k];
-    uto[k] = h ? ut[4 + k] : ut[k];
     W[k] = tb.w[k & 1] * tb.w[k >> 1] * h3[0] * h3[1] * tb.w[h] * h3[2];
     y[k] = mass * W[k] * uo[k];
   }
@@ -178,7 +176,7 @@ __global__ void __launch_bounds__(128)
       A hiN = zero;
       T vt[4];  // the neighbour's layer h
       if (interior) {
-        hiN = Ar::from(hiax[cn]);
+        hiN = ld_val<T, A>(hiax[cn]);
         q1_load4<T>(src + (cell + (int64_t)(cn - cax) * cstr) * 8 + 4 * h, vec, vt);
       }
 #pragma unroll
@@ -196,7 +194,7 @@ __global__ void __launch_bounds__(128)
         dnin = dnin * sgn * hiK;
         A fv, fg;
         if (interior) {
-          const A v0 = Ar::from(vt[k0]), v1 = Ar::from(vt[k1]);
+          const A v0 = ld_val<T, A>(vt[k0]), v1 = ld_val<T, A>(vt[k1]);
           A uout = zero, dnout = zero;
           uout = Ar::fma(tb.L[1 - s][0], v0, uout);
           dnout = Ar::fma(tb.dL[1 - s][0], v0, dnout);
@@ -234,7 +232,7 @@ __global__ void __launch_bounds__(128)
     A hiN = zero;
     T vt[8];
     if (interior) {
-      hiN = Ar::from(a.hi2[cn]);
+      hiN = ld_val<T, A>(a.hi2[cn]);
       q1_load<T, A>(src + (cell + (int64_t)(cn - ci[2]) * a.n0 * (int64_t)a.n1) * 8, vec, vt);
     }
     A c_own[4], c_par[4];
@@ -254,7 +252,7 @@ __global__ void __launch_bounds__(128)
         dnin = dnin * sgn * hiK;
         A fv, fg;
         if (interior) {
-          const A v0 = Ar::from(vt[t]), v1 = Ar::from(vt[4 + t]);
+          const A v0 = ld_val<T, A>(vt[t]), v1 = ld_val<T, A>(vt[4 + t]);
           A uout = zero, dnout = zero;
           uout = Ar::fma(tb.L[1 - s][0], v0, uout);
           dnout = Ar::fma(tb.dL[1 - s][0], v0, dnout);
@@ -299,7 +297,7 @@ __global__ void __launch_bounds__(128)
     // x += d; r -= dinv y; dst = c1 d + c2 r
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const T dk = uto[k];
+      const T dk = a.csrc[o + k];
       a.cx[o + k] += dk;
       const T rk = a.cr[o + k] - a.cdinv[o + k] * yt[k];
       a.cr[o + k] = rk;

@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(256)
   const int64_t cL = cbase + (int64_t)cl_ax * cstr, cR = cbase + (int64_t)cr_ax * cstr;
   const T* hiax = ax == 0 ? a.hi0 : (ax == 1 ? a.hi1 : a.hi2);
   const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
-  const A visc = Ar::from(a.visc), advc = Ar::from(a.adv), pen = Ar::from(a.pen);
-  const A hiL = hasL ? Ar::from(hiax[cl_ax]) : zero, hiR = hasR ? Ar::from(hiax[cr_ax]) : zero;
+  const A visc = ld_val<T, A>(a.visc), advc = ld_val<T, A>(a.adv), pen = ld_val<T, A>(a.pen);
+  const A hiL = hasL ? ld_val<T, A>(hiax[cl_ax]) : zero, hiR = hasR ? ld_val<T, A>(hiax[cr_ax]) : zero;
   // tangential weight: face quadrature weight times the face measure
   A wt = Ar::c(1.0);
   {
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256)
     for (int b = 0; b < DIM; ++b) {
       if (b == ax) continue;
       const T* hb = b == 0 ? a.h0 : (b == 1 ? a.h1 : a.h2);
-      wt = wt * tb.w[tt % N] * Ar::from(hb[pick3(b, fc[0], fc[1], fc[2])]);
+      wt = wt * tb.w[tt % N] * ld_val<T, A>(hb[pick3(b, fc[0], fc[1], fc[2])]);
       tt /= N;
     }
   }
@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const int nd = node_of(N, ax, i, t, DIM);
-      if (hasL) unL = Ar::fma(tb.L[1][i], Ar::from(__ldg(&uba[cL * NB + nd])), unL);
-      if (hasR) unR = Ar::fma(tb.L[0][i], Ar::from(__ldg(&uba[cR * NB + nd])), unR);
+      if (hasL) unL = Ar::fma(tb.L[1][i], ld_val<T, A>(__ldg(&uba[cL * NB + nd])), unL);
+      if (hasR) unR = Ar::fma(tb.L[0][i], ld_val<T, A>(__ldg(&uba[cR * NB + nd])), unR);
     }
   }
   for (int c = 0; c < a.ncomp; ++c) {
@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(256)
     for (int i = 0; i < N; ++i) {
       const int nd = node_of(N, ax, i, t, DIM);
       if (hasL) {
-        const A v = Ar::from(__ldg(&srcc[cL * NB + nd]));
+        const A v = ld_val<T, A>(__ldg(&srcc[cL * NB + nd]));
         uL = Ar::fma(tb.L[1][i], v, uL);
         dL = Ar::fma(tb.dL[1][i], v, dL);
       }
       if (hasR) {
-        const A v = Ar::from(__ldg(&srcc[cR * NB + nd]));
+        const A v = ld_val<T, A>(__ldg(&srcc[cR * NB + nd]));
         uR = Ar::fma(tb.L[0][i], v, uR);
         dR = Ar::fma(tb.dL[0][i], v, dR);
       }
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < a.ncell;
   const A zero = Ar::c(0.0);
-  const A mass = Ar::from(a.mass), visc = Ar::from(a.visc), advc = Ar::from(a.adv);
+  const A mass = ld_val<T, A>(a.mass), visc = ld_val<T, A>(a.visc), advc = ld_val<T, A>(a.adv);
   const int n[3] = {a.n0, a.n1, a.n2};
   const int per[3] = {a.per0, a.per1, a.per2};
   const int64_t f0 = faces_of_axis(0, n, per), f1 = faces_of_axis(1, n, per);
@@ -177,19 +177,19 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   for (int b = 0; b < DIM; ++b) ubn[b] = zero;
   if (active) {
     lex_coords(cell, a.n0, a.n1, ci);
-    h[0] = Ar::from(a.h0[ci[0]]);
-    h[1] = Ar::from(a.h1[ci[1]]);
-    hi[0] = Ar::from(a.hi0[ci[0]]);
-    hi[1] = Ar::from(a.hi1[ci[1]]);
+    h[0] = ld_val<T, A>(a.h0[ci[0]]);
+    h[1] = ld_val<T, A>(a.h1[ci[1]]);
+    hi[0] = ld_val<T, A>(a.hi0[ci[0]]);
+    hi[1] = ld_val<T, A>(a.hi1[ci[1]]);
     if (DIM == 3) {
-      h[2] = Ar::from(a.h2[ci[2]]);
-      hi[2] = Ar::from(a.hi2[ci[2]]);
+      h[2] = ld_val<T, A>(a.h2[ci[2]]);
+      hi[2] = ld_val<T, A>(a.hi2[ci[2]]);
     }
     W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
     if (DIM == 3) W = W * tb.w[ii[2]] * h[2];
     if (ADV) {
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) ubn[b] = Ar::from(ub[((int64_t)b * a.ncell + cell) * NB + node]);
+      for (int b = 0; b < DIM; ++b) ubn[b] = ld_val<T, A>(ub[((int64_t)b * a.ncell + cell) * NB + node]);
     }
   }
   // face indices of this node's 2d face points (the same for every component)
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
       for (int q = 0; q < 2 * DIM; ++q) cp_async<2 * sizeof(A)>(&s_fl[cl][node][q][0], fl + fpos[q] * 2);
     }
     cp_async_commit();
-    if (active) s_u[cl][node] = Ar::from(srcc[cell * NB + node]);
+    if (active) s_u[cl][node] = ld_val<T, A>(srcc[cell * NB + node]);
     __syncthreads();
     if (active) {
 #pragma unroll
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
       if (a.cheb) {
-        const T dk = srcc[cell * NB + node];
+        const T dk = a.csrc[o];
         a.cx[o] += dk;
         const T rk = a.cr[o] - a.cdinv[o] * yt;
         a.cr[o] = rk;
