@@ -364,7 +364,8 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
   dg_status st = DG_OK;
   const char* opname[3] = {"pressure", "momentum", "momentum+advection"};
   for (int prec = 0; prec < 2 && st == DG_OK; ++prec) {
-    for (int op = 0; op < 3 && st == DG_OK; ++op) {
+    // multigrid levels apply the pressure operator only
+    for (int op = 0; op < (m->level ? 1 : 3) && st == DG_OK; ++op) {
       float best = 1e30f, times[kTuneVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
       int bestv = 1;
       // the two-threads-per-cell Q1 kernel exists for the 3D pressure

@@ -206,6 +206,28 @@ __device__ __forceinline__ df64 df_split(double x) {
   return df_fast_two_sum(hi, lo);
 }
 
+// Sum of products in the arithmetic type A: a plain FMA chain for float and
+// double, the compensated accumulator for float-float.
+template <typename A>
+struct SumOf {
+  A v;
+  __device__ __forceinline__ void start(A x, A y) { v = x * y; }
+  __device__ __forceinline__ void fma(A x, A y) { v = __fma_any(x, y, v); }
+  __device__ __forceinline__ A value() const { return v; }
+  __device__ __forceinline__ static A __fma_any(A x, A y, A c) {
+    if constexpr (sizeof(A) == 4) return __fmaf_rn(x, y, c);
+    else return __fma_rn(x, y, c);
+  }
+};
+
+template <>
+struct SumOf<df64> {
+  DfAcc a;
+  __device__ __forceinline__ void start(df64 x, df64 y) { a = acc_prod(x, y); }
+  __device__ __forceinline__ void fma(df64 x, df64 y) { acc_fma(a, x, y); }
+  __device__ __forceinline__ df64 value() const { return acc_value(a); }
+};
+
 // Arithmetic-type adapters for kernels templated on the arithmetic type A
 // (float, double or df64) and the storage type T (float or double).
 template <typename A>

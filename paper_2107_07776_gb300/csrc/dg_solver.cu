@@ -115,8 +115,13 @@ dg_status solve_momentum(dg_solver* s, const dg_momentum_coeffs* co, const doubl
   LinOp A = [&](const double* in, double* out) {
     return dg_apply_momentum(m, co, ubar, in, out, s->stream);
   };
-  return gmres_solve(s->vo, s->nu, A, dinv, rhs, x, s->V, s->w, s->hdev, o->restart, o->tol_rel,
-                     o->max_iter, o->timeout_s, info);
+  // ubar stays unchanged during the solve: the float-float applies split it
+  // once instead of once per iteration
+  keep_presplit_ubar(m, ubar);
+  st = gmres_solve(s->vo, s->nu, A, dinv, rhs, x, s->V, s->w, s->hdev, o->restart, o->tol_rel,
+                   o->max_iter, o->timeout_s, info);
+  keep_presplit_ubar(m, nullptr);
+  return st;
 }
 
 dg_status solve_helmholtz(dg_solver* s, double alpha, const double* rhs, double* x,

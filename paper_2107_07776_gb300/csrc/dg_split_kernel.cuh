@@ -90,56 +90,116 @@ __global__ void __launch_bounds__(256)
   A unL = zero, unR = zero;
   if (ADV) {
     const T* uba = ub + (int64_t)ax * a.ncell * NB;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int nd = node_of(N, ax, i, t, DIM);
-      if (hasL) unL = Ar::fma(tb.L[1][i], ld_val<T, A>(__ldg(&uba[cL * NB + nd])), unL);
-      if (hasR) unR = Ar::fma(tb.L[0][i], ld_val<T, A>(__ldg(&uba[cR * NB + nd])), unR);
-    }
-  }
-  for (int c = 0; c < a.ncomp; ++c) {
-    const T* srcc = src + (int64_t)c * a.ncell * NB;
-    A uL = zero, dL = zero, uR = zero, dR = zero;
+    SumOf<A> sL, sR;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const int nd = node_of(N, ax, i, t, DIM);
       if (hasL) {
-        const A v = ld_val<T, A>(__ldg(&srcc[cL * NB + nd]));
-        uL = Ar::fma(tb.L[1][i], v, uL);
-        dL = Ar::fma(tb.dL[1][i], v, dL);
+        const A v = ld_val<T, A>(__ldg(&uba[cL * NB + nd]));
+        if (i == 0) sL.start(tb.L[1][i], v);
+        else sL.fma(tb.L[1][i], v);
       }
       if (hasR) {
-        const A v = ld_val<T, A>(__ldg(&srcc[cR * NB + nd]));
-        uR = Ar::fma(tb.L[0][i], v, uR);
-        dR = Ar::fma(tb.dL[0][i], v, dR);
+        const A v = ld_val<T, A>(__ldg(&uba[cR * NB + nd]));
+        if (i == 0) sR.start(tb.L[0][i], v);
+        else sR.fma(tb.L[0][i], v);
       }
     }
+    if (hasL) unL = sL.value();
+    if (hasR) unR = sR.value();
+  }
+  // Flux coefficients of this face point, the same for every component.
+  // Interior face (normal +e_ax, seen from the lower cell L), with C the
+  // penalty average and lambda = max(|unL|, |unR|):
+  //   F0 = aL uL + aR uR + cDL dL + cDR dR,   G = cG (uL - uR)
+  //   aL = wt (visc C + adv (unL + lambda)/2), aR = wt (adv (unR - lambda)/2 - visc C)
+  //   cDL = -wt visc hiL / 2, cDR = -wt visc hiR / 2, cG = -wt visc / 2
+  // (the SIP terms and the LF flux of Section 3 with the traces u and the
+  // reference normal derivatives d of both sides).  Wall face of one cell
+  // (sg = -1 when the wall is the cell's lower face): with its trace u_in,
+  // derivative d_in and sigma = pen / h,
+  //   F0 = aL u_in + cDL d_in,  G = cG u_in
+  //   aL = sg wt (2 visc sigma + adv |un|), cDL = -wt visc / h, cG = -sg wt visc
+  // so that the reader's rule (value flux -F0 below, +F0 above; derivative
+  // coefficient G over its own extent) reproduces the one-sided flux.
+  const bool interior = hasL && hasR;
+  const bool low = hasR;  // on a wall: the wall is the lower face of cell R
+  A aL = zero, aR = zero, cDL = zero, cDR = zero, cG = zero;
+  if (interior) {
+    const A Cv = visc * (half * pen * (hiL + hiR));
+    const A hw = half * (wt * visc);
+    if (ADV) {
+      const A lam = Ar::max(Ar::abs(unL), Ar::abs(unR));
+      const A ha = half * advc;
+      aL = wt * (Cv + ha * (unL + lam));
+      aR = wt * (ha * (unR - lam) - Cv);
+    } else {
+      aL = wt * Cv;
+      aR = -aL;
+    }
+    cDL = -(hw * hiL);
+    cDR = -(hw * hiR);
+    cG = -hw;
+  } else if (a.walls) {
+    const A hin = low ? hiR : hiL;
+    const A wv = wt * visc;
+    A base = two * (wv * (pen * hin));
+    if (ADV) base = base + wt * (advc * Ar::abs(low ? unR : unL));
+    aL = low ? -base : base;
+    cDL = -(wv * hin);
+    cG = low ? wv : -wv;
+  }
+  for (int c = 0; c < a.ncomp; ++c) {
+    const T* srcc = src + (int64_t)c * a.ncell * NB;
     A F0 = zero, G = zero;
-    if (hasL && hasR) {  // interior face, from the lower cell's side (normal +e_ax)
-      const A dnL = dL * hiL, dnR = dR * hiR;
-      const A Cpen = half * pen * (hiL + hiR);
-      const A jump = uL - uR;
-      A fv = visc * (Cpen * jump - half * (dnL + dnR));
-      const A fgr = -(half * visc * jump);
-      if (ADV) {
-        const A lam = Ar::max(Ar::abs(unL), Ar::abs(unR));
-        fv += advc * (half * (uL * unL + uR * unR) + half * lam * jump);
+    if (interior) {
+      SumOf<A> uL, dL, uR, dR;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int nd = node_of(N, ax, i, t, DIM);
+        const A vl = ld_val<T, A>(__ldg(&srcc[cL * NB + nd]));
+        const A vr = ld_val<T, A>(__ldg(&srcc[cR * NB + nd]));
+        if (i == 0) {
+          uL.start(tb.L[1][i], vl);
+          dL.start(tb.dL[1][i], vl);
+          uR.start(tb.L[0][i], vr);
+          dR.start(tb.dL[0][i], vr);
+        } else {
+          uL.fma(tb.L[1][i], vl);
+          dL.fma(tb.dL[1][i], vl);
+          uR.fma(tb.L[0][i], vr);
+          dR.fma(tb.dL[0][i], vr);
+        }
       }
-      F0 = wt * fv;
-      G = wt * fgr;
+      const A ul = uL.value(), ur = uR.value();
+      SumOf<A> f;
+      f.start(aL, ul);
+      f.fma(aR, ur);
+      f.fma(cDL, dL.value());
+      f.fma(cDR, dR.value());
+      F0 = f.value();
+      G = cG * (ul - ur);
     } else if (a.walls) {
-      // one-sided wall flux of the single cell (normal -e_ax below, +e_ax above)
-      const bool low = hasR;  // the wall is the lower face of cell R
-      const A uin = low ? uR : uL;
-      const A dnin = low ? -(dR * hiR) : dL * hiL;
-      const A sig = pen * (low ? hiR : hiL);
-      A fv = visc * (two * sig * uin - dnin);
-      const A fgr = -(visc * uin);
-      if (ADV) fv += advc * Ar::abs(low ? -unR : unL) * uin;
-      // stored so that the reader's rule (value flux -F0 below / +F0 above,
-      // derivative coefficient G times its inverse extent) reproduces it
-      F0 = low ? -(wt * fv) : wt * fv;
-      G = low ? -(wt * fgr) : wt * fgr;
+      const int64_t cin = low ? cR : cL;
+      const int sd = low ? 0 : 1;
+      SumOf<A> ui, di;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const A v = ld_val<T, A>(__ldg(&srcc[cin * NB + node_of(N, ax, i, t, DIM)]));
+        if (i == 0) {
+          ui.start(tb.L[sd][i], v);
+          di.start(tb.dL[sd][i], v);
+        } else {
+          ui.fma(tb.L[sd][i], v);
+          di.fma(tb.dL[sd][i], v);
+        }
+      }
+      const A u_in = ui.value();
+      SumOf<A> f;
+      f.start(aL, u_in);
+      f.fma(cDL, di.value());
+      F0 = f.value();
+      G = cG * u_in;
     }
     A* fo = flux + ((c * nface + fg) * NF + t) * 2;
     fo[0] = F0;
@@ -163,33 +223,46 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < a.ncell;
   const A zero = Ar::c(0.0);
-  const A mass = ld_val<T, A>(a.mass), visc = ld_val<T, A>(a.visc), advc = ld_val<T, A>(a.adv);
   const int n[3] = {a.n0, a.n1, a.n2};
   const int per[3] = {a.per0, a.per1, a.per2};
   const int64_t f0 = faces_of_axis(0, n, per), f1 = faces_of_axis(1, n, per);
   const int64_t f2 = DIM == 3 ? faces_of_axis(2, n, per) : 0;
   const int64_t nface = f0 + f1 + f2;
   int ci[3] = {0, 0, 0};
-  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  A W = zero, ubn[DIM];
+  // per-node coefficients, the same for every component: the mass weight
+  // mass W, the gradient-term factors visc W / h_b^2 and -adv W ubar_b / h_b
+  // (both inverse extents of the gradient and its transpose folded in), and
+  // the normal-derivative weights L_i'(s) / h_b of the face terms
+  A cm = zero, cv[DIM], ca[DIM], gdl[DIM][2];
 #pragma unroll
-  for (int b = 0; b < DIM; ++b) ubn[b] = zero;
+  for (int b = 0; b < DIM; ++b) {
+    cv[b] = zero;
+    ca[b] = zero;
+    gdl[b][0] = gdl[b][1] = zero;
+  }
   if (active) {
     lex_coords(cell, a.n0, a.n1, ci);
+    A h[3], hi[3];
     h[0] = ld_val<T, A>(a.h0[ci[0]]);
     h[1] = ld_val<T, A>(a.h1[ci[1]]);
     hi[0] = ld_val<T, A>(a.hi0[ci[0]]);
     hi[1] = ld_val<T, A>(a.hi1[ci[1]]);
+    h[2] = hi[2] = Ar::c(1.0);
     if (DIM == 3) {
       h[2] = ld_val<T, A>(a.h2[ci[2]]);
       hi[2] = ld_val<T, A>(a.hi2[ci[2]]);
     }
-    W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
+    A W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
     if (DIM == 3) W = W * tb.w[ii[2]] * h[2];
-    if (ADV) {
+    cm = ld_val<T, A>(a.mass) * W;
+    const A vW = ld_val<T, A>(a.visc) * W, aW = -(ld_val<T, A>(a.adv) * W);
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) ubn[b] = ld_val<T, A>(ub[((int64_t)b * a.ncell + cell) * NB + node]);
+    for (int b = 0; b < DIM; ++b) {
+      cv[b] = vW * hi[b] * hi[b];
+      if (ADV) ca[b] = aW * hi[b] * ld_val<T, A>(ub[((int64_t)b * a.ncell + cell) * NB + node]);
+      gdl[b][0] = tb.dL[0][ii[b]] * hi[b];
+      gdl[b][1] = tb.dL[1][ii[b]] * hi[b];
     }
   }
   // face indices of this node's 2d face points (the same for every component)
@@ -217,43 +290,50 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
     if (active) s_u[cl][node] = ld_val<T, A>(srcc[cell * NB + node]);
     __syncthreads();
     if (active) {
+      const A u = s_u[cl][node];
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
-        A du = zero;
+        SumOf<A> du;
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
-          du = Ar::fma(tb.D[ii[b]][m], s_u[cl][j[0] + N * (j[1] + N * j[2])], du);
+          const A v = s_u[cl][j[0] + N * (j[1] + N * j[2])];
+          if (m == 0) du.start(tb.D[ii[b]][m], v);
+          else du.fma(tb.D[ii[b]][m], v);
         }
-        A q = visc * du * hi[b];
-        if (ADV) q -= advc * s_u[cl][node] * ubn[b];
-        s_q[b][cl][node] = W * q;
+        SumOf<A> q;
+        q.start(cv[b], du.value());
+        if (ADV) q.fma(ca[b], u);
+        s_q[b][cl][node] = q.value();
       }
     }
     __syncthreads();
     if (active) {
-      A y = mass * W * s_u[cl][node];
+      SumOf<A> y;
+      y.start(cm, s_u[cl][node]);
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
-        A acc = zero;
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
-          acc = Ar::fma(tb.D[m][ii[b]], s_q[b][cl][j[0] + N * (j[1] + N * j[2])], acc);
+          y.fma(tb.D[m][ii[b]], s_q[b][cl][j[0] + N * (j[1] + N * j[2])]);
         }
-        y = Ar::fma(acc, hi[b], y);
-        if (b == 0) cp_async_wait_all();  // the thread's own copies (no barrier needed)
+      }
+      cp_async_wait_all();  // the thread's own copies (no barrier needed)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           const A F0 = s_fl[cl][node][2 * b + s][0], G = s_fl[cl][node][2 * b + s][1];
-          y = Ar::fma(s ? F0 : -F0, tb.L[s][ii[b]], y);
-          y = Ar::fma(G * hi[b], tb.dL[s][ii[b]], y);
+          y.fma(s ? F0 : -F0, tb.L[s][ii[b]]);
+          y.fma(G, gdl[b][s]);
         }
       }
+      const A yv = y.value();
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
-      const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
+      const T yt = sizeof(T) == 8 ? (T)Ar::to_d(yv) : (T)Ar::to_f(yv);
       if (a.cheb) {
         const T dk = a.csrc[o];
         a.cx[o] += dk;
