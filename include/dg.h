@@ -305,8 +305,48 @@ typedef struct {
   double fixed_point_tol;
 } dg_step_params;
 
+/* The two comparison projection schemes of Section 2 on the same DG
+ * operators, in artificial compressibility form (a project addition for the
+ * paper's method comparison):
+ *  DG_SCHEME_BCG (Bell-Colella-Glaz, Eqs. momentum_BCG, helmholtz_BCG):
+ *    (M/dt + A/(2Re) + C(w)/2) u* = M u^n/dt + E_v u^n/(2Re) + E_a(w) u^n/2
+ *        + G p^n (+ data, + M (f^n + f^{n+1})/2), with the midpoint advecting
+ *    field w = (u* + u^n)/2 found by Picard solves (fixed_point > 1, starting
+ *    from u^n, stopping below fixed_point_tol as in trbdf2_step) or, with
+ *    fixed_point <= 1, one solve with w = 3/2 u^n - 1/2 u^{n-1};
+ *    (alpha M^p + K) dp = D u* / dt, alpha = 1/(c dt)^2;
+ *    u^{n+1} = u* - dt M^-1 P dp, p^{n+1} = p^n + dp.
+ *  DG_SCHEME_BDF2 (Guermond-Quartapelle, Eqs. momentum_HI, helmholtz_HI):
+ *    (3M/(2dt) + A/Re + C(w)) u* = M (4u^n - u^{n-1})/(2dt) + G p^n
+ *        (+ data, + M f^{n+1}), w the previous step's predicted velocity
+ *    u^{n,*} (u^n on the solver's first such step);
+ *    u** = u* + tau M^-1 P p^n, tau = 2dt/3,
+ *    (alpha M^p + K) p^{n+1} = alpha M^p p^n + D u** / tau, alpha = 1/(c tau)^2,
+ *    u^{n+1} = u** - tau M^-1 P p^{n+1}.
+ * The solver keeps u^{n-1} as its history level (dg_solver_set_history sets
+ * it; before the first step it is u^n); a solver steps with one scheme.  uD:
+ * Dirichlet data at t^{n+1} (tangential, as in dg_step_params) or NULL;
+ * f_n, f_n1: forcing at t^n and t^{n+1} or NULL.  info[2] (host): momentum,
+ * Helmholtz.  Synchronous, on the solver's stream. */
+enum { DG_SCHEME_BCG = 1, DG_SCHEME_BDF2 = 2 };
+
+typedef struct {
+  int32_t scheme;
+  double dt;
+  const double* uD;
+  const double* f_n;
+  const double* f_n1;
+  dg_solve_opts mom, helm;
+  int32_t fixed_point;
+  double fixed_point_tol;
+} dg_projection_params;
+
+dg_status dg_projection_step(dg_solver* solver, const dg_projection_params* params, double* u,
+                             double* p, dg_solve_info info[2]);
+
 /* Picard solves taken by each momentum stage of the last trbdf2_step
- * (iterations[0] stage 1, [1] stage 2; 1 without fixed-point iterations). */
+ * (iterations[0] stage 1, [1] stage 2; 1 without fixed-point iterations) or
+ * by the momentum predictor of the last dg_projection_step (iterations[0]). */
 dg_status dg_solver_get_fixed_point(const dg_solver* solver, int32_t iterations[2]);
 
 /* One TR-BDF2 step (Section 2, Eqs. first_stage ... helmholtz3a; algebraic

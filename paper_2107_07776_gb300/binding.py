@@ -20,6 +20,7 @@ DG_MAP_CARTESIAN, DG_MAP_GRADED_TANH, DG_MAP_PERTURBED_SIN = 0, 1, 2
 DG_SYS_MOMENTUM, DG_SYS_HELMHOLTZ = 0, 1
 DG_PC_NONE, DG_PC_JACOBI, DG_PC_MG_FP64, DG_PC_MG_FP32 = 0, 1, 2, 3
 DG_GUESS_ZERO, DG_GUESS_EXTRAP, DG_GUESS_LEARNED, DG_GUESS_GIVEN = 0, 1, 2, 3
+DG_SCHEME_BCG, DG_SCHEME_BDF2 = 1, 2
 GAMMA = 2.0 - math.sqrt(2.0)
 
 c_double_p = ctypes.c_void_p
@@ -68,6 +69,13 @@ class dg_guess_stats(ctypes.Structure):
                 ("history", ctypes.c_int32 * 4)]
 
 
+class dg_projection_params(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("dt", ctypes.c_double), ("uD", c_void_p),
+                ("f_n", c_void_p), ("f_n1", c_void_p), ("mom", dg_solve_opts),
+                ("helm", dg_solve_opts), ("fixed_point", ctypes.c_int32),
+                ("fixed_point_tol", ctypes.c_double)]
+
+
 class dg_step_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("extrapolate", ctypes.c_int32), ("uD_stage1", c_void_p),
@@ -102,6 +110,7 @@ SIGNATURES = {
     "dg_solver_set_history": (ctypes.c_int, [c_void_p, c_void_p]),
     "dg_solver_set_stream": (ctypes.c_int, [c_void_p, c_void_p]),
     "dg_solver_get_fixed_point": (ctypes.c_int, [c_void_p, P(ctypes.c_int32)]),
+    "dg_projection_step": (ctypes.c_int, [c_void_p, P(dg_projection_params), c_void_p, c_void_p, P(dg_solve_info)]),
     "dg_solver_set_tracing": (ctypes.c_int, [c_void_p, ctypes.c_int32]),
     "dg_solver_get_trace": (ctypes.c_int, [c_void_p, P(ctypes.c_double), P(ctypes.c_int64)]),
     "dg_guess_configure": (ctypes.c_int, [c_void_p, P(dg_guess_opts)]),
@@ -283,6 +292,13 @@ def dg_solver_set_history(solver: int, u_hist) -> None:
 
 def dg_solver_set_stream(solver: int, stream=None) -> None:
     check(lib().dg_solver_set_stream(solver, stream_ptr(stream)), "dg_solver_set_stream")
+
+
+def dg_projection_step(solver: int, params: dg_projection_params, u, p):
+    info = (dg_solve_info * 2)()
+    check(lib().dg_projection_step(solver, ctypes.byref(params), ptr(u), ptr(p), info),
+          "dg_projection_step")
+    return list(info)
 
 
 def dg_solver_get_fixed_point(solver: int):

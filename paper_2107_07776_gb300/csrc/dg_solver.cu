@@ -38,6 +38,8 @@ struct dg_solver {
   double *rhs_p = nullptr, *p_g = nullptr;
   bool has_hist = false;
   int fp_iters[2] = {1, 1};  // Picard solves of the last step's momentum stages
+  double* u_pred = nullptr;  // BDF2 projection steps: the last predicted velocity
+  bool has_pred = false;
   std::vector<void*> allocs;
   dg::MultiGrid<float>* mg32 = nullptr;   // built on first use
   dg::MultiGrid<double>* mg64 = nullptr;
@@ -372,20 +374,31 @@ dg_status finish_guess(dg_solver* s, int slot, int mode, const double* xs) {
 // fixed_point_tol.  The right-hand side depends on the advecting field only
 // through the Dirichlet data's Lax-Friedrichs term, so it is rebuilt only
 // when there is wall data.  x = s->ustar holds the guess on entry.
-dg_status momentum_stage(dg_solver* s, const dg_step_params* prm, int stage,
+//
+// mid = nullptr: the next advecting field is the iterate itself (the
+// TR-BDF2 stages); otherwise the midpoint (iterate + mid)/2 (the
+// Bell-Colella-Glaz predictor), whose right-hand side depends on the field
+// through its explicit advection as well (rebuild_rhs).
+dg_status momentum_stage(dg_solver* s, int fixed_point, double fixed_point_tol, int stage,
                          const dg_momentum_coeffs* co, const dg_momentum_rhs* rd,
-                         const dg_solve_opts* mo, dg_solve_info* info) {
+                         const dg_solve_opts* mo, dg_solve_info* info,
+                         const double* mid = nullptr, bool rebuild_rhs = false) {
   dg_status st = dg_solve_stage(s, co, 0.0, s->ub, s->rhs_u, s->ustar, mo, info);
   s->fp_iters[stage] = 1;
-  if (st != DG_OK || prm->fixed_point <= 1) return st;
+  if (st != DG_OK || fixed_point <= 1) return st;
   dg_solve_opts o = *mo;
   o.guess = DG_GUESS_GIVEN;  // each Picard solve starts from the previous iterate
   const int64_t nu = s->nu;
   int it = 1;
-  while (it < prm->fixed_point) {
-    DG_CUDA(cudaMemcpyAsync(s->ub, s->ustar, sizeof(double) * nu, cudaMemcpyDeviceToDevice,
-                            s->stream));
-    if (rd->uD) {
+  while (it < fixed_point) {
+    if (mid) {
+      st = s->vo.axpby(nu, 0.5, s->ustar, 0.5, mid, s->ub);
+      if (st != DG_OK) return st;
+    } else {
+      DG_CUDA(cudaMemcpyAsync(s->ub, s->ustar, sizeof(double) * nu, cudaMemcpyDeviceToDevice,
+                              s->stream));
+    }
+    if (rd->uD || rebuild_rhs) {
       st = dg_rhs_momentum(s->mesh, rd, s->rhs_u, s->stream);
       if (st != DG_OK) return st;
     }
@@ -396,8 +409,10 @@ dg_status momentum_stage(dg_solver* s, const dg_step_params* prm, int stage,
     info->status = inf.status;
     ++it;
     if (st != DG_OK) break;
+    // change from the previous iterate: ub - it, or 2 ub - mid with a midpoint
     double dd[2];
-    st = s->vo.axpby(nu, 1.0, s->ustar, -1.0, s->ub, s->w);
+    st = s->vo.axpby(nu, 1.0, s->ustar, mid ? -2.0 : -1.0, s->ub, s->w);
+    if (st == DG_OK && mid) st = s->vo.axpby(nu, 1.0, s->w, 1.0, mid, s->w);
     if (st == DG_OK) st = s->vo.dots_host(nu, 1, s->w, s->w, nu, dd);
     if (st == DG_OK) st = s->vo.dots_host(nu, 1, s->ustar, s->ustar, nu, dd + 1);
     if (st != DG_OK) break;
@@ -406,7 +421,7 @@ dg_status momentum_stage(dg_solver* s, const dg_step_params* prm, int stage,
       st = DG_EBREAKDOWN;
       break;
     }
-    if (std::sqrt(dd[0]) < prm->fixed_point_tol * std::max(std::sqrt(dd[1]), 1e-300)) break;
+    if (std::sqrt(dd[0]) < fixed_point_tol * std::max(std::sqrt(dd[1]), 1e-300)) break;
   }
   s->fp_iters[stage] = it;
   return st;
@@ -544,6 +559,7 @@ dg_status dg_solver_set_history(dg_solver* s, const double* u_hist) {
     set_error("dg_solver_set_history: null solver");
     return DG_EINVAL;
   }
+  s->has_pred = false;
   if (!u_hist) {
     s->has_hist = false;
     return DG_OK;
@@ -633,7 +649,7 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(1);
   STEP(prepare_guess(s, 0, prm->mom.guess, s->rhs_u, s->ustar));
   tr.mark(2);
-  STEP(momentum_stage(s, prm, 0, &co1, &r1, &mo, &info[0]));
+  STEP(momentum_stage(s, prm->fixed_point, prm->fixed_point_tol, 0, &co1, &r1, &mo, &info[0]));
   tr.mark(1);
   STEP(finish_guess(s, 0, prm->mom.guess, s->ustar));
   tr.mark(3);
@@ -690,7 +706,7 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(1);
   STEP(prepare_guess(s, 2, prm->mom.guess, s->rhs_u, s->ustar));
   tr.mark(2);
-  STEP(momentum_stage(s, prm, 1, &co2, &r2, &mo, &info[2]));
+  STEP(momentum_stage(s, prm->fixed_point, prm->fixed_point_tol, 1, &co2, &r2, &mo, &info[2]));
   tr.mark(1);
   STEP(finish_guess(s, 2, prm->mom.guess, s->ustar));
   tr.mark(3);
@@ -716,6 +732,118 @@ dg_status trbdf2_step(dg_solver* s, const dg_step_params* prm, double* u, double
   tr.mark(5);
   DG_CUDA(cudaStreamSynchronize(st_));
   tr.finish();
+#undef STEP
+  return DG_OK;
+}
+
+dg_status dg_projection_step(dg_solver* s, const dg_projection_params* prm, double* u, double* p,
+                             dg_solve_info info[2]) {
+  if (!s || !prm || !u || !p || !(prm->dt > 0.0) ||
+      (prm->scheme != DG_SCHEME_BCG && prm->scheme != DG_SCHEME_BDF2)) {
+    set_error("dg_projection_step: bad argument");
+    return DG_EINVAL;
+  }
+  if (!check_opts(&prm->mom, "dg_projection_step") || !check_opts(&prm->helm, "dg_projection_step"))
+    return DG_EINVAL;
+  if (prm->fixed_point > 1 && !(prm->fixed_point_tol > 0.0)) {
+    set_error("dg_projection_step: fixed_point > 1 needs fixed_point_tol > 0");
+    return DG_EINVAL;
+  }
+  if (join_caller(s) != DG_OK) return DG_ECUDA;
+  dg_solve_info loc[2];
+  if (!info) info = loc;
+  std::memset(info, 0, sizeof(dg_solve_info) * 2);
+  dg_mesh* m = s->mesh;
+  VecOps& vo = s->vo;
+  const cudaStream_t st_ = s->stream;
+  const int64_t nu = s->nu, np = s->np;
+  const double dt = prm->dt;
+  const bool bcg = prm->scheme == DG_SCHEME_BCG;
+  dg_solve_opts mo = prm->mom, ho = prm->helm;
+  mo.system = DG_SYS_MOMENTUM;
+  ho.system = DG_SYS_HELMHOLTZ;
+  if (mo.guess != DG_GUESS_ZERO) mo.guess = DG_GUESS_GIVEN;
+  dg_status st;
+#define STEP(call)              \
+  do {                          \
+    st = (call);                \
+    if (st != DG_OK) return st; \
+  } while (0)
+  if (!s->has_hist) {  // u^{n-1} = u^n before the first step
+    DG_CUDA(cudaMemcpyAsync(s->u_hist, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+    s->has_hist = true;
+  }
+  if (!bcg && !s->u_pred) STEP(dalloc(s, &s->u_pred, nu));
+  // ---------------- momentum predictor ----------------
+  dg_momentum_coeffs co;
+  dg_momentum_rhs r;
+  std::memset(&r, 0, sizeof(r));
+  if (bcg) {  // Eq. momentum_BCG: Crank-Nicolson with the midpoint advecting field
+    co = {1.0 / dt, 1.0 / (2.0 * s->Re), 0.5};
+    if (prm->fixed_point > 1)
+      DG_CUDA(cudaMemcpyAsync(s->ub, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+    else
+      STEP(vo.axpby(nu, 1.5, u, -0.5, s->u_hist, s->ub));
+    r.mass = co.mass;
+    r.u_mass = u;
+    r.n_terms = 1;
+    r.visc[0] = co.visc;
+    r.adv[0] = co.adv;
+    r.w[0] = u;
+    r.wbar[0] = s->ub;
+    if (prm->f_n && prm->f_n1) {
+      STEP(vo.axpby(nu, 0.5, prm->f_n, 0.5, prm->f_n1, s->fcomb));
+      r.f = s->fcomb;
+    }
+  } else {  // Eq. momentum_HI: BDF2 with the previous predicted velocity as field
+    co = {1.5 / dt, 1.0 / s->Re, 1.0};
+    DG_CUDA(cudaMemcpyAsync(s->ub, s->has_pred ? s->u_pred : u, sizeof(double) * nu,
+                            cudaMemcpyDeviceToDevice, st_));
+    STEP(vo.axpby(nu, 4.0, u, -1.0, s->u_hist, s->uss));
+    r.mass = 1.0 / (2.0 * dt);
+    r.u_mass = s->uss;
+    r.f = prm->f_n1;
+  }
+  r.p = p;
+  r.uD = prm->uD;
+  r.dir_visc = co.visc;
+  r.dir_adv = co.adv;
+  r.ubar = s->ub;
+  STEP(dg_rhs_momentum(m, &r, s->rhs_u, st_));
+  if (mo.guess != DG_GUESS_ZERO)
+    DG_CUDA(cudaMemcpyAsync(s->ustar, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+  if (bcg)
+    STEP(momentum_stage(s, prm->fixed_point, prm->fixed_point_tol, 0, &co, &r, &mo, &info[0], u,
+                        true));
+  else
+    STEP(momentum_stage(s, 1, 0.0, 0, &co, &r, &mo, &info[0]));
+  s->fp_iters[1] = 1;
+  // ---------------- projection ----------------
+  if (bcg) {  // Eq. helmholtz_BCG: the pressure increment
+    const double alpha = 1.0 / (s->c * s->c * dt * dt);
+    DG_CUDA(cudaMemsetAsync(s->p_g, 0, sizeof(double) * np, st_));
+    STEP(dg_rhs_pressure(m, alpha, dt, s->ustar, s->p_g, s->rhs_p, st_));
+    ho.guess = DG_GUESS_ZERO;
+    STEP(dg_solve_stage(s, nullptr, alpha, nullptr, s->rhs_p, s->p_g, &ho, &info[1]));
+    DG_CUDA(cudaMemcpyAsync(s->u_hist, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+    STEP(project_fused(m, s->p_g, s->ut_new, s->ustar, -dt, nullptr, u, st_));
+    STEP(vo.axpby(np, 1.0, p, 1.0, s->p_g, p));
+  } else {  // Eq. helmholtz_HI with tau = 2 dt / 3
+    const double tau = 2.0 * dt / 3.0, alpha = 1.0 / (s->c * s->c * tau * tau);
+    STEP(project_fused(m, p, s->ut_old, s->ustar, tau, nullptr, s->uss, st_));
+    STEP(dg_rhs_pressure(m, alpha, tau, s->uss, p, s->rhs_p, st_));
+    if (ho.guess != DG_GUESS_ZERO) {
+      ho.guess = DG_GUESS_GIVEN;
+      DG_CUDA(cudaMemcpyAsync(s->p_g, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
+    }
+    STEP(dg_solve_stage(s, nullptr, alpha, nullptr, s->rhs_p, s->p_g, &ho, &info[1]));
+    DG_CUDA(cudaMemcpyAsync(s->u_pred, s->ustar, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+    s->has_pred = true;
+    DG_CUDA(cudaMemcpyAsync(s->u_hist, u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st_));
+    STEP(project_fused(m, s->p_g, s->ut_new, s->ustar, -tau, s->ut_old, u, st_));
+    DG_CUDA(cudaMemcpyAsync(p, s->p_g, sizeof(double) * np, cudaMemcpyDeviceToDevice, st_));
+  }
+  DG_CUDA(cudaStreamSynchronize(st_));
 #undef STEP
   return DG_OK;
 }
