@@ -361,10 +361,30 @@ def run_ours(args, rank, world):
                      "value": (mesh2.n_dofs_u + mesh2.n_dofs_p) / (ms2 * 1e-3) / 1e9,
                      "unit": "GDoF/s", "solvers": summarise(w2, res2, args.steps, train2)}
         mesh2.close()
+    study = None if args.no_guess_study else guess_study(b)
     return dict(value=value, ms_per_step=ms_per_step, clocks=main["clocks"], e2e=e2e,
                 roofline=roof, gpu_launches=main["launches"], solvers=solvers, apply=apply,
-                dofs=dofs, autotune=autotune, secondary=secondary,
+                dofs=dofs, autotune=autotune, secondary=secondary, guess_study=study,
                 iterations=np.array(main["iters"]).mean(axis=0).round(2).tolist())
+
+
+def guess_study(b):
+    """The learned initial guess over a long run (48^3 Q2/Q1 Taylor-Green
+    vortex, 400 steps: the nets train during the first 200 and only infer
+    during the last 200) against the extrapolated guess on the same steps,
+    FP32 multigrid Helmholtz: Krylov iterations per solve and ms per step
+    over the evaluated steps, for the pressure net alone and for both nets."""
+    from paper_2107_07776_gb300 import guessstudy as gs
+    w = W.TGV48
+    base, ub, pb = gs.run(w, 400, 200, False, 1, b.DG_PC_MG_FP32, 1e-8)
+    out = {"workload": workload_label(w), "steps": 400, "train_steps": 200,
+           "extrapolated": {k: base[k] for k in ("iterations_per_solve", "ms_per_step")}}
+    for systems, name in ((1, "learned_pressure"), (3, "learned_both")):
+        lrn, ul, pl = gs.run(w, 400, 200, True, systems, b.DG_PC_MG_FP32, 1e-8)
+        out[name] = {k: lrn[k] for k in ("iterations_per_solve", "ms_per_step")}
+        out[name]["step_time_vs_extrapolated"] = lrn["ms_per_step"] / base["ms_per_step"]
+        out[name]["final_u_rel_diff"] = float(np.linalg.norm(ul - ub) / np.linalg.norm(ub))
+    return out
 
 
 def time_applies(args, b, w, mesh, dev, stream, flush, u0):
@@ -539,6 +559,8 @@ def main():
                          "default per workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-guess-study", action="store_true",
+                    help="skip the 400-step learned-guess study on the 48^3 vortex")
     ap.add_argument("--mg-degree", type=int, default=0,
                     help="Chebyshev degree of the multigrid smoother for --solver (0: its default)")
     ap.add_argument("--oracle-budget", type=float, default=30.0,
@@ -587,7 +609,8 @@ def main():
             "data": "synthetic", "config": cfg, "clocks": r["clocks"], "e2e": r["e2e"],
             "gpu_launches": r["gpu_launches"], "iterations_per_step": r["iterations"],
             "solvers": r["solvers"], "apply": r["apply"], "roofline": r["roofline"],
-            "secondary": r["secondary"], "autotune": r["autotune"], "cpu_baseline": cb}
+            "secondary": r["secondary"], "guess_study": r["guess_study"],
+            "autotune": r["autotune"], "cpu_baseline": cb}
     print(json.dumps(line))
 
 

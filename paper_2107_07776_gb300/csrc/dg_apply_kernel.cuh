@@ -321,7 +321,7 @@ constexpr int smem_words(int cpb) {
 // default cells per CTA with the registers per thread capped at 96 and 80
 // (more resident CTAs per SM, possibly at the price of spills); variants 5
 // and 6 are the face-once form (face fluxes, then cells) with the default
-// cells per CTA, uncapped and capped at 80 registers; variant 7 is the
+// cells per CTA, capped at 72 and 80 registers; variant 7 is the
 // thread-per-cell Q1 kernel (3D scalar operators without advection on two
 // points per direction; elsewhere it runs as variant 1).
 // (kTuneVariants, variant_split and variant_q1 are in dg_common.cuh.)
@@ -339,7 +339,7 @@ constexpr int cpb_variant(int v) {
 template <typename T, int DIM, int N, bool ADV>
 constexpr int minb_variant(int v) {
   const int threads = ((cpb_variant<T, DIM, N, ADV>(v) * Shape<N, DIM>::NB + 31) / 32) * 32;
-  const int cap = v == 3 ? 96 : (v == 4 || v == 6 ? 80 : 0);
+  const int cap = v == 3 ? 96 : (v == 4 || v == 6 ? 80 : (v == 5 ? 72 : 0));
   if (cap == 0) return 1;
   const int b = 65536 / (threads * cap);
   return b < 1 ? 1 : b;

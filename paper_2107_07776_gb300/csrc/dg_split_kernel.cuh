@@ -218,6 +218,9 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   __shared__ A s_u[CPB][NB];
   __shared__ A s_q[DIM][CPB][NB];
   __shared__ __align__(16) A s_fl[CPB][NB][2 * DIM][2];
+  // the thread's own gradient-term factors (cv, ca), kept in shared memory
+  // rather than registers: more resident CTAs per SM
+  __shared__ A s_cva[CPB][NB][2 * DIM];
   const int tid = threadIdx.x;
   const int cl = tid / NB, node = tid - (tid / NB) * NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
@@ -234,13 +237,9 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   // mass W, the gradient-term factors visc W / h_b^2 and -adv W ubar_b / h_b
   // (both inverse extents of the gradient and its transpose folded in), and
   // the normal-derivative weights L_i'(s) / h_b of the face terms
-  A cm = zero, cv[DIM], ca[DIM], gdl[DIM][2];
+  A cm = zero, gdl[DIM][2];
 #pragma unroll
-  for (int b = 0; b < DIM; ++b) {
-    cv[b] = zero;
-    ca[b] = zero;
-    gdl[b][0] = gdl[b][1] = zero;
-  }
+  for (int b = 0; b < DIM; ++b) gdl[b][0] = gdl[b][1] = zero;
   if (active) {
     lex_coords(cell, a.n0, a.n1, ci);
     A h[3], hi[3];
@@ -259,8 +258,9 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
     const A vW = ld_val<T, A>(a.visc) * W, aW = -(ld_val<T, A>(a.adv) * W);
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
-      cv[b] = vW * hi[b] * hi[b];
-      if (ADV) ca[b] = aW * hi[b] * ld_val<T, A>(ub[((int64_t)b * a.ncell + cell) * NB + node]);
+      s_cva[cl][node][b] = vW * hi[b] * hi[b];
+      s_cva[cl][node][DIM + b] =
+          ADV ? aW * hi[b] * ld_val<T, A>(ub[((int64_t)b * a.ncell + cell) * NB + node]) : zero;
       gdl[b][0] = tb.dL[0][ii[b]] * hi[b];
       gdl[b][1] = tb.dL[1][ii[b]] * hi[b];
     }
@@ -303,8 +303,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
           else du.fma(tb.D[ii[b]][m], v);
         }
         SumOf<A> q;
-        q.start(cv[b], du.value());
-        if (ADV) q.fma(ca[b], u);
+        q.start(s_cva[cl][node][b], du.value());
+        if (ADV) q.fma(s_cva[cl][node][DIM + b], u);
         s_q[b][cl][node] = q.value();
       }
     }
