@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) presplit_kernel(int64_t n, const double* 
   }
 }
 
-static dg_status presplit(int64_t n, const double* x, double* out, cudaStream_t s) {
+dg_status presplit(int64_t n, const double* x, double* out, cudaStream_t s) {
   if (n <= 0) return DG_OK;
   int64_t blocks = (n / 2 + 255) / 256;
   blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 8));

@@ -169,6 +169,9 @@ struct dg_mesh {
   // the copy in ps_ub was made from
   const double* ub_keep = nullptr;
   const double* ub_split_of = nullptr;
+  // split copies of the explicit terms' fields (float-float right-hand
+  // sides), velocity-sized, allocated on first use
+  double* ps_pool[4] = {nullptr, nullptr, nullptr, nullptr};
   bool level = false;       // a multigrid level (pressure space only)
   // autotuned tile shape of the operator kernels: variant index per
   // [precision: 0 FP64, 1 FP32][operator: 0 pressure, 1 momentum, 2 momentum
@@ -213,6 +216,9 @@ void keep_presplit_ubar(dg_mesh* m, const double* ubar);
 // host-side split of a double into a float pair, packed in a double's bits
 // (the layout df_bits reads)
 double pack_pair(double x);
+
+// out[i] = x[i] as float pairs in double-sized slots (one kernel on s)
+dg_status presplit(int64_t n, const double* x, double* out, cudaStream_t s);
 
 // launchers (dg_apply.cu)
 template <typename T>

@@ -172,6 +172,25 @@ __device__ __forceinline__ double df_widen(float f) {
   return __longlong_as_double((long long)bits);
 }
 
+// A double narrowed to float with integer operations only (no FP64-pipe
+// conversion): the leading 24 significant bits, truncated (relative error
+// below 2^-23); magnitudes below FP32's normal range give a signed zero,
+// above it (and infinities) a signed infinity, NaN stays NaN.  For FP32
+// preconditioner arithmetic on FP64 data.
+__device__ __forceinline__ float df_narrow(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int top = (unsigned int)(b >> 32);
+  const unsigned int sign = top & 0x80000000u;
+  const int e = (int)((top >> 20) & 0x7FFu);
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return __int_as_float((int)sign);
+  if (ef >= 255) {
+    const bool nan = e == 0x7FF && (b & 0xFFFFFFFFFFFFFull) != 0ull;
+    return __int_as_float((int)(sign | 0x7F800000u | (nan ? 0x00400000u : 0u)));
+  }
+  return __int_as_float((int)(sign | ((unsigned int)ef << 23) | (unsigned int)((b >> 29) & 0x7FFFFFull)));
+}
+
 // hi + lo rounded once to double (a single FP64 addition)
 __device__ __forceinline__ double df_to(df64 a) { return df_widen(a.hi) + df_widen(a.lo); }
 

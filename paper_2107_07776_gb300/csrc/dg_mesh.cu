@@ -473,6 +473,8 @@ void dg_mesh_destroy(dg_mesh* m) {
   }
   if (m->ps_src) cudaFree(m->ps_src);
   if (m->ps_ub) cudaFree(m->ps_ub);
+  for (double* q : m->ps_pool)
+    if (q) cudaFree(q);
   free_geometry(m);
   delete m;
 }

@@ -8,6 +8,8 @@
 // cells per CTA, cell data in shared memory, neighbour traces from global
 // memory, every output written once (deterministic).  These run once per
 // stage, not per Krylov iteration.
+#include <type_traits>
+
 #include "dg_common.cuh"
 #include "dg_df64.cuh"
 #include "dg_geom.cuh"
@@ -228,6 +230,16 @@ struct ExplTerms {
   const double* wb[2];
 };
 
+// The explicit-term kernels in float-float arithmetic read their fields w,
+// wbar pre-split into float pairs (one split pass per field and call instead
+// of one split per read; run_explicit_terms_a makes the copies); in native
+// FP64 they read the fields themselves.
+template <typename A>
+__device__ __forceinline__ A ldw(double v) {
+  if constexpr (std::is_same<A, df64>::value) return df_bits(v);
+  else return Arith<A>::from(v);
+}
+
 template <int N, int DIM>
 constexpr int expl_minb(int threads) {
   return 65536 / (threads * 96) < 1 ? 1 : 65536 / (threads * 96);
@@ -275,7 +287,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
     for (int t = 0; t < NT; ++t)
 #pragma unroll
       for (int b = 0; b < DIM; ++b)
-        s_wb[t][b][cl][node] = Ar::from(et.wb[t][((int64_t)b * g.ncell + cell) * NB + node]);
+        s_wb[t][b][cl][node] = ldw<A>(et.wb[t][((int64_t)b * g.ncell + cell) * NB + node]);
   }
   __syncthreads();
   if (active) {  // normal traces of the advecting fields, both sides (walls: inside only)
@@ -290,7 +302,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
         for (int i = 0; i < N; ++i) {
           const int nd = nodeof(N, DIM, ax, i, t);
           wi = Ar::fma(tb.L[s][i], s_wb[tt][ax][cl][nd], wi);
-          if (nb >= 0) wo += tb.L[1 - s][i] * Ar::from(__ldg(&et.wb[tt][((int64_t)ax * g.ncell + nb) * NB + nd]));
+          if (nb >= 0) wo += tb.L[1 - s][i] * ldw<A>(__ldg(&et.wb[tt][((int64_t)ax * g.ncell + nb) * NB + nd]));
         }
         s_wn[tt][cl][fp][0] = wi * sgn;
         s_wn[tt][cl][fp][1] = wo * sgn;
@@ -302,7 +314,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
       A v = zero;
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        const A u = Ar::from(et.w[t][((int64_t)c * g.ncell + cell) * NB + node]);
+        const A u = ldw<A>(et.w[t][((int64_t)c * g.ncell + cell) * NB + node]);
         s_u[t][cl][node] = u;
         v += visc[t] * u;
       }
@@ -364,7 +376,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
             A v = zero;
 #pragma unroll
             for (int tt = 0; tt < NT; ++tt) {
-              const A u = Ar::from(__ldg(&et.w[tt][((int64_t)c * g.ncell + nb) * NB + nd]));
+              const A u = ldw<A>(__ldg(&et.w[tt][((int64_t)c * g.ncell + nb) * NB + nd]));
               uout[tt] += tb.L[1 - s][i] * u;
               v += visc[tt] * u;
             }
@@ -475,8 +487,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const int nd = nodeof(N, DIM, ax, i, t);
-      if (hasL) l = Ar::fma(tb.L[1][i], Ar::from(__ldg(&wa[cL * NB + nd])), l);
-      if (hasR) r = Ar::fma(tb.L[0][i], Ar::from(__ldg(&wa[cR * NB + nd])), r);
+      if (hasL) l = Ar::fma(tb.L[1][i], ldw<A>(__ldg(&wa[cL * NB + nd])), l);
+      if (hasR) r = Ar::fma(tb.L[0][i], ldw<A>(__ldg(&wa[cR * NB + nd])), r);
     }
     wnL[tt] = l;
     wnR[tt] = r;
@@ -493,12 +505,12 @@ __global__ void __launch_bounds__(256)
       for (int tt = 0; tt < NT; ++tt) {
         const double* wc = et.w[tt] + (int64_t)c * g.ncell * NB;
         if (hasL) {
-          const A u = Ar::from(__ldg(&wc[cL * NB + nd]));
+          const A u = ldw<A>(__ldg(&wc[cL * NB + nd]));
           uL[tt] = Ar::fma(tb.L[1][i], u, uL[tt]);
           vl = Ar::fma(visc[tt], u, vl);
         }
         if (hasR) {
-          const A u = Ar::from(__ldg(&wc[cR * NB + nd]));
+          const A u = ldw<A>(__ldg(&wc[cR * NB + nd]));
           uR[tt] = Ar::fma(tb.L[0][i], u, uR[tt]);
           vr = Ar::fma(visc[tt], u, vr);
         }
@@ -570,7 +582,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   for (int tt = 0; tt < NT; ++tt)
 #pragma unroll
     for (int b = 0; b < DIM; ++b)
-      wbn[tt][b] = active ? Ar::from(et.wb[tt][((int64_t)b * g.ncell + cell) * NB + node]) : zero;
+      wbn[tt][b] = active ? ldw<A>(et.wb[tt][((int64_t)b * g.ncell + cell) * NB + node]) : zero;
   int64_t fpos[2 * DIM];
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
@@ -586,7 +598,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       A v = zero;
 #pragma unroll
       for (int tt = 0; tt < NT; ++tt) {
-        u[tt] = Ar::from(et.w[tt][((int64_t)c * g.ncell + cell) * NB + node]);
+        u[tt] = ldw<A>(et.w[tt][((int64_t)c * g.ncell + cell) * NB + node]);
         v = Ar::fma(visc[tt], u[tt], v);
       }
       s_v[cl][node] = v;
@@ -1022,6 +1034,20 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 }
 
 // ------------------------------------------------------------------
+// FP64 data in the diagonal's arithmetic type: float by integer narrowing
+// (no FP64-pipe conversion), double as is; and 1/d stored as double (FP32
+// reciprocal widened exactly for float, an FP64 division for double).
+template <typename R>
+__device__ __forceinline__ R to_r(double v) {
+  if constexpr (sizeof(R) == 4) return df_narrow(v);
+  else return v;
+}
+template <typename R>
+__device__ __forceinline__ double inv_r(R d) {
+  if constexpr (sizeof(R) == 4) return df_widen(__frcp_rn(d));
+  else return 1.0 / d;
+}
+
 // Diagonal of mass M + visc A + adv C(ubar) (walls = 1) or of
 // alpha M^p + K (walls = 0, adv = 0), one thread per node.
 template <int DIM, int N, typename R, int CPB>
@@ -1048,12 +1074,12 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
         const double* ua = ub + (int64_t)ax * g.ncell * NB;
         R unin = 0.0, unout = 0.0;
 #pragma unroll
-        for (int i = 0; i < N; ++i) unin = Ar::fma(tb.L[s][i], (R)__ldg(&ua[cell * NB + nodeof(N, DIM, ax, i, t)]), unin);
+        for (int i = 0; i < N; ++i) unin = Ar::fma(tb.L[s][i], to_r<R>(__ldg(&ua[cell * NB + nodeof(N, DIM, ax, i, t)])), unin);
         const int64_t nb = neighbour(g, ci, ax, s);
         if (nb >= 0) {
 #pragma unroll
           for (int i = 0; i < N; ++i)
-            unout = Ar::fma(tb.L[1 - s][i], (R)__ldg(&ua[nb * NB + nodeof(N, DIM, ax, i, t)]), unout);
+            unout = Ar::fma(tb.L[1 - s][i], to_r<R>(__ldg(&ua[nb * NB + nodeof(N, DIM, ax, i, t)])), unout);
         }
         s_in[cl][fp] = sgn * unin;
         s_out[cl][fp] = sgn * unout;
@@ -1065,8 +1091,8 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
   R h[3] = {1, 1, 1}, hi[3] = {1, 1, 1};
   for (int b = 0; b < DIM; ++b) {
-    h[b] = (R)g.h[b][ci[b]];
-    hi[b] = (R)g.hi[b][ci[b]];
+    h[b] = to_r<R>(g.h[b][ci[b]]);
+    hi[b] = to_r<R>(g.hi[b][ci[b]]);
   }
   auto Wat = [&](const int j[3]) {
     R W = 1.0;
@@ -1084,7 +1110,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       acc += Wat(j) * dm * dm;
     }
     d += visc * acc;
-    if (adv != R(0.0)) d -= adv * W * (R)ub[((int64_t)b * g.ncell + cell) * NB + node] * tb.D[ii[b]][ii[b]] * hi[b];
+    if (adv != R(0.0)) d -= adv * W * to_r<R>(ub[((int64_t)b * g.ncell + cell) * NB + node]) * tb.D[ii[b]][ii[b]] * hi[b];
   }
   for (int ax = 0; ax < DIM; ++ax) {
     const int t = tangof(N, DIM, ax, ii);
@@ -1099,7 +1125,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       const R unin = adv != R(0.0) ? s_in[cl][(2 * ax + s) * NF + t] : R(0.0);
       R fv = 0.0, fg = 0.0;
       if (nb >= 0) {
-        const R hiN = (R)g.hi[ax][neighbour_coord(g, ci, ax, s)];
+        const R hiN = to_r<R>(g.hi[ax][neighbour_coord(g, ci, ax, s)]);
         // a one-cell period makes the cell its own neighbour
         const R uout = nb == cell ? tb.L[1 - s][ii[ax]] : R(0.0);
         const R dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] * hiN : R(0.0);
@@ -1120,10 +1146,10 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     }
   }
   if (inv_copies > 0) {  // the Jacobi scaling itself, 1/d, for each of inv_copies components
-    const double id = 1.0 / (double)d;
+    const double id = inv_r<R>(d);
     for (int c = 0; c < inv_copies; ++c) diag[((int64_t)c * g.ncell + cell) * NB + node] = id;
   } else {
-    diag[cell * NB + node] = (double)d;
+    diag[cell * NB + node] = sizeof(R) == 4 ? df_widen((float)d) : (double)d;
   }
 }
 
@@ -1181,9 +1207,36 @@ dg_status run_explicit_a(const dg_mesh* m, int mode, double visc, double adv, co
   return DG_OK;
 }
 
+// Float-float explicit terms: each distinct field of et split once into the
+// mesh's pool (slots allocated on first use), the kernels then read pairs.
+dg_status split_fields(const dg_mesh* mc, ExplTerms& et, cudaStream_t s) {
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  const int64_t n = (int64_t)m->dim * m->ncell * m->nbu;
+  const double* src[4];
+  int nsrc = 0;
+  const double** fields[4] = {&et.w[0], &et.w[1], &et.wb[0], &et.wb[1]};
+  for (const double** f : fields) {
+    int k = 0;
+    while (k < nsrc && src[k] != *f) ++k;
+    if (k == nsrc) {
+      src[nsrc++] = *f;
+      if (!m->ps_pool[k]) DG_CUDA(cudaMalloc(&m->ps_pool[k], sizeof(double) * n));
+      const dg_status st = presplit(n, *f, m->ps_pool[k], s);
+      if (st != DG_OK) return st;
+    }
+    *f = m->ps_pool[k];
+  }
+  return DG_OK;
+}
+
 template <typename A, int DIM, int N>
-dg_status run_explicit_terms_a(const dg_mesh* m, const ExplTerms& et, int nt, double* rhs,
+dg_status run_explicit_terms_a(const dg_mesh* m, const ExplTerms& et_in, int nt, double* rhs,
                                cudaStream_t s) {
+  ExplTerms et = et_in;
+  if constexpr (std::is_same<A, df64>::value) {
+    const dg_status st = split_fields(m, et, s);
+    if (st != DG_OK) return st;
+  }
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
