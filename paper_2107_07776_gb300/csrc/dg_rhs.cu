@@ -788,7 +788,8 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
 // along the others, and so on; partial sums that meet the same remaining
 // tables are added before they are contracted further.  Face term: the
 // quadrature-weighted normal flux w |face| n {{u}} is tested against the
-// pressure basis, tangential axes first.
+// pressure basis, tangential axes first.  In float-float arithmetic uss
+// arrives pre-split (run_pressure_rhs_a).
 template <typename A, int DIM, int N, int NP, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
     pressure_rhs_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
@@ -824,7 +825,7 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
       A Wq = tb.w[q0] * h[0] * tb.w[q1] * h[1];
       if (DIM == 3) Wq = Wq * tb.w[q2] * h[2];
       s_u[c][cl][nd] = Wq * sel3(c, hiv[0], hiv[1], hiv[2]) *
-                       Ar::from(uss[((int64_t)c * g.ncell + cell) * NB + nd]);
+                       ldw<A>(uss[((int64_t)c * g.ncell + cell) * NB + nd]);
     }
     for (int fp = node; fp < NFP; fp += NBP) {
       const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
@@ -837,7 +838,7 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
       A uin = zero;
 #pragma unroll
       for (int i = 0; i < N; ++i)
-        uin = Ar::fma(tb.L[s][i], Ar::from(__ldg(&uss[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)])),
+        uin = Ar::fma(tb.L[s][i], ldw<A>(__ldg(&uss[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)])),
                       uin);
       A uav = uin;
       if (nb >= 0) {
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
 #pragma unroll
         for (int i = 0; i < N; ++i)
           uout = Ar::fma(tb.L[1 - s][i],
-                         Ar::from(__ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)])), uout);
+                         ldw<A>(__ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)])), uout);
         uav = half * (uin + uout);
       }
       s_f[cl][fp] = wt * sgn * uav;
@@ -1307,6 +1308,14 @@ dg_status run_mass_grad(const dg_mesh* m, double mass, const double* um, const d
 template <typename A, int DIM, int N>
 dg_status run_pressure_rhs_a(const dg_mesh* m, double alpha, double inv_tau, const double* uss,
                              const double* p_old, double* rhs, cudaStream_t s) {
+  if constexpr (std::is_same<A, df64>::value) {  // the kernel reads uss pre-split
+    dg_mesh* mm = const_cast<dg_mesh*>(m);
+    const int64_t n = (int64_t)m->dim * m->ncell * m->nbu;
+    if (!mm->ps_pool[0]) DG_CUDA(cudaMalloc(&mm->ps_pool[0], sizeof(double) * n));
+    const dg_status st = presplit(n, uss, mm->ps_pool[0], s);
+    if (st != DG_OK) return st;
+    uss = mm->ps_pool[0];
+  }
   constexpr int NP = N - 1;
   constexpr int CPB = cpb_for<NP, DIM>();
   constexpr int threads = ((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32;
