@@ -156,7 +156,11 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * on one tuned mesh from different streams must not overlap.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
  * Trilinear meshes use one tile shape per kernel: the call records an empty
- * report.  Allocates temporary device buffers; synchronous. */
+ * report.  Results are cached in a JSON file (path DG_TUNE_CACHE, default
+ * $HOME/.cache/dgns_autotune.json when that directory exists; "off"
+ * disables it), keyed by device name, compute capability, library build and
+ * mesh signature: a hit restores the choices without timing.  Allocates
+ * temporary device buffers; synchronous. */
 dg_status dg_autotune(dg_mesh* mesh, void* stream);
 
 /* Sets the operator kernels' tile variant of this mesh by hand (0..7, the

@@ -18,6 +18,7 @@
 // atomics, and the result is deterministic.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -336,6 +337,94 @@ static int cpb_for_mesh(const dg_mesh* m, bool pressure, bool adv, int v) {
   return adv ? cpb_dim<T, 3, true>(v, N) : cpb_dim<T, 3, false>(v, N);
 }
 
+// ---------------------------------------------------------------- cache
+// Tuning results persist in a JSON file (DG_TUNE_CACHE, else
+// $HOME/.cache/dgns_autotune.json; DG_TUNE_CACHE=off disables it), one entry
+// per key: the device name, its compute capability, this library build and
+// the mesh signature (dimension, cells, periodicity, degree, mapping,
+// multigrid level).  A hit restores the chosen variants and the report of
+// the run that timed them without timing again; the build stamp keeps an
+// entry from outliving the kernels it measured.
+static std::string tune_cache_path() {
+  const char* e = std::getenv("DG_TUNE_CACHE");
+  if (e && std::strcmp(e, "off") == 0) return std::string();
+  if (e && *e) return std::string(e);
+  const char* home = std::getenv("HOME");
+  return home && *home ? std::string(home) + "/.cache/dgns_autotune.json" : std::string();
+}
+
+static std::string tune_key(const dg_mesh* m) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof(prop));
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaGetDeviceProperties(&prop, dev);
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s|sm_%d%d|%s %s|d%d|n%d,%d,%d|p%d%d%d|k%d|map%d:%.17g,%.17g,%.17g|lv%d",
+                prop.name, prop.major, prop.minor, __DATE__, __TIME__, m->dim, m->n[0], m->n[1],
+                m->n[2], m->periodic[0], m->periodic[1], m->periodic[2], m->k, m->desc.map,
+                m->desc.map_param[0], m->desc.map_param[1], m->desc.map_param[2], m->level ? 1 : 0);
+  std::string k(buf);
+  for (char& c : k)
+    if (c == '"' || c == '\\') c = '_';
+  return k;
+}
+
+static std::string read_file(const std::string& path) {
+  std::string out;
+  FILE* f = path.empty() ? nullptr : std::fopen(path.c_str(), "rb");
+  if (!f) return out;
+  char buf[4096];
+  size_t r;
+  while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) out.append(buf, r);
+  std::fclose(f);
+  return out;
+}
+
+// entries are lines {"key": "...", "tune": [6 ints], "report": <JSON>}
+static bool tune_cache_lookup(dg_mesh* m) {
+  const std::string path = tune_cache_path();
+  const std::string text = read_file(path);
+  const std::string needle = "{\"key\": \"" + tune_key(m) + "\", \"tune\": [";
+  const size_t at = text.find(needle);
+  if (at == std::string::npos) return false;
+  int v[6];
+  const char* q = text.c_str() + at + needle.size();
+  for (int i = 0; i < 6; ++i) {
+    char* end = nullptr;
+    const long x = std::strtol(q, &end, 10);
+    if (end == q || x < 0 || x >= kTuneVariants) return false;
+    v[i] = (int)x;
+    q = end;
+    while (*q == ',' || *q == ' ') ++q;
+  }
+  const char* rep = std::strstr(q, "\"report\": ");
+  const char* eol = rep ? std::strchr(rep, '\n') : nullptr;
+  if (!rep || !eol || eol - rep < 12) return false;
+  for (int i = 0; i < 6; ++i) m->tune[i / 3][i % 3] = v[i];
+  m->tune_report = std::string(rep + 10, eol - 1);  // drop the entry's closing brace
+  m->tuned = true;
+  return true;
+}
+
+static void tune_cache_store(const dg_mesh* m) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return;
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos && slash > 0) {
+    const std::string dir = path.substr(0, slash);
+    FILE* probe = std::fopen((dir + "/.dgns_probe").c_str(), "ab");
+    if (!probe) return;  // directory missing or not writable: no cache
+    std::fclose(probe);
+    std::remove((dir + "/.dgns_probe").c_str());
+  }
+  FILE* f = std::fopen(path.c_str(), "ab");
+  if (!f) return;
+  std::fprintf(f, "{\"key\": \"%s\", \"tune\": [%d, %d, %d, %d, %d, %d], \"report\": %s}\n",
+               tune_key(m).c_str(), m->tune[0][0], m->tune[0][1], m->tune[0][2], m->tune[1][0],
+               m->tune[1][1], m->tune[1][2], m->tune_report.c_str());
+  std::fclose(f);
+}
+
 // Time every tile-shape variant of the mesh's operator kernels (CUDA events,
 // median of 7 launches after 2 warm-up launches, inputs zero: the kernels'
 // work does not depend on values) and keep the fastest.  Results do not
@@ -351,6 +440,7 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
     dg_status st0 = alloc_split_flux(m);
     if (st0 != DG_OK) return st0;
   }
+  if (tune_cache_lookup(m)) return DG_OK;
   const int64_t nu = m->ncell * m->nbu * m->dim, np = m->ncell * m->nbp;
   void* buf = nullptr;
   const size_t bytes = sizeof(double) * (size_t)(3 * nu + 2 * np);
@@ -434,6 +524,7 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
   if (st != DG_OK) return st;
   m->tuned = true;
   m->tune_report = rep;
+  tune_cache_store(m);
   return DG_OK;
 }
 

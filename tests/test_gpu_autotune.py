@@ -80,3 +80,30 @@ def test_autotune_on_trilinear_mesh_is_a_no_op():
     gm = b.Mesh(3, (4, 3, 3), (0, 0, 0), (1, 1, 1), (False,) * 3, 2, 2, (0.04, 0, 0))
     b.dg_autotune(gm.handle)
     assert json.loads(b.dg_autotune_report(gm.handle)) == []
+
+
+def test_tuning_cache_keyed_by_device_and_mesh(tmp_path, monkeypatch):
+    """The autotuner writes its choices to the JSON cache under a key naming
+    the device, its compute capability and the mesh; a second mesh with the
+    same signature restores them (same report) without timing, and a mesh
+    with another signature gets its own entry."""
+    from paper_2107_07776_gb300 import binding as b
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("DG_TUNE_CACHE", str(cache))
+    g1 = b.Mesh(3, (6, 5, 4), (0, 0, 0), (1, 1, 1), (True,) * 3, 2)
+    b.dg_autotune(g1.handle)
+    r1 = b.dg_autotune_report(g1.handle)
+    lines = cache.read_text().splitlines()
+    assert len(lines) >= 2          # the mesh and its multigrid levels
+    name = torch.cuda.get_device_name(0)
+    major, minor = torch.cuda.get_device_capability(0)
+    assert all(name.replace('"', "_") in l and f"sm_{major}{minor}" in l for l in lines)
+    entry = json.loads(lines[0])
+    assert json.loads(r1) == entry["report"] and len(entry["tune"]) == 6
+    g2 = b.Mesh(3, (6, 5, 4), (0, 0, 0), (1, 1, 1), (True,) * 3, 2)
+    b.dg_autotune(g2.handle)
+    assert b.dg_autotune_report(g2.handle) == r1
+    assert len(cache.read_text().splitlines()) == len(lines)   # a hit adds nothing
+    g3 = b.Mesh(3, (6, 5, 6), (0, 0, 0), (1, 1, 1), (True,) * 3, 2)
+    b.dg_autotune(g3.handle)
+    assert len(cache.read_text().splitlines()) > len(lines)
