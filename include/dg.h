@@ -155,8 +155,8 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * the face-once form shares that scratch between its applies, so applies
  * on one tuned mesh from different streams must not overlap.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
- * Trilinear meshes use one tile shape per kernel: the call records an empty
- * report.  Results are cached in a JSON file (path DG_TUNE_CACHE, default
+ * Trilinear meshes time the general kernel's three tile shapes (half,
+ * default and double the cells per CTA) instead.  Results are cached in a JSON file (path DG_TUNE_CACHE, default
  * $HOME/.cache/dgns_autotune.json when that directory exists; "off"
  * disables it), keyed by device name, compute capability, library build and
  * mesh signature: a hit restores the choices without timing.  Allocates
@@ -170,7 +170,8 @@ dg_status dg_autotune(dg_mesh* mesh, void* stream);
  * operators without advection on two points per direction, in every
  * precision; other operators run variant 1 instead) for every operator and
  * precision; a face-once variant allocates the mesh's flux scratch.
- * Trilinear meshes ignore it. */
+ * Trilinear meshes take 0-2 as the general kernel's tile shapes (half,
+ * default, double the cells per CTA) and run 1 for the others. */
 dg_status dg_mesh_set_variant(dg_mesh* mesh, int32_t variant);
 
 /* JSON list of the tuning choices and timings of a mesh ("[]" if untuned),

@@ -129,6 +129,8 @@ static dg_status launch_general_op(const dg_mesh* m, bool pressure, T mass, T vi
   }
   const bool use_adv = !pressure && ubar != nullptr && adv != T(0);
   const int kind = pressure ? 0 : (use_adv ? 2 : 1);
+  const int v = m->tune[sizeof(T) == 8 ? 0 : 1][kind];
+  a.variant = v < kGeneralVariants ? v : 1;
   return dispatch_general(m, pressure, kind, pressure ? m->np : m->nu, a, ubar, src, dst, s);
 }
 
@@ -329,6 +331,21 @@ static dg_status alloc_split_flux(dg_mesh* m) {
   return DG_OK;
 }
 
+// cells per CTA of the general (trilinear) kernel's tile shapes (reporting)
+template <int DIM>
+static int general_cpb_dim(int N, bool adv, int v) {
+  switch (N) {
+    case 2: return adv ? gen_cpb<double, DIM, 2, true>(v) : gen_cpb<double, DIM, 2, false>(v);
+    case 3: return adv ? gen_cpb<double, DIM, 3, true>(v) : gen_cpb<double, DIM, 3, false>(v);
+    case 4: return adv ? gen_cpb<double, DIM, 4, true>(v) : gen_cpb<double, DIM, 4, false>(v);
+    default: return adv ? gen_cpb<double, DIM, 5, true>(v) : gen_cpb<double, DIM, 5, false>(v);
+  }
+}
+static int general_cpb_for_mesh(const dg_mesh* m, bool pressure, bool adv, int v) {
+  const int N = pressure ? m->np : m->nu;
+  return m->dim == 2 ? general_cpb_dim<2>(N, adv, v) : general_cpb_dim<3>(N, adv, v);
+}
+
 // cells per CTA of a tuning variant (reporting)
 template <typename T>
 static int cpb_for_mesh(const dg_mesh* m, bool pressure, bool adv, int v) {
@@ -431,12 +448,7 @@ static void tune_cache_store(const dg_mesh* m) {
 // depend on the choice: each output is computed by one thread in a fixed
 // order whatever the number of cells per CTA.
 dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
-  if (!m->affine) {  // trilinear cells: one tile shape per kernel, nothing to choose
-    m->tuned = true;
-    m->tune_report = "[]";
-    return DG_OK;
-  }
-  if (!m->split_flux) {  // face-flux scratch of the face-once variants
+  if (m->affine && !m->split_flux) {  // face-flux scratch of the face-once variants
     dg_status st0 = alloc_split_flux(m);
     if (st0 != DG_OK) return st0;
   }
@@ -465,8 +477,11 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
       // on tgv32) and wins back-to-back with a warm instruction cache (28 vs
       // 31 us) but loses inside the step, between other kernels (49 vs
       // 31 us cold).  Not timed: reported as 0.
-      const bool q1_ok = op == 0 && m->dim == 3 && m->np == 2 && prec == 1;
-      for (int v = 0; v < kTuneVariants && st == DG_OK; ++v) {
+      const bool q1_ok = op == 0 && m->dim == 3 && m->np == 2 && prec == 1 && m->affine;
+      // trilinear meshes: the general kernel's tile shapes (cells per CTA
+      // half, default, double)
+      const int nvar = m->affine ? kTuneVariants : kGeneralVariants;
+      for (int v = 0; v < nvar && st == DG_OK; ++v) {
         if (variant_q1(v) && !q1_ok) continue;
         m->tune[prec][op] = v;
         auto run = [&]() -> dg_status {
@@ -501,9 +516,19 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
       char line[1024];
       const bool p = op == 0, adv = op == 2;
       auto cp = [&](int v) {
+        if (!m->affine) return v < kGeneralVariants ? general_cpb_for_mesh(m, p, adv, v) : 0;
         if (variant_q1(v)) return 64;  // two threads per cell, 128 threads per CTA
         return prec == 0 ? cpb_for_mesh<double>(m, p, adv, v) : cpb_for_mesh<float>(m, p, adv, v);
       };
+      if (!m->affine) {
+        std::snprintf(line, sizeof(line),
+                      "%s{\"op\": \"%s\", \"precision\": \"%s\", \"kernel\": \"general_op_kernel\", "
+                      "\"cells_per_cta\": [%d, %d, %d], \"ms\": [%.5f, %.5f, %.5f], \"chosen_variant\": %d}",
+                      rep.size() > 1 ? ", " : "", opname[op], prec == 0 ? "f64" : "f32", cp(0), cp(1),
+                      cp(2), times[0], times[1], times[2], bestv);
+        rep += line;
+        continue;
+      }
       std::snprintf(line, sizeof(line),
                     "%s{\"op\": \"%s\", \"precision\": \"%s\", "
                     "\"cells_per_cta\": [%d, %d, %d, %d, %d, %d, %d, %d], "
@@ -549,8 +574,10 @@ dg_status dg_mesh_set_variant(dg_mesh* m, int32_t variant) {
     dg_status st = alloc_split_flux(m);
     if (st != DG_OK) return st;
   }
+  // trilinear meshes take the general kernel's tile shapes 0-2 (others: 1)
+  const int v = m->affine || variant < kGeneralVariants ? variant : 1;
   for (auto& row : m->tune)
-    for (int& v : row) v = variant;
+    for (int& x : row) x = v;
   return DG_OK;
 }
 

@@ -73,6 +73,7 @@ inline cudaError_t launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
 // Operator-kernel variants chosen by the autotuner: 0-4 cell-centric tile
 // shapes, 5-6 face-once, 7 thread-per-cell Q1.
 constexpr int kTuneVariants = 8;
+constexpr int kGeneralVariants = 3;  // trilinear cells: half, default, double cells per CTA
 __host__ __device__ constexpr bool variant_split(int v) { return v == 5 || v == 6; }
 __host__ __device__ constexpr bool variant_q1(int v) { return v == 7; }
 

@@ -47,6 +47,7 @@ struct GenArgs {
   T* cr;
   const T* cdinv;
   T cc1, cc2;
+  int variant;    // tile shape: 0 half, 1 default, 2 double the cells per CTA
 };
 
 // metric term i: from the float-pair copy in float-float arithmetic, else
@@ -65,8 +66,10 @@ constexpr int gen_smem_words(int cpb) {
 }
 
 template <typename T, int DIM, int N, bool ADV>
-constexpr int gen_cpb() {
+constexpr int gen_cpb(int variant = 1) {
   int c = default_cpb<N, DIM>();
+  if (variant == 0) c = c > 1 ? c / 2 : 1;
+  if (variant == 2) c *= 2;
   // shared-memory words are 8 bytes (double or float-float) at most
   while (c > 1 && (c * Shape<N, DIM>::NB > 1024 || 8 * gen_smem_words<N, DIM, ADV>(c) > 46 * 1024))
     c /= 2;
@@ -337,10 +340,9 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
   }
 }
 
-template <typename T, typename A, int DIM, int N, bool ADV, bool VEL>
-dg_status launch_general_fixed(const GenArgs<T>& args, const Tab1D<A>& tb, const T* ub,
-                               const T* src, T* dst, cudaStream_t s) {
-  constexpr int CPB = gen_cpb<T, DIM, N, ADV>();
+template <typename T, typename A, int DIM, int N, bool ADV, bool VEL, int CPB>
+dg_status launch_general_cpb(const GenArgs<T>& args, const Tab1D<A>& tb, const T* ub,
+                             const T* src, T* dst, cudaStream_t s) {
   constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
   const int64_t blocks = (args.ncell + CPB - 1) / CPB;
   if (blocks > 0x7fffffff) {
@@ -351,6 +353,18 @@ dg_status launch_general_fixed(const GenArgs<T>& args, const Tab1D<A>& tb, const
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
+}
+
+// the autotuner's tile shape (GenArgs::variant); the clamped cell counts of
+// neighbouring variants can coincide
+template <typename T, typename A, int DIM, int N, bool ADV, bool VEL>
+dg_status launch_general_fixed(const GenArgs<T>& args, const Tab1D<A>& tb, const T* ub,
+                               const T* src, T* dst, cudaStream_t s) {
+  switch (args.variant) {
+    case 0: return launch_general_cpb<T, A, DIM, N, ADV, VEL, gen_cpb<T, DIM, N, ADV>(0)>(args, tb, ub, src, dst, s);
+    case 2: return launch_general_cpb<T, A, DIM, N, ADV, VEL, gen_cpb<T, DIM, N, ADV>(2)>(args, tb, ub, src, dst, s);
+    default: return launch_general_cpb<T, A, DIM, N, ADV, VEL, gen_cpb<T, DIM, N, ADV>(1)>(args, tb, ub, src, dst, s);
+  }
 }
 
 // kind: 0 pressure (pressure layout, no advection), 1 velocity without
