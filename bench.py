@@ -449,7 +449,7 @@ def roofline(w, mesh, autotune, apply_ms):
     for r in autotune or []:
         if r.get("op") == "momentum+advection" and r.get("precision") == "f64":
             variant = r["chosen_variant"]
-            face_once = bool(r["face_once"][variant])
+            face_once = bool(r.get("face_once", [0] * 8)[variant])
     if w.map == 2:
         kname = ("general_op_kernel<double,df64> (momentum apply on trilinear cells; flop model of "
                  "the affine operator, a lower bound of the work)")
