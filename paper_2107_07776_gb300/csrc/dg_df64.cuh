@@ -111,6 +111,14 @@ __device__ __forceinline__ void acc_add(DfAcc& a, df64 x) {
 
 __device__ __forceinline__ df64 acc_value(const DfAcc& a) { return df_fast_two_sum(a.s, a.e); }
 
+// a += b for two partial sums (independent accumulators shorten the
+// dependency chain of a long sum; they are merged at the end)
+__device__ __forceinline__ void acc_merge(DfAcc& a, const DfAcc& b) {
+  const df64 t = df_two_sum(a.s, b.s);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, b.e));
+}
+
 // A float-float value stored in 8 bytes of a double-typed array (the
 // pre-split copies the FP64 operator kernels read): the bits are the pair.
 __device__ __forceinline__ df64 df_bits(double v) {
@@ -233,6 +241,7 @@ struct SumOf {
   __device__ __forceinline__ void start(A x, A y) { v = x * y; }
   __device__ __forceinline__ void fma(A x, A y) { v = __fma_any(x, y, v); }
   __device__ __forceinline__ A value() const { return v; }
+  __device__ __forceinline__ void merge(const SumOf& o) { v = v + o.v; }
   __device__ __forceinline__ static A __fma_any(A x, A y, A c) {
     if constexpr (sizeof(A) == 4) return __fmaf_rn(x, y, c);
     else return __fma_rn(x, y, c);
@@ -245,6 +254,7 @@ struct SumOf<df64> {
   __device__ __forceinline__ void start(df64 x, df64 y) { a = acc_prod(x, y); }
   __device__ __forceinline__ void fma(df64 x, df64 y) { acc_fma(a, x, y); }
   __device__ __forceinline__ df64 value() const { return acc_value(a); }
+  __device__ __forceinline__ void merge(const SumOf& o) { acc_merge(a, o.a); }
 };
 
 // Arithmetic-type adapters for kernels templated on the arithmetic type A

@@ -310,28 +310,34 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
     }
     __syncthreads();
     if (active) {
-      SumOf<A> y;
-      y.start(cm, s_u[cl][node]);
+      // one partial sum per direction (the mass term joins the first), so
+      // that the three dependency chains interleave; merged at the end
+      SumOf<A> y[DIM];
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
-          y.fma(tb.D[m][ii[b]], s_q[b][cl][j[0] + N * (j[1] + N * j[2])]);
+          const A q = s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
+          if (m == 0) y[b].start(tb.D[m][ii[b]], q);
+          else y[b].fma(tb.D[m][ii[b]], q);
         }
       }
+      y[0].fma(cm, s_u[cl][node]);
       cp_async_wait_all();  // the thread's own copies (no barrier needed)
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           const A F0 = s_fl[cl][node][2 * b + s][0], G = s_fl[cl][node][2 * b + s][1];
-          y.fma(s ? F0 : -F0, tb.L[s][ii[b]]);
-          y.fma(G, gdl[b][s]);
+          y[b].fma(s ? F0 : -F0, tb.L[s][ii[b]]);
+          y[b].fma(G, gdl[b][s]);
         }
       }
-      const A yv = y.value();
+#pragma unroll
+      for (int b = 1; b < DIM; ++b) y[0].merge(y[b]);
+      const A yv = y[0].value();
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(yv) : (T)Ar::to_f(yv);
       if (a.cheb) {
