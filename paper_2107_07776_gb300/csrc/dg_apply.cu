@@ -131,6 +131,34 @@ static dg_status launch_general_op(const dg_mesh* m, bool pressure, T mass, T vi
   const int kind = pressure ? 0 : (use_adv ? 2 : 1);
   const int v = m->tune[sizeof(T) == 8 ? 0 : 1][kind];
   a.variant = v < kGeneralVariants ? v : 1;
+  a.csrc = src;
+  if constexpr (sizeof(T) == 8) {
+    if (m->fp64_arith == 0) {  // float-float: the kernel reads pre-split inputs
+      dg_mesh* mm = const_cast<dg_mesh*>(m);
+      const int N = pressure ? m->np : m->nu;
+      const int64_t nb = m->dim == 3 ? (int64_t)N * N * N : (int64_t)N * N;
+      if (!m->ps_src || (use_adv && !m->ps_ub)) {
+        set_error("operator apply: float-float split buffers missing on this mesh");
+        return DG_EINVAL;
+      }
+      dg_status st = presplit((int64_t)ncomp * m->ncell * nb, src, m->ps_src, s);
+      if (st != DG_OK) return st;
+      const T* ub_ps = nullptr;
+      if (use_adv) {
+        if (!(m->ub_keep == ubar && m->ub_split_of == ubar)) {
+          st = presplit((int64_t)m->dim * m->ncell * m->nbu, ubar, m->ps_ub, s);
+          if (st != DG_OK) return st;
+          mm->ub_split_of = ubar;
+        }
+        ub_ps = m->ps_ub;
+      }
+      a.mass = (T)pack_pair((double)a.mass);
+      a.visc = (T)pack_pair((double)a.visc);
+      a.adv = (T)pack_pair((double)a.adv);
+      a.pen = (T)pack_pair((double)a.pen);
+      return dispatch_general(m, pressure, kind, N, a, ub_ps, m->ps_src, dst, s);
+    }
+  }
   return dispatch_general(m, pressure, kind, pressure ? m->np : m->nu, a, ubar, src, dst, s);
 }
 

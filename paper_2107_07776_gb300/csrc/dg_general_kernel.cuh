@@ -48,6 +48,7 @@ struct GenArgs {
   const T* cdinv;
   T cc1, cc2;
   int variant;    // tile shape: 0 half, 1 default, 2 double the cells per CTA
+  const T* csrc;  // the caller's source vector (the Chebyshev update reads it)
 };
 
 // metric term i: from the float-pair copy in float-float arithmetic, else
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < a.ncell;
   const A zero = Ar::c(0.0), half = Ar::c(0.5), two = Ar::c(2.0);
-  const A mass = Ar::from(a.mass), visc = Ar::from(a.visc), advc = Ar::from(a.adv),
-          pen = Ar::from(a.pen);
+  const A mass = ld_val<T, A>(a.mass), visc = ld_val<T, A>(a.visc), advc = ld_val<T, A>(a.adv),
+          pen = ld_val<T, A>(a.pen);
 
   int ci[3] = {0, 0, 0};
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
       A ubn[DIM];
 #pragma unroll
       for (int r = 0; r < DIM; ++r) {
-        ubn[r] = Ar::from(ub[((int64_t)r * a.ncell + cell) * NB + node]);
+        ubn[r] = ld_val<T, A>(ub[((int64_t)r * a.ncell + cell) * NB + node]);
         s_ub[r][cl][node] = ubn[r];
       }
 #pragma unroll
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
 
   for (int c = 0; c < a.ncomp; ++c) {
     const T* srcc = src + (int64_t)c * a.ncell * NB;
-    if (active) s_u[cl][node] = Ar::from(srcc[cell * NB + node]);
+    if (active) s_u[cl][node] = ld_val<T, A>(srcc[cell * NB + node]);
     __syncthreads();
     if (active) {
       // ---- volume flux at this node ----
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
         if (interior) {
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const A v = Ar::from(__ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]));
+            const A v = ld_val<T, A>(__ldg(&srcc[nb * NB + node_of(N, ax, i, t, DIM)]));
             uout = Ar::fma(tb.L[1 - s][i], v, uout);
             dnout = Ar::fma(tb.dL[1 - s][i], v, dnout);
           }
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
               const int nd = node_of(N, ax, i, t, DIM);
               wi = Ar::fma(tb.L[s][i], s_ub[r][cl][nd], wi);
               if (interior)
-                wo = Ar::fma(tb.L[1 - s][i], Ar::from(__ldg(&ub[((int64_t)r * a.ncell + nb) * NB + nd])), wo);
+                wo = Ar::fma(tb.L[1 - s][i], ld_val<T, A>(__ldg(&ub[((int64_t)r * a.ncell + nb) * NB + nd])), wo);
             }
             unin += nr * wi;
             unout += nr * wo;
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
       if (a.cheb) {
-        const T dk = srcc[cell * NB + node];
+        const T dk = a.csrc[(int64_t)c * a.ncell * NB + cell * NB + node];
         a.cx[o] += dk;
         const T rk = a.cr[o] - a.cdinv[o] * yt;
         a.cr[o] = rk;

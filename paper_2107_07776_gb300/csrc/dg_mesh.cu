@@ -281,9 +281,17 @@ dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
   cudaError_t e = cudaMalloc(&m->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "mesh status word");
+  // float-float applies: the per-apply split buffers of the source vector
+  // and advecting field (and, on affine meshes, split copies of the extents)
+  {
+    const int64_t nps =
+        (m->level ? (int64_t)m->nbp : std::max<int64_t>((int64_t)m->dim * m->nbu, m->nbp)) * m->ncell;
+    e = cudaMalloc(&m->ps_src, sizeof(double) * nps);
+    if (e == cudaSuccess && !m->level)
+      e = cudaMalloc(&m->ps_ub, sizeof(double) * (int64_t)m->dim * m->nbu * m->ncell);
+    if (e != cudaSuccess) return cuda_fail(e, "mesh float-float split buffers");
+  }
   if (!m->affine) return build_geometry(m, !m->level, s);
-  // float-float applies: split copies of the extents and the per-apply
-  // split buffers of the source vector and advecting field
   for (int a = 0; a < 3; ++a) {
     const int na = m->n[a];
     std::vector<double> hp(na), hip(na);
@@ -301,12 +309,6 @@ dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "mesh upload (float-float extents)");
   }
-  const int64_t nps = (m->level ? (int64_t)m->nbp : std::max<int64_t>((int64_t)m->dim * m->nbu, m->nbp)) *
-                      m->ncell;
-  e = cudaMalloc(&m->ps_src, sizeof(double) * nps);
-  if (e == cudaSuccess && !m->level)
-    e = cudaMalloc(&m->ps_ub, sizeof(double) * (int64_t)m->dim * m->nbu * m->ncell);
-  if (e != cudaSuccess) return cuda_fail(e, "mesh float-float split buffers");
   return DG_OK;
 }
 
