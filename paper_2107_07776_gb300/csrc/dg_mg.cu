@@ -234,6 +234,103 @@ __global__ void restrict_sum_kernel(int64_t ncoarse_dofs, int nbc, int nchild,
   bc[gid] = acc;
 }
 
+// 3D transfers between Q1 levels (two points per direction on both sides,
+// the h-coarsening levels), by sum factorisation: one thread per fine cell
+// (prolongation) or coarse cell (restriction) with the cell's 8 values in
+// registers; along axis a the 1D map is the 2x2 matrix M[s][i][j] of the
+// child's position s (0 or 1 on a coarsened axis, 2 otherwise).  Same
+// weights as prolong_add_kernel / restrict_*_kernel, 3 sweeps of 2 terms
+// instead of 8 terms of 3 factors per value.
+template <typename T>
+__device__ __forceinline__ void q1_tensor_map(const Transfer& tr, const int sel[3], bool transpose,
+                                              const T in[8], T out[8]) {
+  T t1[8], t2[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {  // axis 0 (x fastest)
+    const int i0 = i & 1, rest = i & 6;
+    const T w0 = transpose ? transfer_w<T>(tr, sel[0], 0, i0) : transfer_w<T>(tr, sel[0], i0, 0);
+    const T w1 = transpose ? transfer_w<T>(tr, sel[0], 1, i0) : transfer_w<T>(tr, sel[0], i0, 1);
+    t1[i] = w0 * in[rest] + w1 * in[rest | 1];
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {  // axis 1
+    const int i1 = (i >> 1) & 1, rest = i & 5;
+    const T w0 = transpose ? transfer_w<T>(tr, sel[1], 0, i1) : transfer_w<T>(tr, sel[1], i1, 0);
+    const T w1 = transpose ? transfer_w<T>(tr, sel[1], 1, i1) : transfer_w<T>(tr, sel[1], i1, 1);
+    t2[i] = w0 * t1[rest] + w1 * t1[rest | 2];
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {  // axis 2
+    const int i2 = i >> 2, rest = i & 3;
+    const T w0 = transpose ? transfer_w<T>(tr, sel[2], 0, i2) : transfer_w<T>(tr, sel[2], i2, 0);
+    const T w1 = transpose ? transfer_w<T>(tr, sel[2], 1, i2) : transfer_w<T>(tr, sel[2], i2, 1);
+    out[i] = w0 * t2[rest] + w1 * t2[rest | 4];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) prolong_q1_kernel(const __grid_constant__ Transfer tr,
+                                                         int64_t nfine_cells,
+                                                         const T* __restrict__ xc, T* __restrict__ xf) {
+  pdl_entry();
+  for (int64_t fc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; fc < nfine_cells;
+       fc += (int64_t)gridDim.x * blockDim.x) {
+    int fi[3];
+    lex_coords(fc, tr.nfine[0], tr.nfine[1], fi);
+    int ci[3], sel[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = tr.hco[a] ? fi[a] >> 1 : fi[a];
+      sel[a] = tr.hco[a] ? (fi[a] & 1) : 2;
+    }
+    const int64_t cc = ci[0] + (int64_t)tr.ncoarse[0] * (ci[1] + (int64_t)tr.ncoarse[1] * ci[2]);
+    T in[8], out[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) in[j] = xc[cc * 8 + j];
+    q1_tensor_map<T>(tr, sel, false, in, out);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xf[fc * 8 + i] += out[i];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) restrict_q1_kernel(const __grid_constant__ Transfer tr,
+                                                          int64_t ncoarse_cells,
+                                                          const T* __restrict__ rf, T* __restrict__ bc) {
+  pdl_entry();
+  for (int64_t cc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cc < ncoarse_cells;
+       cc += (int64_t)gridDim.x * blockDim.x) {
+    int ci[3];
+    lex_coords(cc, tr.ncoarse[0], tr.ncoarse[1], ci);
+    T acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = T(0);
+    // children in a fixed order (bit a of ch along the a-th coarsened axis)
+    for (int ch = 0; ch < 8; ++ch) {
+      int fi[3] = {ci[0], ci[1], ci[2]}, sel[3] = {2, 2, 2}, t = ch;
+      bool skip = false;
+      for (int a = 0; a < 3; ++a) {
+        if (tr.hco[a]) {
+          sel[a] = t & 1;
+          t >>= 1;
+          fi[a] = 2 * ci[a] + sel[a];
+        }
+      }
+      skip = t != 0;  // ch enumerates only 2^(coarsened axes) children
+      if (skip) continue;
+      const int64_t fc = fi[0] + (int64_t)tr.nfine[0] * (fi[1] + (int64_t)tr.nfine[1] * fi[2]);
+      T in[8], out[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) in[i] = rf[fc * 8 + i];
+      q1_tensor_map<T>(tr, sel, true, in, out);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] += out[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) bc[cc * 8 + j] = acc[j];
+  }
+}
+
 // Largest/smallest eigenvalues of a symmetric tridiagonal matrix by
 // bisection on Sturm sequence counts.
 void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, double* lo,
@@ -673,17 +770,26 @@ dg_status MultiGrid<T>::vcycle(int l) {
       if (t.hco[a]) nchild *= 2;
     const int nbc = t.dim == 3 ? t.nc * t.nc * t.nc : t.nc * t.nc;
     const int64_t ncc = C.n / nbc, nterm = C.n * nchild;
-    // the fine level's spare direction buffer holds the partial sums
-    // (nchild * coarse DoFs = fine cells * coarse nodes <= fine DoFs)
-    launch(restrict_part_kernel<T>, (unsigned)((nterm + 255) / 256), 256, 0, stream, t, ncc, nchild, L.r, L.d2);
-    count_launch();
-    launch(restrict_sum_kernel<T>, (unsigned)((C.n + 255) / 256), 256, 0, stream, C.n, nbc, nchild, L.d2, C.b);
-    count_launch();
+    if (t.dim == 3 && t.nf == 2 && t.nc == 2) {  // Q1 -> Q1: sum-factorised, one pass
+      launch(restrict_q1_kernel<T>, grid1(ncc), 256, 0, stream, t, ncc, L.r, C.b);
+      count_launch();
+    } else {
+      // the fine level's spare direction buffer holds the partial sums
+      // (nchild * coarse DoFs = fine cells * coarse nodes <= fine DoFs)
+      launch(restrict_part_kernel<T>, (unsigned)((nterm + 255) / 256), 256, 0, stream, t, ncc, nchild, L.r, L.d2);
+      count_launch();
+      launch(restrict_sum_kernel<T>, (unsigned)((C.n + 255) / 256), 256, 0, stream, C.n, nbc, nchild, L.d2, C.b);
+      count_launch();
+    }
   }
   DG_CUDA(cudaGetLastError());
   st = vcycle(l + 1);
   if (st != DG_OK) return st;
-  launch(prolong_add_kernel<T>, grid1(L.n), 256, 0, stream, tr[l], L.n, C.x, L.x); count_launch();
+  if (tr[l].dim == 3 && tr[l].nf == 2 && tr[l].nc == 2)
+    launch(prolong_q1_kernel<T>, grid1(L.n / 8), 256, 0, stream, tr[l], L.n / 8, C.x, L.x);
+  else
+    launch(prolong_add_kernel<T>, grid1(L.n), 256, 0, stream, tr[l], L.n, C.x, L.x);
+  count_launch();
   DG_CUDA(cudaGetLastError());
   return chebyshev(l, smooth_degree, false);
 }
