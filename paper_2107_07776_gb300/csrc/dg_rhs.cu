@@ -482,61 +482,89 @@ __global__ void __launch_bounds__(256)
   A wnL[NT], wnR[NT];
 #pragma unroll
   for (int tt = 0; tt < NT; ++tt) {
-    A l = zero, r = zero;
     const double* wa = et.wb[tt] + (int64_t)ax * g.ncell * NB;
+    SumOf<A> l, r;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const int nd = nodeof(N, DIM, ax, i, t);
-      if (hasL) l = Ar::fma(tb.L[1][i], ldw<A>(__ldg(&wa[cL * NB + nd])), l);
-      if (hasR) r = Ar::fma(tb.L[0][i], ldw<A>(__ldg(&wa[cR * NB + nd])), r);
+      if (hasL) {
+        const A x = ldw<A>(__ldg(&wa[cL * NB + nd]));
+        if (i == 0) l.start(tb.L[1][i], x);
+        else l.fma(tb.L[1][i], x);
+      }
+      if (hasR) {
+        const A x = ldw<A>(__ldg(&wa[cR * NB + nd]));
+        if (i == 0) r.start(tb.L[0][i], x);
+        else r.fma(tb.L[0][i], x);
+      }
     }
-    wnL[tt] = l;
-    wnR[tt] = r;
+    wnL[tt] = hasL ? l.value() : zero;
+    wnR[tt] = hasR ? r.value() : zero;
+  }
+  // Flux coefficients of this face point, the same for every component:
+  //   F0 = sum_t (cdL_t dL_t + cuL_t uL_t + cdR_t dR_t + cuR_t uR_t)
+  // with u the traces and d the reference normal derivatives of term t's
+  // field on each side.  Interior (central flux, normal +e_ax seen from the
+  // lower cell): cd = wt visc_t / (2h), cu = -wt adv_t wn_t / 2 on both
+  // sides.  Wall of one cell: the one-sided flux, coefficients wt visc_t / h
+  // and -wt adv_t wn_t of its single side, in the same orientation (the
+  // reader takes -F0 on a cell's lower face).
+  A cdL[NT], cuL[NT], cdR[NT], cuR[NT];
+  {
+    const bool interior = hasL && hasR;
+    const A fL = interior ? half * wt : wt, fR = interior ? half * wt : wt;
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt) {
+      cdL[tt] = hasL ? fL * hiL * visc[tt] : zero;
+      cuL[tt] = hasL ? -(fL * adv[tt] * wnL[tt]) : zero;
+      cdR[tt] = hasR ? fR * hiR * visc[tt] : zero;
+      cuR[tt] = hasR ? -(fR * adv[tt] * wnR[tt]) : zero;
+    }
   }
   for (int c = 0; c < DIM; ++c) {
-    A vL = zero, dvL = zero, vR = zero, dvR = zero, uL[NT], uR[NT];
+    SumOf<A> f;
+    bool started = false;
 #pragma unroll
-    for (int tt = 0; tt < NT; ++tt) uL[tt] = uR[tt] = zero;
+    for (int tt = 0; tt < NT; ++tt) {
+      const double* wc = et.w[tt] + (int64_t)c * g.ncell * NB;
+      if (hasL) {
+        SumOf<A> u, d;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int nd = nodeof(N, DIM, ax, i, t);
-      A vl = zero, vr = zero;
-#pragma unroll
-      for (int tt = 0; tt < NT; ++tt) {
-        const double* wc = et.w[tt] + (int64_t)c * g.ncell * NB;
-        if (hasL) {
-          const A u = ldw<A>(__ldg(&wc[cL * NB + nd]));
-          uL[tt] = Ar::fma(tb.L[1][i], u, uL[tt]);
-          vl = Ar::fma(visc[tt], u, vl);
+        for (int i = 0; i < N; ++i) {
+          const A x = ldw<A>(__ldg(&wc[cL * NB + nodeof(N, DIM, ax, i, t)]));
+          if (i == 0) {
+            u.start(tb.L[1][i], x);
+            d.start(tb.dL[1][i], x);
+          } else {
+            u.fma(tb.L[1][i], x);
+            d.fma(tb.dL[1][i], x);
+          }
         }
-        if (hasR) {
-          const A u = ldw<A>(__ldg(&wc[cR * NB + nd]));
-          uR[tt] = Ar::fma(tb.L[0][i], u, uR[tt]);
-          vr = Ar::fma(visc[tt], u, vr);
-        }
+        if (!started) f.start(cdL[tt], d.value());
+        else f.fma(cdL[tt], d.value());
+        started = true;
+        f.fma(cuL[tt], u.value());
       }
-      vL = Ar::fma(tb.L[1][i], vl, vL);
-      dvL = Ar::fma(tb.dL[1][i], vl, dvL);
-      vR = Ar::fma(tb.L[0][i], vr, vR);
-      dvR = Ar::fma(tb.dL[0][i], vr, dvR);
+      if (hasR) {
+        SumOf<A> u, d;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const A x = ldw<A>(__ldg(&wc[cR * NB + nodeof(N, DIM, ax, i, t)]));
+          if (i == 0) {
+            u.start(tb.L[0][i], x);
+            d.start(tb.dL[0][i], x);
+          } else {
+            u.fma(tb.L[0][i], x);
+            d.fma(tb.dL[0][i], x);
+          }
+        }
+        if (!started) f.start(cdR[tt], d.value());
+        else f.fma(cdR[tt], d.value());
+        started = true;
+        f.fma(cuR[tt], u.value());
+      }
     }
-    A F0 = zero;
-    if (hasL && hasR) {
-      A a = zero;
-#pragma unroll
-      for (int tt = 0; tt < NT; ++tt) a += adv[tt] * (uL[tt] * wnL[tt] + uR[tt] * wnR[tt]);
-      F0 = wt * (half * (dvL * hiL + dvR * hiR - a));
-    } else if (hasR) {  // lower wall of cell R (outward normal -e_ax)
-      A a = zero;
-#pragma unroll
-      for (int tt = 0; tt < NT; ++tt) a += adv[tt] * uR[tt] * wnR[tt];
-      F0 = -(wt * (a - dvR * hiR));
-    } else {  // upper wall of cell L
-      A a = zero;
-#pragma unroll
-      for (int tt = 0; tt < NT; ++tt) a += adv[tt] * uL[tt] * wnL[tt];
-      F0 = wt * (dvL * hiL - a);
-    }
+    const A F0 = started ? f.value() : zero;
     flux[(c * nface + fg) * NF + t] = F0;
   }
 }
@@ -551,38 +579,46 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF;
   __shared__ A s_v[CPB][NB];
   __shared__ A s_q[DIM][CPB][NB];
+  // the thread's own advective factors W adv_t ubar_t,b / h_b (shared memory
+  // rather than registers)
+  __shared__ A s_ca[CPB][NB][NT * DIM];
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
   const A zero = Ar::c(0.0);
-  A visc[NT], adv[NT];
+  A visc[NT];
 #pragma unroll
-  for (int tt = 0; tt < NT; ++tt) {
-    visc[tt] = Ar::from(et.visc[tt]);
-    adv[tt] = Ar::from(et.adv[tt]);
-  }
+  for (int tt = 0; tt < NT; ++tt) visc[tt] = Ar::from(et.visc[tt]);
   const int64_t f0 = faces_of_axis(0, g.n, g.per), f1 = faces_of_axis(1, g.n, g.per);
   const int64_t nface = f0 + f1 + (DIM == 3 ? faces_of_axis(2, g.n, g.per) : 0);
   int ci[3] = {0, 0, 0};
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  A h[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)}, hi[3] = {Ar::c(1.0), Ar::c(1.0), Ar::c(1.0)};
-  A W = zero, wbn[NT][DIM];
+  // per-node factors, the same for every component: the viscous one
+  // -W / h_b^2 (both inverse extents of the gradient and its transpose
+  // folded in) and the advective ones above
+  A cv[DIM];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) cv[b] = zero;
   if (active) {
     cell_coords(g, cell, ci);
+    A h[3], hi[3];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
       h[b] = Ar::from(g.h[b][ci[b]]);
       hi[b] = Ar::from(g.hi[b][ci[b]]);
     }
-    W = Ar::c(1.0);
+    A W = Ar::c(1.0);
 #pragma unroll
     for (int b = 0; b < DIM; ++b) W = W * tb.w[ii[b]] * h[b];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      cv[b] = -(W * hi[b] * hi[b]);
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt)
+        s_ca[cl][node][tt * DIM + b] =
+            W * hi[b] * Ar::from(et.adv[tt]) * ldw<A>(et.wb[tt][((int64_t)b * g.ncell + cell) * NB + node]);
+    }
   }
-#pragma unroll
-  for (int tt = 0; tt < NT; ++tt)
-#pragma unroll
-    for (int b = 0; b < DIM; ++b)
-      wbn[tt][b] = active ? ldw<A>(et.wb[tt][((int64_t)b * g.ncell + cell) * NB + node]) : zero;
   int64_t fpos[2 * DIM];
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
@@ -595,50 +631,56 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   for (int c = 0; c < DIM; ++c) {
     A u[NT];
     if (active) {
-      A v = zero;
+      SumOf<A> v;
 #pragma unroll
       for (int tt = 0; tt < NT; ++tt) {
         u[tt] = ldw<A>(et.w[tt][((int64_t)c * g.ncell + cell) * NB + node]);
-        v = Ar::fma(visc[tt], u[tt], v);
+        if (tt == 0) v.start(visc[tt], u[tt]);
+        else v.fma(visc[tt], u[tt]);
       }
-      s_v[cl][node] = v;
+      s_v[cl][node] = v.value();
     }
     __syncthreads();
     if (active) {
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
-        A dv = zero;
+        SumOf<A> dv;
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
-          dv = Ar::fma(tb.D[ii[b]][m], s_v[cl][j[0] + N * (j[1] + N * j[2])], dv);
+          const A x = s_v[cl][j[0] + N * (j[1] + N * j[2])];
+          if (m == 0) dv.start(tb.D[ii[b]][m], x);
+          else dv.fma(tb.D[ii[b]][m], x);
         }
-        A q = -(dv * hi[b]);
+        SumOf<A> q;
+        q.start(cv[b], dv.value());
 #pragma unroll
-        for (int tt = 0; tt < NT; ++tt) q += adv[tt] * u[tt] * wbn[tt][b];
-        s_q[b][cl][node] = W * q;
+        for (int tt = 0; tt < NT; ++tt) q.fma(s_ca[cl][node][tt * DIM + b], u[tt]);
+        s_q[b][cl][node] = q.value();
       }
     }
     __syncthreads();
     if (active) {
-      A y = zero;
       const A* fl = flux + (int64_t)c * nface * NF;
+      SumOf<A> y[DIM];  // one partial sum per direction, merged at the end
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
-        A acc = zero;
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
-          acc = Ar::fma(tb.D[m][ii[b]], s_q[b][cl][j[0] + N * (j[1] + N * j[2])], acc);
+          const A x = s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
+          if (m == 0) y[b].start(tb.D[m][ii[b]], x);
+          else y[b].fma(tb.D[m][ii[b]], x);
         }
-        y = Ar::fma(acc, hi[b], y);
         const A F0lo = fl[fpos[2 * b]], F0hi = fl[fpos[2 * b + 1]];
-        y = Ar::fma(-F0lo, tb.L[0][ii[b]], y);
-        y = Ar::fma(F0hi, tb.L[1][ii[b]], y);
+        y[b].fma(-F0lo, tb.L[0][ii[b]]);
+        y[b].fma(F0hi, tb.L[1][ii[b]]);
       }
-      rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += Ar::to_d(y);
+#pragma unroll
+      for (int b = 1; b < DIM; ++b) y[0].merge(y[b]);
+      rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += Ar::to_d(y[0].value());
     }
     __syncthreads();
   }
