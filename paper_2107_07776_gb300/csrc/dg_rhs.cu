@@ -1137,21 +1137,21 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     h[b] = to_r<R>(g.h[b][ci[b]]);
     hi[b] = to_r<R>(g.hi[b][ci[b]]);
   }
-  auto Wat = [&](const int j[3]) {
-    R W = 1.0;
-    for (int b = 0; b < DIM; ++b) W *= tb.w[j[b]] * h[b];
-    return W;
-  };
-  const R W = Wat(ii);
+  // W = prod_b w(i_b) h_b.  The stiffness diagonal along axis b is
+  // sum_m W(j: j_b = m) (D[m][i_b] / h_b)^2 = (W / w(i_b)) h_b^-2 sum_m w(m) D[m][i_b]^2:
+  // the tangential weights factor out of the 1D sum.
+  R wl[3] = {1, 1, 1};
+  for (int b = 0; b < DIM; ++b) wl[b] = tb.w[ii[b]] * h[b];
+  const R W = DIM == 3 ? wl[0] * wl[1] * wl[2] : wl[0] * wl[1];
   R d = mass * W;
   for (int b = 0; b < DIM; ++b) {
-    R acc = 0.0;
-    for (int m = 0; m < N; ++m) {
-      int j[3] = {ii[0], ii[1], ii[2]};
-      j[b] = m;
-      const R dm = tb.D[m][ii[b]] * hi[b];
-      acc += Wat(j) * dm * dm;
-    }
+    R sb = 0.0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) sb += tb.w[m] * tb.D[m][ii[b]] * tb.D[m][ii[b]];
+    R wt = h[b];  // W / w(i_b), times h_b h_b^-2 below
+    for (int c = 0; c < DIM; ++c)
+      if (c != b) wt *= wl[c];
+    const R acc = wt * sb * hi[b] * hi[b];
     d += visc * acc;
     if (adv != R(0.0)) d -= adv * W * to_r<R>(ub[((int64_t)b * g.ncell + cell) * NB + node]) * tb.D[ii[b]][ii[b]] * hi[b];
   }
