@@ -454,7 +454,8 @@ def roofline(w, mesh, autotune, apply_ms):
         kname = ("general_op_kernel<double,df64> (momentum apply on trilinear cells; flop model of "
                  "the affine operator, a lower bound of the work)")
     elif face_once:
-        kname = ("face_flux_kernel + cell_split_kernel<double,df64> (momentum apply, face-once form, "
+        cell = "cell_split_nc_kernel" if variant == 6 else "cell_split_kernel"
+        kname = (f"face_flux_kernel + {cell}<double,df64> (momentum apply, face-once form, "
                  "float-float FP64 arithmetic)")
     else:
         kname = "scalar_op_kernel<double,df64> (momentum apply, float-float FP64 arithmetic)"

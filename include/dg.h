@@ -166,7 +166,8 @@ dg_status dg_autotune(dg_mesh* mesh, void* stream);
 /* Sets the operator kernels' tile variant of this mesh by hand (0..7, the
  * candidates listed in dg_autotune's report: 0-2 cells per CTA half /
  * default / double, 3-4 default with 96 / 80 registers, 5-6 face-once
- * capped at 72 / 80 registers, 7 two threads per Q1 cell -- 3D scalar
+ * capped at 72 registers (6: every component's volume sums between the
+ * same two barriers), 7 two threads per Q1 cell -- 3D scalar
  * operators without advection on two points per direction, in every
  * precision; other operators run variant 1 instead) for every operator and
  * precision; a face-once variant allocates the mesh's flux scratch.

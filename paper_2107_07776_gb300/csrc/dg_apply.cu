@@ -560,7 +560,7 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
       std::snprintf(line, sizeof(line),
                     "%s{\"op\": \"%s\", \"precision\": \"%s\", "
                     "\"cells_per_cta\": [%d, %d, %d, %d, %d, %d, %d, %d], "
-                    "\"register_cap\": [0, 0, 0, 96, 80, 0, 80, 0], \"face_once\": [0, 0, 0, 0, 0, 1, 1, 0], "
+                    "\"register_cap\": [0, 0, 0, 96, 80, 0, 72, 0], \"face_once\": [0, 0, 0, 0, 0, 1, 1, 0], "
                     "\"thread_per_cell\": [0, 0, 0, 0, 0, 0, 0, 1], "
                     "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f, %.5f, %.5f, %.5f], \"chosen_variant\": %d}",
                     rep.size() > 1 ? ", " : "", opname[op], prec == 0 ? "f64" : "f32", cp(0), cp(1),

@@ -321,7 +321,8 @@ constexpr int smem_words(int cpb) {
 // default cells per CTA with the registers per thread capped at 96 and 80
 // (more resident CTAs per SM, possibly at the price of spills); variants 5
 // and 6 are the face-once form (face fluxes, then cells) with the default
-// cells per CTA, capped at 72 and 80 registers; variant 7 is the
+// cells per CTA and 72 registers (variant 6 with the components-interleaved
+// cell pass, cell_split_nc_kernel); variant 7 is the
 // thread-per-cell Q1 kernel (3D scalar operators without advection on two
 // points per direction; elsewhere it runs as variant 1).
 // (kTuneVariants, variant_split and variant_q1 are in dg_common.cuh.)
@@ -339,7 +340,7 @@ constexpr int cpb_variant(int v) {
 template <typename T, int DIM, int N, bool ADV>
 constexpr int minb_variant(int v) {
   const int threads = ((cpb_variant<T, DIM, N, ADV>(v) * Shape<N, DIM>::NB + 31) / 32) * 32;
-  const int cap = v == 3 ? 96 : (v == 4 || v == 6 ? 80 : (v == 5 ? 72 : 0));
+  const int cap = v == 3 ? 96 : (v == 4 ? 80 : (v == 5 || v == 6 ? 72 : 0));
   if (cap == 0) return 1;
   const int b = 65536 / (threads * cap);
   return b < 1 ? 1 : b;
@@ -360,7 +361,32 @@ static dg_status launch_cpb(const OpArgs<T>& args, const Tab1D<A>& tb, const T* 
   return DG_OK;
 }
 
-template <typename T, typename A, int DIM, int N, bool ADV, int CPB, int MINB>
+// the components-interleaved cell pass (dynamic shared memory, above the
+// 48 KB static limit for some shapes: the opt-in is set once per device)
+template <typename T, typename A, int DIM, int N, int NC, bool ADV, int CPB, int MINB>
+static dg_status launch_cell_nc(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
+                                const A* flux, T* dst, cudaStream_t s) {
+  constexpr int smem = NcSplitSmem<A, DIM, N, NC, CPB>::bytes;
+  static_assert(smem <= 227 * 1024, "cell_split_nc_kernel: shared memory");
+  auto kern = cell_split_nc_kernel<T, A, DIM, N, NC, ADV, CPB, MINB>;
+  if (smem > 48 * 1024) {
+    static unsigned long long opted = 0;  // devices (bit i: device i < 64) already opted in
+    int dev = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(__atomic_load_n(&opted, __ATOMIC_ACQUIRE) & bit)) {
+      DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      if (bit) __atomic_fetch_or(&opted, bit, __ATOMIC_ACQ_REL);
+    }
+  }
+  constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
+  const int64_t blocks = (args.ncell + CPB - 1) / CPB;
+  launch(kern, (unsigned)blocks, threads, smem, s, args, tb, src, ub, flux, dst);
+  count_launch();
+  return DG_OK;
+}
+
+template <typename T, typename A, int DIM, int N, bool ADV, int CPB, int MINB, bool NCK = false>
 static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub, const T* src,
                               T* dst, cudaStream_t s) {
   const int n[3] = {args.n0, args.n1, args.n2};
@@ -375,9 +401,20 @@ static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T
   const int64_t fthreads = nface * Shape<N, DIM>::NF;
   launch(face_flux_kernel<T, A, DIM, N, ADV>, (unsigned)((fthreads + 255) / 256), 256, 0, s, args, tb, src, ub, flux);
   count_launch();
+  if constexpr (NCK) {
+    if (args.ncomp == DIM || args.ncomp == 1) {
+      const dg_status st =
+          args.ncomp == DIM ? launch_cell_nc<T, A, DIM, N, DIM, ADV, CPB, MINB>(args, tb, ub, src, flux, dst, s)
+                            : launch_cell_nc<T, A, DIM, N, 1, ADV, CPB, MINB>(args, tb, ub, src, flux, dst, s);
+      if (st != DG_OK) return st;
+      DG_CUDA(cudaGetLastError());
+      return DG_OK;
+    }
+  }
   constexpr int threads = ((CPB * Shape<N, DIM>::NB + 31) / 32) * 32;
   const int64_t blocks = (args.ncell + CPB - 1) / CPB;
-  launch(cell_split_kernel<T, A, DIM, N, ADV, CPB, MINB>, (unsigned)blocks, threads, 0, s, args, tb, src, ub, flux, dst);
+  launch(cell_split_kernel<T, A, DIM, N, ADV, CPB, MINB>, (unsigned)blocks, threads, 0, s, args, tb, src, ub,
+         flux, dst);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -406,8 +443,8 @@ static dg_status launch_v(const OpArgs<T>& args, const Tab1D<A>& tb, const T* ub
     }
     return launch_v<T, A, DIM, N, ADV, 1>(args, tb, ub, src, dst, s);
   } else if constexpr (variant_split(V))
-    return launch_split<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V)>(
-        args, tb, ub, src, dst, s);
+    return launch_split<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V),
+                        V == 6>(args, tb, ub, src, dst, s);
   else
     return launch_cpb<T, A, DIM, N, ADV, cpb_variant<T, DIM, N, ADV>(V), minb_variant<T, DIM, N, ADV>(V)>(
         args, tb, ub, src, dst, s);

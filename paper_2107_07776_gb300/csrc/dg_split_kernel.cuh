@@ -354,4 +354,188 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
   }
 }
 
+// Components-interleaved cell pass of the face-once form (NC components,
+// 1 or DIM): the volume sums of all components run between the same two
+// barriers -- NC x DIM independent dependency chains per phase instead of
+// NC sequential phase pairs with a barrier each -- and the flux pairs of all
+// components are staged per face into shared memory by asynchronous copies
+// issued at entry, each face point once per cell rather than once per node
+// (a third of the shared memory of the per-node staging).  Dynamic shared
+// memory: NcSplitSmem::bytes.
+template <typename A, int DIM, int N, int NC, int CPB>
+struct NcSplitSmem {
+  static constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
+  static constexpr int kAlign = 16 / (int)sizeof(A);  // elements per 16 bytes
+  static constexpr int u = 0;
+  static constexpr int q = u + NC * CPB * NB;
+  static constexpr int fl = (q + NC * DIM * CPB * NB + kAlign - 1) / kAlign * kAlign;
+  static constexpr int cva = fl + CPB * NC * 2 * DIM * NF * 2;
+  static constexpr int bytes = (int)sizeof(A) * (cva + CPB * NB * 2 * DIM);
+};
+
+template <typename T, typename A, int DIM, int N, int NC, bool ADV, int CPB, int MINB>
+__global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MINB)
+    cell_split_nc_kernel(const __grid_constant__ OpArgs<T> a, const __grid_constant__ Tab1D<A> tb,
+                         const T* __restrict__ src, const T* __restrict__ ub,
+                         const A* __restrict__ flux, T* __restrict__ dst) {
+  pdl_entry();
+  using Ar = Arith<A>;
+  constexpr int NB = Shape<N, DIM>::NB, NF = Shape<N, DIM>::NF;
+  constexpr int NFC = 2 * DIM * NF;  // face points of a cell
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // [NC][CPB][NB] values, [NC][DIM][CPB][NB] gradient terms, then the flux
+  // pairs [CPB][NC][2 DIM][NF][2] and the per-node factors [CPB][NB][2 DIM]
+  using L = NcSplitSmem<A, DIM, N, NC, CPB>;
+  A* s_u = reinterpret_cast<A*>(smem_raw) + L::u;
+  A* s_q = reinterpret_cast<A*>(smem_raw) + L::q;
+  A* s_fl = reinterpret_cast<A*>(smem_raw) + L::fl;
+  A* s_cva = reinterpret_cast<A*>(smem_raw) + L::cva;
+  const int tid = threadIdx.x;
+  const int cl = tid / NB, node = tid - (tid / NB) * NB;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cl < CPB && cell < a.ncell;
+  const A zero = Ar::c(0.0);
+  const int n[3] = {a.n0, a.n1, a.n2};
+  const int per[3] = {a.per0, a.per1, a.per2};
+  const int64_t f0 = faces_of_axis(0, n, per), f1 = faces_of_axis(1, n, per);
+  const int64_t f2 = DIM == 3 ? faces_of_axis(2, n, per) : 0;
+  const int64_t nface = f0 + f1 + f2;
+  int ci[3] = {0, 0, 0};
+  const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
+  if (active) lex_coords(cell, a.n0, a.n1, ci);
+  // the cell's faces (2b: lower, 2b+1: upper face of axis b), global indices
+  int64_t fidx[2 * DIM];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    const int64_t foff = b == 0 ? 0 : (b == 1 ? f0 : f0 + f1);
+    const int cb = ci[b], hi_l = per[b] ? (cb + 1) % n[b] : cb + 1;
+    fidx[2 * b] = foff + face_index(b, cb, ci, n, per);
+    fidx[2 * b + 1] = foff + face_index(b, hi_l, ci, n, per);
+  }
+  if (active) {
+    A* fcell = s_fl + (int64_t)cl * NC * NFC * 2;
+    for (int q = node; q < NC * NFC; q += NB) {
+      const int c = q / NFC, r = q - c * NFC, f = r / NF, t = r - f * NF;
+      int64_t F = fidx[0];
+#pragma unroll
+      for (int j = 1; j < 2 * DIM; ++j)
+        if (f == j) F = fidx[j];
+      cp_async<2 * sizeof(A)>(fcell + (int64_t)q * 2, flux + (((int64_t)c * nface + F) * NF + t) * 2);
+    }
+  }
+  cp_async_commit();
+  // per-node coefficients, the same for every component (as in
+  // cell_split_kernel): mass weight, gradient-term factors, normal-derivative
+  // weights of the face terms
+  A cm = zero, gdl[DIM][2];
+  A uo[NC];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) gdl[b][0] = gdl[b][1] = zero;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) uo[c] = zero;
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      uo[c] = ld_val<T, A>(src[((int64_t)c * a.ncell + cell) * NB + node]);
+      s_u[(c * CPB + cl) * NB + node] = uo[c];
+    }
+    A h[3], hi[3];
+    h[0] = ld_val<T, A>(a.h0[ci[0]]);
+    h[1] = ld_val<T, A>(a.h1[ci[1]]);
+    hi[0] = ld_val<T, A>(a.hi0[ci[0]]);
+    hi[1] = ld_val<T, A>(a.hi1[ci[1]]);
+    h[2] = hi[2] = Ar::c(1.0);
+    if (DIM == 3) {
+      h[2] = ld_val<T, A>(a.h2[ci[2]]);
+      hi[2] = ld_val<T, A>(a.hi2[ci[2]]);
+    }
+    A W = tb.w[ii[0]] * tb.w[ii[1]] * h[0] * h[1];
+    if (DIM == 3) W = W * tb.w[ii[2]] * h[2];
+    cm = ld_val<T, A>(a.mass) * W;
+    const A vW = ld_val<T, A>(a.visc) * W, aW = -(ld_val<T, A>(a.adv) * W);
+    A* cva = s_cva + ((int64_t)cl * NB + node) * 2 * DIM;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      cva[b] = vW * hi[b] * hi[b];
+      cva[DIM + b] = ADV ? aW * hi[b] * ld_val<T, A>(ub[((int64_t)b * a.ncell + cell) * NB + node]) : zero;
+      gdl[b][0] = tb.dL[0][ii[b]] * hi[b];
+      gdl[b][1] = tb.dL[1][ii[b]] * hi[b];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const A* cva = s_cva + ((int64_t)cl * NB + node) * 2 * DIM;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      const A cv = cva[b], ca = ADV ? cva[DIM + b] : zero;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const A* uc = s_u + (c * CPB + cl) * NB;
+        SumOf<A> du;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          const A v = uc[j[0] + N * (j[1] + N * j[2])];
+          if (m == 0) du.start(tb.D[ii[b]][m], v);
+          else du.fma(tb.D[ii[b]][m], v);
+        }
+        SumOf<A> q;
+        q.start(cv, du.value());
+        if (ADV) q.fma(ca, uo[c]);
+        s_q[((c * DIM + b) * CPB + cl) * NB + node] = q.value();
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (active) {
+    const A* fcell = s_fl + (int64_t)cl * NC * NFC * 2;
+    int tq[DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) tq[b] = tang_of<N, DIM>(b, ii);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      SumOf<A> y[DIM];  // one partial sum per direction, merged at the end
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        const A* qb = s_q + ((c * DIM + b) * CPB + cl) * NB;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          int j[3] = {ii[0], ii[1], ii[2]};
+          j[b] = m;
+          const A q = qb[j[0] + N * (j[1] + N * j[2])];
+          if (m == 0) y[b].start(tb.D[m][ii[b]], q);
+          else y[b].fma(tb.D[m][ii[b]], q);
+        }
+      }
+      y[0].fma(cm, uo[c]);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const A* pr = fcell + ((c * 2 * DIM + 2 * b + s) * NF + tq[b]) * 2;
+          const A F0 = pr[0], G = pr[1];
+          y[b].fma(s ? F0 : -F0, tb.L[s][ii[b]]);
+          y[b].fma(G, gdl[b][s]);
+        }
+      }
+#pragma unroll
+      for (int b = 1; b < DIM; ++b) y[0].merge(y[b]);
+      const A yv = y[0].value();
+      const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
+      const T yt = sizeof(T) == 8 ? (T)Ar::to_d(yv) : (T)Ar::to_f(yv);
+      if (a.cheb) {
+        const T dk = a.csrc[o];
+        a.cx[o] += dk;
+        const T rk = a.cr[o] - a.cdinv[o] * yt;
+        a.cr[o] = rk;
+        dst[o] = a.cc1 * dk + a.cc2 * rk;
+      } else {
+        dst[o] = yt;
+      }
+    }
+  }
+}
+
 }  // namespace dg
