@@ -120,7 +120,7 @@ static dg_status launch_general_op(const dg_mesh* m, bool pressure, T mass, T vi
   a.walls = pressure ? 0 : 1;
   a.ncomp = ncomp;
   if (cheb) {
-    a.cheb = 1;
+    a.cheb = cheb->cheb;
     a.cx = cheb->cx;
     a.cr = cheb->cr;
     a.cdinv = cheb->cdinv;
@@ -244,13 +244,22 @@ dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T ad
   return launch_scalar_op_impl<T>(m, pressure, mass, visc, adv, ubar, src, dst, ncomp, nullptr, s);
 }
 
-// dst = c1 src + c2 r after x += src, r -= dinv (alpha M^p + K) src
+// The pressure operator alpha M^p + K applied to src with a fused output
+// stage (op_epilogue's modes 1-4; x, r, dinv, c1, c2 as that mode reads them):
+//   1  x += src; r -= dinv A src; dst = c1 src + c2 r
+//   2  dst = r - A src                      (r holds b)
+//   3  r = dinv (x - A src); dst = c1 r     (x holds b)
+//   4  x += src + c1 src + c2 (r - dinv A src)
 template <typename T>
-dg_status launch_poisson_cheb(const dg_mesh* m, double alpha, const T* src, T* dst, T* x, T* r,
-                              const T* dinv, double c1, double c2, cudaStream_t s) {
+dg_status launch_poisson_epi(int mode, const dg_mesh* m, double alpha, const T* src, T* dst, T* x, T* r,
+                             const T* dinv, double c1, double c2, cudaStream_t s) {
+  if (mode < 1 || mode > 4) {
+    set_error("pressure operator: bad epilogue mode");
+    return DG_EINVAL;
+  }
   OpArgs<T> ch;
   std::memset(&ch, 0, sizeof(ch));
-  ch.cheb = 1;
+  ch.cheb = mode;
   ch.cx = x;
   ch.cr = r;
   ch.cdinv = dinv;
@@ -258,11 +267,11 @@ dg_status launch_poisson_cheb(const dg_mesh* m, double alpha, const T* src, T* d
   ch.cc2 = (T)c2;
   return launch_scalar_op_impl<T>(m, true, (T)alpha, T(1), T(0), nullptr, src, dst, 1, &ch, s);
 }
-template dg_status launch_poisson_cheb<float>(const dg_mesh*, double, const float*, float*, float*,
-                                              float*, const float*, double, double, cudaStream_t);
-template dg_status launch_poisson_cheb<double>(const dg_mesh*, double, const double*, double*,
-                                               double*, double*, const double*, double, double,
-                                               cudaStream_t);
+template dg_status launch_poisson_epi<float>(int, const dg_mesh*, double, const float*, float*, float*,
+                                             float*, const float*, double, double, cudaStream_t);
+template dg_status launch_poisson_epi<double>(int, const dg_mesh*, double, const double*, double*,
+                                              double*, double*, const double*, double, double,
+                                              cudaStream_t);
 
 template <typename T>
 static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
@@ -297,7 +306,7 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
   a.flux = m->split_flux;
   a.flux_bytes = m->split_flux_bytes;
   if (cheb) {
-    a.cheb = 1;
+    a.cheb = cheb->cheb;
     a.cx = cheb->cx;
     a.cr = cheb->cr;
     a.cdinv = cheb->cdinv;

@@ -31,8 +31,9 @@ struct OpArgs {
   T mass, visc, adv, pen;
   int walls;   // 1: SIP + LF Dirichlet terms on wall faces; 0: none (Neumann)
   int ncomp;
-  // fused Chebyshev update (multigrid smoothing, one component): with
-  // y = A src, x += src; r -= dinv y; dst = c1 src + c2 r
+  // fused epilogue (multigrid smoothing, one component; op_epilogue): 0 none,
+  // 1 a Chebyshev step, 2 the residual, 3 the smoother's start from a
+  // nonzero iterate, 4 the last Chebyshev step with the final update
   int cheb;
   T* cx;
   T* cr;
@@ -45,6 +46,43 @@ struct OpArgs {
   // reads it; the kernels' src may be a pre-split copy)
   const T* csrc;
 };
+
+// The operator kernels' output stage at output index o, y = (A src)_o
+// (fields as in OpArgs / GenArgs):
+//   0  dst = y
+//   1  Chebyshev step, d = the caller's src:  x += d; r -= dinv y; dst = c1 d + c2 r
+//   2  residual, r holding b:                  dst = r - y
+//   3  smoother start from the iterate src, x holding b:
+//                                              r = dinv (b - y); dst = c1 r
+//   4  last Chebyshev step and final update:   x += d + c1 d + c2 (r - dinv y)
+//      (r and the next direction are not stored)
+template <typename Args, typename T>
+__device__ __forceinline__ void op_epilogue(const Args& a, int64_t o, T y, T* __restrict__ dst) {
+  switch (a.cheb) {
+    case 1: {
+      const T dk = a.csrc[o];
+      a.cx[o] += dk;
+      const T rk = a.cr[o] - a.cdinv[o] * y;
+      a.cr[o] = rk;
+      dst[o] = a.cc1 * dk + a.cc2 * rk;
+      break;
+    }
+    case 2: dst[o] = a.cr[o] - y; break;
+    case 3: {
+      const T rk = a.cdinv[o] * (a.cx[o] - y);
+      a.cr[o] = rk;
+      dst[o] = a.cc1 * rk;
+      break;
+    }
+    case 4: {
+      const T dk = a.csrc[o];
+      const T rk = a.cr[o] - a.cdinv[o] * y;
+      a.cx[o] += dk + (a.cc1 * dk + a.cc2 * rk);
+      break;
+    }
+    default: dst[o] = y;
+  }
+}
 
 // Float-float kernels on FP64 storage (T = double, A = df64) receive every
 // FP64 input pre-split: the source vector and advecting field as float
@@ -288,15 +326,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
       }
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
-      if (a.cheb) {
-        const T dk = a.csrc[o];
-        a.cx[o] += dk;
-        const T rk = a.cr[o] - a.cdinv[o] * yt;
-        a.cr[o] = rk;
-        dst[o] = a.cc1 * dk + a.cc2 * rk;
-      } else {
-        dst[o] = yt;
-      }
+      op_epilogue(a, o, yt, dst);
     }
     __syncthreads();
   }

@@ -225,9 +225,10 @@ dg_status presplit(int64_t n, const double* x, double* out, cudaStream_t s);
 template <typename T>
 dg_status launch_scalar_op(const dg_mesh* m, bool pressure, T mass, T visc, T adv,
                            const T* ubar, const T* src, T* dst, int ncomp, cudaStream_t s);
-// fused Chebyshev smoothing step on a pressure-space level (see dg_mg.cu)
+// the pressure operator with a fused output stage on a multigrid level
+// (modes 1-4 of op_epilogue; see dg_apply.cu and dg_mg.cu)
 template <typename T>
-dg_status launch_poisson_cheb(const dg_mesh* m, double alpha, const T* src, T* dst, T* x, T* r,
-                              const T* dinv, double c1, double c2, cudaStream_t s);
+dg_status launch_poisson_epi(int mode, const dg_mesh* m, double alpha, const T* src, T* dst, T* x, T* r,
+                             const T* dinv, double c1, double c2, cudaStream_t s);
 
 }  // namespace dg

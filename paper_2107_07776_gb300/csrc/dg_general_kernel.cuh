@@ -42,7 +42,7 @@ struct GenArgs {
   T mass, visc, adv, pen;
   int walls;      // 1: SIP + LF wall terms (homogeneous Dirichlet); 0: none (Neumann)
   int ncomp;
-  int cheb;       // fused Chebyshev update, as in OpArgs
+  int cheb;       // fused epilogue, as in OpArgs (op_epilogue)
   T* cx;
   T* cr;
   const T* cdinv;
@@ -327,15 +327,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32)
       }
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(y) : (T)Ar::to_f(y);
-      if (a.cheb) {
-        const T dk = a.csrc[(int64_t)c * a.ncell * NB + cell * NB + node];
-        a.cx[o] += dk;
-        const T rk = a.cr[o] - a.cdinv[o] * yt;
-        a.cr[o] = rk;
-        dst[o] = a.cc1 * dk + a.cc2 * rk;
-      } else {
-        dst[o] = yt;
-      }
+      op_epilogue(a, o, yt, dst);
     }
     __syncthreads();
   }

@@ -91,14 +91,6 @@ __global__ void add_kernel(int64_t n, const T* __restrict__ d, T* __restrict__ x
        k += (int64_t)gridDim.x * blockDim.x)
     x[k] += d[k];
 }
-template <typename T>
-__global__ void sub_kernel(int64_t n, const T* __restrict__ b, const T* __restrict__ t,
-                           T* __restrict__ r) {
-  pdl_entry();
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    r[k] = b[k] - t[k];
-}
 // I = identity (n x n)
 template <typename T>
 __global__ void identity_kernel(int64_t n, T* __restrict__ I) {
@@ -622,9 +614,12 @@ dg_status MultiGrid<T>::set_alpha(double a) {
 }
 
 // Chebyshev smoothing on level l: x <- x + poly(D^-1 A) D^-1 (b - A x).
-// Every step after the first is one fused launch: the operator apply whose
-// epilogue does x += d, r -= D^-1 A d, d' = c1 d + c2 r (into the second
-// direction buffer, since neighbouring cells still read d).
+// From a nonzero x the start (r = D^-1 (b - A x), d = r / theta) is the
+// operator apply with that output stage.  Every step after the first is one
+// fused launch: the operator apply whose epilogue does x += d,
+// r -= D^-1 A d, d' = c1 d + c2 r (into the second direction buffer, since
+// neighbouring cells still read d); the last one adds d + d' to x instead
+// and stores neither r nor d'.
 template <typename T>
 dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
   MGLevel<T>& L = lv[l];
@@ -639,23 +634,28 @@ dg_status MultiGrid<T>::chebyshev(int l, int degree, bool x_zero) {
     launch(cheb_init_kernel<T>, grid1(n), 256, 0, stream, n, L.b, nullptr, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
     DG_CUDA(cudaMemsetAsync(L.x, 0, sizeof(T) * n, stream));
   } else {
-    st = level_apply<T>(L, alpha, L.x, L.t, stream);
+    st = launch_poisson_epi<T>(3, L.mesh, alpha, L.x, L.d, L.b, L.r, dinv, 1.0 / theta, 0.0, stream);
     if (st != DG_OK) return st;
-    launch(cheb_init_kernel<T>, grid1(n), 256, 0, stream, n, L.b, L.t, dinv, (T)(1.0 / theta), L.r, L.d); count_launch();
   }
   int swaps = 0;
   for (int k = 0; k + 1 < degree; ++k) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    st = launch_poisson_cheb<T>(L.mesh, alpha, L.d, L.d2, L.x, L.r, dinv, rho_new * rho,
-                                2.0 * rho_new / delta, stream);
+    const bool last = k + 2 == degree;
+    st = launch_poisson_epi<T>(last ? 4 : 1, L.mesh, alpha, L.d, L.d2, L.x, L.r, dinv, rho_new * rho,
+                               2.0 * rho_new / delta, stream);
     if (st != DG_OK) return st;
-    T* tmp = L.d;
-    L.d = L.d2;
-    L.d2 = tmp;
-    ++swaps;
+    if (!last) {
+      T* tmp = L.d;
+      L.d = L.d2;
+      L.d2 = tmp;
+      ++swaps;
+    }
     rho = rho_new;
   }
-  launch(add_kernel<T>, grid1(n), 256, 0, stream, n, L.d, L.x); count_launch();
+  if (degree <= 1) {
+    launch(add_kernel<T>, grid1(n), 256, 0, stream, n, L.d, L.x);
+    count_launch();
+  }
   DG_CUDA(cudaGetLastError());
   if (swaps & 1) {  // the direction is consumed: give every call the same buffers
     T* tmp = L.d;
@@ -760,9 +760,9 @@ dg_status MultiGrid<T>::vcycle(int l) {
   MGLevel<T>& C = lv[l + 1];
   st = chebyshev(l, smooth_degree, true);
   if (st != DG_OK) return st;
-  st = level_apply<T>(L, alpha, L.x, L.t, stream);
+  // r = b - A x in one launch (the operator's residual output stage)
+  st = launch_poisson_epi<T>(2, L.mesh, alpha, L.x, L.r, nullptr, L.b, nullptr, 0.0, 0.0, stream);
   if (st != DG_OK) return st;
-  launch(sub_kernel<T>, grid1(L.n), 256, 0, stream, L.n, L.b, L.t, L.r); count_launch();
   {
     const Transfer& t = tr[l];
     int nchild = 1;

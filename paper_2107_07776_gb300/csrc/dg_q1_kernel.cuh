@@ -294,15 +294,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
   for (int k = 0; k < 4; ++k) yt[k] = sizeof(T) == 8 ? (T)Ar::to_d(y[k]) : (T)Ar::to_f(y[k]);
   if (a.cheb) {
-    // x += d; r -= dinv y; dst = c1 d + c2 r
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const T dk = a.csrc[o + k];
-      a.cx[o + k] += dk;
-      const T rk = a.cr[o + k] - a.cdinv[o + k] * yt[k];
-      a.cr[o + k] = rk;
-      dst[o + k] = a.cc1 * dk + a.cc2 * rk;
-    }
+    for (int k = 0; k < 4; ++k) op_epilogue(a, o + k, yt[k], dst);
   } else if (vec) {
     if constexpr (sizeof(T) == 4) {
       reinterpret_cast<float4*>(dst + o)[0] = make_float4(yt[0], yt[1], yt[2], yt[3]);

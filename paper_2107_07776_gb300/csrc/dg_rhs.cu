@@ -245,6 +245,9 @@ constexpr int expl_minb(int threads) {
   return 65536 / (threads * 96) < 1 ? 1 : 65536 / (threads * 96);
 }
 
+// resident CTAs per SM that keep a thread at 72 registers at most
+constexpr int minb_cap72(int threads) { return 65536 / (threads * 72) < 1 ? 1 : 65536 / (threads * 72); }
+
 template <typename A, int DIM, int N, int NT, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
                                   expl_minb<N, DIM>(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32))
@@ -570,15 +573,18 @@ __global__ void __launch_bounds__(256)
 }
 
 template <typename A, int DIM, int N, int NT, int CPB>
-__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
+__global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32,
+                                  minb_cap72(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32))
     explicit_cell_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<A> tb,
                          const __grid_constant__ ExplTerms et, const A* __restrict__ flux,
                          double* __restrict__ rhs) {
   pdl_entry();
   using Ar = Arith<A>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF;
-  __shared__ A s_v[CPB][NB];
-  __shared__ A s_q[DIM][CPB][NB];
+  // every component's values and gradient terms: the three phases below run
+  // once for all components, each between the same two barriers
+  __shared__ A s_v[DIM][CPB][NB];
+  __shared__ A s_q[DIM][DIM][CPB][NB];
   // the thread's own advective factors W adv_t ubar_t,b / h_b (shared memory
   // rather than registers)
   __shared__ A s_ca[CPB][NB][NT * DIM];
@@ -628,40 +634,51 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     fpos[2 * b] = (foff + face_index(b, ci[b], ci, g.n, g.per)) * NF + t;
     fpos[2 * b + 1] = (foff + face_index(b, hi_l, ci, g.n, g.per)) * NF + t;
   }
-  for (int c = 0; c < DIM; ++c) {
-    A u[NT];
-    if (active) {
+  A u[DIM][NT];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt) u[c][tt] = zero;
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
       SumOf<A> v;
 #pragma unroll
       for (int tt = 0; tt < NT; ++tt) {
-        u[tt] = ldw<A>(et.w[tt][((int64_t)c * g.ncell + cell) * NB + node]);
-        if (tt == 0) v.start(visc[tt], u[tt]);
-        else v.fma(visc[tt], u[tt]);
+        u[c][tt] = ldw<A>(et.w[tt][((int64_t)c * g.ncell + cell) * NB + node]);
+        if (tt == 0) v.start(visc[tt], u[c][tt]);
+        else v.fma(visc[tt], u[c][tt]);
       }
-      s_v[cl][node] = v.value();
+      s_v[c][cl][node] = v.value();
     }
-    __syncthreads();
-    if (active) {
+  }
+  __syncthreads();
+  if (active) {
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) {
+    for (int b = 0; b < DIM; ++b) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
         SumOf<A> dv;
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
-          const A x = s_v[cl][j[0] + N * (j[1] + N * j[2])];
+          const A x = s_v[c][cl][j[0] + N * (j[1] + N * j[2])];
           if (m == 0) dv.start(tb.D[ii[b]][m], x);
           else dv.fma(tb.D[ii[b]][m], x);
         }
         SumOf<A> q;
         q.start(cv[b], dv.value());
 #pragma unroll
-        for (int tt = 0; tt < NT; ++tt) q.fma(s_ca[cl][node][tt * DIM + b], u[tt]);
-        s_q[b][cl][node] = q.value();
+        for (int tt = 0; tt < NT; ++tt) q.fma(s_ca[cl][node][tt * DIM + b], u[c][tt]);
+        s_q[c][b][cl][node] = q.value();
       }
     }
-    __syncthreads();
-    if (active) {
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
       const A* fl = flux + (int64_t)c * nface * NF;
       SumOf<A> y[DIM];  // one partial sum per direction, merged at the end
 #pragma unroll
@@ -670,7 +687,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
         for (int m = 0; m < N; ++m) {
           int j[3] = {ii[0], ii[1], ii[2]};
           j[b] = m;
-          const A x = s_q[b][cl][j[0] + N * (j[1] + N * j[2])];
+          const A x = s_q[c][b][cl][j[0] + N * (j[1] + N * j[2])];
           if (m == 0) y[b].start(tb.D[m][ii[b]], x);
           else y[b].fma(tb.D[m][ii[b]], x);
         }
@@ -682,7 +699,6 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       for (int b = 1; b < DIM; ++b) y[0].merge(y[b]);
       rhs[(int64_t)c * g.ncell * NB + cell * NB + node] += Ar::to_d(y[0].value());
     }
-    __syncthreads();
   }
 }
 
@@ -727,20 +743,22 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       if (node < NBP) s_p[cl][node] = Ar::from(p[cell * NBP + node]);
       for (int idx = node; idx < 2 * DIM * NPF; idx += NB) {
         const int fc = idx / NPF, t = idx % NPF, ax = fc >> 1, s = fc & 1;
-        A pin = zero;
-#pragma unroll
-        for (int j = 0; j < NP; ++j)
-          pin = Ar::fma(tp.L[s][j], Ar::from(__ldg(&p[cell * NBP + nodeof(NP, DIM, ax, j, t)])), pin);
-        A pav = pin;
+        // {{p}} = (p_in + p_out) / 2 as one compensated sum of both traces
         const int64_t nb = neighbour(g, ci, ax, s);
+        const A wi = nb >= 0 ? half : Ar::c(1.0);
+        SumOf<A> pav;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          const A x = Ar::from(__ldg(&p[cell * NBP + nodeof(NP, DIM, ax, j, t)]));
+          if (j == 0) pav.start(wi * tp.L[s][j], x);
+          else pav.fma(wi * tp.L[s][j], x);
+        }
         if (nb >= 0) {
-          A pout = zero;
 #pragma unroll
           for (int j = 0; j < NP; ++j)
-            pout = Ar::fma(tp.L[1 - s][j], Ar::from(__ldg(&p[nb * NBP + nodeof(NP, DIM, ax, j, t)])), pout);
-          pav = half * (pin + pout);
+            pav.fma(half * tp.L[1 - s][j], Ar::from(__ldg(&p[nb * NBP + nodeof(NP, DIM, ax, j, t)])));
         }
-        s_t[cl][idx] = pav;
+        s_t[cl][idx] = pav.value();
       }
     }
   }
@@ -802,22 +820,33 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   }
   __syncthreads();
   if (active) {
+    // compensated sums of the node's terms (one rounding per output)
+    const A mW = mass * W;
+    A hic[3] = {zero, zero, zero};
+    if (p)
+      for (int b = 0; b < DIM; ++b) hic[b] = Ar::from(g.hi[b][ci[b]]);
+#pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const int64_t o = (int64_t)c * g.ncell * NB + cell * NB + node;
-      A y = zero;
-      if (u_mass) y += mass * W * Ar::from(u_mass[o]);
-      if (f) y += W * Ar::from(f[o]);
+      SumOf<A> y;
+      if (u_mass) y.start(mW, Ar::from(u_mass[o]));
+      else y.start(zero, zero);
+      if (f) y.fma(W, Ar::from(f[o]));
       if (p) {
-        A acc = zero;
+        const int ic = sel3(c, ii[0], ii[1], ii[2]);
+        SumOf<A> acc;
+#pragma unroll
         for (int m = 0; m < N; ++m) {
           const int j0 = c == 0 ? m : ii[0], j1 = c == 1 ? m : ii[1], j2 = c == 2 ? m : ii[2];
-          acc = Ar::fma(tb.D[m][sel3(c, ii[0], ii[1], ii[2])], s_g[cl][j0 + N * (j1 + N * j2)], acc);
+          if (m == 0) acc.start(tb.D[m][ic], s_g[cl][j0 + N * (j1 + N * j2)]);
+          else acc.fma(tb.D[m][ic], s_g[cl][j0 + N * (j1 + N * j2)]);
         }
-        y += acc * Ar::from(g.hi[c][ci[c]]);
+        y.fma(acc.value(), hic[c]);
         const int t = tangof(N, DIM, c, ii);
-        for (int s = 0; s < 2; ++s) y += s_f[cl][(2 * c + s) * NF + t] * tb.L[s][sel3(c, ii[0], ii[1], ii[2])];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) y.fma(s_f[cl][(2 * c + s) * NF + t], tb.L[s][ic]);
       }
-      rhs[o] = Ar::to_d(y);
+      rhs[o] = Ar::to_d(y.value());
     }
   }
 }
@@ -877,21 +906,22 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
       const int ba = ax == 0 ? 1 : 0, bb = ax == 2 ? 1 : 2;
       A wt = tb.w[ta] * sel3(ba, h[0], h[1], h[2]);
       if (DIM == 3) wt = wt * tb.w[tb2] * sel3(bb, h[0], h[1], h[2]);
-      A uin = zero;
+      // w |face| n {{u}}: both traces in one compensated sum, the weight
+      // folded into the coefficients
+      const A wf = sgn * (nb >= 0 ? half * wt : wt);
+      SumOf<A> uav;
 #pragma unroll
-      for (int i = 0; i < N; ++i)
-        uin = Ar::fma(tb.L[s][i], ldw<A>(__ldg(&uss[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)])),
-                      uin);
-      A uav = uin;
+      for (int i = 0; i < N; ++i) {
+        const A x = ldw<A>(__ldg(&uss[((int64_t)ax * g.ncell + cell) * NB + nodeof(N, DIM, ax, i, t)]));
+        if (i == 0) uav.start(wf * tb.L[s][i], x);
+        else uav.fma(wf * tb.L[s][i], x);
+      }
       if (nb >= 0) {
-        A uout = zero;
 #pragma unroll
         for (int i = 0; i < N; ++i)
-          uout = Ar::fma(tb.L[1 - s][i],
-                         ldw<A>(__ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)])), uout);
-        uav = half * (uin + uout);
+          uav.fma(wf * tb.L[1 - s][i], ldw<A>(__ldg(&uss[((int64_t)ax * g.ncell + nb) * NB + nodeof(N, DIM, ax, i, t)])));
       }
-      s_f[cl][fp] = wt * sgn * uav;
+      s_f[cl][fp] = uav.value();
     }
   }
   __syncthreads();
@@ -949,32 +979,37 @@ __global__ void __launch_bounds__(((CPB * Sh<NP, DIM>::NB + 31) / 32) * 32)
   }
   if (!active) return;
   const int pi[3] = {node % NP, (node / NP) % NP, DIM == 3 ? node / (NP * NP) : 0};
-  A acc = zero;
+  // the cell and face terms as one compensated sum
+  SumOf<A> acc;
   if (DIM == 3) {  // axis 2: I^T on (x0 + x1 so far), D^T on x2
 #pragma unroll
     for (int q2 = 0; q2 < N; ++q2) {
       const int q = pi[0] + NP * (pi[1] + NP * q2);
-      acc = Ar::fma(mx.I[q2][pi[2]], s_y[0][cl][q], acc);
-      acc = Ar::fma(mx.D[q2][pi[2]], s_y[1][cl][q], acc);
+      if (q2 == 0) acc.start(mx.I[q2][pi[2]], s_y[0][cl][q]);
+      else acc.fma(mx.I[q2][pi[2]], s_y[0][cl][q]);
+      acc.fma(mx.D[q2][pi[2]], s_y[1][cl][q]);
     }
   } else {  // axis 1 in 2D: I^T on x0, D^T on x1
 #pragma unroll
     for (int q1 = 0; q1 < N; ++q1) {
       const int q = pi[0] + NP * q1;
-      acc = Ar::fma(mx.I[q1][pi[1]], s_x[0][cl][q], acc);
-      acc = Ar::fma(mx.D[q1][pi[1]], s_x[DIM - 1][cl][q], acc);
+      if (q1 == 0) acc.start(mx.I[q1][pi[1]], s_x[0][cl][q]);
+      else acc.fma(mx.I[q1][pi[1]], s_x[0][cl][q]);
+      acc.fma(mx.D[q1][pi[1]], s_x[DIM - 1][cl][q]);
     }
   }
   // face term: - sum_faces (tested flux) L_s(normal index)
 #pragma unroll
   for (int fc = 0; fc < 2 * DIM; ++fc) {
     const int ax = fc >> 1, s = fc & 1;
-    acc = Ar::fma(-tp.L[s][sel3(ax, pi[0], pi[1], pi[2])], s_F[cl][fc * NPF + tangof(NP, DIM, ax, pi)], acc);
+    acc.fma(-tp.L[s][sel3(ax, pi[0], pi[1], pi[2])], s_F[cl][fc * NPF + tangof(NP, DIM, ax, pi)]);
   }
   A Wp = Ar::c(1.0);
   for (int b = 0; b < DIM; ++b) Wp = Wp * tp.w[pi[b]] * h[b];
-  rhs[cell * NBP + node] =
-      Ar::to_d(Ar::from(alpha_d) * Wp * Ar::from(p_old[cell * NBP + node]) + Ar::from(inv_tau_d) * acc);
+  SumOf<A> r;
+  r.start(Ar::from(alpha_d) * Wp, Ar::from(p_old[cell * NBP + node]));
+  r.fma(Ar::from(inv_tau_d), acc.value());
+  rhs[cell * NBP + node] = Ar::to_d(r.value());
 }
 
 // ------------------------------------------------------------------
@@ -1086,13 +1121,29 @@ __device__ __forceinline__ R to_r(double v) {
   else return v;
 }
 template <typename R>
+__device__ __forceinline__ R abs_r(R x) { return x < R(0.0) ? -x : x; }
+template <typename R>
+__device__ __forceinline__ R max_r(R x, R y) { return x < y ? y : x; }
+template <typename R>
 __device__ __forceinline__ double inv_r(R d) {
   if constexpr (sizeof(R) == 4) return df_widen(__frcp_rn(d));
   else return 1.0 / d;
 }
 
 // Diagonal of mass M + visc A + adv C(ubar) (walls = 1) or of
-// alpha M^p + K (walls = 0, adv = 0), one thread per node.
+// alpha M^p + K (walls = 0, adv = 0), one thread per node.  A face point's
+// contribution to the node i on its normal line (i the node's index along
+// the normal, t its tangential index) factors into per-face-point
+// coefficients and per-node table values: with u_in = L_s(i) and
+// dn_in = sgn h^-1 L'_s(i),
+//   interior face:  w_t (K u_in^2 - visc u_in dn_in),
+//                   K = visc C + adv (un_in + lambda) / 2, C = pen (h_K^-1 + h_N^-1) / 2
+//   wall face:      w_t (K u_in^2 - 2 visc u_in dn_in),  K = 2 visc pen h_K^-1 + adv |un_in|
+// (the SIP and Lax-Friedrichs terms of the operator, Section 3, with the
+// outer trace of a basis function zero).  The coefficients are formed once
+// per face point (P = w_t K, Q = kappa w_t visc sgn h_K^-1) and each node
+// adds P L_s(i)^2 - Q L_s(i) L'_s(i).  On a one-cell periodic axis the
+// outer trace is the cell's own: those faces take the full flux per node.
 template <int DIM, int N, typename R, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb, R mass, R visc, R adv,
@@ -1100,43 +1151,66 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
   pdl_entry();
   using Ar = Arith<R>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
-  // normal advecting velocity on each face point, own and neighbour trace,
-  // evaluated once per cell (each is shared by the N nodes of its line)
+  // per face point: the normal advecting velocity (own and neighbour trace)
+  // and the two coefficients P and Q above
   __shared__ R s_in[CPB][NFP];
   __shared__ R s_out[CPB][NFP];
+  __shared__ R s_P[CPB][NFP];
+  __shared__ R s_Q[CPB][NFP];
   const int tid = threadIdx.x, cl = tid / NB, node = tid % NB;
   const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
   const bool active = cl < CPB && cell < g.ncell;
   int ci[3] = {0, 0, 0};
-  if (active) cell_coords(g, cell, ci);
-  if (adv != R(0.0)) {
-    if (active) {
-      for (int fp = node; fp < NFP; fp += NB) {
-        const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
-        const R sgn = s ? R(1.0) : R(-1.0);
+  R h[3] = {1, 1, 1}, hi[3] = {1, 1, 1};
+  if (active) {
+    cell_coords(g, cell, ci);
+    for (int b = 0; b < DIM; ++b) {
+      h[b] = to_r<R>(g.h[b][ci[b]]);
+      hi[b] = to_r<R>(g.hi[b][ci[b]]);
+    }
+    for (int fp = node; fp < NFP; fp += NB) {
+      const int fc = fp / NF, t = fp % NF, ax = fc >> 1, s = fc & 1;
+      const R sgn = s ? R(1.0) : R(-1.0);
+      const int64_t nb = neighbour(g, ci, ax, s);
+      R unin = 0.0, unout = 0.0;
+      if (adv != R(0.0)) {
         const double* ua = ub + (int64_t)ax * g.ncell * NB;
-        R unin = 0.0, unout = 0.0;
 #pragma unroll
-        for (int i = 0; i < N; ++i) unin = Ar::fma(tb.L[s][i], to_r<R>(__ldg(&ua[cell * NB + nodeof(N, DIM, ax, i, t)])), unin);
-        const int64_t nb = neighbour(g, ci, ax, s);
+        for (int i = 0; i < N; ++i)
+          unin = Ar::fma(tb.L[s][i], to_r<R>(__ldg(&ua[cell * NB + nodeof(N, DIM, ax, i, t)])), unin);
         if (nb >= 0) {
 #pragma unroll
           for (int i = 0; i < N; ++i)
             unout = Ar::fma(tb.L[1 - s][i], to_r<R>(__ldg(&ua[nb * NB + nodeof(N, DIM, ax, i, t)])), unout);
         }
-        s_in[cl][fp] = sgn * unin;
-        s_out[cl][fp] = sgn * unout;
+        unin = sgn * unin;
+        unout = sgn * unout;
       }
+      s_in[cl][fp] = unin;
+      s_out[cl][fp] = unout;
+      // tangential weight of the face point
+      const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+      R wt = tb.w[t % N] * sel3(b0, h[0], h[1], h[2]);
+      if (DIM == 3) wt *= tb.w[t / N] * sel3(b1, h[0], h[1], h[2]);
+      const R hiK = sel3(ax, hi[0], hi[1], hi[2]);
+      R P = 0.0, Q = 0.0;
+      if (nb >= 0) {
+        const R hiN = to_r<R>(g.hi[ax][neighbour_coord(g, ci, ax, s)]);
+        const R C = R(0.5) * pen * (hiK + hiN);
+        const R lam = max_r(abs_r(unin), abs_r(unout));
+        P = wt * (visc * C + R(0.5) * adv * (unin + lam));
+        Q = wt * visc;
+      } else if (walls) {
+        P = wt * (R(2.0) * visc * pen * hiK + adv * abs_r(unin));
+        Q = R(2.0) * wt * visc;
+      }
+      s_P[cl][fp] = P;
+      s_Q[cl][fp] = Q * sgn * hiK;
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (!active) return;
   const int ii[3] = {node % N, (node / N) % N, DIM == 3 ? node / (N * N) : 0};
-  R h[3] = {1, 1, 1}, hi[3] = {1, 1, 1};
-  for (int b = 0; b < DIM; ++b) {
-    h[b] = to_r<R>(g.h[b][ci[b]]);
-    hi[b] = to_r<R>(g.hi[b][ci[b]]);
-  }
   // W = prod_b w(i_b) h_b.  The stiffness diagonal along axis b is
   // sum_m W(j: j_b = m) (D[m][i_b] / h_b)^2 = (W / w(i_b)) h_b^-2 sum_m w(m) D[m][i_b]^2:
   // the tangential weights factor out of the 1D sum.
@@ -1156,36 +1230,32 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     if (adv != R(0.0)) d -= adv * W * to_r<R>(ub[((int64_t)b * g.ncell + cell) * NB + node]) * tb.D[ii[b]][ii[b]] * hi[b];
   }
   for (int ax = 0; ax < DIM; ++ax) {
-    const int t = tangof(N, DIM, ax, ii);
-    R wt = 1.0;
-    for (int b = 0; b < DIM; ++b)
-      if (b != ax) wt *= tb.w[ii[b]] * h[b];
+    const int t = tangof(N, DIM, ax, ii), i = ii[ax];
+    const bool self = g.per[ax] && g.n[ax] == 1;  // the cell is its own neighbour
     for (int s = 0; s < 2; ++s) {
-      const R sgn = s ? R(1.0) : R(-1.0);
-      const int64_t nb = neighbour(g, ci, ax, s);
-      const R hiK = hi[ax];
-      const R uin = tb.L[s][ii[ax]], dnin = sgn * tb.dL[s][ii[ax]] * hiK;
-      const R unin = adv != R(0.0) ? s_in[cl][(2 * ax + s) * NF + t] : R(0.0);
-      R fv = 0.0, fg = 0.0;
-      if (nb >= 0) {
-        const R hiN = to_r<R>(g.hi[ax][neighbour_coord(g, ci, ax, s)]);
-        // a one-cell period makes the cell its own neighbour
-        const R uout = nb == cell ? tb.L[1 - s][ii[ax]] : R(0.0);
-        const R dnout = nb == cell ? sgn * tb.dL[1 - s][ii[ax]] * hiN : R(0.0);
-        const R C = R(0.5) * pen * (hiK + hiN);
-        const R jump = uin - uout;
-        fv = visc * (R(-0.5) * (dnin + dnout) + C * jump);
-        fg = R(-0.5) * visc * jump;
-        if (adv != R(0.0)) {
-          const R unout = s_out[cl][(2 * ax + s) * NF + t];
-          const R lam = fmax(fabs(unin), fabs(unout));
-          fv += adv * (R(0.5) * (uin * unin + uout * unout) + R(0.5) * lam * jump);
-        }
-      } else if (walls) {
-        fv = visc * (-dnin + R(2.0) * (pen * hiK) * uin) + adv * fabs(unin) * uin;
-        fg = -visc * uin;
+      const int fp = (2 * ax + s) * NF + t;
+      const R Ls = tb.L[s][i], dLs = tb.dL[s][i];
+      if (!self) {
+        d += s_P[cl][fp] * Ls * Ls - s_Q[cl][fp] * Ls * dLs;
+        continue;
       }
-      d += wt * (fv * tb.L[s][ii[ax]] + fg * sgn * tb.dL[s][ii[ax]] * hiK);
+      const R sgn = s ? R(1.0) : R(-1.0);
+      R wt = 1.0;
+      for (int b = 0; b < DIM; ++b)
+        if (b != ax) wt *= wl[b];
+      const R hiK = hi[ax];
+      const R uin = Ls, dnin = sgn * dLs * hiK;
+      const R uout = tb.L[1 - s][i], dnout = sgn * tb.dL[1 - s][i] * hiK;
+      const R unin = s_in[cl][fp], unout = s_out[cl][fp];
+      const R C = pen * hiK;
+      const R jump = uin - uout;
+      R fv = visc * (R(-0.5) * (dnin + dnout) + C * jump);
+      const R fg = R(-0.5) * visc * jump;
+      if (adv != R(0.0)) {
+        const R lam = max_r(abs_r(unin), abs_r(unout));
+        fv += adv * (R(0.5) * (uin * unin + uout * unout) + R(0.5) * lam * jump);
+      }
+      d += wt * (fv * uin + fg * dnin);
     }
   }
   if (inv_copies > 0) {  // the Jacobi scaling itself, 1/d, for each of inv_copies components

@@ -340,15 +340,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
       const A yv = y[0].value();
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(yv) : (T)Ar::to_f(yv);
-      if (a.cheb) {
-        const T dk = a.csrc[o];
-        a.cx[o] += dk;
-        const T rk = a.cr[o] - a.cdinv[o] * yt;
-        a.cr[o] = rk;
-        dst[o] = a.cc1 * dk + a.cc2 * rk;
-      } else {
-        dst[o] = yt;
-      }
+      op_epilogue(a, o, yt, dst);
     }
     __syncthreads();
   }
@@ -525,15 +517,7 @@ __global__ void __launch_bounds__(((CPB * Shape<N, DIM>::NB + 31) / 32) * 32, MI
       const A yv = y[0].value();
       const int64_t o = (int64_t)c * a.ncell * NB + cell * NB + node;
       const T yt = sizeof(T) == 8 ? (T)Ar::to_d(yv) : (T)Ar::to_f(yv);
-      if (a.cheb) {
-        const T dk = a.csrc[o];
-        a.cx[o] += dk;
-        const T rk = a.cr[o] - a.cdinv[o] * yt;
-        a.cr[o] = rk;
-        dst[o] = a.cc1 * dk + a.cc2 * rk;
-      } else {
-        dst[o] = yt;
-      }
+      op_epilogue(a, o, yt, dst);
     }
   }
 }
