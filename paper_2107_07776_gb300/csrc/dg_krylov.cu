@@ -113,15 +113,55 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// w -= sum_i h[i] V_i  (h on the device)
-__global__ void multi_axpy_kernel(int64_t n, int nv, const double* __restrict__ h,
-                                  const double* __restrict__ V, int64_t ldv, double* __restrict__ w) {
+// w -= sum_i h[i] V_i, then this block's partial sums of <w, U_i>
+// (i < nu; U = V, or U = w itself when self_dot) in multi_dot_kernel's
+// per-thread order and block tree, so the sums equal those of
+// multi_dot_kernel run after the update.  Each thread reads back only the w
+// elements it wrote.  Grid: red_blocks(n).
+__global__ void __launch_bounds__(kRedThreads)
+    axpy_dots_kernel(int64_t n, int nv, const double* __restrict__ h, const double* __restrict__ V,
+                     int64_t ldv, double* __restrict__ w, int nu, int self_dot,
+                     double* __restrict__ partial) {
+  pdl_entry();
+  __shared__ double s[kRedThreads];
+  const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, dk = (int64_t)gridDim.x * blockDim.x;
+  if (nu == 1) {  // one pass: the update and the single product together
+    const double* u = self_dot ? nullptr : V;
+    double acc = 0.0;
+    for (int64_t k = k0; k < n; k += dk) {
+      double wk = w[k];
+      for (int i = 0; i < nv; ++i) wk -= h[i] * V[(int64_t)i * ldv + k];
+      w[k] = wk;
+      acc += wk * (u ? u[k] : wk);
+    }
+    acc = block_tree_sum(acc, s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+    return;
+  }
+  for (int64_t k = k0; k < n; k += dk) {
+    double wk = w[k];
+    for (int i = 0; i < nv; ++i) wk -= h[i] * V[(int64_t)i * ldv + k];
+    w[k] = wk;
+  }
+  for (int i = 0; i < nu; ++i) {
+    const double* u = self_dot ? w : V + (int64_t)i * ldv;
+    double acc = 0.0;
+    for (int64_t k = k0; k < n; k += dk) acc += w[k] * u[k];
+    acc = block_tree_sum(acc, s);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * nu + i] = acc;
+  }
+}
+
+// v = a x (in place allowed), z = dinv .* v: a new Arnoldi vector and its
+// Jacobi-preconditioned copy in one pass
+__global__ void scale_precondition_kernel(int64_t n, double a, const double* x, double* v,
+                                          const double* __restrict__ dinv, double* __restrict__ z) {
   pdl_entry();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    double acc = w[k];
-    for (int i = 0; i < nv; ++i) acc -= h[i] * V[(int64_t)i * ldv + k];
-    w[k] = acc;
+    const double vk = a * x[k] + 0.0;
+    v[k] = vk;
+    z[k] = dinv[k] * vk;
   }
 }
 
@@ -312,8 +352,15 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
     info->res_final = beta;
     if (beta <= tol * bnorm) return DG_OK;
     if (it >= max_iter) return DG_ENOCONV;
-    st = vo.axpby(n, 1.0 / beta, V, 0.0, nullptr, V);
-    if (st != DG_OK) return st;
+    // V_0 = r / beta, and its preconditioned copy z = D^-1 V_0 staged in V_1
+    if (dinv) {
+      launch(scale_precondition_kernel, grid_for(n), 256, 0, vo.stream, n, 1.0 / beta, V, V, dinv, V + n);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+    } else {
+      st = vo.axpby(n, 1.0 / beta, V, 0.0, nullptr, V);
+      if (st != DG_OK) return st;
+    }
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int j = 0;
@@ -321,25 +368,28 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
     for (; j < m && it < max_iter; ++j, ++it) {
       double* vj = V + (int64_t)j * n;
       double* vj1 = V + (int64_t)(j + 1) * n;
-      // w = A D^-1 v_j   (z = D^-1 v_j staged in v_{j+1})
-      if (dinv) {
-        st = vo.mul(n, dinv, vj, vj1);
-        if (st != DG_OK) return st;
-        st = A(vj1, w);
-      } else {
-        st = A(vj, w);
-      }
+      // w = A D^-1 v_j   (z = D^-1 v_j staged in v_{j+1} by the kernel that
+      // wrote v_j)
+      st = A(dinv ? vj1 : vj, w);
       if (st != DG_OK) return st;
-      // two classical Gram-Schmidt passes on the device, then |w|^2
-      for (int pass = 0; pass < 2; ++pass) {
-        double* hc = pass == 0 ? h1 : h2;
-        st = vo.dots(n, j + 1, w, V, n, hc);
+      // two classical Gram-Schmidt passes on the device, then |w|^2: each
+      // pass's update fused with the next pass's products
+      {
+        const int nb = red_blocks(n);
+        st = vo.dots(n, j + 1, w, V, n, h1);
         if (st != DG_OK) return st;
-        launch(multi_axpy_kernel, grid_for(n), 256, 0, vo.stream, n, j + 1, hc, V, n, w); count_launch();
+        launch(axpy_dots_kernel, nb, kRedThreads, 0, vo.stream, n, j + 1, h1, V, (int64_t)n, w, j + 1, 0,
+               vo.partial);
+        count_launch();
+        launch(reduce_kernel, j + 1, kRedThreads, 0, vo.stream, nb, j + 1, vo.partial, h2);
+        count_launch();
+        launch(axpy_dots_kernel, nb, kRedThreads, 0, vo.stream, n, j + 1, h2, V, (int64_t)n, w, 1, 1,
+               vo.partial);
+        count_launch();
+        launch(reduce_kernel, 1, kRedThreads, 0, vo.stream, nb, 1, vo.partial, hw);
+        count_launch();
         DG_CUDA(cudaGetLastError());
       }
-      st = vo.dots(n, 1, w, w, n, hw);
-      if (st != DG_OK) return st;
       DG_CUDA(cudaMemcpyAsync(hs, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, vo.stream));
       DG_CUDA(cudaMemcpyAsync(hs + 256, h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, vo.stream));
       DG_CUDA(cudaMemcpyAsync(hs + 512, hw, sizeof(double), cudaMemcpyDeviceToHost, vo.stream));
@@ -373,9 +423,17 @@ dg_status gmres_solve(VecOps& vo, int64_t n, const LinOp& A, const double* dinv,
         break;
       }
       // v_{j+1} = w / |w| only when the cycle goes on (a converged cycle
-      // never reads it)
-      st = vo.axpby(n, 1.0 / hnext, w, 0.0, nullptr, vj1);
-      if (st != DG_OK) return st;
+      // never reads it), with the next step's z = D^-1 v_{j+1} in v_{j+2}
+      // when that step belongs to this cycle
+      if (dinv && j + 1 < m) {
+        launch(scale_precondition_kernel, grid_for(n), 256, 0, vo.stream, n, 1.0 / hnext, w, vj1, dinv,
+               vj1 + n);
+        count_launch();
+        DG_CUDA(cudaGetLastError());
+      } else {
+        st = vo.axpby(n, 1.0 / hnext, w, 0.0, nullptr, vj1);
+        if (st != DG_OK) return st;
+      }
       if (timeout_s > 0 &&
           std::chrono::duration<double>(clock::now() - t0).count() > timeout_s) {
         ++j;
