@@ -279,6 +279,7 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
                                        const OpArgs<T>* cheb, cudaStream_t s) {
   if (!m->affine) return launch_general_op<T>(m, pressure, mass, visc, adv, ubar, src, dst, ncomp, cheb, s);
   OpArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
   a.ncell = m->ncell;
   a.n0 = m->n[0];
   a.n1 = m->n[1];
@@ -305,6 +306,9 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
   a.cc1 = a.cc2 = T(0);
   a.flux = m->split_flux;
   a.flux_bytes = m->split_flux_bytes;
+  a.q1tab = pressure ? m->q1tab : nullptr;
+  a.q1tab_off1 = m->q1tab_off[1];
+  a.q1tab_off2 = m->q1tab_off[2];
   if (cheb) {
     a.cheb = cheb->cheb;
     a.cx = cheb->cx;
@@ -354,6 +358,15 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
 void keep_presplit_ubar(dg_mesh* m, const double* ubar) {
   m->ub_keep = ubar;
   m->ub_split_of = nullptr;
+}
+
+// split the kept ubar now (float-float meshes with the pair buffer), so that
+// the kernels before the first apply can read the pairs too
+dg_status presplit_kept_ubar(dg_mesh* m, cudaStream_t s) {
+  if (!m->ub_keep || !m->ps_ub || m->fp64_arith || m->ub_split_of == m->ub_keep) return DG_OK;
+  const dg_status st = presplit((int64_t)m->dim * m->ncell * m->nbu, m->ub_keep, m->ps_ub, s);
+  if (st == DG_OK) m->ub_split_of = m->ub_keep;
+  return st;
 }
 
 // face-flux scratch of the face-once variants: 2 values of at most 8 bytes

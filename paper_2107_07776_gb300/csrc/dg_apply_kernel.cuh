@@ -45,6 +45,10 @@ struct OpArgs {
   // the caller's source vector in its storage type (the Chebyshev update
   // reads it; the kernels' src may be a pre-split copy)
   const T* csrc;
+  // the mesh's Q1 tensor-product tables (null: none) and the first rows of
+  // axes 1 and 2 (a row: one axis cell, 4 float4)
+  const float4* q1tab;
+  int q1tab_off1, q1tab_off2;
 };
 
 // The operator kernels' output stage at output index o, y = (A src)_o
@@ -453,6 +457,20 @@ static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T
 template <typename T, typename A>
 static dg_status launch_q1(const OpArgs<T>& args, const Tab1D<A>& tb, const T* src, T* dst,
                            cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<A, float>::value) {
+    // FP32 pressure operator (no wall terms): the tensor-product form
+    if (args.q1tab && !args.walls) {
+      const int64_t tblocks = (args.ncell + 127) / 128;
+      if (tblocks > 0x7fffffff) {
+        set_error("operator apply: grid too large");
+        return DG_EINVAL;
+      }
+      launch(q1_tensor_kernel<T>, (unsigned)tblocks, 128, 0, s, args, src, dst);
+      count_launch();
+      DG_CUDA(cudaGetLastError());
+      return DG_OK;
+    }
+  }
   const int64_t blocks = (2 * args.ncell + 127) / 128;  // two threads per cell
   if (blocks > 0x7fffffff) {
     set_error("operator apply: grid too large");

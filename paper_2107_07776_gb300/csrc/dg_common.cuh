@@ -165,6 +165,12 @@ struct dg_mesh {
   double* ps_ub = nullptr;          // dim * nbu * ncell slots (not on multigrid levels)
   double* d_hdf[3] = {nullptr, nullptr, nullptr};
   double* d_hidf[3] = {nullptr, nullptr, nullptr};
+  // 1D tables of the Q1 pressure operator's tensor-product form (affine 3D
+  // meshes with two pressure points per direction): per axis cell 4 float4,
+  // the tangential weights w_i h, then the own, lower- and upper-neighbour
+  // 2x2 blocks of the 1D SIP matrix; axis a starts at row q1tab_off[a]
+  float4* q1tab = nullptr;
+  int q1tab_off[3] = {0, 0, 0};
   // advecting field whose split copy may be reused while the caller keeps
   // it unchanged (the solver around its Krylov iterations), and the field
   // the copy in ps_ub was made from
@@ -213,6 +219,9 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s);
 // The advecting field `ubar` stays unchanged until the next call (nullptr:
 // no such promise): float-float momentum applies with it split it once.
 void keep_presplit_ubar(dg_mesh* m, const double* ubar);
+// split the kept field now (no-op without one, on FP64-arithmetic meshes, or
+// when already split)
+dg_status presplit_kept_ubar(dg_mesh* m, cudaStream_t s);
 
 // host-side split of a double into a float pair, packed in a double's bits
 // (the layout df_bits reads)

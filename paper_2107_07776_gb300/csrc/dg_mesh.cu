@@ -235,6 +235,68 @@ namespace dg {
 
 // Tables, per-axis extents and the status word of a mesh whose sizes and
 // vertex lattice are set.
+// 1D tables of the pressure operator alpha M^p + K on Q1 cells in
+// tensor-product form (q1_tensor_kernel).  With the collocated two-point
+// Gauss rule the mass is diagonal and the SIP operator (Eqs. weakform_p_1,
+// penconst1) is the sum over the axes a of the 1D DG SIP matrix along a times
+// the diagonal tangential masses.  Per axis cell c (extent h, neighbours
+// across the lower and upper face, wrapped on a periodic axis, none on a wall
+// where the pressure operator has no face terms), with the trace L_s, its
+// derivative L'_s, sgn = -1 / +1 on the lower / upper face and
+// C = pen (1/h + 1/h_N) / 2:
+//   own block    K_ij = (1/h) sum_q w_q D_qi D_qj
+//                     + sum_s [(C L_s(j) - sgn L'_s(j)/(2h)) L_s(i) - L_s(j) sgn L'_s(i)/(2h)]
+//   neighbour s  N_ij = (-C L_{1-s}(j) - sgn L'_{1-s}(j)/(2 h_N)) L_s(i) + L_{1-s}(j) sgn L'_s(i)/(2h)
+// (own node i, the neighbour's node j on the same line), the terms of the
+// per-face-point flux of the Q1 kernel expanded in the nodal values.
+static dg_status build_q1_tables(dg_mesh* m, cudaStream_t s) {
+  const Tab1D<double>& t = m->tp64;
+  const double pen = (double)(m->np * m->np);
+  std::vector<float> tab;
+  for (int a = 0; a < 3; ++a) {
+    const int na = m->n[a];
+    m->q1tab_off[a] = (int)(tab.size() / 16);  // in rows (axis cells)
+    for (int c = 0; c < na; ++c) {
+      const double h = m->vx[a][c + 1] - m->vx[a][c], hiK = 1.0 / h;
+      double K[2][2], Nb[2][2][2];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          double v = 0.0;
+          for (int q = 0; q < 2; ++q) v += t.w[q] * t.D[q][i] * t.D[q][j];
+          K[i][j] = hiK * v;
+          Nb[0][i][j] = Nb[1][i][j] = 0.0;
+        }
+      for (int sd = 0; sd < 2; ++sd) {
+        int cn = c + (sd ? 1 : -1);
+        if (cn < 0 || cn >= na) {
+          if (!m->periodic[a]) continue;
+          cn = cn < 0 ? na - 1 : 0;
+        }
+        const double hiN = 1.0 / (m->vx[a][cn + 1] - m->vx[a][cn]);
+        const double sgn = sd ? 1.0 : -1.0, C = 0.5 * pen * (hiK + hiN);
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j) {
+            K[i][j] += (C * t.L[sd][j] - 0.5 * sgn * hiK * t.dL[sd][j]) * t.L[sd][i] -
+                       0.5 * t.L[sd][j] * sgn * hiK * t.dL[sd][i];
+            Nb[sd][i][j] = (-C * t.L[1 - sd][j] - 0.5 * sgn * hiN * t.dL[1 - sd][j]) * t.L[sd][i] +
+                           0.5 * t.L[1 - sd][j] * sgn * hiK * t.dL[sd][i];
+          }
+      }
+      const float row[16] = {(float)(t.w[0] * h), (float)(t.w[1] * h), 0.0f, 0.0f,
+                             (float)K[0][0], (float)K[0][1], (float)K[1][0], (float)K[1][1],
+                             (float)Nb[0][0][0], (float)Nb[0][0][1], (float)Nb[0][1][0], (float)Nb[0][1][1],
+                             (float)Nb[1][0][0], (float)Nb[1][0][1], (float)Nb[1][1][0], (float)Nb[1][1][1]};
+      tab.insert(tab.end(), row, row + 16);
+    }
+  }
+  cudaError_t e = cudaMalloc(&m->q1tab, sizeof(float) * tab.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->q1tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host table dies here
+  if (e != cudaSuccess) return cuda_fail(e, "mesh upload (Q1 tables)");
+  return DG_OK;
+}
+
 dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
   cudaGetDevice(&m->device);
   m->nu = m->k + 1;
@@ -309,6 +371,7 @@ dg_status finish_mesh(dg_mesh* m, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "mesh upload (float-float extents)");
   }
+  if (m->dim == 3 && m->np == 2) return build_q1_tables(m, s);
   return DG_OK;
 }
 
@@ -472,6 +535,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   for (int a = 0; a < 3; ++a) {
     if (m->d_hdf[a]) cudaFree(m->d_hdf[a]);
     if (m->d_hidf[a]) cudaFree(m->d_hidf[a]);
+    if (a == 0 && m->q1tab) cudaFree(m->q1tab);
   }
   if (m->ps_src) cudaFree(m->ps_src);
   if (m->ps_ub) cudaFree(m->ps_ub);

@@ -309,4 +309,148 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// The FP32 pressure operator alpha M^p + visc K on Q1 cells of a Cartesian
+// mesh in tensor-product form, one thread per cell.  The mass is diagonal
+// (alpha w_i0 h_0 w_i1 h_1 w_i2 h_2 per node) and K is the sum over the axes
+// of the 1D SIP matrix along the axis times the tangential masses: along axis
+// a, each of the cell's 4 lines takes its own 2x2 block and the blocks of its
+// lower and upper neighbours' lines, all tabulated per axis cell at mesh
+// setup (build_q1_tables).  The same operator as q1_cell_kernel, with the
+// face terms folded into the tables instead of formed per face point.
+template <int AX>
+__device__ __forceinline__ void q1_line_block(const float4 K, const float v[8], const float mt[4], float s[8]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int n0 = q1_node(AX, 0, t), n1 = q1_node(AX, 1, t);
+    const float a0 = fmaf(K.y, v[n1], K.x * v[n0]);
+    const float a1 = fmaf(K.w, v[n1], K.z * v[n0]);
+    s[n0] = fmaf(mt[t], a0, s[n0]);
+    s[n1] = fmaf(mt[t], a1, s[n1]);
+  }
+}
+
+template <int AX>
+__device__ __forceinline__ void q1_axis_terms(const OpArgs<float>& a, const float4* row, const int ci[3],
+                                              int64_t cell, const float* __restrict__ src, bool vec,
+                                              const float u[8], const float mt[4], float s[8]) {
+  const int c = ci[AX], n = AX == 0 ? a.n0 : (AX == 1 ? a.n1 : a.n2);
+  const int per = AX == 0 ? a.per0 : (AX == 1 ? a.per1 : a.per2);
+  const int64_t stride = AX == 0 ? 1 : (AX == 1 ? (int64_t)a.n0 : (int64_t)a.n0 * a.n1);
+  q1_line_block<AX>(__ldg(row + 1), u, mt, s);
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    int cn = c + (sd ? 1 : -1);
+    if (cn < 0 || cn >= n) {
+      if (!per) continue;  // wall: the pressure operator has no face terms there
+      cn = cn < 0 ? n - 1 : 0;
+    }
+    float v[8];
+    q1_load<float, float>(src + (cell + (int64_t)(cn - c) * stride) * 8, vec, v);
+    q1_line_block<AX>(__ldg(row + 2 + sd), v, mt, s);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    q1_tensor_kernel(const __grid_constant__ OpArgs<T> a, const T* __restrict__ src, T* __restrict__ dst) {
+  static_assert(std::is_same<T, float>::value, "q1_tensor_kernel: FP32 only");
+  pdl_entry();
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= a.ncell) return;
+  int ci[3];
+  lex_coords(cell, a.n0, a.n1, ci);
+  const float4* r0 = a.q1tab + 4 * (int64_t)ci[0];
+  const float4* r1 = a.q1tab + 4 * ((int64_t)a.q1tab_off1 + ci[1]);
+  const float4* r2 = a.q1tab + 4 * ((int64_t)a.q1tab_off2 + ci[2]);
+  const float4 w0 = __ldg(r0), w1 = __ldg(r1), w2 = __ldg(r2);  // (w_0 h, w_1 h, -, -) per axis
+  uintptr_t align = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst);
+  const bool vec = (align & 15u) == 0;
+  // the epilogue's vectors too (a null pointer is aligned)
+  const bool vec_all = vec && ((reinterpret_cast<uintptr_t>(a.cx) | reinterpret_cast<uintptr_t>(a.cr) |
+                                reinterpret_cast<uintptr_t>(a.cdinv) | reinterpret_cast<uintptr_t>(a.csrc)) &
+                               15u) == 0;
+  float u[8], s[8];
+  q1_load<float, float>(src + cell * 8, vec, u);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s[k] = 0.0f;
+  {  // axis 0: lines t = i1 + 2 i2
+    const float mt[4] = {w1.x * w2.x, w1.y * w2.x, w1.x * w2.y, w1.y * w2.y};
+    q1_axis_terms<0>(a, r0, ci, cell, src, vec, u, mt, s);
+  }
+  {  // axis 1: lines t = i0 + 2 i2
+    const float mt[4] = {w0.x * w2.x, w0.y * w2.x, w0.x * w2.y, w0.y * w2.y};
+    q1_axis_terms<1>(a, r1, ci, cell, src, vec, u, mt, s);
+  }
+  {  // axis 2: lines t = i0 + 2 i1
+    const float mt[4] = {w0.x * w1.x, w0.y * w1.x, w0.x * w1.y, w0.y * w1.y};
+    q1_axis_terms<2>(a, r2, ci, cell, src, vec, u, mt, s);
+  }
+  float y[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float m = ((k & 1) ? w0.y : w0.x) * ((k & 2) ? w1.y : w1.x) * ((k & 4) ? w2.y : w2.x);
+    y[k] = fmaf(a.visc, s[k], a.mass * m * u[k]);
+  }
+  const int64_t o = cell * 8;
+  if (a.cheb && vec_all) {  // op_epilogue's modes on the cell's 8 contiguous values, 16-byte accesses
+    float d[8], r[8], x[8], di[8], out[8];
+    if (a.cheb == 1 || a.cheb == 4) q1_load<float, float>(a.csrc + o, true, d);
+    // x and r are written in this launch (each element by its own thread
+    // only): plain loads, not the read-only path
+    auto ld8 = [](const float* p, float v[8]) {
+      const float4 lo = reinterpret_cast<const float4*>(p)[0], hi = reinterpret_cast<const float4*>(p)[1];
+      v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+      v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+    };
+    if (a.cheb != 3) ld8(a.cr + o, r);
+    if (a.cheb != 2) q1_load<float, float>(a.cdinv + o, true, di);
+    if (a.cheb != 2) ld8(a.cx + o, x);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      switch (a.cheb) {
+        case 1: {
+          x[k] += d[k];
+          r[k] = r[k] - di[k] * y[k];
+          out[k] = a.cc1 * d[k] + a.cc2 * r[k];
+          break;
+        }
+        case 2: out[k] = r[k] - y[k]; break;
+        case 3: {
+          r[k] = di[k] * (x[k] - y[k]);
+          out[k] = a.cc1 * r[k];
+          break;
+        }
+        default: {
+          const float rk = r[k] - di[k] * y[k];
+          x[k] += d[k] + (a.cc1 * d[k] + a.cc2 * rk);
+        }
+      }
+    }
+    float4* xv = reinterpret_cast<float4*>(a.cx + o);
+    float4* rv = reinterpret_cast<float4*>(a.cr + o);
+    float4* ov = reinterpret_cast<float4*>(dst + o);
+    if (a.cheb == 1 || a.cheb == 4) {
+      xv[0] = make_float4(x[0], x[1], x[2], x[3]);
+      xv[1] = make_float4(x[4], x[5], x[6], x[7]);
+    }
+    if (a.cheb == 1 || a.cheb == 3) {
+      rv[0] = make_float4(r[0], r[1], r[2], r[3]);
+      rv[1] = make_float4(r[4], r[5], r[6], r[7]);
+    }
+    if (a.cheb != 4) {
+      ov[0] = make_float4(out[0], out[1], out[2], out[3]);
+      ov[1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+  } else if (a.cheb) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) op_epilogue(a, o + k, y[k], dst);
+  } else if (vec) {
+    reinterpret_cast<float4*>(dst + o)[0] = make_float4(y[0], y[1], y[2], y[3]);
+    reinterpret_cast<float4*>(dst + o)[1] = make_float4(y[4], y[5], y[6], y[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[o + k] = y[k];
+  }
+}
+
 }  // namespace dg

@@ -1120,6 +1120,15 @@ __device__ __forceinline__ R to_r(double v) {
   if constexpr (sizeof(R) == 4) return df_narrow(v);
   else return v;
 }
+// an advecting-field value for the diagonal: from the float-pair copy (its
+// leading float) when the field arrives pre-split, else narrowed
+template <typename R>
+__device__ __forceinline__ R ld_ub(double v, int pairs) {
+  if constexpr (sizeof(R) == 4) {
+    if (pairs) return df_bits(v).hi;
+  }
+  return to_r<R>(v);
+}
 template <typename R>
 __device__ __forceinline__ R abs_r(R x) { return x < R(0.0) ? -x : x; }
 template <typename R>
@@ -1147,7 +1156,8 @@ __device__ __forceinline__ double inv_r(R d) {
 template <int DIM, int N, typename R, int CPB>
 __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
     diag_kernel(const __grid_constant__ Grid g, const __grid_constant__ Tab1D<R> tb, R mass, R visc, R adv,
-                R pen, int walls, const double* __restrict__ ub, double* __restrict__ diag, int inv_copies) {
+                R pen, int walls, const double* __restrict__ ub, int ub_pairs, double* __restrict__ diag,
+                int inv_copies) {
   pdl_entry();
   using Ar = Arith<R>;
   constexpr int NB = Sh<N, DIM>::NB, NF = Sh<N, DIM>::NF, NFP = Sh<N, DIM>::NFP;
@@ -1177,11 +1187,11 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
         const double* ua = ub + (int64_t)ax * g.ncell * NB;
 #pragma unroll
         for (int i = 0; i < N; ++i)
-          unin = Ar::fma(tb.L[s][i], to_r<R>(__ldg(&ua[cell * NB + nodeof(N, DIM, ax, i, t)])), unin);
+          unin = Ar::fma(tb.L[s][i], ld_ub<R>(__ldg(&ua[cell * NB + nodeof(N, DIM, ax, i, t)]), ub_pairs), unin);
         if (nb >= 0) {
 #pragma unroll
           for (int i = 0; i < N; ++i)
-            unout = Ar::fma(tb.L[1 - s][i], to_r<R>(__ldg(&ua[nb * NB + nodeof(N, DIM, ax, i, t)])), unout);
+            unout = Ar::fma(tb.L[1 - s][i], ld_ub<R>(__ldg(&ua[nb * NB + nodeof(N, DIM, ax, i, t)]), ub_pairs), unout);
         }
         unin = sgn * unin;
         unout = sgn * unout;
@@ -1227,7 +1237,7 @@ __global__ void __launch_bounds__(((CPB * Sh<N, DIM>::NB + 31) / 32) * 32)
       if (c != b) wt *= wl[c];
     const R acc = wt * sb * hi[b] * hi[b];
     d += visc * acc;
-    if (adv != R(0.0)) d -= adv * W * to_r<R>(ub[((int64_t)b * g.ncell + cell) * NB + node]) * tb.D[ii[b]][ii[b]] * hi[b];
+    if (adv != R(0.0)) d -= adv * W * ld_ub<R>(ub[((int64_t)b * g.ncell + cell) * NB + node], ub_pairs) * tb.D[ii[b]][ii[b]] * hi[b];
   }
   for (int ax = 0; ax < DIM; ++ax) {
     const int t = tangof(N, DIM, ax, ii), i = ii[ax];
@@ -1472,14 +1482,18 @@ dg_status run_diag(const dg_mesh* m, bool pressure, double mass, double visc, do
   constexpr int CPB = cpb_for<N, DIM>();
   constexpr int threads = ((CPB * Sh<N, DIM>::NB + 31) / 32) * 32;
   const unsigned blocks = (unsigned)((m->ncell + CPB - 1) / CPB);
+  // the FP32 diagonal reads the float-pair copy of ubar when the mesh holds
+  // one for this field (kept for a solve: keep_presplit_ubar)
+  const bool pairs = fp32 && ub && m->ps_ub && m->ub_keep == ub && m->ub_split_of == ub;
   if (fp32)
     launch(diag_kernel<DIM, N, float, CPB>, blocks, threads, 0, s, 
         make_grid<DIM>(m), pressure ? m->tp32 : m->tu32, (float)mass, (float)visc, (float)adv,
-        (float)(N * N), pressure ? 0 : 1, ub, diag, inv_copies);
+        (float)(N * N), pressure ? 0 : 1, pairs ? (const double*)m->ps_ub : ub, pairs ? 1 : 0, diag,
+        inv_copies);
   else
     launch(diag_kernel<DIM, N, double, CPB>, blocks, threads, 0, s, 
         make_grid<DIM>(m), pressure ? m->tp64 : m->tu64, mass, visc, adv, (double)(N * N),
-        pressure ? 0 : 1, ub, diag, inv_copies);
+        pressure ? 0 : 1, ub, 0, diag, inv_copies);
   count_launch();
   DG_CUDA(cudaGetLastError());
   return DG_OK;

@@ -98,28 +98,42 @@ dg_status solve_momentum(dg_solver* s, const dg_momentum_coeffs* co, const doubl
   dg_mesh* m = s->mesh;
   dg_status st;
   const double* dinv = nullptr;
+  // ubar stays unchanged during the solve: the float-float applies split it
+  // once instead of once per iteration, and the FP32 diagonal reads the pairs
+  keep_presplit_ubar(m, ubar);
   if (o->precond == DG_PC_JACOBI) {
     if (m->affine) {  // diagonal and its inverse in one pass
-      st = momentum_inv_diagonal_fp32(m, co, ubar, s->dinv_u, s->stream);
+      st = presplit_kept_ubar(m, s->stream);
+      if (st == DG_OK) st = momentum_inv_diagonal_fp32(m, co, ubar, s->dinv_u, s->stream);
     } else {
       st = momentum_diagonal_fp32(m, co, ubar, s->diag_s, s->stream);
       if (st == DG_OK) st = s->vo.invert(s->nu, s->diag_s, s->nus, s->dinv_u);
     }
-    if (st != DG_OK) return st;
+    if (st != DG_OK) {
+      keep_presplit_ubar(m, nullptr);
+      return st;
+    }
     dinv = s->dinv_u;
   } else if (o->precond != DG_PC_NONE) {
+    keep_presplit_ubar(m, nullptr);
     set_error("dg_solve_stage: momentum systems take NONE or JACOBI preconditioning");
     return DG_EINVAL;
   }
-  if (o->guess == DG_GUESS_ZERO) DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * s->nu, s->stream));
+  if (o->guess == DG_GUESS_ZERO) {
+    const cudaError_t e = cudaMemsetAsync(x, 0, sizeof(double) * s->nu, s->stream);
+    if (e != cudaSuccess) {
+      keep_presplit_ubar(m, nullptr);
+      return cuda_fail(e, "dg_solve_stage");
+    }
+  }
   st = ensure_basis(s, o->restart);
-  if (st != DG_OK) return st;
+  if (st != DG_OK) {
+    keep_presplit_ubar(m, nullptr);
+    return st;
+  }
   LinOp A = [&](const double* in, double* out) {
     return dg_apply_momentum(m, co, ubar, in, out, s->stream);
   };
-  // ubar stays unchanged during the solve: the float-float applies split it
-  // once instead of once per iteration
-  keep_presplit_ubar(m, ubar);
   st = gmres_solve(s->vo, s->nu, A, dinv, rhs, x, s->V, s->w, s->hdev, o->restart, o->tol_rel,
                    o->max_iter, o->timeout_s, info);
   keep_presplit_ubar(m, nullptr);
