@@ -310,3 +310,88 @@ def test_pressure_penalty_jump_3d():
     p = np.zeros(m.n_p)
     p[: m.nb_p] = 1.0
     assert abs(p @ (m.csr("sipg_p") @ p) - 4.0) < 1e-12
+
+
+def _sipg_1d(vx, periodic, pen):
+    """Textbook 1D SIP matrix on the cells [vx_c, vx_c+1] with the two-point
+    Gauss nodal basis: sum_c int u'v' + sum over interior faces of
+    (-{{u'}}[v] - [u]{{v'}} + sigma [u][v]), [w] = w_left - w_right,
+    sigma = pen (1/h_left + 1/h_right)/2; no terms on boundary faces
+    (natural boundary); a periodic axis adds the face between the last and
+    the first cell.  Also the diagonal mass w_i h."""
+    g = 1.0 / math.sqrt(3.0)
+    xr = np.array([(1 - g) / 2, (1 + g) / 2])
+    n = len(vx) - 1
+    h = np.diff(vx)
+
+    def val(i, t):  # nodal basis i on [0, 1] at t
+        return (t - xr[1 - i]) / (xr[i] - xr[1 - i])
+
+    def der(i):
+        return 1.0 / (xr[i] - xr[1 - i])
+
+    K = np.zeros((2 * n, 2 * n))
+    M = np.zeros(2 * n)
+    for c in range(n):
+        for i in range(2):
+            M[2 * c + i] = 0.5 * h[c]
+            for j in range(2):
+                K[2 * c + i, 2 * c + j] += h[c] * der(i) * der(j) / h[c] ** 2  # two-point rule is exact
+    faces = [(c, c + 1) for c in range(n - 1)] + ([(n - 1, 0)] if periodic else [])
+    for L, R in faces:
+        sig = pen * (1 / h[L] + 1 / h[R]) / 2
+        # traces and derivatives of the basis functions of both cells at the face
+        tr = {(L, i): (val(i, 1.0), der(i) / h[L]) for i in range(2)}
+        tr.update({(R, i): (-val(i, 0.0), der(i) / h[R]) for i in range(2)})  # jump sign: minus on the right
+        funcs = [(L, 0), (L, 1), (R, 0), (R, 1)]
+        for cu, iu in funcs:
+            ju, du = tr[(cu, iu)]
+            for cv, iv in funcs:
+                jv, dv = tr[(cv, iv)]
+                K[2 * cv + iv, 2 * cu + iu] += -0.5 * du * jv - 0.5 * ju * dv + sig * ju * jv
+    return K, M
+
+
+@pytest.mark.parametrize("name,per", [("cart3d", [True, True, True]), ("graded3d", [True, False, False]),
+                                      ("cart3d", [True, True, False])])
+def test_q1_pressure_operator_is_a_kronecker_sum(name, per):
+    """On Cartesian (and tanh-graded) cells with the collocated two-point
+    Gauss rule the pressure SIP operator of degree-2 velocity meshes (Q1
+    pressure, penalty k^2 = 4) is the sum over the axes of the 1D SIP matrix
+    along that axis times the diagonal masses of the others: the oracle's
+    3D face-by-face assembly against textbook 1D matrices."""
+    spec = dict(MESHES[name])
+    spec["periodic"] = per
+    m = Mesh(spec["dim"], spec["n"], spec["lo"], spec["hi"], spec["periodic"], 2, map=spec["map"],
+             map_param=spec.get("map_param", [0, 0, 0]))
+    n = spec["n"]
+    Xp = m.node_coords(True).reshape(3, n[2], n[1], n[0], 2, 2, 2)
+    g = 1.0 / math.sqrt(3.0)
+    vx = []
+    for a in range(3):  # the vertex lattice from the nodes of one line of cells
+        line = [Xp[0][0, 0, :, 0, 0, :], Xp[1][0, :, 0, 0, :, 0], Xp[2][:, 0, 0, :, 0, 0]][a]
+        hh = (line[:, 1] - line[:, 0]) / g
+        lo = line[:, 0] - hh * (1 - g) / 2
+        vx.append(np.append(lo, lo[-1] + hh[-1]))
+    Ks, Ms = zip(*[_sipg_1d(vx[a], per[a], 4.0) for a in range(3)])
+    Dm = [np.diag(x) for x in Ms]
+    # (c2 i2, c1 i1, c0 i0) ordering, x fastest
+    K = (np.kron(np.kron(Dm[2], Dm[1]), Ks[0]) + np.kron(np.kron(Dm[2], Ks[1]), Dm[0])
+         + np.kron(np.kron(Ks[2], Dm[1]), Dm[0]))
+    # to the oracle's (cell, node) ordering: cell = c0 + n0 (c1 + n1 c2), node = i0 + 2 i1 + 4 i2
+    perm = np.empty(K.shape[0], dtype=int)
+    for c2 in range(n[2]):
+        for c1 in range(n[1]):
+            for c0 in range(n[0]):
+                for i2 in range(2):
+                    for i1 in range(2):
+                        for i0 in range(2):
+                            kron = (((c2 * 2 + i2) * n[1] + c1) * 2 + i1) * 2 * n[0] + 2 * c0 + i0
+                            perm[(c0 + n[0] * (c1 + n[1] * c2)) * 8 + i0 + 2 * i1 + 4 * i2] = kron
+    K = K[np.ix_(perm, perm)]
+    A = m.assemble("sipg_p")
+    Ad = np.array([A.apply(e) for e in np.eye(K.shape[0])]).T
+    assert np.abs(Ad - K).max() < 1e-11 * np.abs(K).max()
+    Mp = m.assemble("mass_p")
+    mass = np.kron(np.kron(Ms[2], Ms[1]), Ms[0])[perm]
+    assert np.abs(Mp.apply(np.ones(K.shape[0])) - mass).max() < 1e-13 * mass.max()
