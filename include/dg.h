@@ -149,9 +149,10 @@ dg_status dg_apply_poisson_f32(dg_mesh* mesh, double alpha, const float* src, fl
  * keeps the fastest for later applies.  Candidates: cells per CTA, a
  * register cap, the face-once form (every face evaluated once into a
  * per-mesh flux scratch, then the cells: a different rounding order, the
- * same result to FP64 rounding) and, for the FP32 3D pressure operator on
- * two points per direction, two threads per Q1 cell with the cell in
- * registers (again the same result up to rounding order).  A mesh using
+ * same result to FP64 rounding) and, for the 3D pressure operator on two
+ * points per direction in FP32 and float-float arithmetic, the
+ * tensor-product form (1D SIP blocks tabulated per axis cell, one thread per
+ * cell; again the same result up to rounding order).  A mesh using
  * the face-once form shares that scratch between its applies, so applies
  * on one tuned mesh from different streams must not overlap.
  * Multigrid levels built afterwards from a tuned mesh are tuned too.
@@ -167,9 +168,10 @@ dg_status dg_autotune(dg_mesh* mesh, void* stream);
  * candidates listed in dg_autotune's report: 0-2 cells per CTA half /
  * default / double, 3-4 default with 96 / 80 registers, 5-6 face-once
  * capped at 72 registers (6: every component's volume sums between the
- * same two barriers), 7 two threads per Q1 cell -- 3D scalar
- * operators without advection on two points per direction, in every
- * precision; other operators run variant 1 instead) for every operator and
+ * same two barriers), 7 the Q1 tensor-product form (two threads per Q1
+ * cell with native FP64 arithmetic) -- 3D scalar operators without
+ * advection on two points per direction, in every precision; other
+ * operators run variant 1 instead) for every operator and
  * precision; a face-once variant allocates the mesh's flux scratch.
  * Trilinear meshes take 0-2 as the general kernel's tile shapes (half,
  * default, double the cells per CTA) and run 1 for the others. */

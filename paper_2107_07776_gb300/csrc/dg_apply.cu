@@ -307,6 +307,7 @@ static dg_status launch_scalar_op_impl(const dg_mesh* m, bool pressure, T mass, 
   a.flux = m->split_flux;
   a.flux_bytes = m->split_flux_bytes;
   a.q1tab = pressure ? m->q1tab : nullptr;
+  a.q1tab_df = pressure ? m->q1tab_df : nullptr;
   a.q1tab_off1 = m->q1tab_off[1];
   a.q1tab_off2 = m->q1tab_off[2];
   if (cheb) {
@@ -520,14 +521,12 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
     for (int op = 0; op < (m->level ? 1 : 3) && st == DG_OK; ++op) {
       float best = 1e30f, times[kTuneVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
       int bestv = 1;
-      // the two-threads-per-cell Q1 kernel exists for the 3D pressure
-      // operator on two points per direction only (elsewhere variant 7 would
-      // time variant 1 again), and is a candidate in FP32 only: its
-      // float-float form is instruction-heavy (8.4 k instructions per warp
-      // on tgv32) and wins back-to-back with a warm instruction cache (28 vs
-      // 31 us) but loses inside the step, between other kernels (49 vs
-      // 31 us cold).  Not timed: reported as 0.
-      const bool q1_ok = op == 0 && m->dim == 3 && m->np == 2 && prec == 1 && m->affine;
+      // variant 7 (the Q1 tensor-product kernel) exists for the 3D pressure
+      // operator on two points per direction only (elsewhere it would time
+      // variant 1 again), in FP32 and float-float; with native FP64
+      // arithmetic it would run the two-threads-per-cell kernel, which is
+      // not offered.  Not timed: reported as 0.
+      const bool q1_ok = op == 0 && m->dim == 3 && m->np == 2 && m->affine && (prec == 1 || !m->fp64_arith);
       // trilinear meshes: the general kernel's tile shapes (cells per CTA
       // half, default, double)
       const int nvar = m->affine ? kTuneVariants : kGeneralVariants;
@@ -567,7 +566,7 @@ dg_status autotune_mesh(dg_mesh* m, cudaStream_t s) {
       const bool p = op == 0, adv = op == 2;
       auto cp = [&](int v) {
         if (!m->affine) return v < kGeneralVariants ? general_cpb_for_mesh(m, p, adv, v) : 0;
-        if (variant_q1(v)) return 64;  // two threads per cell, 128 threads per CTA
+        if (variant_q1(v)) return 128;  // the tensor-product kernel: one thread per cell
         return prec == 0 ? cpb_for_mesh<double>(m, p, adv, v) : cpb_for_mesh<float>(m, p, adv, v);
       };
       if (!m->affine) {

@@ -48,6 +48,7 @@ struct OpArgs {
   // the mesh's Q1 tensor-product tables (null: none) and the first rows of
   // axes 1 and 2 (a row: one axis cell, 4 float4)
   const float4* q1tab;
+  const double* q1tab_df;  // the same rows as float pairs
   int q1tab_off1, q1tab_off2;
 };
 
@@ -457,15 +458,19 @@ static dg_status launch_split(const OpArgs<T>& args, const Tab1D<A>& tb, const T
 template <typename T, typename A>
 static dg_status launch_q1(const OpArgs<T>& args, const Tab1D<A>& tb, const T* src, T* dst,
                            cudaStream_t s) {
-  if constexpr (std::is_same<T, float>::value && std::is_same<A, float>::value) {
-    // FP32 pressure operator (no wall terms): the tensor-product form
-    if (args.q1tab && !args.walls) {
+  if constexpr ((std::is_same<T, float>::value && std::is_same<A, float>::value) || kPreSplit<T, A>) {
+    // FP32 or float-float pressure operator (no wall terms): the
+    // tensor-product form
+    if ((kPreSplit<T, A> ? args.q1tab_df != nullptr : args.q1tab != nullptr) && !args.walls) {
       const int64_t tblocks = (args.ncell + 127) / 128;
       if (tblocks > 0x7fffffff) {
         set_error("operator apply: grid too large");
         return DG_EINVAL;
       }
-      launch(q1_tensor_kernel<T>, (unsigned)tblocks, 128, 0, s, args, src, dst);
+      if constexpr (kPreSplit<T, A>)
+        launch(q1_tensor_df_kernel<T>, (unsigned)tblocks, 128, 0, s, args, src, dst);
+      else
+        launch(q1_tensor_kernel<T>, (unsigned)tblocks, 128, 0, s, args, src, dst);
       count_launch();
       DG_CUDA(cudaGetLastError());
       return DG_OK;

@@ -171,6 +171,9 @@ struct dg_mesh {
   // 2x2 blocks of the 1D SIP matrix; axis a starts at row q1tab_off[a]
   float4* q1tab = nullptr;
   int q1tab_off[3] = {0, 0, 0};
+  // the same rows as float pairs packed in doubles (16 per row), for the
+  // float-float form of the kernel
+  double* q1tab_df = nullptr;
   // advecting field whose split copy may be reused while the caller keeps
   // it unchanged (the solver around its Krylov iterations), and the field
   // the copy in ps_ub was made from

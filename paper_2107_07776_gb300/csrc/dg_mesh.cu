@@ -249,10 +249,13 @@ namespace dg {
 //   neighbour s  N_ij = (-C L_{1-s}(j) - sgn L'_{1-s}(j)/(2 h_N)) L_s(i) + L_{1-s}(j) sgn L'_s(i)/(2h)
 // (own node i, the neighbour's node j on the same line), the terms of the
 // per-face-point flux of the Q1 kernel expanded in the nodal values.
+double pack_pair(double x);
+
 static dg_status build_q1_tables(dg_mesh* m, cudaStream_t s) {
   const Tab1D<double>& t = m->tp64;
   const double pen = (double)(m->np * m->np);
   std::vector<float> tab;
+  std::vector<double> tabd;
   for (int a = 0; a < 3; ++a) {
     const int na = m->n[a];
     m->q1tab_off[a] = (int)(tab.size() / 16);  // in rows (axis cells)
@@ -287,12 +290,19 @@ static dg_status build_q1_tables(dg_mesh* m, cudaStream_t s) {
                              (float)Nb[0][0][0], (float)Nb[0][0][1], (float)Nb[0][1][0], (float)Nb[0][1][1],
                              (float)Nb[1][0][0], (float)Nb[1][0][1], (float)Nb[1][1][0], (float)Nb[1][1][1]};
       tab.insert(tab.end(), row, row + 16);
+      const double rowd[16] = {t.w[0] * h, t.w[1] * h, 0.0, 0.0, K[0][0], K[0][1], K[1][0], K[1][1],
+                               Nb[0][0][0], Nb[0][0][1], Nb[0][1][0], Nb[0][1][1],
+                               Nb[1][0][0], Nb[1][0][1], Nb[1][1][0], Nb[1][1][1]};
+      for (double v : rowd) tabd.push_back(pack_pair(v));
     }
   }
   cudaError_t e = cudaMalloc(&m->q1tab, sizeof(float) * tab.size());
+  if (e == cudaSuccess) e = cudaMalloc(&m->q1tab_df, sizeof(double) * tabd.size());
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->q1tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host table dies here
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->q1tab_df, tabd.data(), sizeof(double) * tabd.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables die here
   if (e != cudaSuccess) return cuda_fail(e, "mesh upload (Q1 tables)");
   return DG_OK;
 }
@@ -536,6 +546,7 @@ void dg_mesh_destroy(dg_mesh* m) {
     if (m->d_hdf[a]) cudaFree(m->d_hdf[a]);
     if (m->d_hidf[a]) cudaFree(m->d_hidf[a]);
     if (a == 0 && m->q1tab) cudaFree(m->q1tab);
+    if (a == 0 && m->q1tab_df) cudaFree(m->q1tab_df);
   }
   if (m->ps_src) cudaFree(m->ps_src);
   if (m->ps_ub) cudaFree(m->ps_ub);

@@ -453,4 +453,106 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// The same tensor-product operator in float-float FP64 arithmetic (T =
+// double storage, the source pre-split into float pairs, the tables' rows as
+// float pairs): one compensated sum per node for the stiffness terms, then
+// y = (alpha w h w h w h) u + visc K u rounded once.
+template <int AX>
+__device__ __forceinline__ void q1_line_block_df(const double* __restrict__ K, const df64 v[8], const df64 mt[4],
+                                                 DfAcc st[8]) {
+  const df64 k00 = df_bits(__ldg(K)), k01 = df_bits(__ldg(K + 1)), k10 = df_bits(__ldg(K + 2)),
+             k11 = df_bits(__ldg(K + 3));
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int n0 = q1_node(AX, 0, t), n1 = q1_node(AX, 1, t);
+    SumOf<df64> a0, a1;
+    a0.start(k00, v[n0]);
+    a0.fma(k01, v[n1]);
+    a1.start(k10, v[n0]);
+    a1.fma(k11, v[n1]);
+    acc_fma(st[n0], mt[t], a0.value());
+    acc_fma(st[n1], mt[t], a1.value());
+  }
+}
+
+template <int AX>
+__device__ __forceinline__ void q1_axis_terms_df(const OpArgs<double>& a, const double* row, const int ci[3],
+                                                 int64_t cell, const double* __restrict__ src, bool vec,
+                                                 const df64 u[8], const df64 mt[4], DfAcc st[8]) {
+  const int c = ci[AX], n = AX == 0 ? a.n0 : (AX == 1 ? a.n1 : a.n2);
+  const int per = AX == 0 ? a.per0 : (AX == 1 ? a.per1 : a.per2);
+  const int64_t stride = AX == 0 ? 1 : (AX == 1 ? (int64_t)a.n0 : (int64_t)a.n0 * a.n1);
+  q1_line_block_df<AX>(row + 4, u, mt, st);
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    int cn = c + (sd ? 1 : -1);
+    if (cn < 0 || cn >= n) {
+      if (!per) continue;  // wall: the pressure operator has no face terms there
+      cn = cn < 0 ? n - 1 : 0;
+    }
+    double vt[8];
+    q1_load<double, df64>(src + (cell + (int64_t)(cn - c) * stride) * 8, vec, vt);
+    df64 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = df_bits(vt[k]);
+    q1_line_block_df<AX>(row + 8 + 4 * sd, v, mt, st);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, 4)
+    q1_tensor_df_kernel(const __grid_constant__ OpArgs<T> a, const T* __restrict__ src, T* __restrict__ dst) {
+  static_assert(std::is_same<T, double>::value, "q1_tensor_df_kernel: FP64 storage only");
+  pdl_entry();
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= a.ncell) return;
+  int ci[3];
+  lex_coords(cell, a.n0, a.n1, ci);
+  const double* r0 = a.q1tab_df + 16 * (int64_t)ci[0];
+  const double* r1 = a.q1tab_df + 16 * ((int64_t)a.q1tab_off1 + ci[1]);
+  const double* r2 = a.q1tab_df + 16 * ((int64_t)a.q1tab_off2 + ci[2]);
+  const df64 w0[2] = {df_bits(__ldg(r0)), df_bits(__ldg(r0 + 1))};
+  const df64 w1[2] = {df_bits(__ldg(r1)), df_bits(__ldg(r1 + 1))};
+  const df64 w2[2] = {df_bits(__ldg(r2)), df_bits(__ldg(r2 + 1))};
+  const bool vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+  double ut[8];
+  q1_load<double, df64>(src + cell * 8, vec, ut);
+  df64 u[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) u[k] = df_bits(ut[k]);
+  DfAcc st[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) st[k] = acc_prod(df_const(0.0), df_const(0.0));
+  {  // axis 0: lines t = i1 + 2 i2
+    const df64 mt[4] = {w1[0] * w2[0], w1[1] * w2[0], w1[0] * w2[1], w1[1] * w2[1]};
+    q1_axis_terms_df<0>(a, r0, ci, cell, src, vec, u, mt, st);
+  }
+  {  // axis 1: lines t = i0 + 2 i2
+    const df64 mt[4] = {w0[0] * w2[0], w0[1] * w2[0], w0[0] * w2[1], w0[1] * w2[1]};
+    q1_axis_terms_df<1>(a, r1, ci, cell, src, vec, u, mt, st);
+  }
+  {  // axis 2: lines t = i0 + 2 i1
+    const df64 mt[4] = {w0[0] * w1[0], w0[1] * w1[0], w0[0] * w1[1], w0[1] * w1[1]};
+    q1_axis_terms_df<2>(a, r2, ci, cell, src, vec, u, mt, st);
+  }
+  const df64 mass = df_bits(a.mass), visc = df_bits(a.visc);
+  const int64_t o = cell * 8;
+  double yd[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const df64 m = w0[k & 1] * w1[(k >> 1) & 1] * w2[k >> 2];
+    SumOf<df64> y;
+    y.start(mass * m, u[k]);
+    y.fma(visc, acc_value(st[k]));
+    yd[k] = df_to(y.value());
+  }
+  if (a.cheb || (reinterpret_cast<uintptr_t>(dst) & 15u) != 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) op_epilogue(a, o + k, yd[k], dst);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(dst + o)[q] = make_double2(yd[2 * q], yd[2 * q + 1]);
+  }
+}
+
 }  // namespace dg

@@ -140,8 +140,9 @@ def test_face_once_variants_match_oracle(ci, variant):
 
 @pytest.mark.parametrize("ci", [i for i, c in enumerate(CASES) if c[0] == 3 and c[5] == 2 and c[6] != 2])
 def test_q1_thread_per_cell_variant_matches_oracle(ci):
-    """Variant 7 (one thread per Q1 cell) for the pressure operator in
-    float-float, native FP64 and FP32 against the oracle; the momentum
+    """Variant 7 for the pressure operator against the oracle: the
+    tensor-product kernel in float-float and FP32, the two-threads-per-cell
+    kernel in native FP64; the momentum
     operator (not Q1 scalar) runs its fallback and stays exact."""
     from paper_2107_07776_gb300 import binding as b
     gm, om = meshes(CASES[ci])
@@ -171,7 +172,7 @@ def test_q1_thread_per_cell_variant_matches_oracle(ci):
 
 def test_q1_thread_per_cell_variant_in_multigrid():
     """The Chebyshev-fused epilogues of variants 5, 6 (face-once, per
-    component and components interleaved) and 7 (two threads per Q1 cell):
+    component and components interleaved) and 7 (the Q1 tensor-product form):
     an FP32-multigrid Helmholtz solve on a Q2/Q1 mesh whose operators all run
     one variant converges to the same solution as with the default
     variant."""
@@ -259,7 +260,7 @@ def test_full_size_benchmark_variants_sampled_cells(wname, tuning):
     """The kernels the benchmark times, at full size: after dg_autotune (the
     benchmark's own call) or with the face-once variants (5, 6: every face's
     flux once into the mesh's scratch, then the cells) and the
-    two-threads-per-Q1-cell variant (7) forced.  64 sampled cells of the
+    Q1 tensor-product variant (7) forced.  64 sampled cells of the
     float-float FP64 applies at 1e-12, and of the FP32 Poisson apply (the
     multigrid's finest operator) at 2e-5, against the oracle's rows."""
     from paper_2107_07776_gb300 import binding as b

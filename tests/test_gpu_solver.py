@@ -105,7 +105,7 @@ def test_tg2d_workload_steps_match_oracle():
 def test_periodic_3d_taylor_green_benchmark_path_matches_oracle(tuning):
     """The benchmark's solver path on the 3D periodic Taylor-Green vortex
     (Section 4.1's Taylor-Green case; 32^3 in the benchmark, 4^3 here):
-    Q2/Q1, an autotuned (or face-once / two-threads-per-Q1-cell) mesh, the
+    Q2/Q1, an autotuned (or face-once / Q1 tensor-product) mesh, the
     FP32 multigrid Helmholtz preconditioner and the learned initial guess
     (training on, both nets), 6 steps each compared with the oracle.  Both
     sides solve to 1e-13, so the mixed-precision preconditioner and the
