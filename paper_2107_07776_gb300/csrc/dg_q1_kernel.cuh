@@ -353,8 +353,8 @@ __device__ __forceinline__ void q1_axis_terms(const OpArgs<float>& a, const floa
 template <typename T>
 __global__ void __launch_bounds__(128)
     q1_tensor_kernel(const __grid_constant__ OpArgs<T> a, const T* __restrict__ src, T* __restrict__ dst) {
-  static_assert(std::is_same<T, float>::value, "q1_tensor_kernel: FP32 only");
   pdl_entry();
+  static_assert(std::is_same<T, float>::value, "q1_tensor_kernel: FP32 only");
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= a.ncell) return;
   int ci[3];
@@ -502,8 +502,8 @@ __device__ __forceinline__ void q1_axis_terms_df(const OpArgs<double>& a, const 
 template <typename T>
 __global__ void __launch_bounds__(128, 4)
     q1_tensor_df_kernel(const __grid_constant__ OpArgs<T> a, const T* __restrict__ src, T* __restrict__ dst) {
-  static_assert(std::is_same<T, double>::value, "q1_tensor_df_kernel: FP64 storage only");
   pdl_entry();
+  static_assert(std::is_same<T, double>::value, "q1_tensor_df_kernel: FP64 storage only");
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= a.ncell) return;
   int ci[3];
